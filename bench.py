@@ -1,0 +1,337 @@
+"""Benchmark: FMM particles/s on the 1,048,576-particle uniform workload (p = 10, leaf 64).
+
+One step = one full evaluation (root box, keys, sort, cells, lists, P2M, M2M, M2L, L2L, L2P,
+P2P and the scatter to the original order) of the workload with inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbfmm|reference]
+                  [--workload NAME] [--no-cpu-baseline]
+
+N > 1 runs under torchrun: every rank evaluates its own replica (independent problems, no
+data-path collective; weak scaling).  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1010_1482_gb300 import inputs  # noqa: E402
+
+METRIC = "FMM particles/s at rel L2 err<=1e-4 on 1 GB300; served p50/p99 latency"
+UNIT = "particles/s"
+L2_FLUSH_BYTES = 256 << 20
+REF_SAMPLE_N = 16384       # oracle step: same distribution, p and mean leaf occupancy (32), depth 3
+CPU_BASELINE_N = 131072    # cpu_baseline sample: same distribution, p and mean leaf occupancy, depth 4
+ERROR_TARGETS = 4096
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def fp32_peak_tflops(sm_count: int) -> tuple[float, float]:
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FFMA) x max SM clock."""
+    mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(mp.get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6], swt=parts[7],
+                                 pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+            if any(r[key].lower() == "active" for r in rows):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_from_profile(kernel_file: str, summary: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_1010_1482_gb300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    text = open(path).read()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_tr) or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    x = inputs.make_particles(REF_SAMPLE_N, w["dist"], w["seed"])
+    for _ in range(args.warmup):
+        oracle.fmm(x, w["p"], w["leaf_size"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fmm(x, w["p"], w["leaf_size"])
+    dt = time.perf_counter() - t0
+    value = REF_SAMPLE_N * args.steps / dt
+    sample = (f"oracle FP64 FMM, full evaluation of {REF_SAMPLE_N} particles of the same distribution, "
+              f"p={w['p']}, leaf {w['leaf_size']} (depth {oracle.uniform_depth(REF_SAMPLE_N, w['leaf_size'])}, "
+              "mean leaf occupancy 32 as in the full workload) per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "leaf_size": w["leaf_size"],
+                   "distribution": w["dist"], "sample_n": REF_SAMPLE_N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def run_gpu(args, w):
+    import torch
+
+    from paper_1010_1482_gb300 import gbfmm as G
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    G.lib()
+
+    n = w["n"]
+    x = inputs.make_particles(n, w["dist"], w["seed"] + rank)
+    fmm = G.FMM(local, p=w["p"], leaf_size=w["leaf_size"], flags=G.FLAG_STAGE_TIMING)
+    L, ws_bytes = fmm.plan(n)
+    xd = torch.from_numpy(x).to(dev)
+    out = torch.empty_like(xd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        fmm.evaluate(xd, out)
+    torch.cuda.synchronize()
+
+    # algorithmic work of the dominant kernels (from this evaluation's own lists)
+    C = G.level_offset(L + 1)
+    m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_M2L, C)
+    m2l_pairs = int(m2l_offs[-1])
+    tree = G.gbfmm_export_tree(fmm.ctx, n, C)
+    p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_P2P, 8 ** L)
+    cnt_leaf = tree["count"][G.level_offset(L): G.level_offset(L) + 8 ** L].astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(tree["count"][p2p_ids].astype(np.int64))])
+    src_per_leaf = cs[p2p_offs[1:]] - cs[p2p_offs[:-1]]
+    p2p_pairs = int(np.sum(cnt_leaf * src_per_leaf))
+    P = w["p"]
+    m2l_flops = m2l_pairs * 2 * P ** 4
+    p2p_flops = p2p_pairs * 20
+
+    step_ms, stage_acc, launches = [], {}, 0
+    clock_ctx = ClockSampler(local) if rank == 0 else None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clock_ctx:
+        clock_ctx.__enter__()
+    for _ in range(args.steps):
+        flush.zero_()  # write 256 MiB (> 129 MB L2) so no step starts from a warm L2
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        G.gbfmm_evaluate(fmm.ctx, fmm.params, xd, out, fmm.workspace)
+        e.record(stream)
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+        for k, v in G.gbfmm_stage_times(fmm.ctx).items():
+            stage_acc.setdefault(k, []).append(v)
+        launches += G.gbfmm_last_launch_count(fmm.ctx)
+    torch.cuda.synchronize()
+    if clock_ctx:
+        clock_ctx.__exit__()
+    G.gbfmm_sync_status(fmm.ctx)
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = n * ws / (ms_per_step / 1e3)
+    stages = {k: float(np.mean(v)) for k, v in stage_acc.items()}
+
+    # end to end through the host-buffer ABI call (pinned host memory, copies in the timed region)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(2):
+        G.gbfmm_evaluate_host(fmm.ctx, fmm.params, hin, hout)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.gbfmm_evaluate_host(fmm.ctx, fmm.params, hin, hout)  # waits for the result on the host
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(sum(e2e_ms))
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = n * ws / (e2e_total / args.steps / 1e3)
+
+    peak, peak_mhz = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
+    m2l_ms = stages.get("M2L/M2P", float("nan"))
+    m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
+    p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "p": P, "leaf_size": w["leaf_size"], "levels": L,
+                   "distribution": w["dist"], "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between steps (256 MiB write outside the per-step events)"},
+        "roofline": {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": m2l_tf / peak,
+                     "traffic": traffic_from_profile("m2l.cu", "m2l_uniform_1m_p10.md"),
+                     "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
+                     "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"},
+        "kernels": {"p2p": {"achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
+                            "flop_per_pair": 20}},
+        "stages_ms": stages,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},
+        "gpu_launches": launches,
+        "clocks": clock_ctx.summary() if clock_ctx else None,
+    }
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        xs = inputs.make_particles(CPU_BASELINE_N, w["dist"], w["seed"])
+        t0 = time.perf_counter()
+        oracle.fmm(xs, P, w["leaf_size"])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": CPU_BASELINE_N / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"oracle FP64 FMM, full evaluation of {CPU_BASELINE_N} particles of the same distribution, "
+                       f"p={P}, leaf {w['leaf_size']} (depth {oracle.uniform_depth(CPU_BASELINE_N, w['leaf_size'])}, "
+                       f"mean leaf occupancy 32 as in the full workload), {dt:.1f} s"),
+        }
+        # accuracy of the timed result on seeded targets against the FP64 direct sum
+        tg = inputs.sample_indices(n, ERROR_TARGETS, w["seed"])
+        ref = oracle.direct(x, targets=tg)
+        got = out.cpu().numpy().astype(np.float64)[tg]
+        line["error_vs_fp64_direct"] = {"targets": len(tg), "phi_rel_l2": oracle.rel_l2(got[:, 0], ref[:, 0]),
+                                        "grad_rel_l2": oracle.rel_l2(got[:, 1:], ref[:, 1:])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fmm.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
+    ap.add_argument("--workload", default="uniform_1m_p10")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = inputs.workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

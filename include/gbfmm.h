@@ -1,0 +1,193 @@
+/*
+ * gbfmm.h -- C ABI of the GB300-native Laplace FMM / treecode library (libgbfmm.so).
+ *
+ * The library evaluates, for N point charges (or masses) x_j with strengths q_j,
+ *     phi_i      = sum_{j != i} q_j / |x_i - x_j|
+ *     grad phi_i = -sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3
+ * which is Eq. 1 of Yokota & Barba, "Treecode and fast multipole method for
+ * N-body simulation with CUDA", without the target mass m_i: the quantity their
+ * P2P kernel (Listing 1) accumulates.  Gravitational acceleration is +grad phi,
+ * the electrostatic field is -grad phi; the caller chooses.
+ *
+ * The far field is approximated by the fast multipole method (Section "Fast
+ * N-body simulation": P2M, M2M, M2L, L2L, L2P; Eq. 2-9) or by the treecode (P2M,
+ * M2M, M2P over the same interaction lists), the near field by the direct P2P
+ * sum over the 27 neighbouring leaf cells.
+ *
+ * Conventions shared by every call:
+ *   - device pointers are CUDA global-memory addresses on the context's device;
+ *     host pointers are ordinary host memory;
+ *   - particle arrays are float32, 4 per particle: (x, y, z, q); outputs are
+ *     float32, 4 per particle: (phi, dphi/dx, dphi/dy, dphi/dz), in the caller's
+ *     original particle order;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     device work is enqueued on it and the call returns without waiting unless
+ *     the call's description says otherwise;
+ *   - every call returns a gbfmm_status; no exception crosses the ABI; after an
+ *     error the context stays usable and gbfmm_last_error() describes it;
+ *   - a context is not thread-safe: use it from one host thread and one stream
+ *     at a time.
+ */
+#ifndef GBFMM_H
+#define GBFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBFMM_VERSION 1
+
+typedef enum gbfmm_status {
+    GBFMM_OK = 0,
+    GBFMM_EINVAL = 1,      /* null pointer, n < 0, non-finite coordinate, bad parameter */
+    GBFMM_ENOMEM = 2,      /* workspace too small, or a library allocation failed */
+    GBFMM_ECUDA = 3,       /* a CUDA runtime call failed (message in gbfmm_last_error) */
+    GBFMM_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    GBFMM_EUNSUPPORTED = 5 /* order p or tree depth not compiled in */
+} gbfmm_status;
+
+enum { GBFMM_METHOD_FMM = 0, GBFMM_METHOD_TREECODE = 1 };
+enum { GBFMM_TREE_UNIFORM = 0 };
+enum { GBFMM_LIST_P2P = 0, GBFMM_LIST_M2L = 1 };
+
+/* flags */
+#define GBFMM_FLAG_STAGE_TIMING 1 /* record CUDA events between stages (gbfmm_stage_times) */
+
+/*
+ * Parameters of one evaluation (Section "Fast N-body simulation").
+ *   p          expansion order in the paper's convention: degrees n = 0..p-1
+ *              (Eq. 4 sums n up to p-1); compiled orders: 4, 6, 8, 10.
+ *   leaf_size  the uniform octree has depth L = the smallest L >= 0 with
+ *              n <= leaf_size * 8^L (mean leaf occupancy <= leaf_size); the paper
+ *              keeps the number of cells proportional to N.  L <= 10.
+ *   tree       GBFMM_TREE_UNIFORM.
+ *   method     GBFMM_METHOD_FMM or GBFMM_METHOD_TREECODE (same lists, M2P).
+ *   eps2       softening added to r^2 in P2P only (Listing 1's eps); pairs at
+ *              exactly zero distance contribute nothing whatever eps2 is.
+ *   has_box    0: root cube from the data (centre of the bounding box, side =
+ *              its largest extent); 1: use box_origin / box_side (particles
+ *              outside it are clamped into the boundary cells).
+ *   flags      GBFMM_FLAG_* bits.
+ */
+typedef struct gbfmm_params {
+    int32_t p;
+    int32_t leaf_size;
+    int32_t tree;
+    int32_t method;
+    double eps2;
+    int32_t has_box;
+    int32_t flags;
+    double box_origin[3];
+    double box_side;
+} gbfmm_params;
+
+typedef struct gbfmm_ctx gbfmm_ctx;
+
+/* Library version (GBFMM_VERSION). */
+int gbfmm_version(void);
+
+/* Fill *prm with p = 10, leaf_size = 64, uniform tree, FMM, eps2 = 0, no box.
+ * EINVAL if prm is NULL. */
+int gbfmm_default_params(gbfmm_params *prm);
+
+/* Create a context on CUDA device `device`.  The library allocates and owns the
+ * context, a device status word and (lazily, per order p) the translation
+ * operator tables (M2L: 343 x p^2 x p^2 floats, M2M and L2L: 8 x p^2 x p^2).
+ * *out is NULL on failure.  ECUDA / ENOMEM on failure. */
+int gbfmm_create(gbfmm_ctx **out, int device);
+
+/* Free the context and everything it owns.  NULL-safe.  Waits for the device. */
+int gbfmm_destroy(gbfmm_ctx *ctx);
+
+/* Message describing the last error of this context ("" if none).  The string
+ * is owned by the context and valid until the next call on it. */
+const char *gbfmm_last_error(const gbfmm_ctx *ctx);
+
+/* Plan an evaluation of n particles: tree depth and the device workspace size
+ * gbfmm_evaluate needs (bytes, an upper bound independent of the particle
+ * positions).  Either output pointer may be NULL.  EINVAL / EUNSUPPORTED. */
+int gbfmm_plan(const gbfmm_params *prm, int64_t n, int32_t *levels, size_t *workspace_bytes);
+
+/*
+ * Evaluate potential and gradient of n particles, fully on the device.
+ *   d_xyzq       device, 4*n floats (x, y, z, q); read only.
+ *   d_out        device, 4*n floats (phi, dphi/dx, dphi/dy, dphi/dz), written in
+ *                the original order.  Must not alias d_xyzq.
+ *   d_workspace  device scratch of at least gbfmm_plan's workspace_bytes, 256-byte
+ *                aligned, owned by the caller; it holds the tree, lists and
+ *                expansions of this evaluation until the next call that uses it.
+ * Asynchronous on `stream`.  The first call with a new p also builds that order's
+ * operator tables on the stream.  Non-finite coordinates are detected on the
+ * device: the output is then undefined (but every access stays in bounds) and
+ * gbfmm_sync_status reports EINVAL.  n = 0 returns OK without work.
+ */
+int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
+                   void *d_workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Same evaluation from HOST buffers: copies h_xyzq to the device, evaluates,
+ * copies the result to h_out and waits for the stream.  The device buffers and
+ * workspace are allocated by the library, kept in the context and grown on
+ * demand.  Returns the device status of the evaluation (as gbfmm_sync_status).
+ */
+int gbfmm_evaluate_host(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *h_xyzq, float *h_out,
+                        void *stream);
+
+/* Wait for `stream`, then return and clear the device status word: OK, EINVAL
+ * (a non-finite coordinate was seen) or ETIMEOUT (a bounded wait gave up). */
+int gbfmm_sync_status(gbfmm_ctx *ctx, void *stream);
+
+/*
+ * Direct O(N^2) evaluation on the device (Eq. 1 over all pairs; the paper's
+ * "direct" curve of Fig. 4), same input/output layout and pair rules as
+ * gbfmm_evaluate: d_src 4*n_src floats, d_tgt 4*n_tgt floats (q ignored),
+ * d_out 4*n_tgt floats in target order.  No workspace.  Asynchronous.
+ */
+int gbfmm_direct(gbfmm_ctx *ctx, int64_t n_src, const float *d_src, int64_t n_tgt, const float *d_tgt, double eps2,
+                 float *d_out, void *stream);
+
+/*
+ * Debug export of the last gbfmm_evaluate on this context (its workspace must
+ * not have been reused).  All outputs are caller-owned HOST buffers; the calls
+ * wait for the device.
+ *
+ * gbfmm_export_tree: origin_side[4] = root origin xyz and side (FP64);
+ *   sorted_leaf_keys[n] = Morton key at depth L of each particle in sorted order
+ *   (the 63-bit key shifted right by 3(21-L)); perm[n] = original index of the
+ *   particle at each sorted position; begin[C], count[C] = particle range of every
+ *   cell, C = (8^(L+1)-1)/7, cell of level l with key k at (8^l-1)/7 + k.
+ *   Any pointer may be NULL to skip it.
+ * gbfmm_export_lists: kind GBFMM_LIST_P2P (rows: the 8^L leaves) or
+ *   GBFMM_LIST_M2L (rows: all C cells); offs[rows+1], ids[cap] = global cell
+ *   indices, each row sorted ascending; *n_entries = entries.  ENOMEM if cap is
+ *   too small (n_entries still set).
+ * gbfmm_export_expansions: which = 0 multipole M, 1 local L; coef[C * p(p+1)]
+ *   FP64 = for every cell the p(p+1)/2 complex coefficients (m >= 0, index
+ *   n(n+1)/2+m, re/im interleaved) in the paper's unscaled normalisation (Eq. 2, 3).
+ *   Levels the method does not form are zero.
+ */
+int gbfmm_export_tree(gbfmm_ctx *ctx, double *origin_side, uint32_t *sorted_leaf_keys, uint32_t *perm,
+                      int32_t *begin, int32_t *count);
+int gbfmm_export_lists(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, int64_t cap, int64_t *n_entries);
+int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef);
+
+/*
+ * Per-stage device times (ms) of the last evaluate run with
+ * GBFMM_FLAG_STAGE_TIMING, in this order: 0 box+keys, 1 sort, 2 cells+lists,
+ * 3 P2M, 4 M2M, 5 M2L (or M2P), 6 L2L, 7 L2P, 8 P2P(+output), 9 operator build
+ * (0 when cached).  Waits for the device.  *count = stages written (<= max).
+ */
+int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
+
+/* Number of library kernels the last gbfmm_evaluate / gbfmm_evaluate_host / gbfmm_direct
+ * on this context enqueued (operator-table builds included; runtime memsets excluded). */
+int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFMM_H */

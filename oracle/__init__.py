@@ -59,6 +59,7 @@ def lib():
             ci = ctypes.c_int
             sig = {
                 "orc_version": (ci, []),
+                "orc_threads": (ci, []),
                 "orc_legendre": (None, [ci, d, P]),
                 "orc_ynm_ri": (None, [ci, d, d, P]),
                 "orc_direct": (None, [i64, P, i64, P, d, P]),
@@ -83,6 +84,11 @@ def lib():
                 f.argtypes = args
             _lib = L
     return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().orc_threads())
 
 
 def _p(a: np.ndarray):

@@ -41,6 +41,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -60,6 +61,18 @@ static void init_fact(void)
 }
 
 int orc_version(void) { return 1; }
+
+/* Number of OpenMP threads the parallel loops use. */
+int orc_threads(void)
+{
+    int t = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        t = omp_get_num_threads();
+    }
+    return t;
+}
 
 /* ------------------------------------------------------------------------- */
 /* Special functions                                                         */

@@ -1,0 +1,609 @@
+// C ABI of libgbfmm (declared in include/gbfmm.h): context, planning, the evaluation
+// pipeline (tree front end -> upward pass -> M2L or M2P -> downward pass -> P2P) and the
+// debug exports.  Host code here only sizes buffers and enqueues kernels; no arithmetic of
+// the method runs on the host.
+#include "common.cuh"
+#include "gbfmm.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+namespace gbfmm {
+void init_expansion_constants();
+void init_m2l_constants();
+}  // namespace gbfmm
+
+using namespace gbfmm;
+
+namespace gbfmm {
+static thread_local int64_t tl_launches = 0;
+void note_launches(int k) { tl_launches += k; }
+}  // namespace gbfmm
+
+namespace {
+
+constexpr int kBoxPartials = 304 * 8;
+constexpr int kStages = 10;
+constexpr int kOrders[4] = {4, 6, 8, 10};
+
+struct OpsCache {
+    int P = 0;
+    float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
+    bool built = false;
+};
+
+int order_slot(int p)
+{
+    for (int i = 0; i < 4; ++i)
+        if (kOrders[i] == p) return i;
+    return -1;
+}
+
+int uniform_depth(int64_t n, int64_t leaf)
+{
+    int L = 0;
+    while (n > leaf * (int64_t(1) << (3 * L))) {
+        ++L;
+        if (L > 20) break;
+    }
+    return L;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct gbfmm_ctx {
+    int device = 0;
+    std::string err;
+    int *d_status = nullptr;
+    unsigned *d_counter = nullptr;
+    float *d_partials = nullptr;
+    float *d_zero = nullptr;
+    OpsCache ops[4];
+    // last evaluation
+    bool have_last = false;
+    Layout last{};
+    unsigned char *last_ws = nullptr;
+    size_t last_keys = 0, last_idx = 0;
+    int last_method = 0;
+    // host-buffer path
+    float *h_in = nullptr, *h_out = nullptr;
+    void *h_ws = nullptr;
+    int64_t h_cap_n = 0;
+    size_t h_ws_bytes = 0;
+    // stage timing
+    cudaEvent_t ev[kStages + 1] = {};
+    bool timed_last = false;
+    bool ops_built_last = false;
+    int64_t launches_last = 0;
+};
+
+namespace {
+
+int fail(gbfmm_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(gbfmm_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, GBFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int check_params(const gbfmm_params *prm, int64_t n, int *L_out, std::string *msg)
+{
+    if (!prm) {
+        *msg = "params is NULL";
+        return GBFMM_EINVAL;
+    }
+    if (n < 0) {
+        *msg = "n < 0";
+        return GBFMM_EINVAL;
+    }
+    if (order_slot(prm->p) < 0) {
+        *msg = "order p not compiled (4, 6, 8, 10)";
+        return GBFMM_EUNSUPPORTED;
+    }
+    if (prm->leaf_size < 1) {
+        *msg = "leaf_size < 1";
+        return GBFMM_EINVAL;
+    }
+    if (prm->tree != GBFMM_TREE_UNIFORM) {
+        *msg = "only the uniform tree is available";
+        return GBFMM_EUNSUPPORTED;
+    }
+    if (prm->method != GBFMM_METHOD_FMM && prm->method != GBFMM_METHOD_TREECODE) {
+        *msg = "unknown method";
+        return GBFMM_EINVAL;
+    }
+    if (!(prm->eps2 >= 0.0) || !isfinite(prm->eps2)) {
+        *msg = "eps2 must be finite and >= 0";
+        return GBFMM_EINVAL;
+    }
+    if (prm->has_box) {
+        if (!(prm->box_side > 0.0) || !isfinite(prm->box_side) || !isfinite(prm->box_origin[0]) ||
+            !isfinite(prm->box_origin[1]) || !isfinite(prm->box_origin[2])) {
+            *msg = "box must be finite with side > 0";
+            return GBFMM_EINVAL;
+        }
+    }
+    if (n > (int64_t)0x7fffffff) {
+        *msg = "n exceeds 2^31 - 1";
+        return GBFMM_EUNSUPPORTED;
+    }
+    int L = uniform_depth(n, prm->leaf_size);
+    if (L > kMaxLevel) {
+        *msg = "tree depth exceeds 10 (raise leaf_size)";
+        return GBFMM_EUNSUPPORTED;
+    }
+    *L_out = L;
+    return GBFMM_OK;
+}
+
+Layout make_layout(int64_t n, int L, int P)
+{
+    Layout lo{};
+    lo.n = n;
+    lo.L = L;
+    lo.P = P;
+    lo.ncells = level_offset(L + 1);
+    lo.nleaves = int64_t(1) << (3 * L);
+    lo.rs_blocks = (n + 4095) / 4096;
+    const int64_t C = lo.ncells, NL = lo.nleaves;
+    const int64_t C2 = L >= 2 ? C - level_offset(2) : 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    lo.box = take(sizeof(Box));
+    lo.keys0 = take(4 * (size_t)n);
+    lo.keys1 = take(4 * (size_t)n);
+    lo.idx0 = take(4 * (size_t)n);
+    lo.idx1 = take(4 * (size_t)n);
+    lo.sx = take(16 * (size_t)n);
+    lo.far = take(16 * (size_t)n);
+    lo.rs_hist = take(4 * (size_t)(256 * lo.rs_blocks + 1));
+    size_t tmpw = std::max({exclusive_scan_tmp_words(256 * lo.rs_blocks), exclusive_scan_tmp_words(C),
+                            exclusive_scan_tmp_words(NL)});
+    lo.scan_tmp = take(4 * tmpw);
+    lo.cell_begin = take(4 * (size_t)C);
+    lo.cell_end = take(4 * (size_t)C);
+    lo.p2p_len = take(4 * (size_t)NL);
+    lo.p2p_offs = take(4 * (size_t)(NL + 1));
+    lo.p2p_ids = take(4 * (size_t)(27 * NL));
+    lo.m2l_len = take(4 * (size_t)C);
+    lo.m2l_offs = take(4 * (size_t)(C + 1));
+    lo.m2l_ids = take(4 * (size_t)(189 * C2 + 1));
+    lo.m2l_code = take(2 * (size_t)(189 * C2 + 1));
+    lo.M = take(4 * (size_t)C * P * P);
+    lo.Lc = take(4 * (size_t)C * P * P);
+    lo.total = off;
+    return lo;
+}
+
+template <class T>
+T *at(void *base, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<unsigned char *>(base) + off);
+}
+
+int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
+{
+    OpsCache &c = ctx->ops[order_slot(P)];
+    *built_now = false;
+    if (c.built) return GBFMM_OK;
+    const size_t PP2 = (size_t)P * P * P * P;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c.m2l, kM2LCodes * PP2 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(m2l ops)");
+    if ((e = cudaMalloc(&c.m2m, 8 * PP2 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(m2m ops)");
+    if ((e = cudaMalloc(&c.l2l, 8 * PP2 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
+    launch_build_operators(P, c.m2l, c.m2m, c.l2l, s);
+    c.P = P;
+    c.built = true;
+    *built_now = true;
+    return GBFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbfmm_version(void) { return GBFMM_VERSION; }
+
+int gbfmm_default_params(gbfmm_params *prm)
+{
+    if (!prm) return GBFMM_EINVAL;
+    memset(prm, 0, sizeof(*prm));
+    prm->p = 10;
+    prm->leaf_size = 64;
+    prm->tree = GBFMM_TREE_UNIFORM;
+    prm->method = GBFMM_METHOD_FMM;
+    prm->eps2 = 0.0;
+    prm->has_box = 0;
+    prm->box_side = 1.0;
+    return GBFMM_OK;
+}
+
+int gbfmm_create(gbfmm_ctx **out, int device)
+{
+    if (!out) return GBFMM_EINVAL;
+    *out = nullptr;
+    gbfmm_ctx *ctx = new (std::nothrow) gbfmm_ctx();
+    if (!ctx) return GBFMM_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return GBFMM_ECUDA;
+    }
+    bool ok = cudaMalloc(&ctx->d_status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&ctx->d_counter, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&ctx->d_partials, kBoxPartials * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&ctx->d_zero, 128 * sizeof(float)) == cudaSuccess;
+    if (ok)
+        ok = cudaMemset(ctx->d_status, 0, sizeof(int)) == cudaSuccess &&
+             cudaMemset(ctx->d_counter, 0, sizeof(unsigned)) == cudaSuccess &&
+             cudaMemset(ctx->d_zero, 0, 128 * sizeof(float)) == cudaSuccess;
+    for (int i = 0; ok && i <= kStages; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    if (ok) {
+        init_expansion_constants();
+        init_m2l_constants();
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (!ok) {
+        gbfmm_destroy(ctx);
+        return GBFMM_ECUDA;
+    }
+    *out = ctx;
+    return GBFMM_OK;
+}
+
+int gbfmm_destroy(gbfmm_ctx *ctx)
+{
+    if (!ctx) return GBFMM_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_counter);
+    cudaFree(ctx->d_partials);
+    cudaFree(ctx->d_zero);
+    for (auto &c : ctx->ops) {
+        cudaFree(c.m2l);
+        cudaFree(c.m2m);
+        cudaFree(c.l2l);
+    }
+    cudaFree(ctx->h_in);
+    cudaFree(ctx->h_out);
+    cudaFree(ctx->h_ws);
+    for (int i = 0; i <= kStages; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+    return GBFMM_OK;
+}
+
+const char *gbfmm_last_error(const gbfmm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gbfmm_plan(const gbfmm_params *prm, int64_t n, int32_t *levels, size_t *workspace_bytes)
+{
+    std::string msg;
+    int L = 0;
+    int rc = check_params(prm, n, &L, &msg);
+    if (rc != GBFMM_OK) return rc;
+    Layout lo = make_layout(n, L, prm->p);
+    if (levels) *levels = L;
+    if (workspace_bytes) *workspace_bytes = lo.total;
+    return GBFMM_OK;
+}
+
+int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
+                   void *d_workspace, size_t workspace_bytes, void *stream)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    ctx->err.clear();
+    std::string msg;
+    int L = 0;
+    int rc = check_params(prm, n, &L, &msg);
+    if (rc != GBFMM_OK) return fail(ctx, rc, msg);
+    if (n == 0) return GBFMM_OK;
+    if (!d_xyzq || !d_out || !d_workspace) return fail(ctx, GBFMM_EINVAL, "null device pointer");
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return fail(ctx, GBFMM_EINVAL, "workspace not 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
+        return fail(ctx, GBFMM_EINVAL, "particle arrays must be 16-byte aligned");
+    if (d_xyzq == d_out) return fail(ctx, GBFMM_EINVAL, "d_out aliases d_xyzq");
+    const int P = prm->p;
+    Layout lo = make_layout(n, L, P);
+    if (workspace_bytes < lo.total) return fail(ctx, GBFMM_ENOMEM, "workspace smaller than gbfmm_plan's size");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool timing = (prm->flags & GBFMM_FLAG_STAGE_TIMING) != 0;
+    auto mark = [&](int k) {
+        if (timing) cudaEventRecord(ctx->ev[k], s);
+    };
+
+    void *ws = d_workspace;
+    const float4 *x = reinterpret_cast<const float4 *>(d_xyzq);
+    float4 *out = reinterpret_cast<float4 *>(d_out);
+    Box *box = at<Box>(ws, lo.box);
+    uint32_t *k0 = at<uint32_t>(ws, lo.keys0), *k1 = at<uint32_t>(ws, lo.keys1);
+    uint32_t *v0 = at<uint32_t>(ws, lo.idx0), *v1 = at<uint32_t>(ws, lo.idx1);
+    float4 *sx = at<float4>(ws, lo.sx), *far = at<float4>(ws, lo.far);
+    uint32_t *hist = at<uint32_t>(ws, lo.rs_hist), *scan_tmp = at<uint32_t>(ws, lo.scan_tmp);
+    int32_t *begin = at<int32_t>(ws, lo.cell_begin), *end = at<int32_t>(ws, lo.cell_end);
+    uint32_t *p2p_len = at<uint32_t>(ws, lo.p2p_len), *p2p_offs = at<uint32_t>(ws, lo.p2p_offs);
+    int32_t *p2p_ids = at<int32_t>(ws, lo.p2p_ids);
+    uint32_t *m2l_len = at<uint32_t>(ws, lo.m2l_len), *m2l_offs = at<uint32_t>(ws, lo.m2l_offs);
+    int32_t *m2l_ids = at<int32_t>(ws, lo.m2l_ids);
+    uint16_t *m2l_code = at<uint16_t>(ws, lo.m2l_code);
+    float *M = at<float>(ws, lo.M), *Lc = at<float>(ws, lo.Lc);
+
+    // operator tables (once per order and context)
+    bool built_now = false;
+    if (L >= 2) {
+        if (timing) cudaEventRecord(ctx->ev[kStages], s);
+        rc = ensure_ops(ctx, P, s, &built_now);
+        if (rc != GBFMM_OK) return rc;
+    }
+    const OpsCache &ops = ctx->ops[order_slot(P)];
+
+    const int64_t launches0 = tl_launches;
+    mark(0);
+    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, ctx->d_partials, ctx->d_counter,
+                ctx->d_status, s);
+    launch_keys(x, n, box, L, k0, v0, s);
+    mark(1);
+    uint32_t *skeys = nullptr, *perm = nullptr;
+    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, hist, lo.rs_blocks, scan_tmp, x, sx, &skeys, &perm, s);
+    mark(2);
+    launch_cells(skeys, n, L, begin, end, s);
+    launch_list_count(L, begin, end, p2p_len, m2l_len, s);
+    launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, scan_tmp, s);
+    launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, scan_tmp, s);
+    launch_list_fill(L, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code, s);
+    mark(3);
+    if (L >= 2) launch_p2m(P, L, box, sx, begin, end, M, s);
+    mark(4);
+    if (L >= 2)
+        for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
+    mark(5);
+    if (L >= 2) {
+        if (prm->method == GBFMM_METHOD_FMM)
+            launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
+        else
+            launch_m2p(P, L, box, sx, begin, end, m2l_offs, m2l_ids, M, far, s);
+    }
+    mark(6);
+    if (L >= 2 && prm->method == GBFMM_METHOD_FMM)
+        for (int l = 3; l <= L; ++l) launch_l2l(P, l, begin, end, ops.l2l, Lc, s);
+    mark(7);
+    if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, box, n, sx, skeys, Lc, far, s);
+    mark(8);
+    launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out, s);
+    mark(9);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+
+    ctx->launches_last = tl_launches - launches0;
+    ctx->have_last = true;
+    ctx->last = lo;
+    ctx->last_ws = static_cast<unsigned char *>(ws);
+    ctx->last_keys = (size_t)(reinterpret_cast<unsigned char *>(skeys) - ctx->last_ws);
+    ctx->last_idx = (size_t)(reinterpret_cast<unsigned char *>(perm) - ctx->last_ws);
+    ctx->last_method = prm->method;
+    ctx->timed_last = timing;
+    ctx->ops_built_last = built_now;
+    return GBFMM_OK;
+}
+
+int gbfmm_sync_status(gbfmm_ctx *ctx, void *stream)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status readback");
+    cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (st & kStatusTimeout) return fail(ctx, GBFMM_ETIMEOUT, "a bounded device wait gave up");
+    if (st & kStatusNonFinite) return fail(ctx, GBFMM_EINVAL, "non-finite particle coordinate");
+    return GBFMM_OK;
+}
+
+int gbfmm_evaluate_host(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *h_xyzq, float *h_out,
+                        void *stream)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    if (n > 0 && (!h_xyzq || !h_out)) return fail(ctx, GBFMM_EINVAL, "null host pointer");
+    int32_t L = 0;
+    size_t ws = 0;
+    int rc = gbfmm_plan(prm, n, &L, &ws);
+    if (rc != GBFMM_OK) return fail(ctx, rc, "invalid parameters");
+    if (n == 0) return GBFMM_OK;
+    cudaSetDevice(ctx->device);
+    cudaError_t e;
+    if (ctx->h_cap_n < n) {
+        cudaFree(ctx->h_in);
+        cudaFree(ctx->h_out);
+        ctx->h_in = ctx->h_out = nullptr;
+        ctx->h_cap_n = 0;
+        if ((e = cudaMalloc(&ctx->h_in, 16 * (size_t)n)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(in)");
+        if ((e = cudaMalloc(&ctx->h_out, 16 * (size_t)n)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(out)");
+        ctx->h_cap_n = n;
+    }
+    if (ctx->h_ws_bytes < ws) {
+        cudaFree(ctx->h_ws);
+        ctx->h_ws = nullptr;
+        ctx->h_ws_bytes = 0;
+        if ((e = cudaMalloc(&ctx->h_ws, ws)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+        ctx->h_ws_bytes = ws;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((e = cudaMemcpyAsync(ctx->h_in, h_xyzq, 16 * (size_t)n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy in");
+    rc = gbfmm_evaluate(ctx, prm, n, ctx->h_in, ctx->h_out, ctx->h_ws, ctx->h_ws_bytes, stream);
+    if (rc != GBFMM_OK) return rc;
+    if ((e = cudaMemcpyAsync(h_out, ctx->h_out, 16 * (size_t)n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy out");
+    return gbfmm_sync_status(ctx, stream);
+}
+
+int gbfmm_direct(gbfmm_ctx *ctx, int64_t n_src, const float *d_src, int64_t n_tgt, const float *d_tgt, double eps2,
+                 float *d_out, void *stream)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    if (n_src < 0 || n_tgt < 0) return fail(ctx, GBFMM_EINVAL, "negative size");
+    if (!(eps2 >= 0.0)) return fail(ctx, GBFMM_EINVAL, "eps2 must be >= 0");
+    if (n_tgt == 0) return GBFMM_OK;
+    if ((n_src > 0 && !d_src) || !d_tgt || !d_out) return fail(ctx, GBFMM_EINVAL, "null device pointer");
+    cudaSetDevice(ctx->device);
+    const int64_t launches0 = tl_launches;
+    launch_direct(n_src, reinterpret_cast<const float4 *>(d_src), n_tgt, reinterpret_cast<const float4 *>(d_tgt),
+                  (float)eps2, reinterpret_cast<float4 *>(d_out), static_cast<cudaStream_t>(stream));
+    ctx->launches_last = tl_launches - launches0;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "direct launch");
+}
+
+int gbfmm_export_tree(gbfmm_ctx *ctx, double *origin_side, uint32_t *sorted_leaf_keys, uint32_t *perm,
+                      int32_t *begin, int32_t *count)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    if (!ctx->have_last) return fail(ctx, GBFMM_EINVAL, "no evaluation to export");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    const Layout &lo = ctx->last;
+    if (origin_side) {
+        Box b;
+        cudaMemcpy(&b, ctx->last_ws + lo.box, sizeof(Box), cudaMemcpyDeviceToHost);
+        origin_side[0] = b.origin[0];
+        origin_side[1] = b.origin[1];
+        origin_side[2] = b.origin[2];
+        origin_side[3] = b.side;
+    }
+    if (sorted_leaf_keys) cudaMemcpy(sorted_leaf_keys, ctx->last_ws + ctx->last_keys, 4 * lo.n, cudaMemcpyDeviceToHost);
+    if (perm) cudaMemcpy(perm, ctx->last_ws + ctx->last_idx, 4 * lo.n, cudaMemcpyDeviceToHost);
+    if (begin || count) {
+        std::vector<int32_t> b(lo.ncells), en(lo.ncells);
+        cudaMemcpy(b.data(), ctx->last_ws + lo.cell_begin, 4 * lo.ncells, cudaMemcpyDeviceToHost);
+        cudaMemcpy(en.data(), ctx->last_ws + lo.cell_end, 4 * lo.ncells, cudaMemcpyDeviceToHost);
+        for (int64_t g = 0; g < lo.ncells; ++g) {
+            int32_t c = en[g] - b[g];
+            if (begin) begin[g] = c > 0 ? b[g] : 0;
+            if (count) count[g] = c;
+        }
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "export copy");
+}
+
+int gbfmm_export_lists(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, int64_t cap, int64_t *n_entries)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    if (!ctx->have_last) return fail(ctx, GBFMM_EINVAL, "no evaluation to export");
+    if (kind != GBFMM_LIST_P2P && kind != GBFMM_LIST_M2L) return fail(ctx, GBFMM_EINVAL, "unknown list kind");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    const Layout &lo = ctx->last;
+    const int64_t rows = kind == GBFMM_LIST_P2P ? lo.nleaves : lo.ncells;
+    std::vector<uint32_t> o(rows + 1);
+    cudaMemcpy(o.data(), ctx->last_ws + (kind == GBFMM_LIST_P2P ? lo.p2p_offs : lo.m2l_offs), 4 * (rows + 1),
+               cudaMemcpyDeviceToHost);
+    const int64_t ne = o[rows];
+    if (n_entries) *n_entries = ne;
+    if (offs)
+        for (int64_t r = 0; r <= rows; ++r) offs[r] = (int32_t)o[r];
+    if (ids) {
+        if (cap < ne) return fail(ctx, GBFMM_ENOMEM, "ids capacity too small");
+        cudaMemcpy(ids, ctx->last_ws + (kind == GBFMM_LIST_P2P ? lo.p2p_ids : lo.m2l_ids), 4 * ne,
+                   cudaMemcpyDeviceToHost);
+        for (int64_t r = 0; r < rows; ++r) std::sort(ids + o[r], ids + o[r + 1]);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "export copy");
+}
+
+int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef)
+{
+    if (!ctx || !coef) return GBFMM_EINVAL;
+    if (!ctx->have_last) return fail(ctx, GBFMM_EINVAL, "no evaluation to export");
+    if (which != 0 && which != 1) return fail(ctx, GBFMM_EINVAL, "which must be 0 (M) or 1 (L)");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    const Layout &lo = ctx->last;
+    const int P = lo.P, PP = P * P, NT = P * (P + 1) / 2;
+    std::vector<float> v((size_t)lo.ncells * PP);
+    std::vector<int32_t> b(lo.ncells), en(lo.ncells);
+    Box box;
+    cudaMemcpy(&box, ctx->last_ws + lo.box, sizeof(Box), cudaMemcpyDeviceToHost);
+    cudaMemcpy(v.data(), ctx->last_ws + (which == 0 ? lo.M : lo.Lc), 4 * v.size(), cudaMemcpyDeviceToHost);
+    cudaMemcpy(b.data(), ctx->last_ws + lo.cell_begin, 4 * lo.ncells, cudaMemcpyDeviceToHost);
+    cudaMemcpy(en.data(), ctx->last_ws + lo.cell_end, 4 * lo.ncells, cudaMemcpyDeviceToHost);
+    for (int l = 0; l <= lo.L; ++l) {
+        const double h = box.side / (double)(int64_t(1) << l);
+        const bool formed = lo.L >= 2 && l >= 2 && (which == 0 || ctx->last_method == GBFMM_METHOD_FMM);
+        for (int64_t g = level_offset(l); g < level_offset(l + 1); ++g) {
+            double *c = coef + (size_t)g * 2 * NT;
+            const bool ok = formed && en[g] > b[g];
+            for (int n = 0; n < P; ++n) {
+                const double sc = which == 0 ? pow(h, n) : pow(h, -(n + 1));
+                for (int m = 0; m <= n; ++m) {
+                    const int t = n * (n + 1) / 2 + m;
+                    double re = 0.0, im = 0.0;
+                    if (ok) {
+                        const float *src = v.data() + (size_t)g * PP;
+                        re = src[m == 0 ? n * n : n * n + 2 * m - 1] * sc;
+                        im = m == 0 ? 0.0 : src[n * n + 2 * m] * sc;
+                    }
+                    c[2 * t] = re;
+                    c[2 * t + 1] = im;
+                }
+            }
+        }
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "export copy");
+}
+
+int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return GBFMM_EINVAL;
+    *count = ctx->launches_last;
+    return GBFMM_OK;
+}
+
+int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count)
+{
+    if (!ctx || !ms) return GBFMM_EINVAL;
+    if (!ctx->timed_last) return fail(ctx, GBFMM_EINVAL, "last evaluation was not timed");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[9]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event sync");
+    int k = 0;
+    for (; k < 9 && k < max; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]);
+        ms[k] = t;
+    }
+    if (k < max) {
+        float t = 0.f;
+        if (ctx->ops_built_last) cudaEventElapsedTime(&t, ctx->ev[kStages], ctx->ev[0]);
+        ms[k++] = t;
+    }
+    if (count) *count = k;
+    return GBFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libgbfmm.
+//
+// Data layout in device memory (one evaluation, uniform octree of depth L):
+//   cells: dense per level, the level-l cell with Morton key k at global index
+//          level_offset(l) + k, level_offset(l) = (8^l - 1) / 7;
+//   expansions: real-packed, P*P floats per cell: degree n occupies
+//          [n*n, (n+1)*(n+1)) as Re C_n^0, Re C_n^1, Im C_n^1, ..., Re C_n^n, Im C_n^n
+//          (C_n^{-m} = conj(C_n^m) is implied, Im C_n^0 = 0 is dropped);
+//          stored scaled by the cell side h of their level: M~_n^m = M_n^m / h^n,
+//          L~_n^m = L_n^m h^(n+1), so every translation operator is independent of
+//          the level and is tabulated once per order p.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GB_DEV __device__ __forceinline__
+#define GB_HD __host__ __device__ __forceinline__
+
+namespace gbfmm {
+
+constexpr int kMaxLevel = 10;
+constexpr int kM2LCodes = 343;  // offsets (dx, dy, dz) in [-3, 3]^3, code = (dx+3) + 7(dy+3) + 49(dz+3)
+
+GB_HD int64_t level_offset(int l) { return ((int64_t(1) << (3 * l)) - 1) / 7; }
+
+GB_HD int m2l_code(int dx, int dy, int dz) { return (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3); }
+
+// Morton interleave of three 10-bit integers (bit 3b+0 = x bit b, 3b+1 = y, 3b+2 = z).
+GB_HD uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+GB_HD uint32_t compact3(uint32_t v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x000003ffu;
+    return v;
+}
+
+GB_HD uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) { return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2); }
+
+GB_HD void demorton3(uint32_t k, int &x, int &y, int &z)
+{
+    x = (int)compact3(k);
+    y = (int)compact3(k >> 1);
+    z = (int)compact3(k >> 2);
+}
+
+// Device status bits (OR-ed into the context's status word).
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusTimeout = 2;
+
+// Root box as computed on the device: origin xyz and side, FP64.
+struct Box {
+    double origin[3];
+    double side;
+};
+
+// Layout of one evaluation's workspace (byte offsets from the workspace base).
+struct Layout {
+    int64_t n;
+    int L;
+    int P;
+    int64_t ncells;     // C
+    int64_t nleaves;    // 8^L
+    int64_t rs_blocks;  // radix-sort tiles
+    size_t box, status_dummy;
+    size_t keys0, keys1, idx0, idx1;
+    size_t sx, far;
+    size_t rs_hist, scan_tmp;
+    size_t cell_begin, cell_end;
+    size_t p2p_len, p2p_offs, p2p_ids;
+    size_t m2l_len, m2l_offs, m2l_ids, m2l_code;
+    size_t M, Lc;
+    size_t total;
+};
+
+// Kernel-launch accounting: every launcher reports the kernels it enqueued (api.cu keeps the
+// count of the current evaluation).
+void note_launches(int k);
+
+// ---- launchers (host functions, one per device stage) -------------------------------------
+// tree.cu
+void launch_bbox(const float4 *x, int64_t n, int has_box, const double *box_origin, double box_side, Box *box_out,
+                 float *partials, unsigned *counter, int *status, cudaStream_t s);
+void launch_keys(const float4 *x, int64_t n, const Box *box, int L, uint32_t *leafkey, uint32_t *idx, cudaStream_t s);
+// sorts (keys, idx) by key (stable) over `bits` low bits; on return the sorted pair is in
+// (*keys_out, *idx_out) (one of the two buffers); also gathers sx[i] = x[idx[i]].
+void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
+                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
+                        uint32_t **idx_out, cudaStream_t s);
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s);
+size_t exclusive_scan_tmp_words(int64_t n);
+void launch_cells(const uint32_t *sorted_leaf_keys, int64_t n, int L, int32_t *begin, int32_t *end, cudaStream_t s);
+void launch_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t *p2p_len, uint32_t *m2l_len,
+                       cudaStream_t s);
+void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
+                      const uint32_t *m2l_offs, int32_t *m2l_ids, uint16_t *m2l_code, cudaStream_t s);
+
+// expansions.cu
+void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_ops, cudaStream_t s);
+void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
+                cudaStream_t s);
+void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s);
+void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *Lc, cudaStream_t s);
+void launch_l2p(int P, int L, const Box *box, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
+                float4 *far, cudaStream_t s);
+void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end,
+                const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s);
+
+// m2l.cu
+void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
+                const int32_t *m2l_ids, const uint16_t *m2l_code, const float *ops, const float *M, float *Lc,
+                const float *zero_block, int *status, cudaStream_t s);
+
+// p2p.cu
+void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
+                const uint32_t *p2p_offs, const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2,
+                float4 *out, cudaStream_t s);
+void launch_direct(int64_t n_src, const float4 *src, int64_t n_tgt, const float4 *tgt, float eps2, float4 *out,
+                   cudaStream_t s);
+
+}  // namespace gbfmm

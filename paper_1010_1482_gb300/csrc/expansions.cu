@@ -1,0 +1,646 @@
+// Expansion kernels of the FMM / treecode: translation-operator tables (FP64 arithmetic,
+// stored FP32), P2M, M2M, L2L, L2P and M2P (FP32).
+//
+// Notation (Section "Fast N-body simulation", Eq. 2-9): Y_n^m as Eq. 6 with the
+// Condon-Shortley phase of Eq. 8; regular solid harmonics R_n^m(v) = |v|^n Y_n^m(v),
+// irregular I_n^m(v) = |v|^(-n-1) Y_n^m(v).  Both are evaluated from Cartesian coordinates
+// with the normalised three-term recurrence in n (Eq. 7 multiplied through by |v|^n) and the
+// diagonal step R_m^m = -sqrt((2m-1)/(2m)) (x + iy) R_{m-1}^{m-1} (Eq. 8), so no
+// trigonometric function is needed on the device.
+//
+//   P2M (Eq. 2):  M_n^m = sum_j q_j R_n^{-m}(x_j - c) = sum_j q_j conj(R_n^m(x_j - c))
+//   L2P (Eq. 3):  phi = sum_{n,m} L_n^m R_n^m(x - c)
+//   M2P (Eq. 2):  phi = sum_{n,m} M_n^m I_n^m(x - c)
+// Gradients use the ladder relations of solid harmonics (d/dz and d/dx + i d/dy lower or
+// raise the degree by one), which stay finite on the expansion's z axis.
+// M2L (Eq. 4-5) and the M2M / L2L translations (Cheng, Greengard & Rokhlin 1999, cited by
+// the paper for its translation operators) are linear maps on the real-packed coefficients;
+// with coefficients scaled by the cell side they do not depend on the level, so each is a
+// dense p^2 x p^2 FP32 matrix computed once per order in FP64.
+#include "common.cuh"
+
+#include <math.h>
+
+namespace gbfmm {
+
+constexpr int kMaxP = 10;
+constexpr int kMaxDeg = 2 * kMaxP;  // harmonics up to degree 2P-2 (M2L) and P (M2P gradient)
+
+// Recurrence and ladder constants, set once per device (init_expansion_constants).
+__constant__ float c_rmm[kMaxDeg + 1];                 // sqrt((2m-1)/(2m))
+__constant__ float c_ra[kMaxDeg + 1][kMaxDeg + 1];     // (2n+1) / sqrt((n+1-m)(n+1+m))
+__constant__ float c_rb[kMaxDeg + 1][kMaxDeg + 1];     // sqrt((n-m)(n+m)) / sqrt((n+1-m)(n+1+m))
+__constant__ float c_sq[2 * kMaxDeg + 4][2 * kMaxDeg + 4];  // sqrt(a*b)
+
+void init_expansion_constants()
+{
+    float rmm[kMaxDeg + 1], ra[kMaxDeg + 1][kMaxDeg + 1], rb[kMaxDeg + 1][kMaxDeg + 1];
+    static float sq[2 * kMaxDeg + 4][2 * kMaxDeg + 4];
+    for (int m = 0; m <= kMaxDeg; ++m) rmm[m] = m ? (float)sqrt((2.0 * m - 1.0) / (2.0 * m)) : 0.f;
+    for (int n = 0; n <= kMaxDeg; ++n)
+        for (int m = 0; m <= kMaxDeg; ++m) {
+            double den = (double)(n + 1 - m) * (double)(n + 1 + m);
+            ra[n][m] = (m <= n) ? (float)((2.0 * n + 1.0) / sqrt(den)) : 0.f;
+            rb[n][m] = (m <= n) ? (float)(sqrt((double)(n - m) * (double)(n + m)) / sqrt(den)) : 0.f;
+        }
+    for (int a = 0; a < 2 * kMaxDeg + 4; ++a)
+        for (int b = 0; b < 2 * kMaxDeg + 4; ++b) sq[a][b] = (float)sqrt((double)a * (double)b);
+    cudaMemcpyToSymbol(c_rmm, rmm, sizeof(rmm));
+    cudaMemcpyToSymbol(c_ra, ra, sizeof(ra));
+    cudaMemcpyToSymbol(c_rb, rb, sizeof(rb));
+    cudaMemcpyToSymbol(c_sq, sq, sizeof(sq));
+}
+
+// real-packed index of Re C_n^m / Im C_n^m
+GB_HD constexpr int re_idx(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
+GB_HD constexpr int im_idx(int n, int m) { return n * n + 2 * m; }
+
+// ------------------------------------------------------------------------------------------
+// Operator tables (FP64 arithmetic, one CTA per operator).
+//   M2L  ops[code][col][row]  (column-major: the M2L kernel streams columns)  code < 343
+//   M2M  ops[c][row][col]     child position c (bit0 x, bit1 y, bit2 z), child -> parent
+//   L2L  ops[c][row][col]     parent -> child c
+// ------------------------------------------------------------------------------------------
+struct C64 {
+    double re, im;
+};
+GB_DEV C64 cmul(C64 a, C64 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+GB_DEV C64 conj64(C64 a) { return {a.re, -a.im}; }
+
+GB_DEV void dof_decode(int i, int &n, int &m, int &im)
+{
+    n = 0;
+    while ((n + 1) * (n + 1) <= i) ++n;
+    int r = i - n * n;
+    if (r == 0) {
+        m = 0;
+        im = 0;
+    } else {
+        m = (r + 1) / 2;
+        im = (r % 2 == 0);
+    }
+}
+
+GB_DEV double fact64(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+}
+GB_DEV double Anm64(int n, int m) { return 1.0 / sqrt(fact64(n - m) * fact64(n + m)); }
+GB_DEV double ipow_even(int e) { return ((e / 2) % 2 == 0) ? 1.0 : -1.0; }
+
+// regular (irreg = 0) or irregular (irreg = 1) solid harmonics H[n(n+1)/2 + m], m >= 0, n < nmax
+GB_DEV void harmonics64(int nmax, double x, double y, double z, int irreg, C64 *H)
+{
+    double r2 = x * x + y * y + z * z;
+    double ir2 = 1.0 / r2;
+    C64 hmm = {irreg ? 1.0 / sqrt(r2) : 1.0, 0.0};
+    for (int m = 0; m < nmax; ++m) {
+        if (m > 0) {
+            double f = -sqrt((2.0 * m - 1.0) / (2.0 * m)) * (irreg ? ir2 : 1.0);
+            C64 t = cmul(C64{x, y}, hmm);
+            hmm = {f * t.re, f * t.im};
+        }
+        H[m * (m + 1) / 2 + m] = hmm;
+        for (int n = m; n + 1 < nmax; ++n) {
+            C64 a = H[n * (n + 1) / 2 + m];
+            C64 b = (n - 1 >= m) ? H[(n - 1) * n / 2 + m] : C64{0.0, 0.0};
+            double s = sqrt((double)(n - m) * (double)(n + m));
+            double d = 1.0 / sqrt((double)(n + 1 - m) * (double)(n + 1 + m));
+            double ca = (2.0 * n + 1.0) * z, cb = s * (irreg ? 1.0 : r2);
+            C64 v = {(ca * a.re - cb * b.re) * d, (ca * a.im - cb * b.im) * d};
+            if (irreg) {
+                v.re *= ir2;
+                v.im *= ir2;
+            }
+            H[(n + 1) * (n + 2) / 2 + m] = v;
+        }
+    }
+}
+
+GB_DEV C64 hfull(const C64 *H, int n, int m)
+{
+    return m >= 0 ? H[n * (n + 1) / 2 + m] : conj64(H[n * (n + 1) / 2 - m]);
+}
+
+// complex coefficient of input C_n^m in output D_j^k for the three operators
+GB_DEV C64 k_m2l(const C64 *I, int j, int k, int n, int m)
+{
+    double f = ipow_even(abs(k - m) - abs(k) - abs(m)) * Anm64(n, m) * Anm64(j, k) / Anm64(j + n, m - k) *
+               ((j & 1) ? -1.0 : 1.0);
+    C64 h = hfull(I, j + n, m - k);
+    return {f * h.re, f * h.im};
+}
+
+GB_DEV C64 k_m2m(const C64 *R, int j, int k, int n, int m)
+{
+    if (j < n || abs(k - m) > j - n) return {0.0, 0.0};
+    int nn = j - n, mm = k - m;
+    double f = ipow_even(abs(k) - abs(mm) - abs(k - mm)) * Anm64(nn, mm) * Anm64(n, m) / Anm64(j, k) / ldexp(1.0, j);
+    C64 h = hfull(R, nn, -mm);
+    return {f * h.re, f * h.im};
+}
+
+GB_DEV C64 k_l2l(const C64 *R, int j, int k, int n, int m)
+{
+    if (n < j || abs(m - k) > n - j) return {0.0, 0.0};
+    double f = ipow_even(abs(m) - abs(m - k) - abs(k)) * Anm64(n - j, m - k) * Anm64(j, k) / Anm64(n, m) /
+               ldexp(1.0, n + 1);
+    C64 h = hfull(R, n - j, m - k);
+    return {f * h.re, f * h.im};
+}
+
+__global__ void k_build_ops(int P, float *m2l, float *m2m, float *l2l)
+{
+    __shared__ C64 H[(2 * kMaxP) * (2 * kMaxP + 1) / 2];
+    const int op = blockIdx.x;
+    const int PP = P * P;
+    int kind;  // 0 m2l, 1 m2m, 2 l2l
+    double v[3];
+    bool used = true;
+    if (op < kM2LCodes) {
+        kind = 0;
+        int dx = op % 7 - 3, dy = (op / 7) % 7 - 3, dz = op / 49 - 3;
+        used = !(abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1);
+        v[0] = dx;  // target centre - source centre = -(source - target); the list stores
+        v[1] = dy;  // source - target, so the operator is built for the negated offset below
+        v[2] = dz;
+        v[0] = -v[0];
+        v[1] = -v[1];
+        v[2] = -v[2];
+    } else {
+        int c = (op - kM2LCodes) % 8;
+        kind = (op - kM2LCodes) < 8 ? 1 : 2;
+        v[0] = (c & 1) - 0.5;  // child centre - parent centre, in child cells
+        v[1] = ((c >> 1) & 1) - 0.5;
+        v[2] = ((c >> 2) & 1) - 0.5;
+    }
+    if (threadIdx.x == 0 && used) harmonics64(kind == 0 ? 2 * P - 1 : P, v[0], v[1], v[2], kind == 0, H);
+    __syncthreads();
+    for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+        int row = e / PP, col = e % PP;
+        float out = 0.f;
+        if (used) {
+            int j, k, rim, n, m, cim;
+            dof_decode(row, j, k, rim);
+            dof_decode(col, n, m, cim);
+            C64 u = cim ? C64{0.0, 1.0} : C64{1.0, 0.0};
+            C64 a, b = {0.0, 0.0};
+            if (kind == 0) {
+                a = k_m2l(H, j, k, n, m);
+                if (m > 0) b = k_m2l(H, j, k, n, -m);
+            } else if (kind == 1) {
+                a = k_m2m(H, j, k, n, m);
+                if (m > 0) b = k_m2m(H, j, k, n, -m);
+            } else {
+                a = k_l2l(H, j, k, n, m);
+                if (m > 0) b = k_l2l(H, j, k, n, -m);
+            }
+            C64 val = cmul(a, u);
+            C64 w = cmul(b, conj64(u));
+            val.re += w.re;
+            val.im += w.im;
+            out = (float)(rim ? val.im : val.re);
+        }
+        if (kind == 0)
+            m2l[(size_t)op * PP * PP + (size_t)col * PP + row] = out;
+        else if (kind == 1)
+            m2m[(size_t)(op - kM2LCodes) * PP * PP + (size_t)row * PP + col] = out;
+        else
+            l2l[(size_t)(op - kM2LCodes - 8) * PP * PP + (size_t)row * PP + col] = out;
+    }
+}
+
+void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_ops, cudaStream_t s)
+{
+    k_build_ops<<<kM2LCodes + 16, 256, 0, s>>>(P, m2l_ops, m2m_ops, l2l_ops);
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 helpers
+// ------------------------------------------------------------------------------------------
+struct CellGeom {
+    float cx, cy, cz, inv_h, h;
+};
+
+GB_DEV CellGeom cell_geom(const Box &b, int l, uint32_t key)
+{
+    int ix, iy, iz;
+    demorton3(key, ix, iy, iz);
+    double h = b.side / (double)(1 << l);
+    CellGeom g;
+    g.cx = (float)(b.origin[0] + (ix + 0.5) * h);
+    g.cy = (float)(b.origin[1] + (iy + 0.5) * h);
+    g.cz = (float)(b.origin[2] + (iz + 0.5) * h);
+    g.h = (float)h;
+    g.inv_h = (float)(1.0 / h);
+    return g;
+}
+
+// ------------------------------------------------------------------------------------------
+// P2M: one warp per leaf; lanes stride over the leaf's particles, each accumulates the full
+// real-packed expansion in registers, then a butterfly reduction sums the lanes.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box, const float4 *__restrict__ sx,
+                                             const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                                             float *__restrict__ M)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t leaf = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (leaf >= (int64_t(1) << (3 * L))) return;
+    const int64_t g = level_offset(L) + leaf;
+    const int b0 = begin[g], e0 = end[g];
+    if (e0 <= b0) return;
+    const Box bx = *box;
+    const CellGeom cg = cell_geom(bx, L, (uint32_t)leaf);
+    float acc[P * P];
+#pragma unroll
+    for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
+    for (int j = b0 + lane; j < e0; j += 32) {
+        float4 p = __ldg(&sx[j]);
+        const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
+        const float q = p.w, r2 = x * x + y * y + z * z;
+        float mre = 1.f, mim = 0.f;  // R_m^m
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            if (m > 0) {
+                const float f = -c_rmm[m];
+                const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
+                mre = tr;
+                mim = ti;
+            }
+            float are = mre, aim = mim, bre = 0.f, bim = 0.f;  // R_n^m, R_{n-1}^m
+#pragma unroll
+            for (int n = m; n < P; ++n) {
+                if (n > m) {
+                    const float ca = c_ra[n - 1][m] * z, cb = c_rb[n - 1][m] * r2;
+                    const float nre = ca * are - cb * bre, nim = ca * aim - cb * bim;
+                    bre = are;
+                    bim = aim;
+                    are = nre;
+                    aim = nim;
+                }
+                acc[re_idx(n, m)] += q * are;
+                if (m > 0) acc[im_idx(n, m)] -= q * aim;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < P * P; ++i) {
+        float v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((i & 31) == lane) M[g * (P * P) + i] = v;
+    }
+}
+
+void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
+                cudaStream_t s)
+{
+    int64_t nl = int64_t(1) << (3 * L);
+    unsigned grid = (unsigned)((nl + 3) / 4);
+    switch (P) {
+    case 4: k_p2m<4><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
+    case 6: k_p2m<6><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
+    case 8: k_p2m<8><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
+    case 10: k_p2m<10><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
+    }
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// M2M: parent (level l) <- its 8 children (level l+1).  One CTA per 8 consecutive parents,
+// one thread per output coefficient; child expansions staged in shared memory per child
+// position.  The operator is block lower-triangular in degree (output degree j reads input
+// degrees <= j).
+// ------------------------------------------------------------------------------------------
+constexpr int kTransGroup = 8;
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2m(int l, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                                             const float *__restrict__ ops, float *__restrict__ M)
+{
+    constexpr int PP = P * P;
+    __shared__ float sm[kTransGroup][PP];
+    const int64_t np = int64_t(1) << (3 * l);
+    const int64_t q0 = blockIdx.x * (int64_t)kTransGroup;
+    const int64_t offp = level_offset(l), offc = level_offset(l + 1);
+    const int r = threadIdx.x;
+    int deg = 0;
+    while ((deg + 1) * (deg + 1) <= r) ++deg;
+    const int ncol = (deg + 1) * (deg + 1);
+    float acc[kTransGroup];
+#pragma unroll
+    for (int i = 0; i < kTransGroup; ++i) acc[i] = 0.f;
+    for (int c = 0; c < 8; ++c) {
+        for (int e = threadIdx.x; e < kTransGroup * PP; e += blockDim.x) {
+            int i = e / PP, k = e % PP;
+            int64_t q = q0 + i;
+            float v = 0.f;
+            if (q < np) {
+                int64_t gc = offc + 8 * q + c;
+                if (end[gc] > begin[gc]) v = M[gc * PP + k];
+            }
+            sm[i][k] = v;
+        }
+        __syncthreads();
+        if (r < PP) {
+            const float *T = ops + (size_t)c * PP * PP + (size_t)r * PP;
+            for (int k = 0; k < ncol; ++k) {
+                float t = __ldg(&T[k]);
+#pragma unroll
+                for (int i = 0; i < kTransGroup; ++i) acc[i] = fmaf(t, sm[i][k], acc[i]);
+            }
+        }
+        __syncthreads();
+    }
+    if (r < PP)
+#pragma unroll
+        for (int i = 0; i < kTransGroup; ++i) {
+            int64_t q = q0 + i;
+            if (q < np && end[offp + q] > begin[offp + q]) M[(offp + q) * PP + r] = acc[i];
+        }
+}
+
+void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s)
+{
+    int64_t np = int64_t(1) << (3 * l);
+    unsigned grid = (unsigned)((np + kTransGroup - 1) / kTransGroup);
+    switch (P) {
+    case 4: k_m2m<4><<<grid, 32, 0, s>>>(l, begin, end, ops, M); break;
+    case 6: k_m2m<6><<<grid, 64, 0, s>>>(l, begin, end, ops, M); break;
+    case 8: k_m2m<8><<<grid, 64, 0, s>>>(l, begin, end, ops, M); break;
+    case 10: k_m2m<10><<<grid, 128, 0, s>>>(l, begin, end, ops, M); break;
+    }
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// L2L: children (level l) += L2L(parent, level l-1).  One CTA per (child position, 8
+// parents); output degree j reads input degrees >= j.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_l2l(int l, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                                             const float *__restrict__ ops, float *__restrict__ Lc)
+{
+    constexpr int PP = P * P;
+    __shared__ float sm[kTransGroup][PP];
+    const int c = blockIdx.y;
+    const int64_t np = int64_t(1) << (3 * (l - 1));
+    const int64_t q0 = blockIdx.x * (int64_t)kTransGroup;
+    const int64_t offp = level_offset(l - 1), offc = level_offset(l);
+    const int r = threadIdx.x;
+    for (int e = threadIdx.x; e < kTransGroup * PP; e += blockDim.x) {
+        int i = e / PP, k = e % PP;
+        int64_t q = q0 + i;
+        float v = 0.f;
+        if (q < np && end[offp + q] > begin[offp + q]) v = Lc[(offp + q) * PP + k];
+        sm[i][k] = v;
+    }
+    __syncthreads();
+    if (r >= PP) return;
+    int deg = 0;
+    while ((deg + 1) * (deg + 1) <= r) ++deg;
+    float acc[kTransGroup];
+#pragma unroll
+    for (int i = 0; i < kTransGroup; ++i) acc[i] = 0.f;
+    const float *T = ops + (size_t)c * PP * PP + (size_t)r * PP;
+    for (int k = deg * deg; k < PP; ++k) {
+        float t = __ldg(&T[k]);
+#pragma unroll
+        for (int i = 0; i < kTransGroup; ++i) acc[i] = fmaf(t, sm[i][k], acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kTransGroup; ++i) {
+        int64_t q = q0 + i;
+        if (q >= np) continue;
+        int64_t gc = offc + 8 * q + c;
+        if (end[gc] > begin[gc]) Lc[gc * PP + r] += acc[i];
+    }
+}
+
+void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *Lc, cudaStream_t s)
+{
+    int64_t np = int64_t(1) << (3 * (l - 1));
+    dim3 grid((unsigned)((np + kTransGroup - 1) / kTransGroup), 8);
+    switch (P) {
+    case 4: k_l2l<4><<<grid, 32, 0, s>>>(l, begin, end, ops, Lc); break;
+    case 6: k_l2l<6><<<grid, 64, 0, s>>>(l, begin, end, ops, Lc); break;
+    case 8: k_l2l<8><<<grid, 64, 0, s>>>(l, begin, end, ops, Lc); break;
+    case 10: k_l2l<10><<<grid, 128, 0, s>>>(l, begin, end, ops, Lc); break;
+    }
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// L2P: one thread per particle (sorted order).  phi = (1/h) sum L~ R(x^), grad = (1/h^2) x
+// ladder sums, x^ = (x - c) / h:
+//   dphi/dz            = sum_{n<P-1} sum_m sqrt((n+1-m)(n+1+m)) L_{n+1}^m R_n^m
+//   dphi/dx + i dphi/dy = sum_{n<P-1} sum_m s(m) sqrt((n+2-m)(n+1-m)) L_{n+1}^{m-1} R_n^m,
+//   s(m) = +1 for m >= 1, -1 for m <= 0.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box, int64_t n,
+                                             const float4 *__restrict__ sx, const uint32_t *__restrict__ leafkey,
+                                             const float *__restrict__ Lc, float4 *__restrict__ far)
+{
+    constexpr int PP = P * P;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t key = leafkey[i];
+    const int64_t g = level_offset(L) + key;
+    const Box bx = *box;
+    const CellGeom cg = cell_geom(bx, L, key);
+    const float *Lg = Lc + g * PP;
+    float4 p = __ldg(&sx[i]);
+    const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
+    const float r2 = x * x + y * y + z * z;
+    float phi = 0.f, gz = 0.f, gpr = 0.f, gpi = 0.f;
+    float mre = 1.f, mim = 0.f;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        if (m > 0) {
+            const float f = -c_rmm[m];
+            const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
+            mre = tr;
+            mim = ti;
+        }
+        float are = mre, aim = mim, bre = 0.f, bim = 0.f;
+#pragma unroll
+        for (int nn = m; nn < P; ++nn) {
+            if (nn > m) {
+                const float ca = c_ra[nn - 1][m] * z, cb = c_rb[nn - 1][m] * r2;
+                const float nre = ca * are - cb * bre, nim = ca * aim - cb * bim;
+                bre = are;
+                bim = aim;
+                are = nre;
+                aim = nim;
+            }
+            // phi: L_nn^m R_nn^m
+            {
+                const float lre = __ldg(&Lg[re_idx(nn, m)]);
+                const float lim = (m > 0) ? __ldg(&Lg[im_idx(nn, m)]) : 0.f;
+                const float w = (m > 0) ? 2.f : 1.f;
+                phi += w * (lre * are - lim * aim);
+            }
+            if (nn + 1 < P) {
+                // d/dz: L_{nn+1}^m R_nn^m
+                {
+                    const float lre = __ldg(&Lg[re_idx(nn + 1, m)]);
+                    const float lim = (m > 0) ? __ldg(&Lg[im_idx(nn + 1, m)]) : 0.f;
+                    const float w = (m > 0) ? 2.f : 1.f;
+                    gz += w * c_sq[nn + 1 - m][nn + 1 + m] * (lre * are - lim * aim);
+                }
+                // d/dx + i d/dy, term mu = m >= 1: + sqrt((nn+2-m)(nn+1-m)) L_{nn+1}^{m-1} R_nn^m
+                if (m >= 1) {
+                    const float lre = __ldg(&Lg[re_idx(nn + 1, m - 1)]);
+                    const float lim = (m - 1 > 0) ? __ldg(&Lg[im_idx(nn + 1, m - 1)]) : 0.f;
+                    const float c = c_sq[nn + 2 - m][nn + 1 - m];
+                    gpr += c * (lre * are - lim * aim);
+                    gpi += c * (lre * aim + lim * are);
+                }
+                // term mu = -m <= 0: - sqrt((nn+2+m)(nn+1+m)) conj(L_{nn+1}^{m+1} R_nn^m)
+                {
+                    const float lre = __ldg(&Lg[re_idx(nn + 1, m + 1)]);
+                    const float lim = __ldg(&Lg[im_idx(nn + 1, m + 1)]);
+                    const float c = c_sq[nn + 2 + m][nn + 1 + m];
+                    gpr -= c * (lre * are - lim * aim);
+                    gpi += c * (lre * aim + lim * are);
+                }
+            }
+        }
+    }
+    const float ih = cg.inv_h, ih2 = ih * ih;
+    far[i] = make_float4(phi * ih, gpr * ih2, gpi * ih2, gz * ih2);
+}
+
+void launch_l2p(int P, int L, const Box *box, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
+                float4 *far, cudaStream_t s)
+{
+    if (n <= 0) return;
+    unsigned grid = (unsigned)((n + 127) / 128);
+    switch (P) {
+    case 4: k_l2p<4><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
+    case 6: k_l2p<6><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
+    case 8: k_l2p<8><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
+    case 10: k_l2p<10><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
+    }
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// M2P (treecode far field): one CTA per target leaf, one thread per target particle; for
+// every level 2..L the sources are the M2L list of the leaf's ancestor.  With x^ = (x - c)/h:
+//   phi = (1/h) sum M~_n^m I_n^m(x^)
+//   dphi/dz             = -(1/h^2) sum sqrt((n+1-m)(n+1+m)) M~_n^m I_{n+1}^m
+//   dphi/dx + i dphi/dy =  (1/h^2) sum s(m) sqrt((n+m+2)(n+m+1)) M~_n^m I_{n+1}^{m+1},
+//   s(m) = +1 for m >= 0, -1 for m < 0.
+// ------------------------------------------------------------------------------------------
+template <int P>
+GB_DEV void m2p_accumulate(const float *__restrict__ Ms, float x, float y, float z, float ih, float *o)
+{
+    const float r2 = x * x + y * y + z * z;
+    const float ir2 = 1.f / r2;
+    float phi = 0.f, gz = 0.f, gpr = 0.f, gpi = 0.f;
+    float mre = rsqrtf(r2), mim = 0.f;  // I_0^0 = 1/r
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            const float f = -c_rmm[m] * ir2;
+            const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
+            mre = tr;
+            mim = ti;
+        }
+        float are = mre, aim = mim, bre = 0.f, bim = 0.f;
+#pragma unroll
+        for (int N = m; N <= P; ++N) {
+            if (N > m) {
+                const float ca = c_ra[N - 1][m] * z, cb = c_rb[N - 1][m];
+                const float nre = (ca * are - cb * bre) * ir2, nim = (ca * aim - cb * bim) * ir2;
+                bre = are;
+                bim = aim;
+                are = nre;
+                aim = nim;
+            }
+            const float w = (m > 0) ? 2.f : 1.f;
+            if (N <= P - 1) {  // phi: M_N^m I_N^m
+                const float lre = Ms[re_idx(N, m)], lim = (m > 0) ? Ms[im_idx(N, m)] : 0.f;
+                phi += w * (lre * are - lim * aim);
+            }
+            if (N >= 1 && m <= N - 1) {  // d/dz: -sqrt((N-m)(N+m)) M_{N-1}^m I_N^m
+                const float lre = Ms[re_idx(N - 1, m)], lim = (m > 0) ? Ms[im_idx(N - 1, m)] : 0.f;
+                gz -= w * c_sq[N - m][N + m] * (lre * are - lim * aim);
+            }
+            if (N >= 1 && m >= 1) {  // mu = m >= 1: + sqrt((N+m)(N+m-1)) M_{N-1}^{m-1} I_N^m
+                const float lre = Ms[re_idx(N - 1, m - 1)], lim = (m - 1 > 0) ? Ms[im_idx(N - 1, m - 1)] : 0.f;
+                const float c = c_sq[N + m][N + m - 1];
+                gpr += c * (lre * are - lim * aim);
+                gpi += c * (lre * aim + lim * are);
+            }
+            if (N >= 1 && m + 1 <= N - 1) {  // mu = -m: - sqrt((N-m)(N-m-1)) conj(M_{N-1}^{m+1} I_N^m)
+                const float lre = Ms[re_idx(N - 1, m + 1)], lim = Ms[im_idx(N - 1, m + 1)];
+                const float c = c_sq[N - m][N - m - 1];
+                gpr -= c * (lre * are - lim * aim);
+                gpi += c * (lre * aim + lim * are);
+            }
+        }
+    }
+    o[0] += phi * ih;
+    const float ih2 = ih * ih;
+    o[1] += gpr * ih2;
+    o[2] += gpi * ih2;
+    o[3] += gz * ih2;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2p(int L, const Box *__restrict__ box, const float4 *__restrict__ sx,
+                                             const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                                             const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
+                                             const float *__restrict__ M, float4 *__restrict__ far)
+{
+    constexpr int PP = P * P;
+    __shared__ float sM[PP];
+    const int64_t leaf = blockIdx.x;
+    const int64_t g = level_offset(L) + leaf;
+    const int b0 = begin[g], e0 = end[g];
+    if (e0 <= b0) return;
+    const Box bx = *box;
+    for (int t0 = b0; t0 < e0; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const bool act = t < e0;
+        float4 p = act ? __ldg(&sx[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int l = 2; l <= L; ++l) {
+            const int64_t a = level_offset(l) + (leaf >> (3 * (L - l)));
+            for (uint32_t e = m2l_offs[a]; e < m2l_offs[a + 1]; ++e) {
+                const int64_t s = m2l_ids[e];
+                __syncthreads();
+                for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[s * PP + k];
+                __syncthreads();
+                const CellGeom cg = cell_geom(bx, l, (uint32_t)(s - level_offset(l)));
+                if (act)
+                    m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                                      (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
+            }
+        }
+        if (act) far[t] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end,
+                const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s)
+{
+    unsigned grid = (unsigned)(int64_t(1) << (3 * L));
+    switch (P) {
+    case 4: k_m2p<4><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 6: k_m2p<6><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 8: k_m2p<8><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 10: k_m2p<10><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    }
+    note_launches(1);
+}
+
+}  // namespace gbfmm

@@ -1,0 +1,579 @@
+// Tree front end of the FMM on the device: root box, Morton keys, stable radix sort of the
+// particles by leaf key, per-level cell ranges and the CSR interaction lists.
+//
+// The paper runs these steps ("sort" and "other": tree construction and list generation) on
+// the host (Section "Improvements of Performance", Fig. 5); here every one is an integer or
+// bandwidth-bound device kernel.  This translation unit is compiled with -fmad=false and the
+// key quantisation uses explicit IEEE round-to-nearest FP64 intrinsics, so the keys are the
+// exact result of floor((x - origin) / side * 2^21) and match any IEEE FP64 evaluation of the
+// same expression bit for bit.
+#include "common.cuh"
+
+#include <math.h>
+
+namespace gbfmm {
+
+// ------------------------------------------------------------------------------------------
+// Root box: min/max reduction with a non-finite check; the last block to finish folds the
+// per-block partials and writes the box (no spin-wait: a completion counter elects it).
+// ------------------------------------------------------------------------------------------
+constexpr int kBoxThreads = 256;
+constexpr int kBoxBlocks = 304;
+
+__global__ void __launch_bounds__(kBoxThreads) k_bbox(const float4 *__restrict__ x, int64_t n, int has_box,
+                                                      double ox, double oy, double oz, double bside, Box *box_out,
+                                                      float *partials, unsigned *counter, int *status)
+{
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 p = __ldg(&x[i]);
+        float c[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (isfinite(c[d])) {
+                mn[d] = fminf(mn[d], c[d]);
+                mx[d] = fmaxf(mx[d], c[d]);
+            } else {
+                bad = 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    bad = __any_sync(0xffffffffu, bad);
+    __shared__ float red[kBoxThreads / 32][6];
+    __shared__ int sbad;
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (lane == 0) {
+        for (int d = 0; d < 3; ++d) {
+            red[warp][d] = mn[d];
+            red[warp][3 + d] = mx[d];
+        }
+        if (bad) atomicOr(&sbad, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r[6];
+        for (int k = 0; k < 6; ++k) r[k] = red[0][k];
+        for (int w = 1; w < kBoxThreads / 32; ++w)
+            for (int d = 0; d < 3; ++d) {
+                r[d] = fminf(r[d], red[w][d]);
+                r[3 + d] = fmaxf(r[3 + d], red[w][3 + d]);
+            }
+        for (int k = 0; k < 6; ++k) partials[blockIdx.x * 8 + k] = r[k];
+        partials[blockIdx.x * 8 + 6] = sbad ? 1.f : 0.f;
+        if (sbad) atomicOr(status, kStatusNonFinite);
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // fold the per-block partials with the whole block (strided loads, then a shuffle reduction)
+    float r[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    int any_bad = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        for (int d = 0; d < 3; ++d) {
+            r[d] = fminf(r[d], __ldcg(&partials[b * 8 + d]));
+            r[3 + d] = fmaxf(r[3 + d], __ldcg(&partials[b * 8 + 3 + d]));
+        }
+        if (__ldcg(&partials[b * 8 + 6]) != 0.f) any_bad = 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = fminf(r[d], __shfl_xor_sync(0xffffffffu, r[d], o));
+            r[3 + d] = fmaxf(r[3 + d], __shfl_xor_sync(0xffffffffu, r[3 + d], o));
+        }
+    any_bad = __any_sync(0xffffffffu, any_bad);
+    __syncthreads();
+    if (lane == 0) {
+        for (int k = 0; k < 6; ++k) red[warp][k] = r[k];
+        if (any_bad) atomicOr(&sbad, 2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBoxThreads / 32; ++w)
+            for (int d = 0; d < 3; ++d) {
+                r[d] = fminf(r[d], red[w][d]);
+                r[3 + d] = fmaxf(r[3 + d], red[w][3 + d]);
+            }
+        any_bad = (sbad & 2) != 0;
+        Box b;
+        if (has_box) {
+            b.origin[0] = ox;
+            b.origin[1] = oy;
+            b.origin[2] = oz;
+            b.side = bside;
+        } else if (n == 0 || any_bad || !(r[0] <= r[3])) {
+            b.origin[0] = b.origin[1] = b.origin[2] = 0.0;
+            b.side = 1.0;
+        } else {
+            double S = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double e = __dsub_rn((double)r[3 + d], (double)r[d]);
+                if (e > S) S = e;
+            }
+            if (S == 0.0) S = 1.0;
+            for (int d = 0; d < 3; ++d) {
+                double c = __dmul_rn(__dadd_rn((double)r[d], (double)r[3 + d]), 0.5);
+                b.origin[d] = __dsub_rn(c, __dmul_rn(S, 0.5));
+            }
+            b.side = S;
+        }
+        *box_out = b;
+        *counter = 0u;  // ready for the next launch on this stream
+    }
+}
+
+void launch_bbox(const float4 *x, int64_t n, int has_box, const double *box_origin, double box_side, Box *box_out,
+                 float *partials, unsigned *counter, int *status, cudaStream_t s)
+{
+    int64_t want = (n + kBoxThreads - 1) / kBoxThreads;
+    int blocks = (int)(want < kBoxBlocks ? (want > 0 ? want : 1) : kBoxBlocks);
+    k_bbox<<<blocks, kBoxThreads, 0, s>>>(x, n, has_box, box_origin[0], box_origin[1], box_origin[2], box_side,
+                                          box_out, partials, counter, status);
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Morton keys at the leaf depth L: k_d = clamp(floor((x_d - origin_d) / side * 2^21), 0, 2^21-1)
+// in IEEE FP64, then the 3L-bit key of the depth-L cell = interleave(k_d >> (21 - L)).
+// ------------------------------------------------------------------------------------------
+__global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__restrict__ box, int L,
+                       uint32_t *__restrict__ leafkey, uint32_t *__restrict__ idx)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Box b = *box;
+    float4 p = __ldg(&x[i]);
+    float c[3] = {p.x, p.y, p.z};
+    uint32_t k[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t = __dsub_rn((double)c[d], b.origin[d]);
+        double u = __ddiv_rn(t, b.side);
+        double v = __dmul_rn(u, 2097152.0);
+        double f = floor(v);
+        if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
+        if (f > 2097151.0) f = 2097151.0;
+        k[d] = (uint32_t)f;
+    }
+    const int sh = 21 - L;
+    leafkey[i] = morton3(k[0] >> sh, k[1] >> sh, k[2] >> sh);
+    idx[i] = (uint32_t)i;
+}
+
+void launch_keys(const float4 *x, int64_t n, const Box *box, int L, uint32_t *leafkey, uint32_t *idx, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, box, L, leafkey, idx);
+    note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Exclusive scan of uint32 (reduce, scan of block sums, apply).  out[n] receives the total.
+// ------------------------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+size_t exclusive_scan_tmp_words(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
+                                                              uint32_t *__restrict__ part)
+{
+    int64_t base = blockIdx.x * (int64_t)kScanTile;
+    uint32_t s = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ uint32_t ws[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of the nb block sums in place; total to *total
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *part, int64_t nb, uint32_t *total)
+{
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = (i < nb) ? part[i] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) ws[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = ws[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            ws[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        uint32_t c = carry;
+        if (i < nb) part[i] = c + ws[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + ws[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
+                                                             const uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t tile[kScanTile];
+    __shared__ uint32_t ws[kScanThreads / 32];
+    int64_t base = blockIdx.x * (int64_t)kScanTile;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
+        tile[r * kScanThreads + threadIdx.x] = (i < n) ? in[i] : 0u;
+    }
+    __syncthreads();
+    uint32_t loc[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = s;
+        s += tile[threadIdx.x * kScanItems + k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += ws[w];
+    uint32_t pre = part[blockIdx.x] + wpre + incl - s;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) tile[threadIdx.x * kScanItems + k] = pre + loc[k];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        int64_t i = base + r * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = tile[r * kScanThreads + threadIdx.x];
+    }
+}
+
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s)
+{
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+        return;
+    }
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb, out + n);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+    note_launches(3);
+}
+
+// ------------------------------------------------------------------------------------------
+// Stable LSD radix sort of (key, index) pairs, 8-bit digits.  Per pass: tile histograms,
+// an exclusive scan of the digit-major histogram, and a scatter that ranks keys stably
+// inside each tile (warp match + per-warp digit counts).  The last pass also gathers the
+// particles into sorted order.
+// ------------------------------------------------------------------------------------------
+constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                        uint32_t mask, uint32_t *__restrict__ hist, int64_t nblk)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = blockIdx.x * (int64_t)kRsTile;
+#pragma unroll 4
+    for (int r = 0; r < kRsItems; ++r) {
+        int64_t i = base + r * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+                                                           uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                           uint32_t mask, const uint32_t *__restrict__ hist_scan,
+                                                           int64_t nblk, const float4 *__restrict__ gx,
+                                                           float4 *__restrict__ gsx)
+{
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[kRsThreads / 32][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    base[tid] = hist_scan[(int64_t)tid * nblk + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kRsThreads / 32; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int64_t tbase = blockIdx.x * (int64_t)kRsTile;
+    for (int r = 0; r < kRsItems; ++r) {
+        int64_t i = tbase + r * kRsThreads + tid;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u, val = valid ? vin[i] : 0u;
+        uint32_t d = valid ? ((key >> shift) & mask) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = base[tid];
+#pragma unroll
+            for (int w = 0; w < kRsThreads / 32; ++w) {
+                uint32_t t = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += t;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+            if (gsx) gsx[pos] = __ldg(&gx[val]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_gather_identity(const float4 *__restrict__ x, float4 *__restrict__ sx, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) sx[i] = x[i];
+}
+
+void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
+                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
+                        uint32_t **idx_out, cudaStream_t s)
+{
+    uint32_t *kin = k0, *kout = k1, *vin = v0, *vout = v1;
+    if (bits <= 0 || n <= 1) {
+        if (n > 0) {
+            k_gather_identity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, sx, n);
+            note_launches(1);
+        }
+        *keys_out = k0;
+        *idx_out = v0;
+        return;
+    }
+    for (int shift = 0; shift < bits; shift += 8) {
+        int nb = bits - shift < 8 ? bits - shift : 8;
+        uint32_t mask = (1u << nb) - 1u;
+        bool last = shift + 8 >= bits;
+        k_rs_hist<<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, n, shift, mask, hist, nblk);
+        launch_exclusive_scan(hist, hist, 256 * nblk, scan_tmp, s);
+        k_rs_scatter<<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, mask, hist, nblk, x,
+                                                           last ? sx : nullptr);
+        note_launches(2);
+        uint32_t *t = kin;
+        kin = kout;
+        kout = t;
+        t = vin;
+        vin = vout;
+        vout = t;
+    }
+    *keys_out = kin;
+    *idx_out = vin;
+}
+
+// ------------------------------------------------------------------------------------------
+// Cells: for every level, the first and one-past-last sorted position of each nonempty cell
+// (arrays zeroed beforehand, so empty cells read begin == end == 0).
+// ------------------------------------------------------------------------------------------
+__global__ void k_cells(const uint32_t *__restrict__ sk, int64_t n, int L, int32_t *__restrict__ begin,
+                        int32_t *__restrict__ end)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t key = sk[i];
+    uint32_t prev = i > 0 ? sk[i - 1] : 0u, next = i + 1 < n ? sk[i + 1] : 0u;
+    for (int l = 0; l <= L; ++l) {
+        int sh = 3 * (L - l);
+        uint32_t pk = key >> sh;
+        int64_t g = level_offset(l) + pk;
+        if (i == 0 || (prev >> sh) != pk) begin[g] = (int32_t)i;
+        if (i + 1 == n || (next >> sh) != pk) end[g] = (int32_t)(i + 1);
+    }
+}
+
+void launch_cells(const uint32_t *sk, int64_t n, int L, int32_t *begin, int32_t *end, cudaStream_t s)
+{
+    size_t C = (size_t)level_offset(L + 1);
+    cudaMemsetAsync(begin, 0, C * sizeof(int32_t), s);
+    cudaMemsetAsync(end, 0, C * sizeof(int32_t), s);
+    if (n > 0) {
+        k_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sk, n, L, begin, end);
+        note_launches(1);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Interaction lists (Section "The P2P kernel implementation": 27 neighbour cells; Section
+// "The M2L kernel implementation": at most 189 well-separated cells).
+//   P2P row of a nonempty leaf: nonempty leaves at Chebyshev index distance <= 1 (itself
+//       included), in ascending offset code (dz, dy, dx);
+//   M2L row of a nonempty cell at level >= 2: nonempty children of the parent's neighbours
+//       that are not neighbours themselves, in ascending offset code; the code
+//       (dx+3) + 7(dy+3) + 49(dz+3) of the offset source - target is stored beside the id.
+// ------------------------------------------------------------------------------------------
+GB_DEV bool nonempty(const int32_t *begin, const int32_t *end, int64_t g) { return end[g] > begin[g]; }
+
+template <class F>
+GB_DEV void for_each_m2l(int l, uint32_t key, const int32_t *begin, const int32_t *end, F f)
+{
+    int x, y, z;
+    demorton3(key, x, y, z);
+    const int side = 1 << l;
+    const int cx = x & 1, cy = y & 1, cz = z & 1;
+    const int64_t off = level_offset(l);
+    for (int oz = -2 - cz; oz <= 3 - cz; ++oz) {
+        int sz = z + oz;
+        if (sz < 0 || sz >= side) continue;
+        for (int oy = -2 - cy; oy <= 3 - cy; ++oy) {
+            int sy = y + oy;
+            if (sy < 0 || sy >= side) continue;
+            for (int ox = -2 - cx; ox <= 3 - cx; ++ox) {
+                int sxx = x + ox;
+                if (sxx < 0 || sxx >= side) continue;
+                if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                int64_t g = off + morton3((uint32_t)sxx, (uint32_t)sy, (uint32_t)sz);
+                if (nonempty(begin, end, g)) f(g, m2l_code(ox, oy, oz));
+            }
+        }
+    }
+}
+
+template <class F>
+GB_DEV void for_each_p2p(int L, uint32_t key, const int32_t *begin, const int32_t *end, F f)
+{
+    int x, y, z;
+    demorton3(key, x, y, z);
+    const int side = 1 << L;
+    const int64_t off = level_offset(L);
+    for (int oz = -1; oz <= 1; ++oz) {
+        int sz = z + oz;
+        if (sz < 0 || sz >= side) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int sy = y + oy;
+            if (sy < 0 || sy >= side) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                int sxx = x + ox;
+                if (sxx < 0 || sxx >= side) continue;
+                int64_t g = off + morton3((uint32_t)sxx, (uint32_t)sy, (uint32_t)sz);
+                if (nonempty(begin, end, g)) f(g);
+            }
+        }
+    }
+}
+
+GB_DEV void cell_of(int64_t g, int &l, uint32_t &key)
+{
+    l = 0;
+    while (level_offset(l + 1) <= g) ++l;
+    key = (uint32_t)(g - level_offset(l));
+}
+
+__global__ void k_list_count(int L, int64_t C, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                             uint32_t *__restrict__ p2p_len, uint32_t *__restrict__ m2l_len)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= C) return;
+    int l;
+    uint32_t key;
+    cell_of(g, l, key);
+    bool ne = nonempty(begin, end, g);
+    uint32_t c = 0;
+    if (ne && l >= 2) for_each_m2l(l, key, begin, end, [&](int64_t, int) { ++c; });
+    m2l_len[g] = c;
+    if (l == L) {
+        uint32_t q = 0;
+        if (ne) for_each_p2p(L, key, begin, end, [&](int64_t) { ++q; });
+        p2p_len[key] = q;
+    }
+}
+
+__global__ void k_list_fill(int L, int64_t C, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                            const uint32_t *__restrict__ p2p_offs, int32_t *__restrict__ p2p_ids,
+                            const uint32_t *__restrict__ m2l_offs, int32_t *__restrict__ m2l_ids,
+                            uint16_t *__restrict__ m2l_code)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= C) return;
+    int l;
+    uint32_t key;
+    cell_of(g, l, key);
+    if (!nonempty(begin, end, g)) return;
+    if (l >= 2) {
+        uint32_t e = m2l_offs[g];
+        for_each_m2l(l, key, begin, end, [&](int64_t s, int code) {
+            m2l_ids[e] = (int32_t)s;
+            m2l_code[e] = (uint16_t)code;
+            ++e;
+        });
+    }
+    if (l == L) {
+        uint32_t e = p2p_offs[key];
+        for_each_p2p(L, key, begin, end, [&](int64_t s) { p2p_ids[e++] = (int32_t)s; });
+    }
+}
+
+void launch_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t *p2p_len, uint32_t *m2l_len,
+                       cudaStream_t s)
+{
+    int64_t C = level_offset(L + 1);
+    k_list_count<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(L, C, begin, end, p2p_len, m2l_len);
+    note_launches(1);
+}
+
+void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
+                      const uint32_t *m2l_offs, int32_t *m2l_ids, uint16_t *m2l_code, cudaStream_t s)
+{
+    int64_t C = level_offset(L + 1);
+    k_list_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(L, C, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids,
+                                                           m2l_code);
+    note_launches(1);
+}
+
+}  // namespace gbfmm

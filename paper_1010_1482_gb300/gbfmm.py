@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libgbfmm.so (include/gbfmm.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as raw device pointers with torch's current
+CUDA stream; every step of the evaluation runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library is missing or fails to load, the import-time helpers raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libgbfmm.so")
+HEADER = os.path.join(ROOT, "include", "gbfmm.h")
+
+GBFMM_OK, GBFMM_EINVAL, GBFMM_ENOMEM, GBFMM_ECUDA, GBFMM_ETIMEOUT, GBFMM_EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+METHOD_FMM, METHOD_TREECODE = 0, 1
+LIST_P2P, LIST_M2L = 0, 1
+FLAG_STAGE_TIMING = 1
+STAGES = ["box+keys", "sort", "cells+lists", "P2M", "M2M", "M2L/M2P", "L2L", "L2P", "P2P", "operators"]
+
+
+class gbfmm_params(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int32),
+        ("leaf_size", ctypes.c_int32),
+        ("tree", ctypes.c_int32),
+        ("method", ctypes.c_int32),
+        ("eps2", ctypes.c_double),
+        ("has_box", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+        ("box_origin", ctypes.c_double * 3),
+        ("box_side", ctypes.c_double),
+    ]
+
+
+class GbfmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/gbfmm.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*\**(gbfmm_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Load libgbfmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgbfmm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i = ctypes.c_int
+    i64 = ctypes.c_int64
+    sig = {
+        "gbfmm_version": (i, []),
+        "gbfmm_default_params": (i, [ctypes.POINTER(gbfmm_params)]),
+        "gbfmm_create": (i, [ctypes.POINTER(P), i]),
+        "gbfmm_destroy": (i, [P]),
+        "gbfmm_last_error": (ctypes.c_char_p, [P]),
+        "gbfmm_plan": (i, [ctypes.POINTER(gbfmm_params), i64, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_size_t)]),
+        "gbfmm_evaluate": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, P, ctypes.c_size_t, P]),
+        "gbfmm_evaluate_host": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, P]),
+        "gbfmm_sync_status": (i, [P, P]),
+        "gbfmm_direct": (i, [P, i64, P, i64, P, ctypes.c_double, P, P]),
+        "gbfmm_export_tree": (i, [P, P, P, P, P, P]),
+        "gbfmm_export_lists": (i, [P, i, P, P, i64, ctypes.POINTER(i64)]),
+        "gbfmm_export_expansions": (i, [P, i, P]),
+        "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
+        "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, rc):
+    if rc != GBFMM_OK:
+        msg = lib().gbfmm_last_error(ctx).decode() if ctx else ""
+        raise GbfmmError(rc, msg)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- same names as the C ABI ----------------------------------------------------------------
+
+def gbfmm_version() -> int:
+    return lib().gbfmm_version()
+
+
+def gbfmm_default_params(**kw) -> gbfmm_params:
+    prm = gbfmm_params()
+    _check(None, lib().gbfmm_default_params(ctypes.byref(prm)))
+    for k, v in kw.items():
+        if k == "box_origin":
+            prm.box_origin[:] = list(v)
+        else:
+            setattr(prm, k, v)
+    return prm
+
+
+def gbfmm_create(device: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(None, lib().gbfmm_create(ctypes.byref(ctx), int(device)))
+    return ctx
+
+
+def gbfmm_destroy(ctx) -> None:
+    lib().gbfmm_destroy(ctx)
+
+
+def gbfmm_last_error(ctx) -> str:
+    return lib().gbfmm_last_error(ctx).decode()
+
+
+def gbfmm_plan(prm: gbfmm_params, n: int) -> tuple[int, int]:
+    lv = ctypes.c_int32()
+    ws = ctypes.c_size_t()
+    _check(None, lib().gbfmm_plan(ctypes.byref(prm), int(n), ctypes.byref(lv), ctypes.byref(ws)))
+    return lv.value, ws.value
+
+
+def gbfmm_evaluate(ctx, prm: gbfmm_params, xyzq: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor,
+                   stream=None) -> None:
+    n = xyzq.shape[0]
+    assert xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous() and xyzq.shape[1] == 4
+    assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.shape == xyzq.shape
+    _check(ctx, lib().gbfmm_evaluate(ctx, ctypes.byref(prm), n, _ptr(xyzq), _ptr(out), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def gbfmm_evaluate_host(ctx, prm: gbfmm_params, xyzq: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+    """xyzq, out: CPU float32 (n, 4) tensors (pinned for asynchronous copies)."""
+    assert not xyzq.is_cuda and not out.is_cuda and xyzq.is_contiguous() and out.is_contiguous()
+    _check(ctx, lib().gbfmm_evaluate_host(ctx, ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _ptr(out),
+                                          _stream(stream)))
+
+
+def gbfmm_sync_status(ctx, stream=None) -> None:
+    _check(ctx, lib().gbfmm_sync_status(ctx, _stream(stream)))
+
+
+def gbfmm_direct(ctx, src: torch.Tensor, tgt: torch.Tensor, out: torch.Tensor, eps2: float = 0.0,
+                 stream=None) -> None:
+    _check(ctx, lib().gbfmm_direct(ctx, src.shape[0], _ptr(src), tgt.shape[0], _ptr(tgt), float(eps2), _ptr(out),
+                                   _stream(stream)))
+
+
+def gbfmm_export_tree(ctx, n: int, ncells: int) -> dict:
+    import numpy as np
+
+    os_ = np.zeros(4)
+    keys = np.zeros(n, dtype=np.uint32)
+    perm = np.zeros(n, dtype=np.uint32)
+    begin = np.zeros(ncells, dtype=np.int32)
+    count = np.zeros(ncells, dtype=np.int32)
+    _check(ctx, lib().gbfmm_export_tree(ctx, _np_ptr(os_), _np_ptr(keys), _np_ptr(perm), _np_ptr(begin),
+                                        _np_ptr(count)))
+    return dict(origin=os_[:3].copy(), side=float(os_[3]), sorted_leaf_keys=keys, perm=perm, begin=begin,
+                count=count)
+
+
+def gbfmm_export_lists(ctx, kind: int, rows: int) -> tuple:
+    import numpy as np
+
+    ne = ctypes.c_int64()
+    offs = np.zeros(rows + 1, dtype=np.int32)
+    _check(ctx, lib().gbfmm_export_lists(ctx, kind, _np_ptr(offs), None, 0, ctypes.byref(ne)))
+    ids = np.zeros(max(1, ne.value), dtype=np.int32)
+    _check(ctx, lib().gbfmm_export_lists(ctx, kind, _np_ptr(offs), _np_ptr(ids), len(ids), ctypes.byref(ne)))
+    return offs, ids[: ne.value]
+
+
+def gbfmm_export_expansions(ctx, which: int, ncells: int, p: int):
+    import numpy as np
+
+    nt = p * (p + 1) // 2
+    buf = np.zeros(ncells * 2 * nt)
+    _check(ctx, lib().gbfmm_export_expansions(ctx, which, _np_ptr(buf)))
+    return (buf[0::2] + 1j * buf[1::2]).reshape(ncells, nt)
+
+
+def gbfmm_stage_times(ctx) -> dict:
+    import numpy as np
+
+    ms = np.zeros(len(STAGES), dtype=np.float32)
+    cnt = ctypes.c_int()
+    _check(ctx, lib().gbfmm_stage_times(ctx, _np_ptr(ms), len(STAGES), ctypes.byref(cnt)))
+    return {STAGES[i]: float(ms[i]) for i in range(cnt.value)}
+
+
+def gbfmm_last_launch_count(ctx) -> int:
+    c = ctypes.c_int64()
+    _check(ctx, lib().gbfmm_last_launch_count(ctx, ctypes.byref(c)))
+    return c.value
+
+
+# ---- convenience wrapper (torch-allocated workspace) -----------------------------------------
+
+def level_offset(l: int) -> int:
+    return (8 ** l - 1) // 7
+
+
+class FMM:
+    """Owns a context and a torch-allocated workspace; evaluate() runs on the current stream."""
+
+    def __init__(self, device: int = 0, **params):
+        self.device = device
+        self.ctx = gbfmm_create(device)
+        self.params = gbfmm_default_params(**params)
+        self.workspace = None
+
+    def close(self):
+        if self.ctx:
+            gbfmm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, n: int):
+        return gbfmm_plan(self.params, n)
+
+    def ensure_workspace(self, n: int) -> torch.Tensor:
+        _, ws = gbfmm_plan(self.params, n)
+        if self.workspace is None or self.workspace.numel() < ws:
+            self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self.workspace
+
+    def evaluate(self, xyzq: torch.Tensor, out: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(xyzq)
+        ws = self.ensure_workspace(xyzq.shape[0])
+        gbfmm_evaluate(self.ctx, self.params, xyzq, out, ws)
+        if check:
+            gbfmm_sync_status(self.ctx)
+        return out

@@ -99,6 +99,8 @@ def workload(name: str) -> dict:
         "uniform_4k_p4": dict(n=4096, dist="uniform", p=4, leaf_size=64, seed=SEED_BASE + 0),
         # single large uniform instance, FP32 path
         "uniform_1m_p10": dict(n=1 << 20, dist="uniform", p=10, leaf_size=64, seed=SEED_BASE + 1),
+        # same distribution, p and mean leaf occupancy (32) at depth 4: the small profiling case
+        "uniform_128k_p10": dict(n=1 << 17, dist="uniform", p=10, leaf_size=64, seed=SEED_BASE + 1),
         # clustered single instance
         "plummer_16m_p8": dict(n=1 << 24, dist="plummer", p=8, leaf_size=64, seed=SEED_BASE + 2),
     }

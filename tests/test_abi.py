@@ -1,0 +1,65 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the header
+declares, and rejects bad parameters in planning."""
+import ctypes
+
+import pytest
+
+import oracle as O
+from paper_1010_1482_gb300 import build as cuda_build
+from paper_1010_1482_gb300 import gbfmm as G
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return G.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = G.declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert G.gbfmm_version() == 1
+
+
+def test_default_params_and_plan(lib):
+    prm = G.gbfmm_default_params()
+    assert (prm.p, prm.leaf_size, prm.method, prm.eps2) == (10, 64, 0, 0.0)
+    L, ws = G.gbfmm_plan(prm, 1 << 20)
+    assert L == O.uniform_depth(1 << 20, 64) == 5
+    assert ws > (1 << 20) * 64
+    for n, leaf in [(4096, 64), (1, 64), (0, 64), (512, 64), (513, 64), (100000, 7)]:
+        prm = G.gbfmm_default_params(p=4, leaf_size=leaf)
+        assert G.gbfmm_plan(prm, n)[0] == O.uniform_depth(n, leaf)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(p=5), G.GBFMM_EUNSUPPORTED),
+    (dict(p=12), G.GBFMM_EUNSUPPORTED),
+    (dict(leaf_size=0), G.GBFMM_EINVAL),
+    (dict(method=7), G.GBFMM_EINVAL),
+    (dict(eps2=-1.0), G.GBFMM_EINVAL),
+    (dict(has_box=1, box_side=0.0), G.GBFMM_EINVAL),
+    (dict(leaf_size=1), G.GBFMM_EUNSUPPORTED),  # depth > 10 for n = 2^31 - 1
+])
+def test_plan_rejects_bad_parameters(lib, kw, code):
+    prm = G.gbfmm_default_params(**kw)
+    with pytest.raises(G.GbfmmError) as ei:
+        G.gbfmm_plan(prm, (1 << 31) - 1 if kw.get("leaf_size") == 1 else 1000)
+    assert ei.value.code == code
+
+
+def test_negative_n_and_null_context(lib):
+    prm = G.gbfmm_default_params()
+    with pytest.raises(G.GbfmmError):
+        G.gbfmm_plan(prm, -1)
+    assert lib.gbfmm_evaluate(None, ctypes.byref(prm), 10, None, None, None, 0, None) == G.GBFMM_EINVAL
+    assert lib.gbfmm_destroy(None) == G.GBFMM_OK
+
+
+def test_workspace_grows_linearly(lib):
+    prm = G.gbfmm_default_params(p=10, leaf_size=64)
+    _, a = G.gbfmm_plan(prm, 1 << 20)
+    _, b = G.gbfmm_plan(prm, 1 << 23)
+    assert 6 < b / a < 10
