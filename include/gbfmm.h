@@ -186,6 +186,30 @@ int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
  * on this context enqueued (operator-table builds included; runtime memsets excluded). */
 int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);
 
+/*
+ * Allocation-free Morton sort (no counterpart in the paper: it exists for callers that may
+ * not allocate device memory -- code whose host framework owns every device byte, plug-ins
+ * handed only their input and output buffers, hooks that run where allocation is forbidden).
+ * It runs the tree front end of gbfmm_evaluate -- root box, depth-L Morton keys (L from
+ * prm->leaf_size as in gbfmm_plan; prm is validated like gbfmm_plan), the stable radix sort
+ * by (leaf key, original index) and the gather -- with no context and no cudaMalloc, cudaFree
+ * or allocating library call.
+ *   d_xyzq              device, 4*n floats, 16-byte aligned, read only
+ *   d_sorted_xyzq       device, 4*n floats, 16-byte aligned: particles in sorted order
+ *   d_perm              device, n uint32: original index of each sorted position
+ *   d_sorted_leaf_keys  device, n uint32: depth-L Morton key of each sorted position
+ * These equal what gbfmm_export_tree reports after gbfmm_evaluate with the same prm.
+ * Scratch: one static device array (about 8.4 MB) per GPU that loads the library, held
+ * until the process exits; n is limited to 1,048,576 (EUNSUPPORTED beyond).  The first call
+ * on a device looks the array's address up (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  Every call clears the scratch words that
+ * must start at zero; calls that overlap on the GPU share the array and race.  Non-finite
+ * coordinates are not reported (they are clamped into boundary cells).  Asynchronous on
+ * `stream`; EINVAL / EUNSUPPORTED / ECUDA.
+ */
+int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_sorted_xyzq, uint32_t *d_perm,
+                      uint32_t *d_sorted_leaf_keys, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,97 @@
+// gbfmm_sort_static: the Morton sort of the tree front end (root box, depth-L keys, stable
+// radix sort, gather) for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a host framework whose
+// allocator owns every device byte, plug-ins that are handed only the buffers they read and
+// write, or hooks that run while the application forbids allocation.  For them this entry
+// point takes its scratch (ping-pong key / index buffers, digit histograms, scan partials,
+// the root-box partials and completion counter) from one file-scope __device__ array of
+// kStaticSortBytes.  Every GPU that loads the library holds that array until the process
+// exits.  The caller still passes the input particles and the three outputs.
+//
+// The array's name is only a host-side stand-in in host code, so its device address is looked
+// up with cudaGetSymbolAddress once per device (with that device current) on the first call
+// there; that first call should therefore come before any stream capture.  All calls share
+// the one array and it keeps the last call's contents: the completion counter and the status
+// word are cleared at the start of every call, and calls that overlap on the GPU (two streams,
+// or two host threads) race on the array.
+#include "common.cuh"
+#include "gbfmm.h"
+
+#include <mutex>
+
+namespace gbfmm {
+
+constexpr int64_t kStaticSortMaxN = int64_t(1) << 20;
+constexpr int64_t kStaticSortBlocks = (kStaticSortMaxN + 4095) / 4096;
+
+// scratch layout (byte offsets, each 256-aligned)
+constexpr size_t kSsBox = 0;
+constexpr size_t kSsCounter = 256;
+constexpr size_t kSsStatus = 512;
+constexpr size_t kSsPartials = 768;                                   // 304 x 8 floats
+constexpr size_t kSsKeys = kSsPartials + 10240;                       // uint32[max n]
+constexpr size_t kSsIdx = kSsKeys + 4 * kStaticSortMaxN;              // uint32[max n]
+constexpr size_t kSsHist = kSsIdx + 4 * kStaticSortMaxN;              // uint32[256 x blocks + 1]
+constexpr size_t kSsScan = kSsHist + 4 * (256 * kStaticSortBlocks + 256);
+constexpr size_t kStaticSortBytes = kSsScan + 4 * 1024;
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticSortBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_addr[kMaxDevices] = {};
+}  // namespace
+
+}  // namespace gbfmm
+
+using namespace gbfmm;
+
+extern "C" int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_sorted_xyzq,
+                                 uint32_t *d_perm, uint32_t *d_sorted_leaf_keys, void *stream)
+{
+    if (!prm || n < 0) return GBFMM_EINVAL;
+    if (n > kStaticSortMaxN) return GBFMM_EUNSUPPORTED;
+    int32_t L = 0;
+    int rc = gbfmm_plan(prm, n, &L, nullptr);
+    if (rc != GBFMM_OK) return rc;
+    if (n == 0) return GBFMM_OK;
+    if (!d_xyzq || !d_sorted_xyzq || !d_perm || !d_sorted_leaf_keys) return GBFMM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 || reinterpret_cast<uintptr_t>(d_sorted_xyzq) % 16)
+        return GBFMM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GBFMM_ECUDA;
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return GBFMM_ECUDA;
+            g_addr[dev] = static_cast<unsigned char *>(p);
+        }
+        base = g_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Box *box = reinterpret_cast<Box *>(base + kSsBox);
+    unsigned *counter = reinterpret_cast<unsigned *>(base + kSsCounter);
+    int *status = reinterpret_cast<int *>(base + kSsStatus);
+    if (cudaMemsetAsync(base + kSsCounter, 0, 512, s) != cudaSuccess) return GBFMM_ECUDA;  // counter, status
+    const int passes = (3 * L + 7) / 8;
+    // the sort ends in its first buffer pair after an even number of passes: start there with
+    // the caller's outputs so the result lands in them
+    uint32_t *k_caller = d_sorted_leaf_keys, *v_caller = d_perm;
+    uint32_t *k_tmp = reinterpret_cast<uint32_t *>(base + kSsKeys), *v_tmp = reinterpret_cast<uint32_t *>(base + kSsIdx);
+    uint32_t *k0 = (passes % 2 == 0) ? k_caller : k_tmp, *v0 = (passes % 2 == 0) ? v_caller : v_tmp;
+    uint32_t *k1 = (passes % 2 == 0) ? k_tmp : k_caller, *v1 = (passes % 2 == 0) ? v_tmp : v_caller;
+    const float4 *x = reinterpret_cast<const float4 *>(d_xyzq);
+    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box,
+                reinterpret_cast<float *>(base + kSsPartials), counter, status, s);
+    launch_keys(x, n, box, L, k0, v0, s);
+    uint32_t *kout = nullptr, *vout = nullptr;
+    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, reinterpret_cast<uint32_t *>(base + kSsHist), (n + 4095) / 4096,
+                       reinterpret_cast<uint32_t *>(base + kSsScan), x, reinterpret_cast<float4 *>(d_sorted_xyzq),
+                       &kout, &vout, s);
+    if (kout != k_caller || vout != v_caller) return GBFMM_ECUDA;  // buffer parity bookkeeping failed
+    return cudaGetLastError() == cudaSuccess ? GBFMM_OK : GBFMM_ECUDA;
+}

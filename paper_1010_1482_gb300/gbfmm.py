@@ -82,6 +82,7 @@ def lib():
         "gbfmm_export_expansions": (i, [P, i, P]),
         "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
+        "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -222,6 +223,14 @@ def gbfmm_last_launch_count(ctx) -> int:
     c = ctypes.c_int64()
     _check(ctx, lib().gbfmm_last_launch_count(ctx, ctypes.byref(c)))
     return c.value
+
+
+def gbfmm_sort_static(prm: gbfmm_params, xyzq: torch.Tensor, sorted_xyzq: torch.Tensor, perm: torch.Tensor,
+                      sorted_leaf_keys: torch.Tensor, stream=None) -> None:
+    """Allocation-free Morton sort (library-owned static scratch; see include/gbfmm.h)."""
+    assert perm.dtype == torch.int32 and sorted_leaf_keys.dtype == torch.int32  # uint32 bit patterns
+    _check(None, lib().gbfmm_sort_static(ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _ptr(sorted_xyzq),
+                                         _ptr(perm), _ptr(sorted_leaf_keys), _stream(stream)))
 
 
 # ---- convenience wrapper (torch-allocated workspace) -----------------------------------------
