@@ -182,6 +182,13 @@ int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef);
  */
 int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
 
+/* Measured arithmetic throughput of the current device, for roofline denominators (no
+ * counterpart in the paper): kind 0 = FP32 FFMA on the CUDA cores, 1 = warp-level TF32 tensor
+ * MMA (m16n8k8), 2 = warp-level BF16 tensor MMA (m16n8k16), FP32 accumulation.  Runs a
+ * register-only kernel on 4 CTAs per SM (allocates and frees a small buffer, synchronises
+ * the device).  *tflops receives TFLOP/s.  EINVAL / ENOMEM / ECUDA. */
+int gbfmm_probe_peak(int kind, double *tflops);
+
 /* Number of library kernels the last gbfmm_evaluate / gbfmm_evaluate_host / gbfmm_direct
  * on this context enqueued (operator-table builds included; runtime memsets excluded). */
 int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);

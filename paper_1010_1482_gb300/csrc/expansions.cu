@@ -57,7 +57,8 @@ GB_HD constexpr int im_idx(int n, int m) { return n * n + 2 * m; }
 
 // ------------------------------------------------------------------------------------------
 // Operator tables (FP64 arithmetic, one CTA per operator).
-//   M2L  ops[code][col][row]  (column-major: the M2L kernel streams columns)  code < 343
+//   M2L  ops[code][col][row]  column-major, rows padded to PR = round_up(p^2, 8) with zeros
+//                             (the M2L kernel streams columns)  code < 343
 //   M2M  ops[c][row][col]     child position c (bit0 x, bit1 y, bit2 z), child -> parent
 //   L2L  ops[c][row][col]     parent -> child c
 // ------------------------------------------------------------------------------------------
@@ -178,6 +179,10 @@ __global__ void k_build_ops(int P, float *m2l, float *m2m, float *l2l)
     }
     if (threadIdx.x == 0 && used) harmonics64(kind == 0 ? 2 * P - 1 : P, v[0], v[1], v[2], kind == 0, H);
     __syncthreads();
+    const int PR = (PP + 7) / 8 * 8;
+    if (kind == 0)  // zero padding rows of the M2L table
+        for (int e = threadIdx.x; e < PP * (PR - PP); e += blockDim.x)
+            m2l[(size_t)op * PP * PR + (size_t)(e / (PR - PP)) * PR + PP + e % (PR - PP)] = 0.f;
     for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
         int row = e / PP, col = e % PP;
         float out = 0.f;
@@ -204,7 +209,7 @@ __global__ void k_build_ops(int P, float *m2l, float *m2m, float *l2l)
             out = (float)(rim ? val.im : val.re);
         }
         if (kind == 0)
-            m2l[(size_t)op * PP * PP + (size_t)col * PP + row] = out;
+            m2l[(size_t)op * PP * PR + (size_t)col * PR + row] = out;
         else if (kind == 1)
             m2m[(size_t)(op - kM2LCodes) * PP * PP + (size_t)row * PP + col] = out;
         else

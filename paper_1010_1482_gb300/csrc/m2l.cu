@@ -5,14 +5,19 @@
 // targets with the same child position tau (key & 7) have the same 189 admissible offsets
 // (children of the parent's neighbours that are not neighbours, Section "The M2L kernel
 // implementation"), so a CTA takes TN targets of one level and one tau and walks those 189
-// offsets in ascending code order; for each it stages T_o and the TN source expansions (one
-// per target, read through the target's CSR list row) in shared memory with TMA bulk copies
-// (double-buffered, mbarrier completion), and accumulates L~(:, targets) += T_o M~(:, sources)
-// with a register-blocked FP32 micro-kernel (RM rows x CN targets per thread).
-// Missing sources (domain boundary, empty cells) are copied from a block of zeros.
-// Every mbarrier wait is bounded; on timeout the kernel raises the status word and the CTA
-// stops after a second bounded wait for its copies in flight.
+// offsets in ascending code order, accumulating L~(:, targets) += T_o M~(:, sources).
+//
+// Warp specialisation: one producer warp keeps each target's CSR list pointer in registers,
+// resolves the source of every target for the next offset, and stages T_o and the TN source
+// expansions into a ring of NSTAGE shared-memory stages with TMA bulk copies (cp.async.bulk,
+// completion on the stage's "full" mbarrier; a block of zeros stands in for missing sources).
+// The consumer warps wait on "full", run a register-blocked FP32 micro-kernel (4 rows x CN
+// targets per thread) and release the stage on its "empty" mbarrier.  No block-wide barrier
+// runs inside the offset loop.  Every wait is bounded (1 s of %globaltimer); on timeout the
+// kernel raises the status word, waits (bounded) for its copies in flight and returns.
 #include "common.cuh"
+
+#include <stdlib.h>
 
 namespace gbfmm {
 
@@ -51,6 +56,11 @@ GB_DEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+GB_DEV void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 GB_DEV void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -78,25 +88,67 @@ GB_DEV uint64_t global_ns()
     return t;
 }
 
-// Bounded wait: true on completion, false after ~limit_ns.
-GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+// try_wait with a suspend-time hint: the waiting thread sleeps in hardware until the phase
+// completes or the hint (ns) expires, instead of spinning on issue slots
+GB_DEV bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with parity `parity` to complete: true on completion, false after
+// ~limit_ns or as soon as *abort is raised by another warp.
+GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns, volatile int *abort)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if ((abort && *abort) || global_ns() - t0 > limit_ns) return false;
+        __nanosleep(64);
     }
 }
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
-// stride (floats) of one staged source column: a multiple of 4 with (stride / 4) odd, so the
-// 16-byte column reads of eight consecutive targets fall in distinct bank groups
-template <int P>
-struct M2LShape {
-    static constexpr int PP = P * P;
-    static constexpr int SB = ((PP / 4) % 2 == 1) ? PP : PP + 4;
+// Register fragments of one k-group (4 consecutive k): CN staged source columns (4 k each)
+// and RM operator rows for each of the 4 k.
+template <int CN, int RM>
+struct Frag {
+    float4 b[CN];
+    float4 a[4][RM / 4];
+    GB_DEV void load(const float *A, const float *B, int k, int PR, int bstride)
+    {
+#pragma unroll
+        for (int j = 0; j < CN; ++j) b[j] = *reinterpret_cast<const float4 *>(B + j * bstride + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int qq = 0; qq < RM / 4; ++qq) a[kk][qq] = *reinterpret_cast<const float4 *>(A + (k + kk) * PR + 4 * qq);
+    }
+    // k outer, targets and rows inner: consecutive FMAs update different accumulators
+    // (RM x CN independent chains per k)
+    GB_DEV void fma(float (&acc)[RM][CN]) const
+    {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int j = 0; j < CN; ++j) {
+                const float bv = kk == 0 ? b[j].x : kk == 1 ? b[j].y : kk == 2 ? b[j].z : b[j].w;
+#pragma unroll
+                for (int qq = 0; qq < RM / 4; ++qq) {
+                    acc[4 * qq + 0][j] = fmaf(a[kk][qq].x, bv, acc[4 * qq + 0][j]);
+                    acc[4 * qq + 1][j] = fmaf(a[kk][qq].y, bv, acc[4 * qq + 1][j]);
+                    acc[4 * qq + 2][j] = fmaf(a[kk][qq].z, bv, acc[4 * qq + 2][j]);
+                    acc[4 * qq + 3][j] = fmaf(a[kk][qq].w, bv, acc[4 * qq + 3][j]);
+                }
+            }
+    }
 };
 
 struct M2LTiles {
@@ -104,29 +156,46 @@ struct M2LTiles {
     int ntiles_level[kMaxLevel + 1];  // tiles of each level (levels processed L, L-1, ..., 2)
 };
 
-template <int P, int TN, int RM, int CN>
-__global__ void __launch_bounds__((P * P / RM) * (TN / CN))
+// Operator tables are stored column-major with the row count padded to a multiple of 8
+// (zero rows), so row blocks of 4 or 8 per thread stay 16-byte aligned.
+GB_HD constexpr int m2l_rows_padded(int P) { return (P * P + 7) / 8 * 8; }
+
+template <int P, int TN, int RM, int CN, int NSTAGE, int MINB>
+struct M2LConfig {
+    static constexpr int PP = P * P;
+    static constexpr int PR = m2l_rows_padded(P);
+    // stride (floats) of one staged source column: a multiple of 4 with (stride / 4) odd, so
+    // the 16-byte column reads of eight consecutive targets fall in distinct bank groups
+    static constexpr int SB = ((PP / 4) % 2 == 1) ? PP : PP + 4;
+    static constexpr int NRG = PR / RM;             // row groups
+    static constexpr int NCG = TN / CN;             // column groups
+    static constexpr int NCT = NRG * NCG;           // consumer threads with work
+    static constexpr int NCW = (NCT + 31) / 32;     // consumer warps
+    static constexpr int NTHREADS = NCW * 32 + 32;  // + one producer warp
+    static constexpr int TPL = TN / 32;             // targets per producer lane
+    static constexpr uint32_t kOpBytes = PP * PR * 4;
+    static constexpr uint32_t kColBytes = PP * 4;
+    static constexpr size_t kStageFloats = (size_t)PP * PR + (size_t)TN * SB;
+    static constexpr size_t kSmemBytes = NSTAGE * kStageFloats * sizeof(float);
+    static_assert(PR % RM == 0 && RM % 4 == 0 && TN % CN == 0 && TN % 32 == 0, "tile shape");
+};
+
+template <int P, int TN, int RM, int CN, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREADS, MINB)
     k_m2l(M2LTiles tiles, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
           const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
           const uint16_t *__restrict__ m2l_code, const float *__restrict__ ops, const float *__restrict__ M,
           float *__restrict__ Lc, const float *__restrict__ zero_block, int *status)
 {
-    constexpr int PP = P * P;
-    constexpr int SB = M2LShape<P>::SB;
-    constexpr int NCG = TN / CN;
-    constexpr int NTH = (PP / RM) * NCG;
-    constexpr uint32_t kOpBytes = PP * PP * 4;
-    constexpr uint32_t kColBytes = PP * 4;
-    static_assert(PP % RM == 0 && TN % CN == 0 && RM == 4, "tile shape");
-    static_assert(NTH >= TN, "one resolving thread per target");
+    using Cfg = M2LConfig<P, TN, RM, CN, NSTAGE, MINB>;
+    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NCT = Cfg::NCT, NCW = Cfg::NCW;
+    constexpr int S = 189;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *sA = reinterpret_cast<float *>(smem_raw);  // [2][PP*PP]  operator, column-major
-    float *sB = sA + 2 * PP * PP;                     // [2][TN*SB]  source columns
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_src[2][TN];
-    __shared__ uint32_t s_ptr[TN], s_end[TN];
-    __shared__ int s_abort;
+    float *stage_base = reinterpret_cast<float *>(smem_raw);  // NSTAGE x [A: PP*PR | B: TN*SB]
+    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
+    __shared__ int s_issued[NSTAGE];
+    __shared__ volatile int s_abort;
 
     // ---- decode tile: levels in descending order ----
     int rem = blockIdx.x, l = tiles.L;
@@ -140,134 +209,144 @@ __global__ void __launch_bounds__((P * P / RM) * (TN / CN))
     const int tau = (int)(rem / qtiles);
     const int64_t q0 = (rem % qtiles) * TN;
     const int64_t off = level_offset(l);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (tid < TN) {
-        int64_t q = q0 + tid;
-        uint32_t a = 0, b = 0;
-        if (q < nq) {
-            int64_t g = off + 8 * q + tau;
-            if (end[g] > begin[g]) {
-                a = m2l_offs[g];
-                b = m2l_offs[g + 1];
-            }
-        }
-        s_ptr[tid] = a;
-        s_end[tid] = b;
-    }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int st = 0; st < NSTAGE; ++st) {
+            mbar_init(&full_bar[st], 1);
+            mbar_init(&empty_bar[st], NCW);
+            s_issued[st] = 0;
+        }
         s_abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    // resolve the source of every target for slot s (threads < TN), into s_src[buf]
-    auto resolve = [&](int s, int buf) {
-        if (tid < TN) {
-            const int code = c_codes[tau][s];
-            uint32_t pidx = s_ptr[tid];
-            int src = -1;
-            if (pidx < s_end[tid] && (int)m2l_code[pidx] == code) {
-                src = m2l_ids[pidx];
-                s_ptr[tid] = pidx + 1;
+    if (warp == NCW) {
+        // ================= producer warp =================
+        uint32_t ptr[Cfg::TPL], pend[Cfg::TPL];
+#pragma unroll
+        for (int k = 0; k < Cfg::TPL; ++k) {
+            const int64_t q = q0 + lane + 32 * k;
+            ptr[k] = pend[k] = 0;
+            if (q < nq) {
+                const int64_t g = off + 8 * q + tau;
+                if (end[g] > begin[g]) {
+                    ptr[k] = m2l_offs[g];
+                    pend[k] = m2l_offs[g + 1];
+                }
             }
-            s_src[buf][tid] = src;
         }
-    };
-    // issue the copies of slot s into buffer buf (after a barrier that published s_src[buf])
-    auto issue = [&](int s, int buf) {
-        if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(&bar[buf], kOpBytes + TN * kColBytes);
+        for (int s = 0; s < S; ++s) {
+            const int st = s % NSTAGE;
+            if (s >= NSTAGE) {
+                const uint32_t parity = ((s / NSTAGE) - 1) & 1;
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait_bounded(&empty_bar[st], parity, kWaitLimitNs, &s_abort) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) s_abort = 1;
+                    break;
+                }
+            }
             const int code = c_codes[tau][s];
-            tma_bulk_g2s(sA + buf * PP * PP, ops + (size_t)code * PP * PP, kOpBytes, &bar[buf]);
-        }
-        __syncthreads();  // expect_tx precedes the column copies
-        if (tid < TN) {
-            const int src = s_src[buf][tid];
-            const float *gsrc = src >= 0 ? M + (size_t)src * PP : zero_block;
+            const float *src_col[Cfg::TPL];
+#pragma unroll
+            for (int k = 0; k < Cfg::TPL; ++k) {
+                const float *src = zero_block;
+                if (ptr[k] < pend[k] && (int)m2l_code[ptr[k]] == code) {
+                    src = M + (size_t)m2l_ids[ptr[k]] * PP;
+                    ++ptr[k];
+                }
+                src_col[k] = src;
+            }
+            float *A = stage_base + st * Cfg::kStageFloats;
+            float *B = A + PP * PR;
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&full_bar[st], Cfg::kOpBytes + TN * Cfg::kColBytes);
+                tma_bulk_g2s(A, ops + (size_t)code * PP * PR, Cfg::kOpBytes, &full_bar[st]);
+                s_issued[st] += 1;
+            }
+            __syncwarp();
             fence_proxy_async();
-            tma_bulk_g2s(sB + buf * TN * SB + tid * SB, gsrc, kColBytes, &bar[buf]);
-        }
-    };
-
-    const int cg = tid % NCG, rg = tid / NCG;
-    float acc[RM][CN];
 #pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < CN; ++j) acc[i][j] = 0.f;
-
-    constexpr int S = 189;
-    uint32_t phase[2] = {0u, 0u};
-    resolve(0, 0);
-    __syncthreads();
-    issue(0, 0);
-    for (int s = 0; s < S; ++s) {
-        const int buf = s & 1;
-        if (s + 1 < S) {
-            resolve(s + 1, buf ^ 1);
-            __syncthreads();  // s_src published; everyone finished reading buffer buf^1 (slot s-1)
-            issue(s + 1, buf ^ 1);
+            for (int k = 0; k < Cfg::TPL; ++k)
+                tma_bulk_g2s(B + (lane + 32 * k) * SB, src_col[k], Cfg::kColBytes, &full_bar[st]);
         }
-        if (mbar_wait_bounded(&bar[buf], phase[buf], kWaitLimitNs))
-            phase[buf] ^= 1u;
-        else
-            s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
-        const float *A = sA + buf * PP * PP + rg * RM;
-        const float *B = sB + buf * TN * SB + cg * SB;
+    } else {
+        // ================= consumer warps =================
+        constexpr int CNN = TN / NCG;
+        const bool work = tid < NCT;
+        const int cg = tid % NCG, rg = tid / NCG;
+        float acc[RM][CNN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < CNN; ++j) acc[i][j] = 0.f;
+        for (int s = 0; s < S; ++s) {
+            const int st = s % NSTAGE;
+            const uint32_t parity = (s / NSTAGE) & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_bounded(&full_bar[st], parity, kWaitLimitNs, &s_abort) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) s_abort = 1;
+                break;
+            }
+            if (work) {
+                const float *A = stage_base + st * Cfg::kStageFloats + rg * RM;
+                const float *B = stage_base + st * Cfg::kStageFloats + PP * PR + cg * SB;
+                // two k-groups per iteration: the compiler overlaps the second group's
+                // fragment loads with the first group's FMAs
 #pragma unroll 2
-        for (int k = 0; k < PP; k += 4) {
-            float4 b[CN];
+                for (int k = 0; k < PP; k += 4) {
+                    Frag<CNN, RM> f;
+                    f.load(A, B, k, PR, NCG * SB);
+                    f.fma(acc);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[st]);
+        }
+        if (work && !s_abort) {
 #pragma unroll
-            for (int j = 0; j < CN; ++j) b[j] = *reinterpret_cast<const float4 *>(B + j * NCG * SB + k);
+            for (int j = 0; j < CNN; ++j) {
+                const int t = cg + j * NCG;
+                const int64_t q = q0 + t;
+                if (q >= nq) continue;
+                const int64_t g = off + 8 * q + tau;
+                if (end[g] <= begin[g]) continue;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float4 a = *reinterpret_cast<const float4 *>(A + (k + kk) * PP);
-#pragma unroll
-                for (int j = 0; j < CN; ++j) {
-                    const float bv = kk == 0 ? b[j].x : kk == 1 ? b[j].y : kk == 2 ? b[j].z : b[j].w;
-                    acc[0][j] = fmaf(a.x, bv, acc[0][j]);
-                    acc[1][j] = fmaf(a.y, bv, acc[1][j]);
-                    acc[2][j] = fmaf(a.z, bv, acc[2][j]);
-                    acc[3][j] = fmaf(a.w, bv, acc[3][j]);
+                for (int qq = 0; qq < RM / 4; ++qq) {
+                    const int r = rg * RM + 4 * qq;
+                    if (r < PP)
+                        *reinterpret_cast<float4 *>(Lc + g * PP + r) = make_float4(
+                            acc[4 * qq][j], acc[4 * qq + 1][j], acc[4 * qq + 2][j], acc[4 * qq + 3][j]);
                 }
             }
         }
     }
+    __syncthreads();
     if (s_abort) {
-        if (tid == 0) atomicOr(status, kStatusTimeout);
-        // let copies in flight land before the CTA's shared memory is released (bounded)
-        mbar_wait_bounded(&bar[0], phase[0], kWaitLimitNs);
-        mbar_wait_bounded(&bar[1], phase[1], kWaitLimitNs);
-        return;
+        // let every issued copy land before the CTA's shared memory is released (bounded)
+        if (tid == 0) {
+            atomicOr(status, kStatusTimeout);
+            for (int st = 0; st < NSTAGE; ++st)
+                if (s_issued[st] > 0) mbar_wait_bounded(&full_bar[st], (s_issued[st] - 1) & 1, kWaitLimitNs, nullptr);
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int j = 0; j < CN; ++j) {
-        const int t = cg + j * NCG;
-        const int64_t q = q0 + t;
-        if (q >= nq) continue;
-        const int64_t g = off + 8 * q + tau;
-        if (end[g] <= begin[g]) continue;
-        float4 v = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-        *reinterpret_cast<float4 *>(Lc + g * PP + rg * RM) = v;
-    }
-    (void)NTH;
 }
 
-template <int P, int TN, int RM, int CN>
+template <int P, int TN, int RM, int CN, int NSTAGE, int MINB>
 static void launch_m2l_t(int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                          const int32_t *m2l_ids, const uint16_t *m2l_code, const float *ops, const float *M,
                          float *Lc, const float *zero_block, int *status, cudaStream_t s)
 {
-    constexpr int PP = P * P;
-    constexpr int NTH = (PP / RM) * (TN / CN);
-    const size_t smem = (size_t)(2 * PP * PP + 2 * TN * M2LShape<P>::SB) * sizeof(float);
-    cudaFuncSetAttribute(k_m2l<P, TN, RM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    using Cfg = M2LConfig<P, TN, RM, CN, NSTAGE, MINB>;
+    cudaFuncSetAttribute(k_m2l<P, TN, RM, CN, NSTAGE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Cfg::kSmemBytes);
     M2LTiles tiles{};
     tiles.L = L;
     int total = 0;
@@ -277,8 +356,8 @@ static void launch_m2l_t(int L, const int32_t *begin, const int32_t *end, const 
         total += tiles.ntiles_level[l];
     }
     if (total == 0) return;
-    k_m2l<P, TN, RM, CN><<<total, NTH, smem, s>>>(tiles, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc,
-                                                  zero_block, status);
+    k_m2l<P, TN, RM, CN, NSTAGE, MINB><<<total, Cfg::NTHREADS, Cfg::kSmemBytes, s>>>(
+        tiles, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status);
     note_launches(1);
 }
 
@@ -287,12 +366,37 @@ void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const ui
                 const float *zero_block, int *status, cudaStream_t s)
 {
     if (L < 2) return;
-    switch (P) {
-    case 4: launch_m2l_t<4, 32, 4, 4>(L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
-    case 6: launch_m2l_t<6, 64, 4, 8>(L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
-    case 8: launch_m2l_t<8, 64, 4, 8>(L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
-    case 10: launch_m2l_t<10, 64, 4, 8>(L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
+    // tile shape (GBFMM_M2L_TILE): 0 = 64 targets x (4 rows x 8 targets per thread), 3 stages;
+    // 1 = 64 targets x (8 x 8), 3 stages; 2 = 32 targets x (4 x 8), 2 stages, 2 CTAs per SM
+    static const int variant = [] {
+        const char *e = getenv("GBFMM_M2L_TILE");
+        const int v = e ? atoi(e) : 0;
+        return (v >= 0 && v <= 2) ? v : 0;
+    }();
+#define GBFMM_M2L_ARGS L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s
+    if (variant == 1) {
+        switch (P) {
+        case 4: launch_m2l_t<4, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 6: launch_m2l_t<6, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 8: launch_m2l_t<8, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 10: launch_m2l_t<10, 64, 8, 8, 3, 1>(GBFMM_M2L_ARGS); break;
+        }
+    } else if (variant == 2) {
+        switch (P) {
+        case 4: launch_m2l_t<4, 32, 4, 8, 4, 2>(GBFMM_M2L_ARGS); break;
+        case 6: launch_m2l_t<6, 32, 4, 8, 4, 2>(GBFMM_M2L_ARGS); break;
+        case 8: launch_m2l_t<8, 32, 4, 8, 3, 2>(GBFMM_M2L_ARGS); break;
+        case 10: launch_m2l_t<10, 32, 4, 8, 2, 2>(GBFMM_M2L_ARGS); break;
+        }
+    } else {
+        switch (P) {
+        case 4: launch_m2l_t<4, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 6: launch_m2l_t<6, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 8: launch_m2l_t<8, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+        case 10: launch_m2l_t<10, 64, 4, 8, 3, 1>(GBFMM_M2L_ARGS); break;
+        }
     }
+#undef GBFMM_M2L_ARGS
 }
 
 }  // namespace gbfmm

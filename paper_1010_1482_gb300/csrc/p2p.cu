@@ -6,18 +6,20 @@
 // and pairs with d2 == 0 (the particle itself, exact duplicates) contribute nothing.
 //
 // Decomposition: one CTA per target leaf.  The leaf's <= 27 neighbour cells are gathered into
-// shared memory (float4 x, y, z, q, in chunks); when the leaf holds fewer targets than the CTA
-// has threads, the threads form G = NT / T groups that split the sources round-robin, so all
+// shared memory (float4 x, y, z, q, in chunks).  Each thread holds TPT targets in registers,
+// so one staged source feeds TPT pair interactions; when the leaf has fewer target slots than
+// the CTA has threads, the threads form G groups that split the sources round-robin, so the
 // lanes stay busy for leaves of any occupancy (the paper instead pads targets to the block
-// size).  Each thread sums its share in FP32; the group partials, and then the far-field value,
-// are combined per target with compensated (Kahan) summation and written to the caller's
-// original particle order.
+// size).  Each thread sums its share in FP32; the group partials, and then the far-field
+// value, are combined per target with compensated (Kahan) summation and written to the
+// caller's original particle order.
 #include "common.cuh"
 
 namespace gbfmm {
 
 constexpr int kP2PThreads = 128;
-constexpr int kSrcCap = 2048;
+constexpr int kP2PTargetsPerThread = 2;
+constexpr int kSrcCap = 1024;
 
 template <bool SOFT>
 GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi, float &gx, float &gy, float &gz)
@@ -45,7 +47,7 @@ struct Kahan {
     }
 };
 
-template <bool SOFT>
+template <bool SOFT, int TPT>
 __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__restrict__ sx,
                                                      const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                                      const uint32_t *__restrict__ p2p_offs,
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__rest
                                                      float4 *__restrict__ out)
 {
     __shared__ float4 src[kSrcCap];
-    __shared__ float4 red[kP2PThreads];
+    __shared__ float4 red[TPT][kP2PThreads];
     __shared__ int s_cb[27], s_pref[28];
     const int64_t leaf = blockIdx.x;
     const int64_t g = level_offset(L) + leaf;
@@ -76,14 +78,24 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__rest
     __syncthreads();
     const int S = s_pref[nrow];
     const int T = e0 - b0;
-    for (int tc = 0; tc < T; tc += kP2PThreads) {
-        const int Tc = min(T - tc, kP2PThreads);
-        const int G = kP2PThreads / Tc;
-        const int tt = tid % Tc, grp = tid / Tc;
+    for (int tc = 0; tc < T; tc += TPT * kP2PThreads) {
+        const int Tc = min(T - tc, TPT * kP2PThreads);
+        const int slots = (Tc + TPT - 1) / TPT;
+        const int G = kP2PThreads / slots;
+        const int slot = tid % slots, grp = tid / slots;
         const bool active = grp < G;
-        const int i = b0 + tc + tt;
-        const float4 xi = __ldg(&sx[i]);
-        float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float tx[TPT], ty[TPT], tz[TPT];
+        float phi[TPT], gx[TPT], gy[TPT], gz[TPT];
+#pragma unroll
+        for (int h = 0; h < TPT; ++h) {
+            // a missing target repeats the slot's first one; its result is discarded
+            const int t = TPT * slot + h < Tc ? TPT * slot + h : TPT * slot;
+            const float4 p = __ldg(&sx[b0 + tc + t]);
+            tx[h] = p.x;
+            ty[h] = p.y;
+            tz[h] = p.z;
+            phi[h] = gx[h] = gy[h] = gz[h] = 0.f;
+        }
         for (int sc = 0; sc < S; sc += kSrcCap) {
             const int chunk = min(kSrcCap, S - sc);
             __syncthreads();
@@ -95,30 +107,41 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__rest
             }
             __syncthreads();
             if (active) {
-#pragma unroll 8
-                for (int j = grp; j < chunk; j += G) pair<SOFT>(xi.x, xi.y, xi.z, src[j], eps2, phi, gx, gy, gz);
+#pragma unroll 4
+                for (int j = grp; j < chunk; j += G) {
+                    const float4 s = src[j];
+#pragma unroll
+                    for (int h = 0; h < TPT; ++h) pair<SOFT>(tx[h], ty[h], tz[h], s, eps2, phi[h], gx[h], gy[h], gz[h]);
+                }
             }
         }
         __syncthreads();
-        red[tid] = make_float4(phi, gx, gy, gz);
+#pragma unroll
+        for (int h = 0; h < TPT; ++h) red[h][tid] = make_float4(phi[h], gx[h], gy[h], gz[h]);
         __syncthreads();
         if (grp == 0) {
-            Kahan a{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f}, bz{0.f, 0.f};
-            for (int k = 0; k < G; ++k) {
-                const float4 v = red[k * Tc + tt];
-                a.add(v.x);
-                bx.add(v.y);
-                by.add(v.z);
-                bz.add(v.w);
+#pragma unroll
+            for (int h = 0; h < TPT; ++h) {
+                const int t = TPT * slot + h;
+                if (t >= Tc) break;
+                const int i = b0 + tc + t;
+                Kahan a{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f}, bz{0.f, 0.f};
+                for (int k = 0; k < G; ++k) {
+                    const float4 v = red[h][k * slots + slot];
+                    a.add(v.x);
+                    bx.add(v.y);
+                    by.add(v.z);
+                    bz.add(v.w);
+                }
+                if (far) {
+                    const float4 f = far[i];
+                    a.add(f.x);
+                    bx.add(f.y);
+                    by.add(f.z);
+                    bz.add(f.w);
+                }
+                out[perm[i]] = make_float4(a.s, bx.s, by.s, bz.s);
             }
-            if (far) {
-                const float4 f = far[i];
-                a.add(f.x);
-                bx.add(f.y);
-                by.add(f.z);
-                bz.add(f.w);
-            }
-            out[perm[i]] = make_float4(a.s, bx.s, by.s, bz.s);
         }
     }
 }
@@ -129,10 +152,11 @@ void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const 
 {
     if (n <= 0) return;
     unsigned grid = (unsigned)(int64_t(1) << (3 * L));
+    constexpr int TPT = kP2PTargetsPerThread;
     if (eps2 > 0.f)
-        k_p2p<true><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
+        k_p2p<true, TPT><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
     else
-        k_p2p<false><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
+        k_p2p<false, TPT><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
     note_launches(1);
 }
 

@@ -83,6 +83,7 @@ def lib():
         "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
         "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
+        "gbfmm_probe_peak": (i, [i, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -223,6 +224,13 @@ def gbfmm_last_launch_count(ctx) -> int:
     c = ctypes.c_int64()
     _check(ctx, lib().gbfmm_last_launch_count(ctx, ctypes.byref(c)))
     return c.value
+
+
+def gbfmm_probe_peak(kind: int) -> float:
+    """Measured TFLOP/s of the current device: 0 FP32 FFMA, 1 TF32 warp MMA, 2 BF16 warp MMA."""
+    t = ctypes.c_double()
+    _check(None, lib().gbfmm_probe_peak(int(kind), ctypes.byref(t)))
+    return t.value
 
 
 def gbfmm_sort_static(prm: gbfmm_params, xyzq: torch.Tensor, sorted_xyzq: torch.Tensor, perm: torch.Tensor,
