@@ -499,17 +499,18 @@ static void deinterleave3(uint64_t key, int bits, int64_t *ix, int64_t *iy, int6
     *iz = c;
 }
 
-/* 63-bit Morton keys at depth 21: k_d = clamp(floor((x_d - origin_d) / S * 2^21), 0, 2^21 - 1),
- * evaluated in IEEE FP64 in that order (built with -ffp-contract=off); bit 3b+0 of
- * the key is bit b of k_x, 3b+1 of k_y, 3b+2 of k_z. */
+/* 63-bit Morton keys at depth 21: with the scale s = 2^21 / S (one IEEE FP64 division),
+ * k_d = clamp(floor((x_d - origin_d) * s), 0, 2^21 - 1), each operation one IEEE FP64
+ * rounding (built with -ffp-contract=off); bit 3b+0 of the key is bit b of k_x, 3b+1 of
+ * k_y, 3b+2 of k_z. */
 void orc_keys(int64_t n, const float *xyzq, const double *origin3, double side, uint64_t *keys)
 {
+    const double scale = 2097152.0 / side;
     for (int64_t i = 0; i < n; ++i) {
         uint64_t k[3];
         for (int d = 0; d < 3; ++d) {
             double t = (double)xyzq[4 * i + d] - origin3[d];
-            double u = t / side;
-            double v = u * 2097152.0;
+            double v = t * scale;
             double f = floor(v);
             if (!(f >= 0.0)) f = 0.0; /* also maps NaN to 0 */
             if (f > 2097151.0) f = 2097151.0;

@@ -201,13 +201,14 @@ int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     OpsCache &c = ctx->ops[order_slot(P)];
     *built_now = false;
     if (c.built) return GBFMM_OK;
-    const size_t PP2 = (size_t)P * P * P * P;
     const size_t PR = ((size_t)P * P + 7) / 8 * 8;
     cudaError_t e;
     if ((e = cudaMalloc(&c.m2l, kM2LCodes * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(m2l ops)");
-    if ((e = cudaMalloc(&c.m2m, 8 * PP2 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(m2m ops)");
-    if ((e = cudaMalloc(&c.l2l, 8 * PP2 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
+    if ((e = cudaMalloc(&c.m2m, 8 * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(m2m ops)");
+    if ((e = cudaMalloc(&c.l2l, 8 * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
     launch_build_operators(P, c.m2l, c.m2m, c.l2l, s);
     c.P = P;
     c.built = true;

@@ -56,6 +56,51 @@ GB_HD void demorton3(uint32_t k, int &x, int &y, int &z)
     z = (int)compact3(k >> 2);
 }
 
+// Translation-operator tables (M2L, M2M, L2L) are stored column-major, [op][col][row], with
+// the row count padded to a multiple of 8 (zero rows), so row blocks of 4 or 8 per thread
+// stay 16-byte aligned.
+GB_HD constexpr int ops_rows_padded(int P) { return (P * P + 7) / 8 * 8; }
+
+// stride (floats) of a staged expansion column in shared memory: a multiple of 4 with
+// (stride / 4) odd, so the 16-byte column reads of eight consecutive columns fall in distinct
+// bank groups
+GB_HD constexpr int staged_col_stride(int P) { return ((P * P / 4) % 2 == 1) ? P * P : P * P + 4; }
+
+// Register fragments of one k-group (4 consecutive k): CN staged source columns (4 k each)
+// and RM operator rows for each of the 4 k.
+template <int CN, int RM>
+struct Frag {
+    float4 b[CN];
+    float4 a[4][RM / 4];
+    GB_DEV void load(const float *A, const float *B, int k, int PR, int bstride)
+    {
+#pragma unroll
+        for (int j = 0; j < CN; ++j) b[j] = *reinterpret_cast<const float4 *>(B + j * bstride + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int qq = 0; qq < RM / 4; ++qq) a[kk][qq] = *reinterpret_cast<const float4 *>(A + (k + kk) * PR + 4 * qq);
+    }
+    // k outer, targets and rows inner: consecutive FMAs update different accumulators
+    // (RM x CN independent chains per k)
+    __device__ __forceinline__ void fma(float (&acc)[RM][CN]) const
+    {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int j = 0; j < CN; ++j) {
+                const float bv = kk == 0 ? b[j].x : kk == 1 ? b[j].y : kk == 2 ? b[j].z : b[j].w;
+#pragma unroll
+                for (int qq = 0; qq < RM / 4; ++qq) {
+                    acc[4 * qq + 0][j] = fmaf(a[kk][qq].x, bv, acc[4 * qq + 0][j]);
+                    acc[4 * qq + 1][j] = fmaf(a[kk][qq].y, bv, acc[4 * qq + 1][j]);
+                    acc[4 * qq + 2][j] = fmaf(a[kk][qq].z, bv, acc[4 * qq + 2][j]);
+                    acc[4 * qq + 3][j] = fmaf(a[kk][qq].w, bv, acc[4 * qq + 3][j]);
+                }
+            }
+    }
+};
+
 // Device status bits (OR-ed into the context's status word).
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
@@ -64,6 +109,7 @@ constexpr int kStatusTimeout = 2;
 struct Box {
     double origin[3];
     double side;
+    double key_scale;  // 2^21 / side, one IEEE FP64 division
 };
 
 // Layout of one evaluation's workspace (byte offsets from the workspace base).

@@ -57,10 +57,10 @@ GB_HD constexpr int im_idx(int n, int m) { return n * n + 2 * m; }
 
 // ------------------------------------------------------------------------------------------
 // Operator tables (FP64 arithmetic, one CTA per operator).
-//   M2L  ops[code][col][row]  column-major, rows padded to PR = round_up(p^2, 8) with zeros
-//                             (the M2L kernel streams columns)  code < 343
-//   M2M  ops[c][row][col]     child position c (bit0 x, bit1 y, bit2 z), child -> parent
-//   L2L  ops[c][row][col]     parent -> child c
+// All three column-major, [op][col][row], rows padded to PR = round_up(p^2, 8) with zeros:
+//   M2L  code < 343 (offset source - target, in cells)
+//   M2M  child position c (bit0 x, bit1 y, bit2 z), child -> parent
+//   L2L  parent -> child c
 // ------------------------------------------------------------------------------------------
 struct C64 {
     double re, im;
@@ -180,9 +180,11 @@ __global__ void k_build_ops(int P, float *m2l, float *m2m, float *l2l)
     if (threadIdx.x == 0 && used) harmonics64(kind == 0 ? 2 * P - 1 : P, v[0], v[1], v[2], kind == 0, H);
     __syncthreads();
     const int PR = (PP + 7) / 8 * 8;
-    if (kind == 0)  // zero padding rows of the M2L table
-        for (int e = threadIdx.x; e < PP * (PR - PP); e += blockDim.x)
-            m2l[(size_t)op * PP * PR + (size_t)(e / (PR - PP)) * PR + PP + e % (PR - PP)] = 0.f;
+    float *table = kind == 0 ? m2l + (size_t)op * PP * PR
+                 : kind == 1 ? m2m + (size_t)(op - kM2LCodes) * PP * PR
+                             : l2l + (size_t)(op - kM2LCodes - 8) * PP * PR;
+    for (int e = threadIdx.x; e < PP * (PR - PP); e += blockDim.x)  // zero padding rows
+        table[(size_t)(e / (PR - PP)) * PR + PP + e % (PR - PP)] = 0.f;
     for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
         int row = e / PP, col = e % PP;
         float out = 0.f;
@@ -208,12 +210,7 @@ __global__ void k_build_ops(int P, float *m2l, float *m2m, float *l2l)
             val.im += w.im;
             out = (float)(rim ? val.im : val.re);
         }
-        if (kind == 0)
-            m2l[(size_t)op * PP * PR + (size_t)col * PR + row] = out;
-        else if (kind == 1)
-            m2m[(size_t)(op - kM2LCodes) * PP * PP + (size_t)row * PP + col] = out;
-        else
-            l2l[(size_t)(op - kM2LCodes - 8) * PP * PP + (size_t)row * PP + col] = out;
+        table[(size_t)col * PR + row] = out;
     }
 }
 
@@ -317,127 +314,144 @@ void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *b
 }
 
 // ------------------------------------------------------------------------------------------
-// M2M: parent (level l) <- its 8 children (level l+1).  One CTA per 8 consecutive parents,
-// one thread per output coefficient; child expansions staged in shared memory per child
-// position.  The operator is block lower-triangular in degree (output degree j reads input
-// degrees <= j).
+// M2M and L2L as batched FP32 contractions over 32 cells per CTA, the same register-blocked
+// micro-kernel as M2L (4 operator rows x 8 cells per thread) on shared-memory-staged operands.
+//   M2M (UP):  M~(parent q) = sum over child positions c of T^M2M_c M~(child 8q + c)
+//   L2L (!UP): L~(child 8q + c) += T^L2L_c L~(parent q), one child position per CTA column
+// M2M is block lower-triangular in degree (output degree j reads input degrees <= j) and L2L
+// block upper-triangular (reads degrees >= j): each thread's k range is cut to its rows'
+// degrees (rounded to whole k-groups of 4).
 // ------------------------------------------------------------------------------------------
-constexpr int kTransGroup = 8;
+constexpr int kTrTN = 32, kTrCN = 8;
 
-template <int P>
-__global__ void __launch_bounds__(128) k_m2m(int l, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                                             const float *__restrict__ ops, float *__restrict__ M)
+template <int P, bool UP>
+struct TransCfg {
+    static constexpr int PP = P * P, PR = ops_rows_padded(P), SB = staged_col_stride(P);
+    static constexpr int NCG = kTrTN / kTrCN, NRG = PR / 4, NT = ((NRG * NCG + 31) / 32) * 32;
+    static constexpr size_t kSmem = ((size_t)PP * PR + (size_t)kTrTN * SB) * sizeof(float);
+};
+
+GB_DEV int degree_of(int r)
 {
-    constexpr int PP = P * P;
-    __shared__ float sm[kTransGroup][PP];
-    const int64_t np = int64_t(1) << (3 * l);
-    const int64_t q0 = blockIdx.x * (int64_t)kTransGroup;
-    const int64_t offp = level_offset(l), offc = level_offset(l + 1);
-    const int r = threadIdx.x;
-    int deg = 0;
-    while ((deg + 1) * (deg + 1) <= r) ++deg;
-    const int ncol = (deg + 1) * (deg + 1);
-    float acc[kTransGroup];
-#pragma unroll
-    for (int i = 0; i < kTransGroup; ++i) acc[i] = 0.f;
-    for (int c = 0; c < 8; ++c) {
-        for (int e = threadIdx.x; e < kTransGroup * PP; e += blockDim.x) {
-            int i = e / PP, k = e % PP;
-            int64_t q = q0 + i;
-            float v = 0.f;
-            if (q < np) {
-                int64_t gc = offc + 8 * q + c;
-                if (end[gc] > begin[gc]) v = M[gc * PP + k];
-            }
-            sm[i][k] = v;
+    int d = 0;
+    while ((d + 1) * (d + 1) <= r) ++d;
+    return d;
+}
+
+template <int P, bool UP>
+__global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate(int l, const int32_t *__restrict__ begin,
+                                                                   const int32_t *__restrict__ end,
+                                                                   const float *__restrict__ ops, float *__restrict__ X)
+{
+    using Cfg = TransCfg<P, UP>;
+    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
+    extern __shared__ __align__(16) float tsm[];
+    float *A = tsm;            // [PP cols][PR rows]
+    float *B = tsm + PP * PR;  // [kTrTN][SB]
+    // parents: level l (M2M) or l - 1 (L2L)
+    const int lp = UP ? l : l - 1;
+    const int64_t np = int64_t(1) << (3 * lp);
+    const int64_t q0 = blockIdx.x * (int64_t)kTrTN;
+    const int64_t offp = level_offset(lp), offc = level_offset(lp + 1);
+    const int tid = threadIdx.x;
+    const bool work = tid < NRG * NCG;
+    const int cg = tid % NCG, rg = tid / NCG;
+    int kbeg = 0, kend = PP;
+    if (work) {
+        const int r0 = min(rg * 4, PP - 1), r1 = min(rg * 4 + 3, PP - 1);
+        if (UP) {
+            const int d = degree_of(r1);
+            kend = min(PP, ((d + 1) * (d + 1) + 3) / 4 * 4);
+        } else {
+            const int d = degree_of(r0);
+            kbeg = (d * d) / 4 * 4;
         }
-        __syncthreads();
-        if (r < PP) {
-            const float *T = ops + (size_t)c * PP * PP + (size_t)r * PP;
-            for (int k = 0; k < ncol; ++k) {
-                float t = __ldg(&T[k]);
-#pragma unroll
-                for (int i = 0; i < kTransGroup; ++i) acc[i] = fmaf(t, sm[i][k], acc[i]);
-            }
-        }
-        __syncthreads();
     }
-    if (r < PP)
+    float acc[4][kTrCN];
 #pragma unroll
-        for (int i = 0; i < kTransGroup; ++i) {
-            int64_t q = q0 + i;
-            if (q < np && end[offp + q] > begin[offp + q]) M[(offp + q) * PP + r] = acc[i];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < kTrCN; ++j) acc[i][j] = 0.f;
+    const int c_first = UP ? 0 : blockIdx.y, c_last = UP ? 7 : blockIdx.y;
+    for (int c = c_first; c <= c_last; ++c) {
+        if (c != c_first) __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(ops + (size_t)c * PP * PR);
+        for (int e = tid; e < PP * PR / 4; e += blockDim.x) reinterpret_cast<float4 *>(A)[e] = __ldg(&src[e]);
+        for (int e = tid; e < kTrTN * (PP / 4); e += blockDim.x) {
+            const int i = e / (PP / 4), k4 = e % (PP / 4);
+            const int64_t q = q0 + i;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < np) {
+                const int64_t g = UP ? offc + 8 * q + c : offp + q;
+                if (end[g] > begin[g]) v = reinterpret_cast<const float4 *>(X + g * PP)[k4];
+            }
+            *reinterpret_cast<float4 *>(B + i * SB + 4 * k4) = v;
         }
+        __syncthreads();
+        if (work) {
+            const float *Ar = A + rg * 4;
+            const float *Bc = B + cg * SB;
+#pragma unroll 2
+            for (int k = kbeg; k < kend; k += 4) {
+                Frag<kTrCN, 4> f;
+                f.load(Ar, Bc, k, PR, NCG * SB);
+                f.fma(acc);
+            }
+        }
+    }
+    if (!work) return;
+#pragma unroll
+    for (int j = 0; j < kTrCN; ++j) {
+        const int64_t q = q0 + cg + j * NCG;
+        if (q >= np) continue;
+        const int r = rg * 4;
+        if (r >= PP) continue;
+        const int64_t g = UP ? offp + q : offc + 8 * q + blockIdx.y;
+        if (end[g] <= begin[g]) continue;
+        float4 *dst = reinterpret_cast<float4 *>(X + g * PP + r);
+        if (UP) {
+            *dst = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        } else {
+            float4 v = *dst;
+            v.x += acc[0][j];
+            v.y += acc[1][j];
+            v.z += acc[2][j];
+            v.w += acc[3][j];
+            *dst = v;
+        }
+    }
+}
+
+template <int P, bool UP>
+static void launch_translate_t(int l, const int32_t *begin, const int32_t *end, const float *ops, float *X,
+                               cudaStream_t s)
+{
+    using Cfg = TransCfg<P, UP>;
+    cudaFuncSetAttribute(k_translate<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    const int64_t np = int64_t(1) << (3 * (UP ? l : l - 1));
+    dim3 grid((unsigned)((np + kTrTN - 1) / kTrTN), UP ? 1 : 8);
+    k_translate<P, UP><<<grid, Cfg::NT, Cfg::kSmem, s>>>(l, begin, end, ops, X);
+    note_launches(1);
 }
 
 void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s)
 {
-    int64_t np = int64_t(1) << (3 * l);
-    unsigned grid = (unsigned)((np + kTransGroup - 1) / kTransGroup);
     switch (P) {
-    case 4: k_m2m<4><<<grid, 32, 0, s>>>(l, begin, end, ops, M); break;
-    case 6: k_m2m<6><<<grid, 64, 0, s>>>(l, begin, end, ops, M); break;
-    case 8: k_m2m<8><<<grid, 64, 0, s>>>(l, begin, end, ops, M); break;
-    case 10: k_m2m<10><<<grid, 128, 0, s>>>(l, begin, end, ops, M); break;
-    }
-    note_launches(1);
-}
-
-// ------------------------------------------------------------------------------------------
-// L2L: children (level l) += L2L(parent, level l-1).  One CTA per (child position, 8
-// parents); output degree j reads input degrees >= j.
-// ------------------------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(128) k_l2l(int l, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                                             const float *__restrict__ ops, float *__restrict__ Lc)
-{
-    constexpr int PP = P * P;
-    __shared__ float sm[kTransGroup][PP];
-    const int c = blockIdx.y;
-    const int64_t np = int64_t(1) << (3 * (l - 1));
-    const int64_t q0 = blockIdx.x * (int64_t)kTransGroup;
-    const int64_t offp = level_offset(l - 1), offc = level_offset(l);
-    const int r = threadIdx.x;
-    for (int e = threadIdx.x; e < kTransGroup * PP; e += blockDim.x) {
-        int i = e / PP, k = e % PP;
-        int64_t q = q0 + i;
-        float v = 0.f;
-        if (q < np && end[offp + q] > begin[offp + q]) v = Lc[(offp + q) * PP + k];
-        sm[i][k] = v;
-    }
-    __syncthreads();
-    if (r >= PP) return;
-    int deg = 0;
-    while ((deg + 1) * (deg + 1) <= r) ++deg;
-    float acc[kTransGroup];
-#pragma unroll
-    for (int i = 0; i < kTransGroup; ++i) acc[i] = 0.f;
-    const float *T = ops + (size_t)c * PP * PP + (size_t)r * PP;
-    for (int k = deg * deg; k < PP; ++k) {
-        float t = __ldg(&T[k]);
-#pragma unroll
-        for (int i = 0; i < kTransGroup; ++i) acc[i] = fmaf(t, sm[i][k], acc[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < kTransGroup; ++i) {
-        int64_t q = q0 + i;
-        if (q >= np) continue;
-        int64_t gc = offc + 8 * q + c;
-        if (end[gc] > begin[gc]) Lc[gc * PP + r] += acc[i];
+    case 4: launch_translate_t<4, true>(l, begin, end, ops, M, s); break;
+    case 6: launch_translate_t<6, true>(l, begin, end, ops, M, s); break;
+    case 8: launch_translate_t<8, true>(l, begin, end, ops, M, s); break;
+    case 10: launch_translate_t<10, true>(l, begin, end, ops, M, s); break;
     }
 }
 
 void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *Lc, cudaStream_t s)
 {
-    int64_t np = int64_t(1) << (3 * (l - 1));
-    dim3 grid((unsigned)((np + kTransGroup - 1) / kTransGroup), 8);
     switch (P) {
-    case 4: k_l2l<4><<<grid, 32, 0, s>>>(l, begin, end, ops, Lc); break;
-    case 6: k_l2l<6><<<grid, 64, 0, s>>>(l, begin, end, ops, Lc); break;
-    case 8: k_l2l<8><<<grid, 64, 0, s>>>(l, begin, end, ops, Lc); break;
-    case 10: k_l2l<10><<<grid, 128, 0, s>>>(l, begin, end, ops, Lc); break;
+    case 4: launch_translate_t<4, false>(l, begin, end, ops, Lc, s); break;
+    case 6: launch_translate_t<6, false>(l, begin, end, ops, Lc, s); break;
+    case 8: launch_translate_t<8, false>(l, begin, end, ops, Lc, s); break;
+    case 10: launch_translate_t<10, false>(l, begin, end, ops, Lc, s); break;
     }
-    note_launches(1);
 }
 
 // ------------------------------------------------------------------------------------------

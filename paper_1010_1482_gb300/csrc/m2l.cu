@@ -116,57 +116,17 @@ GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
-// Register fragments of one k-group (4 consecutive k): CN staged source columns (4 k each)
-// and RM operator rows for each of the 4 k.
-template <int CN, int RM>
-struct Frag {
-    float4 b[CN];
-    float4 a[4][RM / 4];
-    GB_DEV void load(const float *A, const float *B, int k, int PR, int bstride)
-    {
-#pragma unroll
-        for (int j = 0; j < CN; ++j) b[j] = *reinterpret_cast<const float4 *>(B + j * bstride + k);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-            for (int qq = 0; qq < RM / 4; ++qq) a[kk][qq] = *reinterpret_cast<const float4 *>(A + (k + kk) * PR + 4 * qq);
-    }
-    // k outer, targets and rows inner: consecutive FMAs update different accumulators
-    // (RM x CN independent chains per k)
-    GB_DEV void fma(float (&acc)[RM][CN]) const
-    {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-            for (int j = 0; j < CN; ++j) {
-                const float bv = kk == 0 ? b[j].x : kk == 1 ? b[j].y : kk == 2 ? b[j].z : b[j].w;
-#pragma unroll
-                for (int qq = 0; qq < RM / 4; ++qq) {
-                    acc[4 * qq + 0][j] = fmaf(a[kk][qq].x, bv, acc[4 * qq + 0][j]);
-                    acc[4 * qq + 1][j] = fmaf(a[kk][qq].y, bv, acc[4 * qq + 1][j]);
-                    acc[4 * qq + 2][j] = fmaf(a[kk][qq].z, bv, acc[4 * qq + 2][j]);
-                    acc[4 * qq + 3][j] = fmaf(a[kk][qq].w, bv, acc[4 * qq + 3][j]);
-                }
-            }
-    }
-};
 
 struct M2LTiles {
     int L;
     int ntiles_level[kMaxLevel + 1];  // tiles of each level (levels processed L, L-1, ..., 2)
 };
 
-// Operator tables are stored column-major with the row count padded to a multiple of 8
-// (zero rows), so row blocks of 4 or 8 per thread stay 16-byte aligned.
-GB_HD constexpr int m2l_rows_padded(int P) { return (P * P + 7) / 8 * 8; }
-
 template <int P, int TN, int RM, int CN, int NSTAGE, int MINB>
 struct M2LConfig {
     static constexpr int PP = P * P;
-    static constexpr int PR = m2l_rows_padded(P);
-    // stride (floats) of one staged source column: a multiple of 4 with (stride / 4) odd, so
-    // the 16-byte column reads of eight consecutive targets fall in distinct bank groups
-    static constexpr int SB = ((PP / 4) % 2 == 1) ? PP : PP + 4;
+    static constexpr int PR = ops_rows_padded(P);
+    static constexpr int SB = staged_col_stride(P);
     static constexpr int NRG = PR / RM;             // row groups
     static constexpr int NCG = TN / CN;             // column groups
     static constexpr int NCT = NRG * NCG;           // consumer threads with work

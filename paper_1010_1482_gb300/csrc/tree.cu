@@ -5,8 +5,8 @@
 // the host (Section "Improvements of Performance", Fig. 5); here every one is an integer or
 // bandwidth-bound device kernel.  This translation unit is compiled with -fmad=false and the
 // key quantisation uses explicit IEEE round-to-nearest FP64 intrinsics, so the keys are the
-// exact result of floor((x - origin) / side * 2^21) and match any IEEE FP64 evaluation of the
-// same expression bit for bit.
+// exact result of floor((x - origin) * (2^21 / side)) and match any IEEE FP64 evaluation of
+// the same steps bit for bit.
 #include "common.cuh"
 
 #include <math.h>
@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox(const float4 *__restrict__
             }
             b.side = S;
         }
+        b.key_scale = __ddiv_rn(2097152.0, b.side);
         *box_out = b;
         *counter = 0u;  // ready for the next launch on this stream
     }
@@ -148,8 +149,9 @@ void launch_bbox(const float4 *x, int64_t n, int has_box, const double *box_orig
 }
 
 // ------------------------------------------------------------------------------------------
-// Morton keys at the leaf depth L: k_d = clamp(floor((x_d - origin_d) / side * 2^21), 0, 2^21-1)
-// in IEEE FP64, then the 3L-bit key of the depth-L cell = interleave(k_d >> (21 - L)).
+// Morton keys at the leaf depth L: k_d = clamp(floor((x_d - origin_d) * s), 0, 2^21-1) with
+// s = 2^21 / side (one IEEE FP64 division, in the box kernel), every step one IEEE FP64
+// rounding; then the 3L-bit key of the depth-L cell = interleave(k_d >> (21 - L)).
 // ------------------------------------------------------------------------------------------
 __global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__restrict__ box, int L,
                        uint32_t *__restrict__ leafkey, uint32_t *__restrict__ idx)
@@ -163,8 +165,7 @@ __global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__res
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double t = __dsub_rn((double)c[d], b.origin[d]);
-        double u = __ddiv_rn(t, b.side);
-        double v = __dmul_rn(u, 2097152.0);
+        double v = __dmul_rn(t, b.key_scale);
         double f = floor(v);
         if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
         if (f > 2097151.0) f = 2097151.0;
