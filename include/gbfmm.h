@@ -189,6 +189,13 @@ int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
  * the device).  *tflops receives TFLOP/s.  EINVAL / ENOMEM / ECUDA. */
 int gbfmm_probe_peak(int kind, double *tflops);
 
+/* Test of the bounded device waits (no counterpart in the paper): enqueues one CTA that waits
+ * on an mbarrier no thread arrives on, with the same bounded-wait routine the M2L pipeline
+ * uses, limited to limit_ms (0 < limit_ms <= 2000).  When it gives up it raises the context's
+ * status word, so the next gbfmm_sync_status returns ETIMEOUT; the context stays usable.
+ * Asynchronous on `stream`.  EINVAL / ECUDA. */
+int gbfmm_selftest_wait(gbfmm_ctx *ctx, double limit_ms, void *stream);
+
 /* Number of library kernels the last gbfmm_evaluate / gbfmm_evaluate_host / gbfmm_direct
  * on this context enqueued (operator-table builds included; runtime memsets excluded). */
 int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);

@@ -322,3 +322,140 @@ def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
     ref = np.asarray(ref, dtype=np.float64)
     den = float(np.sum(ref * ref))
     return float(np.sqrt(np.sum((a - ref) ** 2) / den)) if den > 0 else float(np.sqrt(np.sum((a - ref) ** 2)))
+
+
+# ----------------------------------------------------------------------------
+# Adaptive tree (cells split while they hold more than leaf_size particles)
+# ----------------------------------------------------------------------------
+
+ADAPTIVE_MAX_LEVEL = 21
+LIST_U, LIST_V, LIST_W, LIST_X = 0, 1, 2, 3
+
+
+def _adaptive_sigs():
+    L = lib()
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    d = ctypes.c_double
+    if getattr(L, "_adaptive_ready", False):
+        return L
+    for name, res, args in (
+        ("orc_adaptive_tree", i64, [i64, P, ci, ci, i64, P, P, P, P, P, P, P, P]),
+        ("orc_adaptive_colleagues", None, [i64, P, P, P, P, P, P]),
+        ("orc_adaptive_list", i64, [ci, i64, P, P, P, P, P, P, P, P, i64]),
+        ("orc_adaptive_passes", ci, [ci, d, P, d, i64, P, P, P, P, P, P, P, P, ci, P, P, P, P, P, P, P, P, P, P,
+                                     P, P, P]),
+        ("orc_p2l_ri", None, [ci, P, i64, P, P]),
+    ):
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    L._adaptive_ready = True
+    return L
+
+
+def p2l(p: int, centre, xyzq) -> np.ndarray:
+    """Eq. 3's L_n^m of a set of charges about `centre` (P2L)."""
+    L = _adaptive_sigs()
+    xyzq = _c(xyzq, np.float64).reshape(-1, 4)
+    ri = np.zeros(2 * ntri(p))
+    L.orc_p2l_ri(p, _p(_c(centre, np.float64)), len(xyzq), _p(xyzq), _p(ri))
+    return _ric(ri)
+
+
+def build_adaptive_tree(xyzq, leaf_size: int, max_level: int = ADAPTIVE_MAX_LEVEL) -> dict:
+    """Adaptive octree over the root cube: particles sorted by (63-bit key, index); a cell
+    splits while it holds more than leaf_size particles and is above max_level."""
+    L = _adaptive_sigs()
+    xyzq = _c(xyzq, np.float32).reshape(-1, 4)
+    n = len(xyzq)
+    origin, side, bad = root_box(xyzq)
+    keys = morton_keys(xyzq, origin, side)
+    perm = np.lexsort((np.arange(n), keys)).astype(np.int64)
+    sk = np.ascontiguousarray(keys[perm])
+    cap = 4 * n + 64
+    while True:
+        a = {k: np.zeros(cap, dtype=np.int32) for k in ("level", "begin", "count", "parent", "child_begin", "nchild")}
+        key = np.zeros(cap, dtype=np.uint64)
+        ls = np.zeros(max_level + 2, dtype=np.int32)
+        nc = L.orc_adaptive_tree(n, _p(sk), leaf_size, max_level, cap, _p(a["level"]), _p(key), _p(a["begin"]),
+                                 _p(a["count"]), _p(a["parent"]), _p(a["child_begin"]), _p(a["nchild"]), _p(ls))
+        if nc >= 0:
+            break
+        cap *= 2
+    t = {k: v[:nc].copy() for k, v in a.items()}
+    t.update(n=n, ncells=int(nc), key=key[:nc].copy(), level_start=ls, origin=origin, side=side, bad=bad,
+             keys=keys, perm=perm, sorted_keys=sk, max_level=max_level)
+    coll = np.zeros(27 * max(nc, 1), dtype=np.int32)
+    L.orc_adaptive_colleagues(nc, _p(t["level"]), _p(t["key"]), _p(t["parent"]), _p(t["child_begin"]),
+                              _p(t["nchild"]), _p(coll))
+    t["colleagues"] = coll.reshape(-1, 27)[:nc]
+    return t
+
+
+def build_adaptive_lists(tree: dict) -> dict:
+    L = _adaptive_sigs()
+    nc = tree["ncells"]
+    coll = np.ascontiguousarray(tree["colleagues"].reshape(-1))
+    out = {}
+    for kind, name in ((LIST_U, "u"), (LIST_V, "v"), (LIST_W, "w"), (LIST_X, "x")):
+        cap = 64 * nc + 64
+        while True:
+            offs = np.zeros(nc + 1, dtype=np.int32)
+            ids = np.zeros(cap, dtype=np.int32)
+            e = L.orc_adaptive_list(kind, nc, _p(tree["level"]), _p(tree["key"]), _p(tree["parent"]),
+                                    _p(tree["child_begin"]), _p(tree["nchild"]), _p(coll), _p(offs), _p(ids), cap)
+            if e >= 0:
+                break
+            cap *= 4
+        out[name + "_offs"] = offs
+        out[name + "_ids"] = ids[:e].copy()
+    return out
+
+
+def fmm_adaptive(xyzq, p: int, leaf_size: int, eps2: float = 0.0, targets=None, keep: bool = False,
+                 max_level: int = ADAPTIVE_MAX_LEVEL) -> dict:
+    """FP64 adaptive FMM: U (P2P), V (M2L), W (M2P), X (P2L) lists.  Returns 'out' (n, 4) in
+    original order; with `targets`, only the leaves holding them are evaluated."""
+    L = _adaptive_sigs()
+    xyzq32 = _c(xyzq, np.float32).reshape(-1, 4)
+    n = len(xyzq32)
+    t = build_adaptive_tree(xyzq32, leaf_size, max_level)
+    ls = build_adaptive_lists(t)
+    nc = t["ncells"]
+    nt = ntri(p)
+    sx = _c(xyzq32[t["perm"]].astype(np.float64), np.float64)
+    M = np.zeros(2 * nc * nt)
+    Lc = np.zeros(2 * nc * nt)
+    out_s = np.zeros((n, 4))
+    need = None
+    if targets is not None:
+        need = np.zeros(nc, dtype=np.uint8)
+        leaf_of = leaf_of_sorted(t)
+        inv = np.empty(n, dtype=np.int64)
+        inv[t["perm"]] = np.arange(n)
+        need[leaf_of[inv[np.asarray(targets)]]] = 1
+    rc = L.orc_adaptive_passes(
+        p, float(eps2), _p(t["origin"]), float(t["side"]), nc, _p(t["level"]), _p(t["key"]), _p(t["begin"]),
+        _p(t["count"]), _p(t["parent"]), _p(t["child_begin"]), _p(t["nchild"]), _p(t["level_start"]),
+        max_level, _p(sx), _p(ls["u_offs"]), _p(ls["u_ids"]), _p(ls["v_offs"]), _p(ls["v_ids"]),
+        _p(ls["w_offs"]), _p(ls["w_ids"]), _p(ls["x_offs"]), _p(ls["x_ids"]),
+        _p(need) if need is not None else None, _p(M), _p(Lc), _p(out_s))
+    if rc != 0:
+        raise MemoryError("oracle adaptive passes failed")
+    out = np.zeros((n, 4))
+    out[t["perm"]] = out_s
+    res = dict(out=out, tree=t)
+    if keep:
+        res.update(lists=ls, M=(M[0::2] + 1j * M[1::2]).reshape(nc, nt), Lc=(Lc[0::2] + 1j * Lc[1::2]).reshape(nc, nt))
+    return res
+
+
+def leaf_of_sorted(tree: dict) -> np.ndarray:
+    """Leaf cell index of every sorted particle position."""
+    leaf_of = np.zeros(tree["n"], dtype=np.int64)
+    leaves = np.nonzero(tree["nchild"] == 0)[0]
+    for c in leaves:
+        leaf_of[tree["begin"][c]: tree["begin"][c] + tree["count"][c]] = c
+    return leaf_of

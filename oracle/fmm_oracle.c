@@ -36,8 +36,10 @@
  * Coefficient storage: complex, m >= 0 only (M_n^{-m} = conj(M_n^m)), index
  * n(n+1)/2 + m.
  *
- * Tree: uniform octree of depth L over the root cube, dense per level: the cell
- * of level l with Morton key k has global index (8^l - 1)/7 + k.
+ * Trees: (1) uniform octree of depth L over the root cube, dense per level: the cell
+ * of level l with Morton key k has global index (8^l - 1)/7 + k; (2) adaptive octree
+ * (cells split while they hold more than leaf_size particles) with the U, V, W, X lists
+ * of Cheng, Greengard & Rokhlin (1999), numbered level by level in key order.
  */
 #include <complex.h>
 #include <math.h>
@@ -775,6 +777,331 @@ int orc_fmm_passes(int p, int L, int method, double eps2, const double *origin3,
                     p2p_one(sxyzq + 4 * (int64_t)i, count[s], sxyzq + 4 * (int64_t)begin[s], eps2,
                             out + 4 * (int64_t)i);
                 }
+        }
+    }
+    free(needc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive octree (Cheng, Greengard & Rokhlin 1999, the adaptive FMM the paper */
+/* cites): a cell splits iff it holds more than leaf_size particles and is above */
+/* max_level; only nonempty children exist.  Cells are numbered level by level, */
+/* in ascending key order within a level, so the children of a cell are         */
+/* consecutive.                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. 3 (the L_n^m factor), P2L: L_n^m += sum_j q_j rho_j^{-n-1} Y_n^{-m}(alpha_j, beta_j),
+ * (rho, alpha, beta) = x_j - centre. */
+void orc_p2l(int p, const double *centre, int64_t np, const double *xyzq, double complex *L)
+{
+    init_fact();
+    double complex Y[TRI(MAXDEG, 0) + MAXDEG];
+    for (int64_t j = 0; j < np; ++j) {
+        double v[3] = {xyzq[4 * j] - centre[0], xyzq[4 * j + 1] - centre[1], xyzq[4 * j + 2] - centre[2]};
+        double rho, al, be;
+        cart2sph(v, &rho, &al, &be);
+        orc_ynm(p, al, be, Y);
+        double q = xyzq[4 * j + 3];
+        for (int n = 0; n < p; ++n)
+            for (int m = 0; m <= n; ++m) L[TRI(n, m)] += q * pow(rho, -n - 1) * yfull(Y, n, -m);
+    }
+}
+
+void orc_p2l_ri(int p, const double *centre, int64_t np, const double *xyzq, double *Lri)
+{
+    double complex L[NT(MAXDEG)];
+    ri2c(NT(p), Lri, L);
+    orc_p2l(p, centre, np, xyzq, L);
+    c2ri(NT(p), L, Lri);
+}
+
+/* Build the adaptive tree from the 63-bit keys of the particles sorted ascending.
+ * Outputs (capacity cap cells): level, key prefix, begin, count, parent, child_begin,
+ * nchild, and level_start[0..max_level+1].  Returns the number of cells, or -1 when cap
+ * is too small. */
+int64_t orc_adaptive_tree(int64_t n, const uint64_t *sk, int leaf_size, int max_level, int64_t cap, int32_t *level,
+                          uint64_t *key, int32_t *begin, int32_t *count, int32_t *parent, int32_t *child_begin,
+                          int32_t *nchild, int32_t *level_start)
+{
+    if (cap < 1) return -1;
+    int64_t nc = 1;
+    level[0] = 0;
+    key[0] = 0;
+    begin[0] = 0;
+    count[0] = (int32_t)n;
+    parent[0] = -1;
+    level_start[0] = 0;
+    int64_t lo = 0, hi = 1; /* cells of the current level */
+    for (int l = 0; l <= max_level; ++l) {
+        level_start[l + 1] = (int32_t)hi;
+        for (int64_t c = lo; c < hi; ++c) {
+            child_begin[c] = (int32_t)nc;
+            nchild[c] = 0;
+            if (count[c] <= leaf_size || l == max_level) continue;
+            const int sh = 3 * (21 - (l + 1));
+            for (int32_t i = begin[c]; i < begin[c] + count[c]; ++i) {
+                uint64_t ck = sk[i] >> sh;
+                if (i == begin[c] || (sk[i - 1] >> sh) != ck) {
+                    if (nc >= cap) return -1;
+                    level[nc] = l + 1;
+                    key[nc] = ck;
+                    begin[nc] = i;
+                    count[nc] = 0;
+                    parent[nc] = (int32_t)c;
+                    nc++;
+                    nchild[c]++;
+                }
+                count[nc - 1]++;
+            }
+        }
+        lo = hi;
+        hi = nc;
+        if (lo == hi) {
+            for (int k = l + 2; k <= max_level + 1; ++k) level_start[k] = (int32_t)hi;
+            break;
+        }
+    }
+    return nc;
+}
+
+/* integer box of a cell at depth 21: lo[d] inclusive, size */
+static void cell_box(int l, uint64_t key, int64_t *lo, int64_t *size)
+{
+    int64_t ix[3];
+    deinterleave3(key, l, &ix[0], &ix[1], &ix[2]);
+    *size = (int64_t)1 << (21 - l);
+    for (int d = 0; d < 3; ++d) lo[d] = ix[d] * (*size);
+}
+
+/* two boxes touch or overlap */
+static int boxes_adjacent(int la, uint64_t ka, int lb, uint64_t kb)
+{
+    int64_t a[3], b[3], sa, sb;
+    cell_box(la, ka, a, &sa);
+    cell_box(lb, kb, b, &sb);
+    for (int d = 0; d < 3; ++d)
+        if (a[d] > b[d] + sb || b[d] > a[d] + sa) return 0;
+    return 1;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Lists of the adaptive tree (Cheng, Greengard & Rokhlin 1999):
+ *   colleagues(B): cells of B's level adjacent to B, B included (coll[27 * c], -1 padded);
+ *   U(B), B leaf: leaves adjacent to B, B included, any level;
+ *   V(B): children of the colleagues of B's parent that are not adjacent to B;
+ *   W(B), B leaf: descendants of B's colleagues whose parent is adjacent to B but which are
+ *         not adjacent to B (the descent stops there);
+ *   X(B): cells C with B in W(C) -- leaves C that are colleagues of a strict ancestor of B,
+ *         adjacent to B's parent and not adjacent to B.
+ * Rows ascending by cell index.  kind: 0 U, 1 V, 2 W, 3 X; offs[ncells + 1]; returns entries,
+ * or -1 when cap is too small. */
+int64_t orc_adaptive_list(int kind, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *parent,
+                          const int32_t *child_begin, const int32_t *nchild, const int32_t *coll, int32_t *offs,
+                          int32_t *ids, int64_t cap)
+{
+    int64_t e = 0;
+    const size_t scratch = (size_t)1 << 20; /* entries per row / descent stack */
+    int32_t *row = (int32_t *)malloc(sizeof(int32_t) * scratch);
+    int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * scratch);
+    if (!row || !stack) {
+        free(row);
+        free(stack);
+        return -1;
+    }
+    for (int64_t b = 0; b < ncells; ++b) {
+        offs[b] = (int32_t)e;
+        int nr = 0;
+        const int leaf = nchild[b] == 0;
+        if (kind == 1 && parent[b] >= 0) {
+            const int32_t *pc = coll + 27 * (int64_t)parent[b];
+            for (int i = 0; i < 27 && pc[i] >= 0; ++i)
+                for (int32_t c = child_begin[pc[i]]; c < child_begin[pc[i]] + nchild[pc[i]]; ++c)
+                    if (!boxes_adjacent(level[b], key[b], level[c], key[c])) row[nr++] = c;
+        } else if ((kind == 0 || kind == 2) && leaf) {
+            const int32_t *bc = coll + 27 * b;
+            for (int i = 0; i < 27 && bc[i] >= 0; ++i) {
+                const int32_t a = bc[i];
+                if (nchild[a] == 0) {
+                    if (kind == 0) row[nr++] = a; /* same-level leaf colleagues, B included */
+                    continue;
+                }
+                /* descend from a non-leaf colleague */
+                int sp = 0;
+                for (int32_t c = child_begin[a]; c < child_begin[a] + nchild[a]; ++c) stack[sp++] = c;
+                while (sp > 0) {
+                    const int32_t d = stack[--sp];
+                    if (boxes_adjacent(level[b], key[b], level[d], key[d])) {
+                        if (nchild[d] == 0) {
+                            if (kind == 0) row[nr++] = d;
+                        } else {
+                            for (int32_t c = child_begin[d]; c < child_begin[d] + nchild[d]; ++c) stack[sp++] = c;
+                        }
+                    } else if (kind == 2) {
+                        row[nr++] = d;
+                    }
+                }
+            }
+            if (kind == 0) /* coarser leaves: leaf colleagues of strict ancestors adjacent to B */
+                for (int32_t anc = parent[b]; anc >= 0; anc = parent[anc]) {
+                    const int32_t *ac = coll + 27 * (int64_t)anc;
+                    for (int i = 0; i < 27 && ac[i] >= 0; ++i)
+                        if (ac[i] != anc && nchild[ac[i]] == 0 &&
+                            boxes_adjacent(level[b], key[b], level[ac[i]], key[ac[i]]))
+                            row[nr++] = ac[i];
+                }
+        } else if (kind == 3 && parent[b] >= 0) {
+            const int32_t pb = parent[b];
+            for (int32_t anc = pb; anc >= 0; anc = parent[anc]) {
+                const int32_t *ac = coll + 27 * (int64_t)anc;
+                for (int i = 0; i < 27 && ac[i] >= 0; ++i) {
+                    const int32_t c = ac[i];
+                    if (c == anc || nchild[c] != 0) continue;
+                    if (boxes_adjacent(level[pb], key[pb], level[c], key[c]) &&
+                        !boxes_adjacent(level[b], key[b], level[c], key[c]))
+                        row[nr++] = c;
+                }
+            }
+        }
+        qsort(row, (size_t)nr, sizeof(int32_t), cmp_i32);
+        if (e + nr > cap) {
+            free(row);
+            free(stack);
+            return -1;
+        }
+        for (int i = 0; i < nr; ++i) ids[e++] = row[i];
+    }
+    offs[ncells] = (int32_t)e;
+    free(row);
+    free(stack);
+    return e;
+}
+
+/* Colleagues of every cell (same level, adjacent, itself included): children of the
+ * colleagues of the parent that are adjacent.  coll[27 * c] ascending, -1 padded. */
+void orc_adaptive_colleagues(int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *parent,
+                             const int32_t *child_begin, const int32_t *nchild, int32_t *coll)
+{
+    for (int64_t c = 0; c < ncells; ++c)
+        for (int i = 0; i < 27; ++i) coll[27 * c + i] = -1;
+    if (ncells > 0) coll[0] = 0;
+    /* cells are in level order, so parents are done before their children */
+    for (int64_t b = 1; b < ncells; ++b) {
+        const int32_t *pc = coll + 27 * (int64_t)parent[b];
+        int nr = 0;
+        int32_t row[27 * 8];
+        for (int i = 0; i < 27 && pc[i] >= 0; ++i)
+            for (int32_t c = child_begin[pc[i]]; c < child_begin[pc[i]] + nchild[pc[i]]; ++c) {
+                int64_t a[3], d[3];
+                deinterleave3(key[b], level[b], &a[0], &a[1], &a[2]);
+                deinterleave3(key[c], level[c], &d[0], &d[1], &d[2]);
+                if (llabs(a[0] - d[0]) <= 1 && llabs(a[1] - d[1]) <= 1 && llabs(a[2] - d[2]) <= 1) row[nr++] = c;
+            }
+        qsort(row, (size_t)nr, sizeof(int32_t), cmp_i32);
+        for (int i = 0; i < nr; ++i) coll[27 * b + i] = row[i];
+    }
+}
+
+/*
+ * Adaptive FMM passes (FP64): P2M at the leaves, M2M up the tree, M2L over V, P2L over X,
+ * L2L down the tree, L2P at the leaves, M2P over W and P2P over U.  Particles sorted by key
+ * (sxyzq); M, Lc zero on entry (ncells * p(p+1)/2 complex, interleaved); out accumulates
+ * (phi, grad) in sorted order.  need: optional mask over cells; when given, only leaves with
+ * need set are evaluated (and only the local expansions they use are formed).
+ */
+int orc_adaptive_passes(int p, double eps2, const double *origin3, double side, int64_t ncells, const int32_t *level,
+                        const uint64_t *key, const int32_t *begin, const int32_t *count, const int32_t *parent,
+                        const int32_t *child_begin, const int32_t *nchild, const int32_t *level_start, int max_level,
+                        const double *sxyzq, const int32_t *u_offs, const int32_t *u_ids, const int32_t *v_offs,
+                        const int32_t *v_ids, const int32_t *w_offs, const int32_t *w_ids, const int32_t *x_offs,
+                        const int32_t *x_ids, const uint8_t *need, double *Mri, double *Lri, double *out)
+{
+    init_fact();
+    const int nt = NT(p);
+    double complex *M = (double complex *)Mri;
+    double complex *Lc = (double complex *)Lri;
+    uint8_t *needc = (uint8_t *)calloc((size_t)ncells, 1);
+    if (!needc) return -1;
+    for (int64_t c = 0; c < ncells; ++c)
+        if (nchild[c] == 0 && (!need || need[c]))
+            for (int32_t a = (int32_t)c; a >= 0; a = parent[a]) needc[a] = 1;
+
+    /* P2M at every leaf at level >= 2 */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < ncells; ++c) {
+        if (nchild[c] != 0 || level[c] < 2) continue;
+        double ctr[3];
+        orc_cell_centre(origin3, side, level[c], key[c], ctr);
+        orc_p2m(p, ctr, count[c], sxyzq + 4 * (int64_t)begin[c], M + c * nt);
+    }
+    /* M2M bottom-up, parents at levels max_level-1 .. 2 */
+    for (int l = max_level - 1; l >= 2; --l) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = level_start[l]; c < level_start[l + 1]; ++c) {
+            if (nchild[c] == 0) continue;
+            double pc[3];
+            orc_cell_centre(origin3, side, l, key[c], pc);
+            for (int32_t ch = child_begin[c]; ch < child_begin[c] + nchild[c]; ++ch) {
+                double cc[3];
+                orc_cell_centre(origin3, side, l + 1, key[ch], cc);
+                orc_m2m(p, cc, pc, M + ch * nt, M + c * nt);
+            }
+        }
+    }
+    /* M2L over V and P2L over X, into every needed cell */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < ncells; ++b) {
+        if (!needc[b] || level[b] < 2) continue;
+        double tc[3];
+        orc_cell_centre(origin3, side, level[b], key[b], tc);
+        for (int32_t e = v_offs[b]; e < v_offs[b + 1]; ++e) {
+            const int32_t s = v_ids[e];
+            double sc[3];
+            orc_cell_centre(origin3, side, level[s], key[s], sc);
+            orc_m2l(p, sc, tc, M + (int64_t)s * nt, Lc + b * nt);
+        }
+        for (int32_t e = x_offs[b]; e < x_offs[b + 1]; ++e) {
+            const int32_t s = x_ids[e];
+            orc_p2l(p, tc, count[s], sxyzq + 4 * (int64_t)begin[s], Lc + b * nt);
+        }
+    }
+    /* L2L top-down, children at levels 3 .. max_level */
+    for (int l = 3; l <= max_level; ++l) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = level_start[l]; c < level_start[l + 1]; ++c) {
+            if (!needc[c]) continue;
+            const int32_t pa = parent[c];
+            double cc[3], pc[3];
+            orc_cell_centre(origin3, side, l, key[c], cc);
+            orc_cell_centre(origin3, side, l - 1, key[pa], pc);
+            orc_l2l(p, pc, cc, Lc + (int64_t)pa * nt, Lc + c * nt);
+        }
+    }
+    /* L2P, M2P over W and P2P over U at the needed leaves */
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t b = 0; b < ncells; ++b) {
+        if (nchild[b] != 0 || !needc[b]) continue;
+        double ctr[3];
+        orc_cell_centre(origin3, side, level[b], key[b], ctr);
+        for (int32_t i = begin[b]; i < begin[b] + count[b]; ++i) {
+            const double *xi = sxyzq + 4 * (int64_t)i;
+            double *oi = out + 4 * (int64_t)i;
+            if (level[b] >= 2) orc_l2p(p, ctr, Lc + b * nt, xi, oi);
+            for (int32_t e = w_offs[b]; e < w_offs[b + 1]; ++e) {
+                const int32_t s = w_ids[e];
+                double sc[3];
+                orc_cell_centre(origin3, side, level[s], key[s], sc);
+                orc_m2p(p, sc, M + (int64_t)s * nt, xi, oi);
+            }
+            for (int32_t e = u_offs[b]; e < u_offs[b + 1]; ++e) {
+                const int32_t s = u_ids[e];
+                p2p_one(xi, count[s], sxyzq + 4 * (int64_t)begin[s], eps2, oi);
+            }
         }
     }
     free(needc);

@@ -580,6 +580,15 @@ int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef)
     return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "export copy");
 }
 
+int gbfmm_selftest_wait(gbfmm_ctx *ctx, double limit_ms, void *stream)
+{
+    if (!ctx || !(limit_ms > 0.0) || limit_ms > 2000.0) return GBFMM_EINVAL;
+    cudaSetDevice(ctx->device);
+    launch_wait_selftest((uint64_t)(limit_ms * 1e6), ctx->d_status, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "self-test launch");
+}
+
 int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return GBFMM_EINVAL;

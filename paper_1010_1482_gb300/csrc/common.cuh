@@ -169,6 +169,8 @@ void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const ui
                 const int32_t *m2l_ids, const uint16_t *m2l_code, const float *ops, const float *M, float *Lc,
                 const float *zero_block, int *status, cudaStream_t s);
 
+void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s);
+
 // p2p.cu
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *p2p_offs, const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2,

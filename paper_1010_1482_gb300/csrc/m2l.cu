@@ -117,6 +117,25 @@ GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
 
+// Exercises the bounded wait on its own: one thread waits on an mbarrier that no thread
+// arrives on, gives up after limit_ns and raises the status word, as a pipeline stage whose
+// copies never land would.
+__global__ void k_wait_selftest(uint64_t limit_ns, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(&bar, 0u, limit_ns, nullptr)) atomicOr(status, kStatusTimeout);
+    }
+}
+
+void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, status);
+    note_launches(1);
+}
+
 struct M2LTiles {
     int L;
     int ntiles_level[kMaxLevel + 1];  // tiles of each level (levels processed L, L-1, ..., 2)

@@ -84,6 +84,7 @@ def lib():
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
         "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
         "gbfmm_probe_peak": (i, [i, ctypes.POINTER(ctypes.c_double)]),
+        "gbfmm_selftest_wait": (i, [P, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -224,6 +225,10 @@ def gbfmm_last_launch_count(ctx) -> int:
     c = ctypes.c_int64()
     _check(ctx, lib().gbfmm_last_launch_count(ctx, ctypes.byref(c)))
     return c.value
+
+
+def gbfmm_selftest_wait(ctx, limit_ms: float, stream=None) -> None:
+    _check(ctx, lib().gbfmm_selftest_wait(ctx, float(limit_ms), _stream(stream)))
 
 
 def gbfmm_probe_peak(kind: int) -> float:

@@ -242,3 +242,16 @@ def test_large_uniform_p10_sampled(G, ctx):
     sub = tg[:512]
     f = O.fmm(x, w["p"], w["leaf_size"], targets=sub)["out"]
     assert O.rel_l2(out[sub], f[sub]) <= TOL_FMM
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(G, ctx):
+    # a wait on an mbarrier that nothing arrives on gives up after 50 ms and raises ETIMEOUT
+    G.gbfmm_selftest_wait(ctx, 50.0)
+    with pytest.raises(G.GbfmmError) as ei:
+        G.gbfmm_sync_status(ctx)
+    assert ei.value.code == G.GBFMM_ETIMEOUT
+    G.gbfmm_sync_status(ctx)  # the status word was cleared
+    x = inputs.uniform_cube(5000, 3)
+    out, _ = run(G, ctx, x, p=4, leaf_size=32)
+    ref = O.fmm(x, 4, 32)["out"]
+    assert O.rel_l2(out, ref) <= TOL_FMM
