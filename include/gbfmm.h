@@ -50,8 +50,17 @@ typedef enum gbfmm_status {
 } gbfmm_status;
 
 enum { GBFMM_METHOD_FMM = 0, GBFMM_METHOD_TREECODE = 1 };
-enum { GBFMM_TREE_UNIFORM = 0 };
-enum { GBFMM_LIST_P2P = 0, GBFMM_LIST_M2L = 1 };
+enum { GBFMM_TREE_UNIFORM = 0, GBFMM_TREE_ADAPTIVE = 1 };
+/* list kinds: the uniform tree's P2P and M2L lists; the adaptive tree's U (P2P), V (M2L),
+ * W (M2P) and X (P2L) lists */
+enum {
+    GBFMM_LIST_P2P = 0,
+    GBFMM_LIST_M2L = 1,
+    GBFMM_LIST_U = 2,
+    GBFMM_LIST_V = 3,
+    GBFMM_LIST_W = 4,
+    GBFMM_LIST_X = 5
+};
 
 /* flags */
 #define GBFMM_FLAG_STAGE_TIMING 1 /* record CUDA events between stages (gbfmm_stage_times) */
@@ -60,11 +69,18 @@ enum { GBFMM_LIST_P2P = 0, GBFMM_LIST_M2L = 1 };
  * Parameters of one evaluation (Section "Fast N-body simulation").
  *   p          expansion order in the paper's convention: degrees n = 0..p-1
  *              (Eq. 4 sums n up to p-1); compiled orders: 4, 6, 8, 10.
- *   leaf_size  the uniform octree has depth L = the smallest L >= 0 with
+ *   leaf_size  uniform tree: depth L = the smallest L >= 0 with
  *              n <= leaf_size * 8^L (mean leaf occupancy <= leaf_size); the paper
  *              keeps the number of cells proportional to N.  L <= 10.
- *   tree       GBFMM_TREE_UNIFORM.
- *   method     GBFMM_METHOD_FMM or GBFMM_METHOD_TREECODE (same lists, M2P).
+ *              adaptive tree: a cell splits while it holds more than leaf_size
+ *              particles, down to level 21 at most.
+ *   tree       GBFMM_TREE_UNIFORM: every level of the octree is dense (Section
+ *              "Fast N-body simulation"; the paper's own experiments);
+ *              GBFMM_TREE_ADAPTIVE: the adaptive octree of the FMM of Cheng,
+ *              Greengard & Rokhlin (1999), which the paper cites for its
+ *              translation operators, with its U, V, W, X lists.  FMM only.
+ *   method     GBFMM_METHOD_FMM or GBFMM_METHOD_TREECODE (same lists, M2P;
+ *              uniform tree only).
  *   eps2       softening added to r^2 in P2P only (Listing 1's eps); pairs at
  *              exactly zero distance contribute nothing whatever eps2 is.
  *   has_box    0: root cube from the data (centre of the bounding box, side =
@@ -108,7 +124,9 @@ const char *gbfmm_last_error(const gbfmm_ctx *ctx);
 
 /* Plan an evaluation of n particles: tree depth and the device workspace size
  * gbfmm_evaluate needs (bytes, an upper bound independent of the particle
- * positions).  Either output pointer may be NULL.  EINVAL / EUNSUPPORTED. */
+ * positions).  Either output pointer may be NULL.  For the adaptive tree the depth
+ * is data dependent: *levels = 21 (the maximum) and *workspace_bytes = 0.
+ * EINVAL / EUNSUPPORTED. */
 int gbfmm_plan(const gbfmm_params *prm, int64_t n, int32_t *levels, size_t *workspace_bytes);
 
 /*
@@ -123,6 +141,11 @@ int gbfmm_plan(const gbfmm_params *prm, int64_t n, int32_t *levels, size_t *work
  * operator tables on the stream.  Non-finite coordinates are detected on the
  * device: the output is then undefined (but every access stays in bounds) and
  * gbfmm_sync_status reports EINVAL.  n = 0 returns OK without work.
+ *
+ * Adaptive tree: d_workspace and workspace_bytes are ignored (NULL / 0 allowed); the
+ * tree, lists and expansions live in device buffers the context owns and grows on
+ * demand.  The call sizes them from counts it reads back while it builds the tree,
+ * so it synchronises `stream` several times and cannot be captured into a CUDA graph.
  */
 int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
                    void *d_workspace, size_t workspace_bytes, void *stream);
@@ -168,11 +191,28 @@ int gbfmm_direct(gbfmm_ctx *ctx, int64_t n_src, const float *d_src, int64_t n_tg
  *   FP64 = for every cell the p(p+1)/2 complex coefficients (m >= 0, index
  *   n(n+1)/2+m, re/im interleaved) in the paper's unscaled normalisation (Eq. 2, 3).
  *   Levels the method does not form are zero.
+ *   After an adaptive evaluation: gbfmm_export_tree returns EINVAL (use
+ *   gbfmm_export_adaptive_tree); gbfmm_export_lists takes GBFMM_LIST_U, _V, _W or
+ *   _X with rows = the adaptive tree's cells; gbfmm_export_expansions writes the
+ *   adaptive tree's cells (levels 0 and 1 are zero).
  */
 int gbfmm_export_tree(gbfmm_ctx *ctx, double *origin_side, uint32_t *sorted_leaf_keys, uint32_t *perm,
                       int32_t *begin, int32_t *count);
 int gbfmm_export_lists(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, int64_t cap, int64_t *n_entries);
 int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef);
+
+/*
+ * Debug export of the last adaptive evaluation (GBFMM_TREE_ADAPTIVE).  Host buffers, any
+ * may be NULL; call once with only ncells to size them.  Cells are numbered level by
+ * level, in key order within a level (root = 0).  origin_side[4] as gbfmm_export_tree;
+ * *ncells = number of cells C; level[C]; key[C] = the cell's Morton key at its level (the
+ * 63-bit particle key shifted right by 3(21 - level)); begin[C], count[C] = its particle
+ * range in sorted order; parent[C] (-1 for the root); perm[n] = original index of each
+ * sorted position (particles sorted by their full 63-bit key, ties by original index).
+ * EINVAL if the last evaluation was not adaptive.  Waits for the device.
+ */
+int gbfmm_export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *ncells, int32_t *level, uint64_t *key,
+                               int32_t *begin, int32_t *count, int32_t *parent, uint32_t *perm);
 
 /*
  * Per-stage device times (ms) of the last evaluate run with

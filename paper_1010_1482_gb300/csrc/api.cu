@@ -23,26 +23,30 @@ using namespace gbfmm;
 namespace gbfmm {
 static thread_local int64_t tl_launches = 0;
 void note_launches(int k) { tl_launches += k; }
+int64_t launch_count() { return tl_launches; }
 }  // namespace gbfmm
 
-namespace {
+#include "context.h"
 
-constexpr int kBoxPartials = 304 * 8;
-constexpr int kStages = 10;
-constexpr int kOrders[4] = {4, 6, 8, 10};
-
-struct OpsCache {
-    int P = 0;
-    float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
-    bool built = false;
-};
-
-int order_slot(int p)
+int gbfmm::order_slot(int p)
 {
     for (int i = 0; i < 4; ++i)
         if (kOrders[i] == p) return i;
     return -1;
 }
+
+int gbfmm::fail(gbfmm_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int gbfmm::cuda_fail(gbfmm_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, GBFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
 
 int uniform_depth(int64_t n, int64_t leaf)
 {
@@ -55,47 +59,6 @@ int uniform_depth(int64_t n, int64_t leaf)
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-}  // namespace
-
-struct gbfmm_ctx {
-    int device = 0;
-    std::string err;
-    int *d_status = nullptr;
-    unsigned *d_counter = nullptr;
-    float *d_partials = nullptr;
-    float *d_zero = nullptr;
-    OpsCache ops[4];
-    // last evaluation
-    bool have_last = false;
-    Layout last{};
-    unsigned char *last_ws = nullptr;
-    size_t last_keys = 0, last_idx = 0;
-    int last_method = 0;
-    // host-buffer path
-    float *h_in = nullptr, *h_out = nullptr;
-    void *h_ws = nullptr;
-    int64_t h_cap_n = 0;
-    size_t h_ws_bytes = 0;
-    // stage timing
-    cudaEvent_t ev[kStages + 1] = {};
-    bool timed_last = false;
-    bool ops_built_last = false;
-    int64_t launches_last = 0;
-};
-
-namespace {
-
-int fail(gbfmm_ctx *ctx, int code, const std::string &msg)
-{
-    if (ctx) ctx->err = msg;
-    return code;
-}
-
-int cuda_fail(gbfmm_ctx *ctx, cudaError_t e, const char *what)
-{
-    return fail(ctx, GBFMM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
 
 int check_params(const gbfmm_params *prm, int64_t n, int *L_out, std::string *msg)
 {
@@ -115,13 +78,17 @@ int check_params(const gbfmm_params *prm, int64_t n, int *L_out, std::string *ms
         *msg = "leaf_size < 1";
         return GBFMM_EINVAL;
     }
-    if (prm->tree != GBFMM_TREE_UNIFORM) {
-        *msg = "only the uniform tree is available";
-        return GBFMM_EUNSUPPORTED;
+    if (prm->tree != GBFMM_TREE_UNIFORM && prm->tree != GBFMM_TREE_ADAPTIVE) {
+        *msg = "unknown tree";
+        return GBFMM_EINVAL;
     }
     if (prm->method != GBFMM_METHOD_FMM && prm->method != GBFMM_METHOD_TREECODE) {
         *msg = "unknown method";
         return GBFMM_EINVAL;
+    }
+    if (prm->tree == GBFMM_TREE_ADAPTIVE && prm->method != GBFMM_METHOD_FMM) {
+        *msg = "the adaptive tree runs the FMM only";
+        return GBFMM_EUNSUPPORTED;
     }
     if (!(prm->eps2 >= 0.0) || !isfinite(prm->eps2)) {
         *msg = "eps2 must be finite and >= 0";
@@ -137,6 +104,10 @@ int check_params(const gbfmm_params *prm, int64_t n, int *L_out, std::string *ms
     if (n > (int64_t)0x7fffffff) {
         *msg = "n exceeds 2^31 - 1";
         return GBFMM_EUNSUPPORTED;
+    }
+    if (prm->tree == GBFMM_TREE_ADAPTIVE) {
+        *L_out = kAdaptiveMaxLevel;
+        return GBFMM_OK;
     }
     int L = uniform_depth(n, prm->leaf_size);
     if (L > kMaxLevel) {
@@ -196,7 +167,9 @@ T *at(void *base, size_t off)
     return reinterpret_cast<T *>(static_cast<unsigned char *>(base) + off);
 }
 
-int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
+}  // namespace
+
+int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
 {
     OpsCache &c = ctx->ops[order_slot(P)];
     *built_now = false;
@@ -215,8 +188,6 @@ int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     *built_now = true;
     return GBFMM_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -287,6 +258,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
     cudaFree(ctx->h_ws);
+    free_adaptive(ctx->ad);
     for (int i = 0; i <= kStages; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -301,8 +273,12 @@ int gbfmm_plan(const gbfmm_params *prm, int64_t n, int32_t *levels, size_t *work
     int L = 0;
     int rc = check_params(prm, n, &L, &msg);
     if (rc != GBFMM_OK) return rc;
-    Layout lo = make_layout(n, L, prm->p);
     if (levels) *levels = L;
+    if (prm->tree == GBFMM_TREE_ADAPTIVE) {
+        if (workspace_bytes) *workspace_bytes = 0;
+        return GBFMM_OK;
+    }
+    Layout lo = make_layout(n, L, prm->p);
     if (workspace_bytes) *workspace_bytes = lo.total;
     return GBFMM_OK;
 }
@@ -317,6 +293,24 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     int rc = check_params(prm, n, &L, &msg);
     if (rc != GBFMM_OK) return fail(ctx, rc, msg);
     if (n == 0) return GBFMM_OK;
+    if (prm->tree == GBFMM_TREE_ADAPTIVE) {
+        if (!d_xyzq || !d_out) return fail(ctx, GBFMM_EINVAL, "null device pointer");
+        if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
+            return fail(ctx, GBFMM_EINVAL, "particle arrays must be 16-byte aligned");
+        if (d_xyzq == d_out) return fail(ctx, GBFMM_EINVAL, "d_out aliases d_xyzq");
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+        ctx->have_last = false;
+        const int64_t launches0 = tl_launches;
+        rc = evaluate_adaptive(ctx, prm, n, d_xyzq, d_out, static_cast<cudaStream_t>(stream));
+        ctx->launches_last = tl_launches - launches0;
+        if (rc != GBFMM_OK) return rc;
+        ctx->have_last = true;
+        ctx->last_adaptive = true;
+        ctx->last_method = prm->method;
+        ctx->timed_last = (prm->flags & GBFMM_FLAG_STAGE_TIMING) != 0;
+        return GBFMM_OK;
+    }
     if (!d_xyzq || !d_out || !d_workspace) return fail(ctx, GBFMM_EINVAL, "null device pointer");
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return fail(ctx, GBFMM_EINVAL, "workspace not 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
@@ -397,6 +391,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
 
     ctx->launches_last = tl_launches - launches0;
     ctx->have_last = true;
+    ctx->last_adaptive = false;
     ctx->last = lo;
     ctx->last_ws = static_cast<unsigned char *>(ws);
     ctx->last_keys = (size_t)(reinterpret_cast<unsigned char *>(skeys) - ctx->last_ws);
@@ -443,7 +438,7 @@ int gbfmm_evaluate_host(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, cons
         if ((e = cudaMalloc(&ctx->h_out, 16 * (size_t)n)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(out)");
         ctx->h_cap_n = n;
     }
-    if (ctx->h_ws_bytes < ws) {
+    if (ws > 0 && ctx->h_ws_bytes < ws) {
         cudaFree(ctx->h_ws);
         ctx->h_ws = nullptr;
         ctx->h_ws_bytes = 0;
@@ -482,6 +477,7 @@ int gbfmm_export_tree(gbfmm_ctx *ctx, double *origin_side, uint32_t *sorted_leaf
 {
     if (!ctx) return GBFMM_EINVAL;
     if (!ctx->have_last) return fail(ctx, GBFMM_EINVAL, "no evaluation to export");
+    if (ctx->last_adaptive) return fail(ctx, GBFMM_EINVAL, "last evaluation used the adaptive tree");
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
@@ -514,10 +510,15 @@ int gbfmm_export_lists(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, in
 {
     if (!ctx) return GBFMM_EINVAL;
     if (!ctx->have_last) return fail(ctx, GBFMM_EINVAL, "no evaluation to export");
-    if (kind != GBFMM_LIST_P2P && kind != GBFMM_LIST_M2L) return fail(ctx, GBFMM_EINVAL, "unknown list kind");
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    if (ctx->last_adaptive) {
+        if (kind < GBFMM_LIST_U || kind > GBFMM_LIST_X)
+            return fail(ctx, GBFMM_EINVAL, "list kind does not match the adaptive tree");
+        return export_adaptive_list(ctx, kind - GBFMM_LIST_U, offs, ids, cap, n_entries);
+    }
+    if (kind != GBFMM_LIST_P2P && kind != GBFMM_LIST_M2L) return fail(ctx, GBFMM_EINVAL, "unknown list kind");
     const Layout &lo = ctx->last;
     const int64_t rows = kind == GBFMM_LIST_P2P ? lo.nleaves : lo.ncells;
     std::vector<uint32_t> o(rows + 1);
@@ -545,6 +546,7 @@ int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef)
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    if (ctx->last_adaptive) return export_adaptive_expansions(ctx, which, coef);
     const Layout &lo = ctx->last;
     const int P = lo.P, PP = P * P, NT = P * (P + 1) / 2;
     std::vector<float> v((size_t)lo.ncells * PP);
@@ -578,6 +580,17 @@ int gbfmm_export_expansions(gbfmm_ctx *ctx, int which, double *coef)
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? GBFMM_OK : cuda_fail(ctx, e, "export copy");
+}
+
+int gbfmm_export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *ncells, int32_t *level, uint64_t *key,
+                               int32_t *begin, int32_t *count, int32_t *parent, uint32_t *perm)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    if (!ctx->have_last || !ctx->last_adaptive) return fail(ctx, GBFMM_EINVAL, "no adaptive evaluation to export");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    return export_adaptive_tree(ctx, origin_side, ncells, level, key, begin, count, parent, perm);
 }
 
 int gbfmm_selftest_wait(gbfmm_ctx *ctx, double limit_ms, void *stream)

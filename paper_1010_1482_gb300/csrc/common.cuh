@@ -56,6 +56,39 @@ GB_HD void demorton3(uint32_t k, int &x, int &y, int &z)
     z = (int)compact3(k >> 2);
 }
 
+// 63-bit Morton interleave of three 21-bit integers (same bit order as morton3).
+GB_HD uint64_t spread21(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+GB_HD uint64_t compact21(uint64_t v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return v;
+}
+
+GB_HD uint64_t morton63(uint64_t x, uint64_t y, uint64_t z) { return spread21(x) | (spread21(y) << 1) | (spread21(z) << 2); }
+
+// integer coordinates of the level-l cell whose key prefix is `key` (3l bits)
+GB_HD void demorton63(uint64_t key, int &x, int &y, int &z)
+{
+    x = (int)compact21(key);
+    y = (int)compact21(key >> 1);
+    z = (int)compact21(key >> 2);
+}
+
 // Translation-operator tables (M2L, M2M, L2L) are stored column-major, [op][col][row], with
 // the row count padded to a multiple of 8 (zero rows), so row blocks of 4 or 8 per thread
 // stay 16-byte aligned.
@@ -165,11 +198,37 @@ void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *b
                 const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s);
 
 // m2l.cu
+constexpr int kM2LTargetsPerTile = 64;  // targets per M2L CTA (tile list mode)
 void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                 const int32_t *m2l_ids, const uint16_t *m2l_code, const float *ops, const float *M, float *Lc,
                 const float *zero_block, int *status, cudaStream_t s);
 
 void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s);
+
+// adaptive tree (targets and sources given as cell lists; cells carry level and 63-bit key)
+void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
+                          uint32_t *hist, int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx,
+                          uint64_t **keys_out, uint32_t **idx_out, cudaStream_t s);
+void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
+                      const int32_t *begin, const int32_t *count, const Box *box, const float4 *sx, float *M,
+                      cudaStream_t s);
+void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,
+                            const int32_t *nchild, const float *ops, float *X, cudaStream_t s);
+void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
+                      const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
+                      const float *ops, const float *M, float *Lc, const float *zero_block, int *status,
+                      cudaStream_t s);
+void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *begin,
+                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const Box *box,
+                      const float4 *sx, float *Lc, cudaStream_t s);
+void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const uint64_t *key,
+                      const Box *box, const float4 *sx, const float *Lc, float4 *far, cudaStream_t s);
+void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
+                      const int32_t *begin, const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids,
+                      const Box *box, const float4 *sx, const float *M, float4 *far, cudaStream_t s);
+void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+                      const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
+                      const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);
 
 // p2p.cu
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,

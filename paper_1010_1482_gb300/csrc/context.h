@@ -1,0 +1,92 @@
+// Internal: the library context shared by the host-side translation units (api.cu for the
+// uniform tree, adaptive.cu for the adaptive tree).  Not part of the C ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gbfmm.h"
+
+namespace gbfmm {
+
+constexpr int kBoxPartials = 304 * 8;
+constexpr int kStages = 10;
+constexpr int kOrders[4] = {4, 6, 8, 10};
+constexpr int kAdaptiveMaxLevel = 21;  // 63-bit keys: 21 bits per axis
+
+struct OpsCache {
+    int P = 0;
+    float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
+    bool built = false;
+};
+
+// a device buffer owned by the context, grown on demand
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    template <class T>
+    T *as() const
+    {
+        return static_cast<T *>(p);
+    }
+};
+
+// device state of the last adaptive evaluation (all buffers owned by the context)
+struct AdaptiveState {
+    DevBuf keys0, keys1, idx0, idx1, sx, far, hist, scan_tmp, flags, scan, pcell, leaf_of, box;
+    DevBuf level, key, begin, count, end, parent, child_begin, nchild, child_of, coll;
+    DevBuf lcnt[4], loffs[4], lids[4], vcode;  // U, V, W, X
+    DevBuf M, Lc, tlist, tdesc, leaves, group_cnt;
+    int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
+    int P = 0, max_level = 0;
+    std::vector<int> level_start;
+    uint64_t *skeys = nullptr;
+    uint32_t *perm = nullptr;
+};
+
+}  // namespace gbfmm
+
+struct gbfmm_ctx {
+    int device = 0;
+    std::string err;
+    int *d_status = nullptr;
+    unsigned *d_counter = nullptr;
+    float *d_partials = nullptr;
+    float *d_zero = nullptr;
+    gbfmm::OpsCache ops[4];
+    // last evaluation
+    bool have_last = false;
+    bool last_adaptive = false;
+    gbfmm::Layout last{};
+    unsigned char *last_ws = nullptr;
+    size_t last_keys = 0, last_idx = 0;
+    int last_method = 0;
+    gbfmm::AdaptiveState ad;
+    // host-buffer path
+    float *h_in = nullptr, *h_out = nullptr;
+    void *h_ws = nullptr;
+    int64_t h_cap_n = 0;
+    size_t h_ws_bytes = 0;
+    // stage timing
+    cudaEvent_t ev[gbfmm::kStages + 1] = {};
+    bool timed_last = false;
+    bool ops_built_last = false;
+    int64_t launches_last = 0;
+};
+
+namespace gbfmm {
+int order_slot(int p);
+int fail(gbfmm_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(gbfmm_ctx *ctx, cudaError_t e, const char *what);
+int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now);
+int64_t launch_count();
+// adaptive tree (adaptive.cu)
+int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
+                      cudaStream_t s);
+int export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *ncells, int32_t *level, uint64_t *key,
+                         int32_t *begin, int32_t *count, int32_t *parent, uint32_t *perm);
+int export_adaptive_expansions(gbfmm_ctx *ctx, int which, double *coef);
+int export_adaptive_list(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, int64_t cap, int64_t *n_entries);
+void free_adaptive(AdaptiveState &a);
+}  // namespace gbfmm

@@ -245,6 +245,62 @@ GB_DEV CellGeom cell_geom(const Box &b, int l, uint32_t key)
 // P2M: one warp per leaf; lanes stride over the leaf's particles, each accumulates the full
 // real-packed expansion in registers, then a butterfly reduction sums the lanes.
 // ------------------------------------------------------------------------------------------
+// acc += sum over particles j = b0 + lane, b0 + lane + 32, ... < e0 of q_j conj(H_n^m(x^_j)),
+// x^ = (x - c) / h, with H the regular harmonics R (P2M, Eq. 2) or the irregular harmonics I
+// (P2L, Eq. 3), real-packed
+template <int P, bool IRREG>
+GB_DEV void p2x_particles(float (&acc)[P * P], const float4 *__restrict__ sx, int b0, int e0, int lane,
+                          const CellGeom &cg)
+{
+    for (int j = b0 + lane; j < e0; j += 32) {
+        float4 p = __ldg(&sx[j]);
+        const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
+        const float q = p.w, r2 = x * x + y * y + z * z;
+        const float ir2 = IRREG ? 1.f / r2 : 1.f;
+        float mre = IRREG ? rsqrtf(r2) : 1.f, mim = 0.f;  // H_m^m
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            if (m > 0) {
+                const float f = -c_rmm[m] * ir2;
+                const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
+                mre = tr;
+                mim = ti;
+            }
+            float are = mre, aim = mim, bre = 0.f, bim = 0.f;  // H_n^m, H_{n-1}^m
+#pragma unroll
+            for (int n = m; n < P; ++n) {
+                if (n > m) {
+                    const float ca = c_ra[n - 1][m] * z, cb = c_rb[n - 1][m] * (IRREG ? 1.f : r2);
+                    float nre = ca * are - cb * bre, nim = ca * aim - cb * bim;
+                    if (IRREG) {
+                        nre *= ir2;
+                        nim *= ir2;
+                    }
+                    bre = are;
+                    bim = aim;
+                    are = nre;
+                    aim = nim;
+                }
+                acc[re_idx(n, m)] += q * are;
+                if (m > 0) acc[im_idx(n, m)] -= q * aim;
+            }
+        }
+    }
+}
+
+// warp-wide butterfly sum of acc; lane (i mod 32) adds / stores coefficient i
+template <int P>
+GB_DEV void warp_store(float (&acc)[P * P], float *dst, int lane, bool add)
+{
+#pragma unroll
+    for (int i = 0; i < P * P; ++i) {
+        float v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((i & 31) == lane) dst[i] = add ? dst[i] + v : v;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box, const float4 *__restrict__ sx,
                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
@@ -261,42 +317,8 @@ __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box,
     float acc[P * P];
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
-    for (int j = b0 + lane; j < e0; j += 32) {
-        float4 p = __ldg(&sx[j]);
-        const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
-        const float q = p.w, r2 = x * x + y * y + z * z;
-        float mre = 1.f, mim = 0.f;  // R_m^m
-#pragma unroll
-        for (int m = 0; m < P; ++m) {
-            if (m > 0) {
-                const float f = -c_rmm[m];
-                const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
-                mre = tr;
-                mim = ti;
-            }
-            float are = mre, aim = mim, bre = 0.f, bim = 0.f;  // R_n^m, R_{n-1}^m
-#pragma unroll
-            for (int n = m; n < P; ++n) {
-                if (n > m) {
-                    const float ca = c_ra[n - 1][m] * z, cb = c_rb[n - 1][m] * r2;
-                    const float nre = ca * are - cb * bre, nim = ca * aim - cb * bim;
-                    bre = are;
-                    bim = aim;
-                    are = nre;
-                    aim = nim;
-                }
-                acc[re_idx(n, m)] += q * are;
-                if (m > 0) acc[im_idx(n, m)] -= q * aim;
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < P * P; ++i) {
-        float v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((i & 31) == lane) M[g * (P * P) + i] = v;
-    }
+    p2x_particles<P, false>(acc, sx, b0, e0, lane, cg);
+    warp_store<P>(acc, M + g * (P * P), lane, false);
 }
 
 void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
@@ -461,21 +483,10 @@ void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const fl
 //   dphi/dx + i dphi/dy = sum_{n<P-1} sum_m s(m) sqrt((n+2-m)(n+1-m)) L_{n+1}^{m-1} R_n^m,
 //   s(m) = +1 for m >= 1, -1 for m <= 0.
 // ------------------------------------------------------------------------------------------
+// value and gradient of the scaled local expansion Lg at x^ (multiplied by 1/h and 1/h^2)
 template <int P>
-__global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box, int64_t n,
-                                             const float4 *__restrict__ sx, const uint32_t *__restrict__ leafkey,
-                                             const float *__restrict__ Lc, float4 *__restrict__ far)
+GB_DEV float4 l2p_eval(const float *__restrict__ Lg, float x, float y, float z, float ih)
 {
-    constexpr int PP = P * P;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t key = leafkey[i];
-    const int64_t g = level_offset(L) + key;
-    const Box bx = *box;
-    const CellGeom cg = cell_geom(bx, L, key);
-    const float *Lg = Lc + g * PP;
-    float4 p = __ldg(&sx[i]);
-    const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
     const float r2 = x * x + y * y + z * z;
     float phi = 0.f, gz = 0.f, gpr = 0.f, gpi = 0.f;
     float mre = 1.f, mim = 0.f;
@@ -532,8 +543,25 @@ __global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box,
             }
         }
     }
-    const float ih = cg.inv_h, ih2 = ih * ih;
-    far[i] = make_float4(phi * ih, gpr * ih2, gpi * ih2, gz * ih2);
+    const float ih2 = ih * ih;
+    return make_float4(phi * ih, gpr * ih2, gpi * ih2, gz * ih2);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box, int64_t n,
+                                             const float4 *__restrict__ sx, const uint32_t *__restrict__ leafkey,
+                                             const float *__restrict__ Lc, float4 *__restrict__ far)
+{
+    constexpr int PP = P * P;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t key = leafkey[i];
+    const int64_t g = level_offset(L) + key;
+    const Box bx = *box;
+    const CellGeom cg = cell_geom(bx, L, key);
+    float4 p = __ldg(&sx[i]);
+    far[i] = l2p_eval<P>(Lc + g * PP, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
+                         cg.inv_h);
 }
 
 void launch_l2p(int P, int L, const Box *box, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
@@ -661,5 +689,297 @@ void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *b
     }
     note_launches(1);
 }
+
+// ==========================================================================================
+// Adaptive tree: cells are given by index; each carries its level and 63-bit key prefix.
+// ==========================================================================================
+GB_DEV CellGeom cell_geom63(const Box &b, int l, uint64_t key)
+{
+    int ix, iy, iz;
+    demorton63(key, ix, iy, iz);
+    double h = b.side / (double)(int64_t(1) << l);
+    CellGeom g;
+    g.cx = (float)(b.origin[0] + (ix + 0.5) * h);
+    g.cy = (float)(b.origin[1] + (iy + 0.5) * h);
+    g.cz = (float)(b.origin[2] + (iz + 0.5) * h);
+    g.h = (float)h;
+    g.inv_h = (float)(1.0 / h);
+    return g;
+}
+
+// P2M at the listed leaves (levels >= 2), one warp per leaf
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ leaves, int64_t nleaves,
+                                                   const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                                                   const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                                   const Box *__restrict__ box, const float4 *__restrict__ sx,
+                                                   float *__restrict__ M)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nleaves) return;
+    const int32_t c = leaves[w];
+    if (level[c] < 2) return;
+    const Box bx = *box;
+    const CellGeom cg = cell_geom63(bx, level[c], key[c]);
+    float acc[P * P];
+#pragma unroll
+    for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
+    p2x_particles<P, false>(acc, sx, begin[c], begin[c] + count[c], lane, cg);
+    warp_store<P>(acc, M + (int64_t)c * (P * P), lane, false);
+}
+
+// P2L over the X list (Eq. 3's L from the particles of each X leaf), one warp per cell; adds
+// into the cell's local expansion
+template <int P>
+__global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t *__restrict__ level,
+                                                   const uint64_t *__restrict__ key, const int32_t *__restrict__ begin,
+                                                   const int32_t *__restrict__ count,
+                                                   const uint32_t *__restrict__ x_offs,
+                                                   const int32_t *__restrict__ x_ids, const Box *__restrict__ box,
+                                                   const float4 *__restrict__ sx, float *__restrict__ Lc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= ncells) return;
+    const uint32_t e0 = x_offs[b], e1 = x_offs[b + 1];
+    if (e0 == e1 || level[b] < 2) return;
+    const Box bx = *box;
+    const CellGeom cg = cell_geom63(bx, level[b], key[b]);
+    float acc[P * P];
+#pragma unroll
+    for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
+    for (uint32_t e = e0; e < e1; ++e) {
+        const int32_t c = x_ids[e];
+        p2x_particles<P, true>(acc, sx, begin[c], begin[c] + count[c], lane, cg);
+    }
+    warp_store<P>(acc, Lc + b * (P * P), lane, true);
+}
+
+// L2P at every particle's leaf (leaves above level 2 carry no local expansion)
+template <int P>
+__global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__restrict__ leaf_of,
+                                                   const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                                                   const Box *__restrict__ box, const float4 *__restrict__ sx,
+                                                   const float *__restrict__ Lc, float4 *__restrict__ far)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = leaf_of[i];
+    if (level[c] < 2) {
+        far[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const Box bx = *box;
+    const CellGeom cg = cell_geom63(bx, level[c], key[c]);
+    float4 p = __ldg(&sx[i]);
+    far[i] = l2p_eval<P>(Lc + (int64_t)c * (P * P), (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                         (p.z - cg.cz) * cg.inv_h, cg.inv_h);
+}
+
+// M2P over the W list, one CTA per listed leaf; adds into the far-field accumulator
+template <int P>
+__global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ leaves,
+                                                  const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                                                  const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                                  const uint32_t *__restrict__ w_offs,
+                                                  const int32_t *__restrict__ w_ids, const Box *__restrict__ box,
+                                                  const float4 *__restrict__ sx, const float *__restrict__ M,
+                                                  float4 *__restrict__ far)
+{
+    constexpr int PP = P * P;
+    __shared__ float sM[PP];
+    const int32_t b = leaves[blockIdx.x];
+    const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
+    if (e0 == e1) return;
+    const Box bx = *box;
+    const int b0 = begin[b], bend = begin[b] + count[b];
+    for (int t0 = b0; t0 < bend; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const bool act = t < bend;
+        float4 p = act ? __ldg(&sx[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+        for (uint32_t e = e0; e < e1; ++e) {
+            const int32_t sc = w_ids[e];
+            __syncthreads();
+            for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[(int64_t)sc * PP + k];
+            __syncthreads();
+            const CellGeom cg = cell_geom63(bx, level[sc], key[sc]);
+            if (act)
+                m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
+                                  cg.inv_h, o);
+        }
+        if (act) {
+            float4 f = far[t];
+            f.x += o[0];
+            f.y += o[1];
+            f.z += o[2];
+            f.w += o[3];
+            far[t] = f;
+        }
+    }
+}
+
+// M2M (up) / L2L (down) over cells given by their parents' index range; children by position
+template <int P, bool UP>
+__global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t lo, int64_t np,
+                                                                         const int32_t *__restrict__ child_of,
+                                                                         const int32_t *__restrict__ nchild,
+                                                                         const float *__restrict__ ops,
+                                                                         float *__restrict__ X)
+{
+    using Cfg = TransCfg<P, UP>;
+    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
+    extern __shared__ __align__(16) float tsm[];
+    float *A = tsm;
+    float *B = tsm + PP * PR;
+    const int64_t q0 = blockIdx.x * (int64_t)kTrTN;
+    const int tid = threadIdx.x;
+    const bool work = tid < NRG * NCG;
+    const int cg = tid % NCG, rg = tid / NCG;
+    int kbeg = 0, kend = PP;
+    if (work) {
+        const int r0 = min(rg * 4, PP - 1), r1 = min(rg * 4 + 3, PP - 1);
+        if (UP) {
+            const int d = degree_of(r1);
+            kend = min(PP, ((d + 1) * (d + 1) + 3) / 4 * 4);
+        } else {
+            const int d = degree_of(r0);
+            kbeg = (d * d) / 4 * 4;
+        }
+    }
+    float acc[4][kTrCN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < kTrCN; ++j) acc[i][j] = 0.f;
+    const int c_first = UP ? 0 : blockIdx.y, c_last = UP ? 7 : blockIdx.y;
+    for (int c = c_first; c <= c_last; ++c) {
+        if (c != c_first) __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(ops + (size_t)c * PP * PR);
+        for (int e = tid; e < PP * PR / 4; e += blockDim.x) reinterpret_cast<float4 *>(A)[e] = __ldg(&src[e]);
+        for (int e = tid; e < kTrTN * (PP / 4); e += blockDim.x) {
+            const int i = e / (PP / 4), k4 = e % (PP / 4);
+            const int64_t q = q0 + i;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < np) {
+                const int64_t pcell = lo + q;
+                const int64_t g = UP ? child_of[pcell * 8 + c] : (child_of[pcell * 8 + c] >= 0 ? pcell : -1);
+                if (g >= 0) v = reinterpret_cast<const float4 *>(X + g * PP)[k4];
+            }
+            *reinterpret_cast<float4 *>(B + i * SB + 4 * k4) = v;
+        }
+        __syncthreads();
+        if (work) {
+            const float *Ar = A + rg * 4;
+            const float *Bc = B + cg * SB;
+#pragma unroll 2
+            for (int k = kbeg; k < kend; k += 4) {
+                Frag<kTrCN, 4> f;
+                f.load(Ar, Bc, k, PR, NCG * SB);
+                f.fma(acc);
+            }
+        }
+    }
+    if (!work) return;
+#pragma unroll
+    for (int j = 0; j < kTrCN; ++j) {
+        const int64_t q = q0 + cg + j * NCG;
+        if (q >= np) continue;
+        const int r = rg * 4;
+        if (r >= PP) continue;
+        const int64_t pcell = lo + q;
+        int64_t g;
+        if (UP) {
+            if (nchild[pcell] == 0) continue;  // a leaf keeps its P2M expansion
+            g = pcell;
+        } else {
+            g = child_of[pcell * 8 + blockIdx.y];
+            if (g < 0) continue;
+        }
+        float4 *dst = reinterpret_cast<float4 *>(X + g * PP + r);
+        if (UP) {
+            *dst = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        } else {
+            float4 v = *dst;
+            v.x += acc[0][j];
+            v.y += acc[1][j];
+            v.z += acc[2][j];
+            v.w += acc[3][j];
+            *dst = v;
+        }
+    }
+}
+
+#define GBFMM_DISPATCH_P(P, CALL)      \
+    switch (P) {                       \
+    case 4: { constexpr int PQ = 4; CALL; } break;   \
+    case 6: { constexpr int PQ = 6; CALL; } break;   \
+    case 8: { constexpr int PQ = 8; CALL; } break;   \
+    case 10: { constexpr int PQ = 10; CALL; } break; \
+    }
+
+void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
+                      const int32_t *begin, const int32_t *count, const Box *box, const float4 *sx, float *M,
+                      cudaStream_t s)
+{
+    if (nleaves <= 0) return;
+    const unsigned grid = (unsigned)((nleaves + 3) / 4);
+    GBFMM_DISPATCH_P(P, (k_p2m_cells<PQ><<<grid, 128, 0, s>>>(leaves, nleaves, level, key, begin, count, box, sx, M)));
+    note_launches(1);
+}
+
+void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *begin,
+                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const Box *box,
+                      const float4 *sx, float *Lc, cudaStream_t s)
+{
+    if (ncells <= 0) return;
+    const unsigned grid = (unsigned)((ncells + 3) / 4);
+    GBFMM_DISPATCH_P(P, (k_p2l_cells<PQ><<<grid, 128, 0, s>>>(ncells, level, key, begin, count, x_offs, x_ids, box,
+                                                              sx, Lc)));
+    note_launches(1);
+}
+
+void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const uint64_t *key,
+                      const Box *box, const float4 *sx, const float *Lc, float4 *far, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, key, box, sx, Lc, far)));
+    note_launches(1);
+}
+
+void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
+                      const int32_t *begin, const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids,
+                      const Box *box, const float4 *sx, const float *M, float4 *far, cudaStream_t s)
+{
+    if (nleaves <= 0) return;
+    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)nleaves, 64, 0, s>>>(leaves, level, key, begin, count, w_offs,
+                                                                          w_ids, box, sx, M, far)));
+    note_launches(1);
+}
+
+template <int P, bool UP>
+static void translate_cells_t(int64_t lo, int64_t np, const int32_t *child_of, const int32_t *nchild, const float *ops,
+                              float *X, cudaStream_t s)
+{
+    using Cfg = TransCfg<P, UP>;
+    cudaFuncSetAttribute(k_translate_cells<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    dim3 grid((unsigned)((np + kTrTN - 1) / kTrTN), UP ? 1 : 8);
+    k_translate_cells<P, UP><<<grid, Cfg::NT, Cfg::kSmem, s>>>(lo, np, child_of, nchild, ops, X);
+    note_launches(1);
+}
+
+void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,
+                            const int32_t *nchild, const float *ops, float *X, cudaStream_t s)
+{
+    if (nparents <= 0) return;
+    if (up) {
+        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, true>(lo, nparents, child_of, nchild, ops, X, s)));
+    } else {
+        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, false>(lo, nparents, child_of, nchild, ops, X, s)));
+    }
+}
+#undef GBFMM_DISPATCH_P
 
 }  // namespace gbfmm

@@ -161,7 +161,8 @@ struct M2LConfig {
 
 template <int P, int TN, int RM, int CN, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREADS, MINB)
-    k_m2l(M2LTiles tiles, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+    k_m2l(M2LTiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
+          const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
           const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
           const uint16_t *__restrict__ m2l_code, const float *__restrict__ ops, const float *__restrict__ M,
           float *__restrict__ Lc, const float *__restrict__ zero_block, int *status)
@@ -176,18 +177,38 @@ __global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREA
     __shared__ int s_issued[NSTAGE];
     __shared__ volatile int s_abort;
 
-    // ---- decode tile: levels in descending order ----
-    int rem = blockIdx.x, l = tiles.L;
-    while (l >= 2 && rem >= tiles.ntiles_level[l]) {
-        rem -= tiles.ntiles_level[l];
-        --l;
+    // ---- decode tile ----
+    // dense uniform levels (levels in descending order, target q of child position tau at
+    // level_offset(l) + 8q + tau), or an explicit tile list (level, tau, start, count) over tlist
+    int l, tau;
+    int64_t q0 = 0, nq = 0, off = 0, tstart = 0;
+    int tcount = 0;
+    if (tdesc) {
+        const int4 d = tdesc[blockIdx.x];
+        l = d.x;
+        tau = d.y;
+        tstart = d.z;
+        tcount = d.w;
+    } else {
+        int rem = blockIdx.x;
+        l = tiles.L;
+        while (l >= 2 && rem >= tiles.ntiles_level[l]) {
+            rem -= tiles.ntiles_level[l];
+            --l;
+        }
+        if (l < 2) return;
+        nq = int64_t(1) << (3 * (l - 1));
+        const int64_t qtiles = (nq + TN - 1) / TN;
+        tau = (int)(rem / qtiles);
+        q0 = (rem % qtiles) * TN;
+        off = level_offset(l);
     }
-    if (l < 2) return;
-    const int64_t nq = int64_t(1) << (3 * (l - 1));
-    const int64_t qtiles = (nq + TN - 1) / TN;
-    const int tau = (int)(rem / qtiles);
-    const int64_t q0 = (rem % qtiles) * TN;
-    const int64_t off = level_offset(l);
+    // global cell index of tile target t, or -1
+    auto target = [&](int t) -> int64_t {
+        if (tdesc) return t < tcount ? (int64_t)tlist[tstart + t] : -1;
+        const int64_t q = q0 + t;
+        return q < nq ? off + 8 * q + tau : -1;
+    };
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -206,10 +227,9 @@ __global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREA
         uint32_t ptr[Cfg::TPL], pend[Cfg::TPL];
 #pragma unroll
         for (int k = 0; k < Cfg::TPL; ++k) {
-            const int64_t q = q0 + lane + 32 * k;
+            const int64_t g = target(lane + 32 * k);
             ptr[k] = pend[k] = 0;
-            if (q < nq) {
-                const int64_t g = off + 8 * q + tau;
+            if (g >= 0) {
                 if (end[g] > begin[g]) {
                     ptr[k] = m2l_offs[g];
                     pend[k] = m2l_offs[g + 1];
@@ -291,10 +311,8 @@ __global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREA
         if (work && !s_abort) {
 #pragma unroll
             for (int j = 0; j < CNN; ++j) {
-                const int t = cg + j * NCG;
-                const int64_t q = q0 + t;
-                if (q >= nq) continue;
-                const int64_t g = off + 8 * q + tau;
+                const int64_t g = target(cg + j * NCG);
+                if (g < 0) continue;
                 if (end[g] <= begin[g]) continue;
 #pragma unroll
                 for (int qq = 0; qq < RM / 4; ++qq) {
@@ -336,8 +354,39 @@ static void launch_m2l_t(int L, const int32_t *begin, const int32_t *end, const 
     }
     if (total == 0) return;
     k_m2l<P, TN, RM, CN, NSTAGE, MINB><<<total, Cfg::NTHREADS, Cfg::kSmemBytes, s>>>(
-        tiles, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status);
+        tiles, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status);
     note_launches(1);
+}
+
+// tile-list mode (adaptive tree): the default tile shape, kM2LTargetsPerTile targets per CTA
+template <int P, int NSTAGE>
+static void launch_m2l_tiles_t(const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
+                               const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
+                               const uint16_t *m2l_code, const float *ops, const float *M, float *Lc,
+                               const float *zero_block, int *status, cudaStream_t s)
+{
+    constexpr int TN = kM2LTargetsPerTile;
+    using Cfg = M2LConfig<P, TN, 4, 8, NSTAGE, 1>;
+    cudaFuncSetAttribute(k_m2l<P, TN, 4, 8, NSTAGE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Cfg::kSmemBytes);
+    M2LTiles tiles{};
+    k_m2l<P, TN, 4, 8, NSTAGE, 1><<<ntiles, Cfg::NTHREADS, Cfg::kSmemBytes, s>>>(
+        tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status);
+    note_launches(1);
+}
+
+void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
+                      const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
+                      const float *ops, const float *M, float *Lc, const float *zero_block, int *status,
+                      cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    switch (P) {
+    case 4: launch_m2l_tiles_t<4, 4>(tdesc, ntiles, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
+    case 6: launch_m2l_tiles_t<6, 4>(tdesc, ntiles, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
+    case 8: launch_m2l_tiles_t<8, 4>(tdesc, ntiles, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
+    case 10: launch_m2l_tiles_t<10, 3>(tdesc, ntiles, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s); break;
+    }
 }
 
 void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,

@@ -20,6 +20,7 @@ namespace gbfmm {
 constexpr int kP2PThreads = 128;
 constexpr int kP2PTargetsPerThread = 2;
 constexpr int kSrcCap = 1024;
+constexpr int kRowCap = 32;
 
 template <bool SOFT>
 GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi, float &gx, float &gy, float &gz)
@@ -48,7 +49,8 @@ struct Kahan {
 };
 
 template <bool SOFT, int TPT>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__restrict__ sx,
+__global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const int32_t *__restrict__ leaves,
+                                                     const float4 *__restrict__ sx,
                                                      const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                                      const uint32_t *__restrict__ p2p_offs,
                                                      const int32_t *__restrict__ p2p_ids, const float4 *__restrict__ far,
@@ -57,26 +59,16 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__rest
 {
     __shared__ float4 src[kSrcCap];
     __shared__ float4 red[TPT][kP2PThreads];
-    __shared__ int s_cb[27], s_pref[28];
-    const int64_t leaf = blockIdx.x;
-    const int64_t g = level_offset(L) + leaf;
+    __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1];
+    // target leaf: dense leaf blockIdx.x of a uniform depth-L tree (list row = leaf), or the
+    // listed cell of an adaptive tree (list row = cell index)
+    const int64_t leaf = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
+    const int64_t g = leaves ? leaf : level_offset(L) + leaf;
     const int b0 = begin[g], e0 = end[g];
     if (e0 <= b0) return;
     const int tid = threadIdx.x;
     const uint32_t r0 = p2p_offs[leaf];
     const int nrow = (int)(p2p_offs[leaf + 1] - r0);
-    if (tid < nrow) {
-        const int c = p2p_ids[r0 + tid];
-        s_cb[tid] = begin[c];
-        s_pref[tid + 1] = end[c] - begin[c];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        s_pref[0] = 0;
-        for (int k = 0; k < nrow; ++k) s_pref[k + 1] += s_pref[k];
-    }
-    __syncthreads();
-    const int S = s_pref[nrow];
     const int T = e0 - b0;
     for (int tc = 0; tc < T; tc += TPT * kP2PThreads) {
         const int Tc = min(T - tc, TPT * kP2PThreads);
@@ -96,22 +88,41 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const float4 *__rest
             tz[h] = p.z;
             phi[h] = gx[h] = gy[h] = gz[h] = 0.f;
         }
-        for (int sc = 0; sc < S; sc += kSrcCap) {
-            const int chunk = min(kSrcCap, S - sc);
+        // source cells in blocks of kRowCap list entries (a uniform tree has <= 27; an
+        // adaptive leaf may touch more, smaller leaves)
+        for (int rb = 0; rb < nrow; rb += kRowCap) {
+            const int nr = min(kRowCap, nrow - rb);
             __syncthreads();
-            for (int k = tid; k < chunk; k += kP2PThreads) {
-                const int s = sc + k;
-                int e = 0;
-                while (s >= s_pref[e + 1]) ++e;
-                src[k] = __ldg(&sx[s_cb[e] + (s - s_pref[e])]);
+            if (tid < nr) {
+                const int c = p2p_ids[r0 + rb + tid];
+                s_cb[tid] = begin[c];
+                s_pref[tid + 1] = end[c] - begin[c];
             }
             __syncthreads();
-            if (active) {
+            if (tid == 0) {
+                s_pref[0] = 0;
+                for (int k = 0; k < nr; ++k) s_pref[k + 1] += s_pref[k];
+            }
+            __syncthreads();
+            const int S = s_pref[nr];
+            for (int sc = 0; sc < S; sc += kSrcCap) {
+                const int chunk = min(kSrcCap, S - sc);
+                if (sc > 0) __syncthreads();
+                for (int k = tid; k < chunk; k += kP2PThreads) {
+                    const int s = sc + k;
+                    int e = 0;
+                    while (s >= s_pref[e + 1]) ++e;
+                    src[k] = __ldg(&sx[s_cb[e] + (s - s_pref[e])]);
+                }
+                __syncthreads();
+                if (active) {
 #pragma unroll 4
-                for (int j = grp; j < chunk; j += G) {
-                    const float4 s = src[j];
+                    for (int j = grp; j < chunk; j += G) {
+                        const float4 s = src[j];
 #pragma unroll
-                    for (int h = 0; h < TPT; ++h) pair<SOFT>(tx[h], ty[h], tz[h], s, eps2, phi[h], gx[h], gy[h], gz[h]);
+                        for (int h = 0; h < TPT; ++h)
+                            pair<SOFT>(tx[h], ty[h], tz[h], s, eps2, phi[h], gx[h], gy[h], gz[h]);
+                    }
                 }
             }
         }
@@ -154,9 +165,26 @@ void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const 
     unsigned grid = (unsigned)(int64_t(1) << (3 * L));
     constexpr int TPT = kP2PTargetsPerThread;
     if (eps2 > 0.f)
-        k_p2p<true, TPT><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
+        k_p2p<true, TPT><<<grid, kP2PThreads, 0, s>>>(L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2,
+                                                      out);
     else
-        k_p2p<false, TPT><<<grid, kP2PThreads, 0, s>>>(L, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out);
+        k_p2p<false, TPT><<<grid, kP2PThreads, 0, s>>>(L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm,
+                                                       eps2, out);
+    note_launches(1);
+}
+
+void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+                      const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
+                      const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
+{
+    if (n <= 0 || nleaves <= 0) return;
+    constexpr int TPT = kP2PTargetsPerThread;
+    if (eps2 > 0.f)
+        k_p2p<true, TPT><<<(unsigned)nleaves, kP2PThreads, 0, s>>>(0, leaves, sx, begin, end, u_offs, u_ids, far, perm,
+                                                                   eps2, out);
+    else
+        k_p2p<false, TPT><<<(unsigned)nleaves, kP2PThreads, 0, s>>>(0, leaves, sx, begin, end, u_offs, u_ids, far, perm,
+                                                                    eps2, out);
     note_launches(1);
 }
 

@@ -314,7 +314,8 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 // ------------------------------------------------------------------------------------------
 constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+template <class KeyT>
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const KeyT *__restrict__ keys, int64_t n, int shift,
                                                         uint32_t mask, uint32_t *__restrict__ hist, int64_t nblk)
 {
     __shared__ uint32_t cnt[256];
@@ -324,14 +325,15 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint32_t *__restri
 #pragma unroll 4
     for (int r = 0; r < kRsItems; ++r) {
         int64_t i = base + r * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & mask], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t *__restrict__ kin,
-                                                           const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+template <class KeyT>
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const KeyT *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
                                                            uint32_t *__restrict__ vout, int64_t n, int shift,
                                                            uint32_t mask, const uint32_t *__restrict__ hist_scan,
                                                            int64_t nblk, const float4 *__restrict__ gx,
@@ -349,8 +351,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t *__res
     for (int r = 0; r < kRsItems; ++r) {
         int64_t i = tbase + r * kRsThreads + tid;
         bool valid = i < n;
-        uint32_t key = valid ? kin[i] : 0u, val = valid ? vin[i] : 0u;
-        uint32_t d = valid ? ((key >> shift) & mask) : 256u;
+        const KeyT key = valid ? kin[i] : KeyT(0);
+        const uint32_t val = valid ? vin[i] : 0u;
+        uint32_t d = valid ? ((uint32_t)(key >> shift) & mask) : 256u;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
@@ -385,11 +388,13 @@ __global__ void k_gather_identity(const float4 *__restrict__ x, float4 *__restri
     if (i < n) sx[i] = x[i];
 }
 
-void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
-                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
-                        uint32_t **idx_out, cudaStream_t s)
+template <class KeyT>
+static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
+                          int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, KeyT **keys_out,
+                          uint32_t **idx_out, cudaStream_t s)
 {
-    uint32_t *kin = k0, *kout = k1, *vin = v0, *vout = v1;
+    KeyT *kin = k0, *kout = k1;
+    uint32_t *vin = v0, *vout = v1;
     if (bits <= 0 || n <= 1) {
         if (n > 0) {
             k_gather_identity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, sx, n);
@@ -403,20 +408,34 @@ void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, 
         int nb = bits - shift < 8 ? bits - shift : 8;
         uint32_t mask = (1u << nb) - 1u;
         bool last = shift + 8 >= bits;
-        k_rs_hist<<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, n, shift, mask, hist, nblk);
+        k_rs_hist<KeyT><<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, n, shift, mask, hist, nblk);
         launch_exclusive_scan(hist, hist, 256 * nblk, scan_tmp, s);
-        k_rs_scatter<<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, mask, hist, nblk, x,
-                                                           last ? sx : nullptr);
+        k_rs_scatter<KeyT><<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, mask, hist, nblk,
+                                                                 x, last ? sx : nullptr);
         note_launches(2);
-        uint32_t *t = kin;
+        KeyT *t = kin;
         kin = kout;
         kout = t;
-        t = vin;
+        uint32_t *u = vin;
         vin = vout;
-        vout = t;
+        vout = u;
     }
     *keys_out = kin;
     *idx_out = vin;
+}
+
+void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
+                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
+                        uint32_t **idx_out, cudaStream_t s)
+{
+    sort_gather_t<uint32_t>(k0, k1, v0, v1, n, bits, hist, nblk, scan_tmp, x, sx, keys_out, idx_out, s);
+}
+
+void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
+                          uint32_t *hist, int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx,
+                          uint64_t **keys_out, uint32_t **idx_out, cudaStream_t s)
+{
+    sort_gather_t<uint64_t>(k0, k1, v0, v1, n, bits, hist, nblk, scan_tmp, x, sx, keys_out, idx_out, s);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -20,7 +20,8 @@ HEADER = os.path.join(ROOT, "include", "gbfmm.h")
 GBFMM_OK, GBFMM_EINVAL, GBFMM_ENOMEM, GBFMM_ECUDA, GBFMM_ETIMEOUT, GBFMM_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
 METHOD_FMM, METHOD_TREECODE = 0, 1
-LIST_P2P, LIST_M2L = 0, 1
+TREE_UNIFORM, TREE_ADAPTIVE = 0, 1
+LIST_P2P, LIST_M2L, LIST_U, LIST_V, LIST_W, LIST_X = range(6)
 FLAG_STAGE_TIMING = 1
 STAGES = ["box+keys", "sort", "cells+lists", "P2M", "M2M", "M2L/M2P", "L2L", "L2P", "P2P", "operators"]
 
@@ -80,6 +81,7 @@ def lib():
         "gbfmm_export_tree": (i, [P, P, P, P, P, P]),
         "gbfmm_export_lists": (i, [P, i, P, P, i64, ctypes.POINTER(i64)]),
         "gbfmm_export_expansions": (i, [P, i, P]),
+        "gbfmm_export_adaptive_tree": (i, [P, P, ctypes.POINTER(i64), P, P, P, P, P, P]),
         "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
         "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
@@ -192,6 +194,25 @@ def gbfmm_export_tree(ctx, n: int, ncells: int) -> dict:
                 count=count)
 
 
+def gbfmm_export_adaptive_tree(ctx, n: int) -> dict:
+    import numpy as np
+
+    nc = ctypes.c_int64()
+    _check(ctx, lib().gbfmm_export_adaptive_tree(ctx, None, ctypes.byref(nc), None, None, None, None, None, None))
+    c = nc.value
+    os_ = np.zeros(4)
+    level = np.zeros(c, dtype=np.int32)
+    key = np.zeros(c, dtype=np.uint64)
+    begin = np.zeros(c, dtype=np.int32)
+    count = np.zeros(c, dtype=np.int32)
+    parent = np.zeros(c, dtype=np.int32)
+    perm = np.zeros(n, dtype=np.uint32)
+    _check(ctx, lib().gbfmm_export_adaptive_tree(ctx, _np_ptr(os_), ctypes.byref(nc), _np_ptr(level), _np_ptr(key),
+                                                 _np_ptr(begin), _np_ptr(count), _np_ptr(parent), _np_ptr(perm)))
+    return dict(origin=os_[:3].copy(), side=float(os_[3]), ncells=c, level=level, key=key, begin=begin,
+                count=count, parent=parent, perm=perm)
+
+
 def gbfmm_export_lists(ctx, kind: int, rows: int) -> tuple:
     import numpy as np
 
@@ -276,7 +297,7 @@ class FMM:
         return gbfmm_plan(self.params, n)
 
     def ensure_workspace(self, n: int) -> torch.Tensor:
-        _, ws = gbfmm_plan(self.params, n)
+        _, ws = gbfmm_plan(self.params, n)  # 0 for the adaptive tree (library-owned buffers)
         if self.workspace is None or self.workspace.numel() < ws:
             self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
         return self.workspace

@@ -1,0 +1,194 @@
+"""GPU parity of the adaptive-tree FMM (U, V, W, X lists of Cheng, Greengard & Rokhlin 1999,
+the FMM the paper cites for its translation operators) against the FP64 adaptive oracle.
+
+Tolerances as for the uniform tree:
+  * cells (level, key, particle range, parent), sort permutation and the four lists: bit-exact;
+  * potentials and gradients vs the oracle adaptive FMM (same tree, same p): relative L2 <= 1e-5;
+  * expansions: per-degree relative L2 of the scaled coefficients <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1010_1482_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FMM = 1e-5
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1010_1482_gb300 import gbfmm
+
+    gbfmm.lib()
+    return gbfmm
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.gbfmm_create(0)
+    yield c
+    G.gbfmm_destroy(c)
+
+
+def run(G, ctx, x, **kw):
+    prm = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, **kw)
+    lv, ws = G.gbfmm_plan(prm, len(x))
+    assert lv == O.ADAPTIVE_MAX_LEVEL and ws == 0
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    out = torch.empty_like(xd)
+    G.gbfmm_evaluate(ctx, prm, xd, out, torch.empty(0, dtype=torch.uint8, device="cuda"))
+    G.gbfmm_sync_status(ctx)
+    return out.cpu().numpy().astype(np.float64)
+
+
+def sorted_rows(offs, ids):
+    ids = ids.copy()
+    for r in range(len(offs) - 1):
+        ids[offs[r]:offs[r + 1]] = np.sort(ids[offs[r]:offs[r + 1]])
+    return ids
+
+
+TREE_CASES = [("plummer", 30000, 32), ("plummer", 100000, 64), ("uniform", 20000, 16)]
+
+
+@pytest.mark.parametrize("dist,n,leaf", TREE_CASES)
+def test_adaptive_tree_and_lists_bit_exact(G, ctx, dist, n, leaf):
+    x = inputs.make_particles(n, dist, 3000 + n)
+    run(G, ctx, x, p=4, leaf_size=leaf)
+    t = O.build_adaptive_tree(x, leaf)
+    g = G.gbfmm_export_adaptive_tree(ctx, n)
+    assert np.array_equal(g["origin"], t["origin"]) and g["side"] == t["side"]
+    assert g["ncells"] == t["ncells"]
+    for k in ("level", "begin", "count", "parent"):
+        assert np.array_equal(g[k], t[k]), k
+    assert np.array_equal(g["key"], t["key"])
+    assert np.array_equal(g["perm"].astype(np.int64), t["perm"])
+    ls = O.build_adaptive_lists(t)
+    nc = t["ncells"]
+    for kind, name in ((G.LIST_U, "u"), (G.LIST_V, "v"), (G.LIST_W, "w"), (G.LIST_X, "x")):
+        offs, ids = G.gbfmm_export_lists(ctx, kind, nc)
+        assert np.array_equal(offs, ls[name + "_offs"]), name
+        assert np.array_equal(ids, sorted_rows(ls[name + "_offs"], ls[name + "_ids"])), name
+    if dist == "plummer":
+        # a clustered set has leaves at several levels: W and X are not empty
+        assert len(ls["w_ids"]) > 0 and len(ls["x_ids"]) > 0
+
+
+@pytest.mark.parametrize("p", [4, 6, 8, 10])
+def test_adaptive_fmm_matches_oracle(G, ctx, p):
+    n, leaf = 20000, 32
+    x = inputs.plummer(n, 4242)
+    out = run(G, ctx, x, p=p, leaf_size=leaf)
+    ref = O.fmm_adaptive(x, p, leaf)["out"]
+    assert O.rel_l2(out[:, 0], ref[:, 0]) <= TOL_FMM
+    assert O.rel_l2(out[:, 1:], ref[:, 1:]) <= TOL_FMM
+    d = O.direct(x)
+    e_or = O.rel_l2(ref[:, 1:], d[:, 1:])
+    assert O.rel_l2(out[:, 1:], d[:, 1:]) <= e_or + TOL_FMM
+
+
+@pytest.mark.parametrize("p", [4, 10])
+def test_adaptive_expansions_match_oracle(G, ctx, p):
+    n, leaf = 20000, 32
+    x = inputs.plummer(n, 515)
+    run(G, ctx, x, p=p, leaf_size=leaf)
+    r = O.fmm_adaptive(x, p, leaf, keep=True)
+    t = r["tree"]
+    nc = t["ncells"]
+    Mg = G.gbfmm_export_expansions(ctx, 0, nc, p)
+    Lg = G.gbfmm_export_expansions(ctx, 1, nc, p)
+    h = t["side"] / 2.0 ** t["level"]
+    deep = t["level"] >= 2
+    assert np.all(Mg[~deep] == 0) and np.all(Lg[~deep] == 0)
+    for n_ in range(p):
+        cols = slice(n_ * (n_ + 1) // 2, (n_ + 1) * (n_ + 2) // 2)
+        for A, B, sc in ((Mg, r["M"], h ** (-n_)), (Lg, r["Lc"], h ** (n_ + 1))):
+            a = A[deep, cols] * sc[deep, None]
+            b = B[deep, cols] * sc[deep, None]
+            assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), n_
+
+
+@pytest.mark.parametrize("kind", ["one", "two", "below_leaf", "duplicates", "shell"])
+def test_adaptive_degenerate_inputs(G, ctx, kind):
+    if kind == "one":
+        x, leaf = np.array([[0.3, 0.2, 0.1, 1.0]], dtype=np.float32), 64
+    elif kind == "two":
+        x, leaf = np.array([[0.3, 0.2, 0.1, 1.0], [0.7, 0.1, 0.9, 2.0]], dtype=np.float32), 64
+    elif kind == "below_leaf":
+        x, leaf = inputs.uniform_cube(50, 4), 64
+    elif kind == "duplicates":
+        # 200 copies of one point: its cell splits down to level 21 and stays over-full there
+        base = inputs.uniform_cube(3000, 8)
+        dup = np.repeat(base[:1], 200, axis=0)
+        x, leaf = np.concatenate([base, dup]).astype(np.float32), 16
+    else:  # particles on a thin spherical shell: leaves at many levels
+        u = inputs.uniform_cube(8000, 9).astype(np.float64)
+        v = u[:, :3] - 0.5
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        x = np.concatenate([v * 0.5 + 0.5, u[:, 3:]], axis=1).astype(np.float32)
+        leaf = 16
+    out = run(G, ctx, x, p=6, leaf_size=leaf)
+    ref = O.fmm_adaptive(x, 6, leaf)["out"]
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    assert np.max(np.abs(out - ref)) <= 2e-5 * scale
+    if kind == "one":
+        assert np.all(out == 0.0)
+
+
+def test_adaptive_uniform_lattice_reduces_to_uniform_tree(G, ctx):
+    # 16^3 lattice points, leaf 8: every leaf sits at level 3 and the adaptive result equals
+    # the uniform-tree result (same lists, W = X = empty)
+    g = (np.arange(16) + 0.5) / 16
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    q = inputs.uniform_cube(4096, 11)[:, 3]
+    x = np.stack([X.ravel(), Y.ravel(), Z.ravel(), q], axis=1).astype(np.float32)
+    ad = run(G, ctx, x, p=8, leaf_size=8)
+    prm = G.gbfmm_default_params(p=8, leaf_size=8)
+    L, ws = G.gbfmm_plan(prm, len(x))
+    assert L == 3
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    G.gbfmm_evaluate(ctx, prm, xd, out, torch.empty(ws, dtype=torch.uint8, device="cuda"))
+    G.gbfmm_sync_status(ctx)
+    un = out.cpu().numpy().astype(np.float64)
+    assert O.rel_l2(ad, un) <= 1e-6
+
+
+def test_adaptive_host_path_timing_and_treecode_rejected(G, ctx):
+    x = inputs.plummer(10000, 31)
+    prm = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, p=4, leaf_size=32, flags=G.FLAG_STAGE_TIMING)
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.empty_like(xh).pin_memory()
+    G.gbfmm_evaluate_host(ctx, prm, xh, oh)
+    ref = O.fmm_adaptive(x, 4, 32)["out"]
+    assert O.rel_l2(oh.numpy().astype(np.float64), ref) <= TOL_FMM
+    st = G.gbfmm_stage_times(ctx)
+    assert st["P2P"] > 0 and st["M2L/M2P"] > 0
+    assert G.gbfmm_last_launch_count(ctx) > 0
+    bad = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, method=G.METHOD_TREECODE)
+    with pytest.raises(G.GbfmmError) as ei:
+        G.gbfmm_plan(bad, 100)
+    assert ei.value.code == G.GBFMM_EUNSUPPORTED
+    with pytest.raises(G.GbfmmError):  # the uniform-tree export refuses an adaptive evaluation
+        G.gbfmm_export_tree(ctx, len(x), 1)
+
+
+def test_large_plummer_p8_sampled(G, ctx):
+    """16,777,216 Plummer particles (scale radius 1, truncated at r = 20), equal masses 1/N,
+    adaptive tree, p = 8, leaf 64, in the bench's launch shape: 2048 seeded targets against
+    the FP64 direct sum over all sources, 256 of them against the FP64 adaptive FMM."""
+    w = inputs.workload("plummer_16m_p8")
+    x = inputs.make_particles(w["n"], w["dist"], w["seed"])
+    out = run(G, ctx, x, p=w["p"], leaf_size=w["leaf_size"])
+    assert np.all(np.isfinite(out))
+    tg = inputs.sample_indices(w["n"], 2048, w["seed"])
+    d = O.direct(x, targets=tg)
+    e_phi = O.rel_l2(out[tg, 0], d[:, 0])
+    e_grad = O.rel_l2(out[tg, 1:], d[:, 1:])
+    assert e_phi <= 1e-4 and e_grad <= 1e-4, (e_phi, e_grad)
+    sub = tg[:256]
+    f = O.fmm_adaptive(x, w["p"], w["leaf_size"], targets=sub)["out"]
+    assert O.rel_l2(out[sub], f[sub]) <= TOL_FMM
