@@ -571,7 +571,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamSynchronize(s);
         std::vector<uint32_t> hcur(hcnt.size());
         std::vector<int4> tiles;
-        constexpr int TN = kM2LTargetsPerTile;
+        const bool tc = ops.m2l_tc != nullptr;
+        const int TN = tc ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
         uint32_t acc = 0;
         for (int l = maxl; l >= 2; --l)
             for (int tau = 0; tau < 8; ++tau) {
@@ -590,9 +591,14 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                                                               A.key.as<uint64_t>(), gcur, A.tlist.as<int32_t>());
         note_launches(1);
         cudaStreamSynchronize(s);  // the host tile vectors go out of scope
-        launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
-                         A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
-                         A.vcode.as<uint16_t>(), ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
+        if (tc)
+            launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
+                                A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
+                                A.vcode.as<uint16_t>(), ops.m2l_tc, M, Lc, ctx->d_status, s);
+        else
+            launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
+                             A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
+                             A.vcode.as<uint16_t>(), ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
         launch_p2l_cells(P, ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(),
                          A.count.as<int32_t>(), A.loffs[kListX].as<uint32_t>(), A.lids[kListX].as<int32_t>(), box,
                          A.sx.as<float4>(), Lc, s);

@@ -16,6 +16,7 @@
 namespace gbfmm {
 void init_expansion_constants();
 void init_m2l_constants();
+void init_m2l_tc_constants();
 }  // namespace gbfmm
 
 using namespace gbfmm;
@@ -183,6 +184,11 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     if ((e = cudaMalloc(&c.l2l, 8 * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
     launch_build_operators(P, c.m2l, c.m2m, c.l2l, s);
+    if (m2l_use_tc()) {
+        if ((e = cudaMalloc(&c.m2l_tc, m2l_tc_table_floats(P) * sizeof(float))) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMalloc(m2l tensor-core ops)");
+        launch_build_m2l_tc(P, c.m2l, c.m2l_tc, s);
+    }
     c.P = P;
     c.built = true;
     *built_now = true;
@@ -231,6 +237,7 @@ int gbfmm_create(gbfmm_ctx **out, int device)
     if (ok) {
         init_expansion_constants();
         init_m2l_constants();
+        init_m2l_tc_constants();
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     if (!ok) {
@@ -254,6 +261,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
         cudaFree(c.m2l);
         cudaFree(c.m2m);
         cudaFree(c.l2l);
+        cudaFree(c.m2l_tc);
     }
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
@@ -373,7 +381,9 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
     mark(5);
     if (L >= 2) {
-        if (prm->method == GBFMM_METHOD_FMM)
+        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc)
+            launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
+        else if (prm->method == GBFMM_METHOD_FMM)
             launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
         else
             launch_m2p(P, L, box, sx, begin, end, m2l_offs, m2l_ids, M, far, s);

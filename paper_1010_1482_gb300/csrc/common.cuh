@@ -218,6 +218,18 @@ void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist
                       const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
                       const float *ops, const float *M, float *Lc, const float *zero_block, int *status,
                       cudaStream_t s);
+// M2L on the tcgen05 tensor cores (3xTF32), 128 targets per CTA
+constexpr int kM2LTcTargetsPerTile = 128;
+bool m2l_use_tc();
+size_t m2l_tc_table_floats(int P);
+void launch_build_m2l_tc(int P, const float *ops, float *tc, cudaStream_t s);
+void launch_m2l_tc(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
+                   const int32_t *m2l_ids, const uint16_t *m2l_code, const float *optc, const float *M, float *Lc,
+                   int *status, cudaStream_t s);
+void launch_m2l_tc_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
+                         const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
+                         const uint16_t *m2l_code, const float *optc, const float *M, float *Lc, int *status,
+                         cudaStream_t s);
 void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *begin,
                       const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const Box *box,
                       const float4 *sx, float *Lc, cudaStream_t s);

@@ -18,6 +18,7 @@ constexpr int kAdaptiveMaxLevel = 21;  // 63-bit keys: 21 bits per axis
 struct OpsCache {
     int P = 0;
     float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
+    float *m2l_tc = nullptr;  // tensor-core operator blocks (hi | lo), when the tcgen05 M2L is on
     bool built = false;
 };
 

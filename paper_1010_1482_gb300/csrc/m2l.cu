@@ -16,6 +16,7 @@
 // runs inside the offset loop.  Every wait is bounded (1 s of %globaltimer); on timeout the
 // kernel raises the status word, waits (bounded) for its copies in flight and returns.
 #include "common.cuh"
+#include "ptx.cuh"
 
 #include <stdlib.h>
 
@@ -38,83 +39,6 @@ void init_m2l_constants()
     cudaMemcpyToSymbol(c_codes, codes, sizeof(codes));
 }
 
-// ---- PTX wrappers -------------------------------------------------------------------------
-GB_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-GB_DEV void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-GB_DEV void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-GB_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-GB_DEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-GB_DEV void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-GB_DEV void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-GB_DEV bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-GB_DEV uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// try_wait with a suspend-time hint: the waiting thread sleeps in hardware until the phase
-// completes or the hint (ns) expires, instead of spinning on issue slots
-GB_DEV bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with parity `parity` to complete: true on completion, false after
-// ~limit_ns or as soon as *abort is raised by another warp.
-GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns, volatile int *abort)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if ((abort && *abort) || global_ns() - t0 > limit_ns) return false;
-        __nanosleep(64);
-    }
-}
-
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
 
 // Exercises the bounded wait on its own: one thread waits on an mbarrier that no thread
