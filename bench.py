@@ -44,6 +44,17 @@ def dist_env():
     return ws, rank, local
 
 
+def tf32_peak_tflops() -> tuple[float, str]:
+    """Dense TF32 tensor peak: the measured BF16 dense burst figure x the nominal TF32/BF16
+    ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16 = float(mp["bf16_tflops"])
+        return bf16 * 1.1 / 2.25, f"measured BF16 dense burst {bf16:.1f} TFLOP/s x nominal TF32/BF16 1.1/2.25 (of measured)"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback BF16 1900 TFLOP/s x nominal TF32/BF16 1.1/2.25 (of fallback)"
+
+
 def fp32_peak_tflops(sm_count: int) -> tuple[float, float]:
     """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FFMA) x max SM clock."""
     mhz = 2070.0
@@ -268,6 +279,28 @@ def run_gpu(args, w):
     m2l_ms = stages.get("M2L/M2P", float("nan"))
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
+    if os.environ.get("GBFMM_M2L_TC", "1") != "0":
+        # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to 8,
+        # 3 TF32 MMAs per product (3xTF32)
+        tpeak, tbasis = tf32_peak_tflops()
+        tiles = sum(8 * -(-(8 ** (l - 1)) // 128) for l in range(2, L + 1))
+        npad, kpad = -(-P * P // 16) * 16, -(-P * P // 8) * 8
+        tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * kpad
+        roofline = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": m2l_tf / tpeak,
+                    "traffic": traffic_from_profile("m2l_tc.cu", "m2l_tc_uniform_1m_p10.md"),
+                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
+                    "peak_basis": tbasis,
+                    "tensor_flop_issued": tensor_flops,
+                    "tensor_pipe_frac": tensor_flops / (m2l_ms / 1e3) / 1e12 / tpeak,
+                    "note": "FP32-accurate products as 3 TF32 MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 "
+                            "by construction; tensor_pipe_frac counts every issued MMA flop"}
+    else:
+        roofline = {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
+                    "frac": m2l_tf / peak,
+                    "traffic": traffic_from_profile("m2l.cu", "m2l_uniform_1m_p10.md"),
+                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
+                    "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -275,13 +308,10 @@ def run_gpu(args, w):
         "config": {"workload": w["name"], "n": n, "p": P, "leaf_size": w["leaf_size"], "levels": L,
                    "distribution": w["dist"], "parallelism": f"replicas x{ws}",
                    "l2": "flushed between steps (256 MiB write outside the per-step events)"},
-        "roofline": {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
-                     "frac": m2l_tf / peak,
-                     "traffic": traffic_from_profile("m2l.cu", "m2l_uniform_1m_p10.md"),
-                     "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
-                     "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"},
+        "roofline": roofline,
         "kernels": {"p2p": {"achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
-                            "flop_per_pair": 20}},
+                            "flop_per_pair": 20, "peak": peak, "bound": "alu",
+                            "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"}},
         "stages_ms": stages,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},
         "gpu_launches": launches,

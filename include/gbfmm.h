@@ -64,6 +64,11 @@ enum {
 
 /* flags */
 #define GBFMM_FLAG_STAGE_TIMING 1 /* record CUDA events between stages (gbfmm_stage_times) */
+/* run M2L on the FP32 CUDA cores instead of the tcgen05 tensor cores (3xTF32 with FP32
+ * accumulation; the default).  Both compute Eq. 4 over the same lists; they differ by
+ * rounding only.  Setting the environment variable GBFMM_M2L_TC=0 before the first
+ * evaluation of an order p disables the tensor-core path for the whole process. */
+#define GBFMM_FLAG_M2L_CUDA_CORES 2
 
 /*
  * Parameters of one evaluation (Section "Fast N-body simulation").

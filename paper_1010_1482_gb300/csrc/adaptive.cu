@@ -571,7 +571,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamSynchronize(s);
         std::vector<uint32_t> hcur(hcnt.size());
         std::vector<int4> tiles;
-        const bool tc = ops.m2l_tc != nullptr;
+        const bool tc = ops.m2l_tc != nullptr && !(prm->flags & GBFMM_FLAG_M2L_CUDA_CORES);
         const int TN = tc ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
         uint32_t acc = 0;
         for (int l = maxl; l >= 2; --l)

@@ -381,7 +381,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
     mark(5);
     if (L >= 2) {
-        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc)
+        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !(prm->flags & GBFMM_FLAG_M2L_CUDA_CORES))
             launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
         else if (prm->method == GBFMM_METHOD_FMM)
             launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);

@@ -12,20 +12,22 @@
 // rounding of lo are below 2^-21 of |x|.  The operator halves are split once, when the table
 // is built; the source halves are split by the threads that gather them.
 //
-// Pipeline (one CTA per tile, warp-specialised, NSTAGE shared-memory stages; a stage holds
-// one K-chunk of one offset):
-//   warps 0-3 (one thread per target): walk the target's CSR list, load the source's K-chunk
-//     (float4, zeros for a missing source), split it and store A_hi / A_lo in the canonical
-//     no-swizzle K-major layout; warp 0 also starts the bulk copy of the operator chunk
-//     (B_hi | B_lo, stored pre-laid-out in global memory) on the stage's "full" mbarrier;
-//   warp 4: allocates the TMEM accumulator; one thread waits on "full", issues the MMAs of
-//     the stage (3 per 8-wide K step) and commits them to the stage's "empty" mbarrier;
-//   drains (warps 0-3): offset o accumulates into TMEM buffer o & 1 (a chain of 3 x K/8
-//     MMAs).  Once it is complete, each thread loads its TMEM lane (its target's row of the
-//     partial) and adds it to FP32 registers, then releases the buffer for offset o + 2.  The
-//     tensor cores' accumulation rounds toward zero; short chains keep that bias at a few
-//     units of 2^-24, and the sum over the 189 offsets is rounded to nearest.
-//   epilogue: each thread writes its target's p^2 local coefficients from the registers.
+// Pipeline (one CTA per tile, warp-specialised, NSTAGE stages; a stage is one K-chunk of one
+// offset).  The A operand lives in tensor memory, so shared memory carries only the operator:
+//   warps 0-7, converters (two per TMEM lane quadrant; thread = target row, K half h): walk the
+//     target's CSR list, load each step's source K-chunk into registers two steps ahead (zeros
+//     for a missing source or k >= p^2), split it into TF32 halves and store them with
+//     tcgen05.st into the stage's A_hi / A_lo columns of its TMEM lane; warp 0 also starts the
+//     bulk copies of the operator chunk (B_hi | B_lo, stored pre-laid-out in the canonical
+//     no-swizzle K-major layout in global memory) on the stage's "full" mbarrier;
+//   warp 8: allocates TMEM; one thread waits on "full", issues the MMAs of the stage (3 per
+//     8-wide K step, A from TMEM, B from shared memory) and commits them to "empty";
+//   drains (warps 0-7): offset o accumulates into TMEM accumulator o & 1 (a chain of 3 x K/8
+//     MMAs).  Once it is complete, each thread loads half of its TMEM lane (its target's row of
+//     the partial) and adds it to FP32 registers, then releases the accumulator for offset
+//     o + 2.  The tensor cores' accumulation rounds toward zero; short chains keep that bias at
+//     a few units of 2^-24, and the sum over the 189 offsets is rounded to nearest;
+//   epilogue: each thread writes its half of its target's p^2 local coefficients.
 // Every wait is bounded (1 s of %globaltimer); on timeout the kernel raises the status word,
 // lets its copies and MMAs in flight finish (bounded), frees its TMEM and returns.
 #include "common.cuh"
@@ -52,27 +54,42 @@ void init_m2l_tc_constants()
     cudaMemcpyToSymbol(c_tc_codes, codes, sizeof(codes));
 }
 
-// Shapes per order.  KS = K steps of 8 per offset, split into NCH chunks of (nearly) equal size.
-template <int P>
+// Shapes per order.  KS = K steps of 8 per offset, split into NCH chunks of (nearly) equal size
+// (at most CK steps each); NS pipeline stages.
+template <int P, int CK, int NS>
 struct TcCfg {
     static constexpr int PP = P * P;
-    static constexpr int PR = (PP + 7) / 8 * 8;      // rows of the CUDA-core operator table
     static constexpr int KP = (PP + 7) / 8 * 8;      // K, padded to the MMA's K step
     static constexpr int NP = (PP + 15) / 16 * 16;   // N, padded to a multiple of 16
+    static constexpr int NH = NP / 2;                // output columns drained per thread
     static constexpr int KS = KP / 8;
-    static constexpr int CKMAX = P == 10 ? 4 : (P == 8 ? 4 : (P == 6 ? 5 : 2));  // K steps per chunk (max)
-    static constexpr int NCH = (KS + CKMAX - 1) / CKMAX;
+    static constexpr int NCH = (KS + CK - 1) / CK;
     static constexpr int KCMAX = 8 * ((KS + NCH - 1) / NCH);  // K width of the largest chunk
     static constexpr int TM = 128;                   // targets per tile (MMA M)
-    static constexpr int NSTAGE = P == 10 ? 3 : (P == 6 ? 3 : 4);
-    static constexpr int TMEM_COLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));  // two accumulators
-    static constexpr int A_FLOATS = TM * KCMAX;      // one of A_hi / A_lo
-    static constexpr int STAGE_FLOATS = 2 * A_FLOATS + 2 * NP * KCMAX;
-    static constexpr size_t kSmemBytes = (size_t)NSTAGE * STAGE_FLOATS * sizeof(float);
-    static constexpr int BLOCK_FLOATS = 2 * NP * KCMAX;  // one (offset, chunk) block of the table
-    static constexpr int NTHREADS = 160;
-    static_assert(NP >= 16 && NP <= 256 && NP % 16 == 0, "MMA N");
+    static constexpr int NSTAGE = NS;
+    // TMEM: two accumulators D0, D1 (NP columns each) at column 0, A stages (A_hi | A_lo, 32
+    // columns each) from column 256
+    static constexpr int TMEM_COLS = 512;
+    static constexpr int A_COL0 = 256;
+    static constexpr int B_FLOATS = 2 * NP * KCMAX;  // one stage: B_hi | B_lo
+    // at least 116 KB of shared memory: one CTA per SM, so the whole of TMEM is this CTA's
+    static constexpr size_t kStageBytes = (size_t)NSTAGE * B_FLOATS * sizeof(float);
+    static constexpr size_t kSmemBytes = kStageBytes > 116 * 1024 ? kStageBytes : 116 * 1024;
+    static constexpr int NTHREADS = 288;             // 8 converter warps (2 per TMEM lane quadrant), 1 MMA warp
+    static_assert(NP >= 16 && NP <= 128 && NP % 16 == 0, "MMA N (two accumulators below column 256)");
+    static_assert(KCMAX <= 32, "a K chunk fits a 32-column TMEM slot");
+    static_assert(A_COL0 + 64 * NS <= TMEM_COLS, "TMEM A stages");
     static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+
+// operator table per offset code: T_hi then T_lo, each [KP/4][NP][4] (the canonical no-swizzle
+// K-major layout of the N x K operand; a K-chunk [k0, k0 + kw) is the contiguous range
+// starting at float k0 * NP)
+template <int P>
+struct TcTable {
+    static constexpr int PP = P * P, PR = (PP + 7) / 8 * 8, KP = (PP + 7) / 8 * 8, NP = (PP + 15) / 16 * 16;
+    static constexpr int HALF = KP * NP;
+    static constexpr int CODE_FLOATS = 2 * HALF;
 };
 
 GB_DEV void chunk_range(int c, int KS, int NCH, int &k0, int &kw)
@@ -85,41 +102,38 @@ GB_DEV void chunk_range(int c, int KS, int NCH, int &k0, int &kw)
 size_t m2l_tc_table_floats(int P)
 {
     switch (P) {
-    case 4: return (size_t)kM2LCodes * TcCfg<4>::NCH * TcCfg<4>::BLOCK_FLOATS;
-    case 6: return (size_t)kM2LCodes * TcCfg<6>::NCH * TcCfg<6>::BLOCK_FLOATS;
-    case 8: return (size_t)kM2LCodes * TcCfg<8>::NCH * TcCfg<8>::BLOCK_FLOATS;
-    case 10: return (size_t)kM2LCodes * TcCfg<10>::NCH * TcCfg<10>::BLOCK_FLOATS;
+    case 4: return (size_t)kM2LCodes * TcTable<4>::CODE_FLOATS;
+    case 6: return (size_t)kM2LCodes * TcTable<6>::CODE_FLOATS;
+    case 8: return (size_t)kM2LCodes * TcTable<8>::CODE_FLOATS;
+    case 10: return (size_t)kM2LCodes * TcTable<10>::CODE_FLOATS;
     }
     return 0;
 }
 
-// (offset code, chunk) blocks: B_hi then B_lo, each [kw/4][NP][4] (canonical K-major layout
-// of the N x kw operand chunk), rows n >= p^2 and columns k >= p^2 zero
+// rows n >= p^2 and columns k >= p^2 zero
 template <int P>
 __global__ void k_build_m2l_tc(const float *__restrict__ ops, float *__restrict__ tc)
 {
-    using C = TcCfg<P>;
-    const int code = blockIdx.x, c = blockIdx.y;
-    int k0, kw;
-    chunk_range(c, C::KS, C::NCH, k0, kw);
-    float *blk = tc + ((size_t)code * C::NCH + c) * C::BLOCK_FLOATS;
-    for (int e = threadIdx.x; e < C::NP * kw; e += blockDim.x) {
-        const int n = e / kw, kk = e % kw, k = k0 + kk;
-        const float v = (n < C::PP && k < C::PP) ? ops[((size_t)code * C::PP + k) * C::PR + n] : 0.f;
+    using T = TcTable<P>;
+    const int code = blockIdx.x;
+    float *blk = tc + (size_t)code * T::CODE_FLOATS;
+    for (int e = threadIdx.x; e < T::NP * T::KP; e += blockDim.x) {
+        const int n = e / T::KP, k = e % T::KP;
+        const float v = (n < T::PP && k < T::PP) ? ops[((size_t)code * T::PP + k) * T::PR + n] : 0.f;
         const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
-        const int o = (kk >> 2) * C::NP * 4 + n * 4 + (kk & 3);
+        const int o = (k >> 2) * T::NP * 4 + n * 4 + (k & 3);
         blk[o] = hi;
-        blk[C::NP * kw + o] = lo;
+        blk[T::HALF + o] = lo;
     }
 }
 
 void launch_build_m2l_tc(int P, const float *ops, float *tc, cudaStream_t s)
 {
     switch (P) {
-    case 4: k_build_m2l_tc<4><<<dim3(kM2LCodes, TcCfg<4>::NCH), 256, 0, s>>>(ops, tc); break;
-    case 6: k_build_m2l_tc<6><<<dim3(kM2LCodes, TcCfg<6>::NCH), 256, 0, s>>>(ops, tc); break;
-    case 8: k_build_m2l_tc<8><<<dim3(kM2LCodes, TcCfg<8>::NCH), 256, 0, s>>>(ops, tc); break;
-    case 10: k_build_m2l_tc<10><<<dim3(kM2LCodes, TcCfg<10>::NCH), 256, 0, s>>>(ops, tc); break;
+    case 4: k_build_m2l_tc<4><<<kM2LCodes, 256, 0, s>>>(ops, tc); break;
+    case 6: k_build_m2l_tc<6><<<kM2LCodes, 256, 0, s>>>(ops, tc); break;
+    case 8: k_build_m2l_tc<8><<<kM2LCodes, 256, 0, s>>>(ops, tc); break;
+    case 10: k_build_m2l_tc<10><<<kM2LCodes, 256, 0, s>>>(ops, tc); break;
     }
     note_launches(1);
 }
@@ -129,18 +143,20 @@ struct TcTiles {
     int ntiles_level[kMaxLevel + 1];
 };
 
-template <int P>
-__global__ void __launch_bounds__(160, 1)
+template <int P, int CK, int NS>
+__global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     k_m2l_tc(TcTiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
              const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
              const uint16_t *__restrict__ m2l_code, const float *__restrict__ optc, const float *__restrict__ M,
              float *__restrict__ Lc, int *status)
 {
-    using C = TcCfg<P>;
-    constexpr int PP = C::PP, NP = C::NP, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
+    using C = TcCfg<P, CK, NS>;
+    using T = TcTable<P>;
+    constexpr int PP = C::PP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
     constexpr int S = 189 * NCH;
     constexpr uint32_t kIdesc = tc_idesc_tf32(TM, NP);
+    constexpr int kMmaWarp = 8;
 
     extern __shared__ __align__(1024) float tsm[];
     __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], drain_full[2], drain_empty[2], done_bar;
@@ -180,38 +196,74 @@ __global__ void __launch_bounds__(160, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int st = 0; st < NSTAGE; ++st) {
-            mbar_init(&full_bar[st], 5);  // 4 producer warps + the operator copy's expect_tx
+            mbar_init(&full_bar[st], 9);  // 8 converter warps + the operator copies' expect_tx
             mbar_init(&empty_bar[st], 1);  // one tcgen05.commit
             s_issued[st] = 0;
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&drain_full[b], 1);   // tcgen05.commit after an offset's last MMA
-            mbar_init(&drain_empty[b], 4);  // the 4 draining warps
+            mbar_init(&drain_empty[b], 8);  // the 8 draining warps
         }
         mbar_init(&done_bar, 1);
         s_abort = 0;
         fence_mbar_init();
     }
-    if (warp == 4) tmem_alloc(&s_tmem, C::TMEM_COLS);
+    if (warp == kMmaWarp) tmem_alloc(&s_tmem, C::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    if (warp < 4) {
-        // ================= producers / drainers: one thread per target row =================
-        const int r = tid;
+    if (warp < kMmaWarp) {
+        // ============ converters / drainers: target row r, K half (and output half) h ============
+        const int quad = warp & 3, h = warp >> 2;
+        const int r = 32 * quad + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
         const int64_t g = target(r);
         uint32_t ptr = 0, pend = 0;
         if (g >= 0 && end[g] > begin[g]) {
             ptr = m2l_offs[g];
             pend = m2l_offs[g + 1];
         }
-        // FP32 sum over offsets of the per-offset TMEM partials (each a chain of few MMAs)
-        float acc[NP];
+        // the target's next list entry (code, source), read one entry ahead so that its latency
+        // is hidden behind the offsets before it
+        int nxt_code = 0xffff, nxt_id = 0;
+        if (ptr < pend) {
+            nxt_code = m2l_code[ptr];
+            nxt_id = m2l_ids[ptr];
+        }
+        // source chunks are loaded into registers two steps ahead of their conversion
+        const float *lsrc = nullptr;
+        auto load = [&](int s2, float4 (&buf)[4]) {
 #pragma unroll
-        for (int n = 0; n < NP; ++n) acc[n] = 0.f;
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            for (int i = 0; i < 4; ++i) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (s2 >= S) return;
+            const int oc2 = s2 / NCH, c2 = s2 % NCH;
+            int k0, kw;
+            chunk_range(c2, C::KS, NCH, k0, kw);
+            if (c2 == 0) {
+                lsrc = nullptr;
+                if (nxt_code == (int)c_tc_codes[tau][oc2]) {
+                    lsrc = M + (size_t)nxt_id * PP;
+                    ++ptr;
+                    nxt_code = 0xffff;
+                    if (ptr < pend) {
+                        nxt_code = m2l_code[ptr];
+                        nxt_id = m2l_ids[ptr];
+                    }
+                }
+            }
+            if (!lsrc) return;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int kk = 16 * h + 4 * i, k = k0 + kk;
+                if (kk < kw && k < PP) buf[i] = __ldg(reinterpret_cast<const float4 *>(lsrc + k));
+            }
+        };
+        // FP32 sum over offsets of the per-offset TMEM partials (each a chain of few MMAs)
+        float acc[NH];
+#pragma unroll
+        for (int n = 0; n < NH; ++n) acc[n] = 0.f;
         auto drain = [&](int oc) -> bool {
             const int b = oc & 1;
             int ok = 1;
@@ -220,11 +272,11 @@ __global__ void __launch_bounds__(160, 1)
             if (!ok) return false;
             tc_fence_after();
 #pragma unroll
-            for (int c0 = 0; c0 < NP; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(b * NP + c0), v);
+            for (int c0 = 0; c0 < NH; c0 += 8) {
+                uint32_t v[8];
+                tmem_ld8(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+                for (int j = 0; j < 8; ++j) acc[c0 + j] += __uint_as_float(v[j]);
             }
             tc_fence_before();
             __syncwarp();
@@ -232,8 +284,7 @@ __global__ void __launch_bounds__(160, 1)
             return true;
         };
         bool alive = true;
-        const float *src = nullptr;
-        for (int s = 0; s < S && alive; ++s) {
+        auto step = [&](int s, float4 (&cur)[4]) {
             const int st = s % NSTAGE, oc = s / NCH, c = s % NCH;
             if (s >= NSTAGE) {
                 int ok = 1;
@@ -242,56 +293,51 @@ __global__ void __launch_bounds__(160, 1)
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     alive = false;
-                    break;
+                    return;
                 }
             }
             int k0, kw;
             chunk_range(c, C::KS, NCH, k0, kw);
-            float *stage = tsm + (size_t)st * C::STAGE_FLOATS;
-            float *Ahi = stage, *Alo = stage + C::A_FLOATS, *B = stage + 2 * C::A_FLOATS;
-            const int code = c_tc_codes[tau][oc];
             if (warp == 0 && lane == 0) {
-                const uint32_t bytes = 2u * NP * kw * 4u;
-                mbar_expect_tx(&full_bar[st], bytes);
-                tma_bulk_g2s(B, optc + ((size_t)code * NCH + c) * C::BLOCK_FLOATS, bytes, &full_bar[st]);
+                const int code = c_tc_codes[tau][oc];
+                const uint32_t half = (uint32_t)NP * kw * 4u;
+                const float *tb = optc + (size_t)code * T::CODE_FLOATS + (size_t)k0 * NP;
+                float *B = tsm + (size_t)st * C::B_FLOATS;
+                mbar_expect_tx(&full_bar[st], 2u * half);
+                tma_bulk_g2s(B, tb, half, &full_bar[st]);
+                tma_bulk_g2s(B + NP * kw, tb + T::HALF, half, &full_bar[st]);
                 s_issued[st] += 1;
             }
-            if (c == 0) {
-                src = nullptr;
-                if (ptr < pend && (int)m2l_code[ptr] == code) {
-                    src = M + (size_t)m2l_ids[ptr] * PP;
-                    ++ptr;
+            // split into TF32 halves and store the thread's 16 columns of A_hi and A_lo (its
+            // TMEM lane = its target row)
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float x[4] = {cur[i].x, cur[i].y, cur[i].z, cur[i].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float a = tf32_rna(x[e]);
+                    hi[4 * i + e] = __float_as_uint(a);
+                    lo[4 * i + e] = __float_as_uint(tf32_rna(x[e] - a));
                 }
             }
-            // gather this chunk of the source expansion, split into TF32 halves
-            float4 v[C::KCMAX / 4];
-#pragma unroll
-            for (int j = 0; j < C::KCMAX / 4; ++j) {
-                const int k = k0 + 4 * j;
-                v[j] = (src && 4 * j < kw && k < PP) ? __ldg(reinterpret_cast<const float4 *>(src + k))
-                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int j = 0; j < C::KCMAX / 4; ++j) {
-                if (4 * j >= kw) break;
-                const float4 x = v[j];
-                float4 h, l;
-                h.x = tf32_rna(x.x);
-                h.y = tf32_rna(x.y);
-                h.z = tf32_rna(x.z);
-                h.w = tf32_rna(x.w);
-                l.x = tf32_rna(x.x - h.x);
-                l.y = tf32_rna(x.y - h.y);
-                l.z = tf32_rna(x.z - h.z);
-                l.w = tf32_rna(x.w - h.w);
-                *reinterpret_cast<float4 *>(Ahi + j * TM * 4 + r * 4) = h;
-                *reinterpret_cast<float4 *>(Alo + j * TM * 4 + r * 4) = l;
-            }
-            fence_proxy_async();
+            const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + 16 * h);
+            tmem_st16(tmem + lane_base + acol, hi);
+            tmem_st16(tmem + lane_base + acol + 32, lo);
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_bar[st]);
+            load(s + 2, cur);
             // the previous offset's partial is complete once this one is queued
             if (c == NCH - 1 && oc >= 1 && !drain(oc - 1)) alive = false;
+        };
+        float4 b0[4], b1[4];
+        load(0, b0);
+        load(1, b1);
+        for (int s = 0; s < S && alive; s += 2) {
+            step(s, b0);
+            if (s + 1 < S && alive) step(s + 1, b1);
         }
         if (alive && !drain(188)) alive = false;
         if (!alive && lane == 0) s_abort = 1;
@@ -303,8 +349,10 @@ __global__ void __launch_bounds__(160, 1)
         __syncwarp();
         if (ok && alive && !s_abort && g >= 0 && end[g] > begin[g]) {
 #pragma unroll
-            for (int n = 0; n < PP; n += 4)
-                *reinterpret_cast<float4 *>(Lc + g * PP + n) = make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
+            for (int n = 0; n < NH; n += 4)
+                if (h * NH + n < PP)
+                    *reinterpret_cast<float4 *>(Lc + g * PP + h * NH + n) =
+                        make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
         }
     } else if (lane == 0) {
         // ================= MMA issuer: offset oc accumulates in TMEM buffer oc & 1 =================
@@ -322,19 +370,16 @@ __global__ void __launch_bounds__(160, 1)
             tc_fence_after();
             int k0, kw;
             chunk_range(c, C::KS, NCH, k0, kw);
-            const float *stage = tsm + (size_t)st * C::STAGE_FLOATS;
-            const float *Ahi = stage, *Alo = stage + C::A_FLOATS;
-            const float *Bhi = stage + 2 * C::A_FLOATS, *Blo = Bhi + NP * kw;
+            const float *Bhi = tsm + (size_t)st * C::B_FLOATS, *Blo = Bhi + NP * kw;
             const uint32_t d = tmem + (uint32_t)(b * NP);
+            const uint32_t ahi = tmem + (uint32_t)(C::A_COL0 + 64 * st), alo = ahi + 32;
             for (int j = 0; j < kw / 8; ++j) {
-                const uint64_t ah = smem_desc(Ahi + j * 2 * TM * 4, TM * 16, 128);
-                const uint64_t al = smem_desc(Alo + j * 2 * TM * 4, TM * 16, 128);
                 const uint64_t bh = smem_desc(Bhi + j * 2 * NP * 4, NP * 16, 128);
                 const uint64_t bl = smem_desc(Blo + j * 2 * NP * 4, NP * 16, 128);
                 // the small cross terms first, the hi*hi term last
-                tc_mma_tf32(d, al, bh, kIdesc, (c > 0 || j > 0) ? 1u : 0u);
-                tc_mma_tf32(d, ah, bl, kIdesc, 1u);
-                tc_mma_tf32(d, ah, bh, kIdesc, 1u);
+                tc_mma_tf32_ta(d, alo + 8 * j, bh, kIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                tc_mma_tf32_ta(d, ahi + 8 * j, bl, kIdesc, 1u);
+                tc_mma_tf32_ta(d, ahi + 8 * j, bh, kIdesc, 1u);
             }
             tc_commit(&empty_bar[st]);
             if (c == NCH - 1) tc_commit(&drain_full[b]);
@@ -353,23 +398,35 @@ __global__ void __launch_bounds__(160, 1)
         }
         __syncthreads();
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         __syncwarp();
         tmem_dealloc(tmem, C::TMEM_COLS);
     }
 }
 
-template <int P>
+template <int P, int CK, int NS>
 static void launch_m2l_tc_t(const TcTiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                             const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                             const int32_t *m2l_ids, const uint16_t *m2l_code, const float *optc, const float *M,
                             float *Lc, int *status, cudaStream_t s)
 {
-    using C = TcCfg<P>;
-    cudaFuncSetAttribute(k_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-    k_m2l_tc<P><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
-                                                          m2l_code, optc, M, Lc, status);
+    using C = TcCfg<P, CK, NS>;
+    cudaFuncSetAttribute(k_m2l_tc<P, CK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+    k_m2l_tc<P, CK, NS><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
+                                                                  m2l_ids, m2l_code, optc, M, Lc, status);
     note_launches(1);
+}
+
+// pipeline shape (GBFMM_M2L_TC_CFG, p = 10): 0 = chunks of <= 4 K steps, 4 stages; 1 = 4 steps,
+// 2 stages; 2 = 2 steps, 4 stages; 3 = 3 steps, 4 stages
+static int tc_variant()
+{
+    static const int v = [] {
+        const char *e = getenv("GBFMM_M2L_TC_CFG");
+        const int x = e ? atoi(e) : 0;
+        return (x >= 0 && x <= 3) ? x : 0;
+    }();
+    return v;
 }
 
 static void dispatch_tc(int P, const TcTiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
@@ -377,12 +434,21 @@ static void dispatch_tc(int P, const TcTiles &tiles, int grid, const int4 *tdesc
                         const uint16_t *m2l_code, const float *optc, const float *M, float *Lc, int *status,
                         cudaStream_t s)
 {
+#define GBFMM_TC_ARGS tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s
     switch (P) {
-    case 4: launch_m2l_tc_t<4>(tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s); break;
-    case 6: launch_m2l_tc_t<6>(tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s); break;
-    case 8: launch_m2l_tc_t<8>(tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s); break;
-    case 10: launch_m2l_tc_t<10>(tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s); break;
+    case 4: launch_m2l_tc_t<4, 2, 4>(GBFMM_TC_ARGS); break;
+    case 6: launch_m2l_tc_t<6, 4, 4>(GBFMM_TC_ARGS); break;
+    case 8: launch_m2l_tc_t<8, 4, 4>(GBFMM_TC_ARGS); break;
+    case 10:
+        switch (tc_variant()) {
+        case 1: launch_m2l_tc_t<10, 4, 2>(GBFMM_TC_ARGS); break;
+        case 2: launch_m2l_tc_t<10, 2, 4>(GBFMM_TC_ARGS); break;
+        case 3: launch_m2l_tc_t<10, 3, 4>(GBFMM_TC_ARGS); break;
+        default: launch_m2l_tc_t<10, 4, 4>(GBFMM_TC_ARGS); break;
+        }
+        break;
     }
+#undef GBFMM_TC_ARGS
 }
 
 void launch_m2l_tc(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,

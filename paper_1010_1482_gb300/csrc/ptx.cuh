@@ -84,6 +84,26 @@ GB_DEV bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
+// ---- cp.async (LDGSTS): 16-byte global -> shared copies, completion by commit groups ----------
+// src_bytes < 16 zero-fills the rest (0: nothing is read and the 16 bytes are zero)
+GB_DEV void cp_async16(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+GB_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// one arrival on the mbarrier once every cp.async this thread issued so far has completed (the
+// arrival is one of the barrier's expected arrivals)
+GB_DEV void cp_async_arrive_noinc(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+template <int N>
+GB_DEV void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---- tcgen05 (5th-generation tensor cores, accumulators in tensor memory) -------------------
 
 // round to TF32 (10 explicit mantissa bits, nearest, ties away), result in FP32 layout
@@ -139,6 +159,16 @@ GB_DEV void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_
         : "memory");
 }
 
+// D (TMEM) = A * B^T (+ D), A from tensor memory (row i of A in lane i), issued by one thread
+GB_DEV void tc_mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // the mbarrier receives one arrival when every tcgen05 operation this thread issued so far has completed
 GB_DEV void tc_commit(uint64_t *bar)
 {
@@ -156,5 +186,28 @@ GB_DEV void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// whole warp: 8 consecutive 32-bit columns of TMEM lane (lane base + lane id)
+GB_DEV void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// whole warp: store 16 consecutive 32-bit columns of TMEM lane (lane base + lane id); the
+// stores are complete for this thread after tmem_wait_st()
+GB_DEV void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+GB_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 }  // namespace gbfmm

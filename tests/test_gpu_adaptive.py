@@ -90,6 +90,15 @@ def test_adaptive_fmm_matches_oracle(G, ctx, p):
     assert O.rel_l2(out[:, 1:], d[:, 1:]) <= e_or + TOL_FMM
 
 
+def test_adaptive_m2l_tensor_cores_and_cuda_cores_agree(G, ctx):
+    x = inputs.plummer(30000, 77)
+    tc = run(G, ctx, x, p=8, leaf_size=32)
+    cc = run(G, ctx, x, p=8, leaf_size=32, flags=G.FLAG_M2L_CUDA_CORES)
+    ref = O.fmm_adaptive(x, 8, 32)["out"]
+    assert O.rel_l2(tc, ref) <= TOL_FMM and O.rel_l2(cc, ref) <= TOL_FMM
+    assert O.rel_l2(tc, cc) <= 5e-6
+
+
 @pytest.mark.parametrize("p", [4, 10])
 def test_adaptive_expansions_match_oracle(G, ctx, p):
     n, leaf = 20000, 32

@@ -138,6 +138,22 @@ def test_fmm_matches_oracle(G, ctx, p):
     assert O.rel_l2(out[:, 1:], d[:, 1:]) <= e_or + TOL_FMM
 
 
+@pytest.mark.parametrize("p", [4, 6, 8, 10])
+def test_m2l_tensor_cores_and_cuda_cores_agree(G, ctx, p):
+    """The tcgen05 M2L (3xTF32, the default) and the FP32 CUDA-core M2L compute Eq. 4 over the
+    same lists: both match the oracle, and each other to rounding."""
+    n, leaf = 30000, 16
+    x = inputs.uniform_cube(n, 123 + p)
+    tc, L = run(G, ctx, x, p=p, leaf_size=leaf)
+    cc, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_CUDA_CORES)
+    assert L == 4
+    ref = O.fmm(x, p, leaf)["out"]
+    for out in (tc, cc):
+        assert O.rel_l2(out[:, 0], ref[:, 0]) <= TOL_FMM
+        assert O.rel_l2(out[:, 1:], ref[:, 1:]) <= TOL_FMM
+    assert O.rel_l2(tc, cc) <= 5e-6
+
+
 def test_fmm_clustered_input(G, ctx):
     x = inputs.plummer(30000, 5)
     out, _ = run(G, ctx, x, p=6, leaf_size=32)
