@@ -15,10 +15,24 @@
 // caller's original particle order.
 #include "common.cuh"
 
+#include <stdlib.h>
+
 namespace gbfmm {
 
 constexpr int kP2PThreads = 128;
-constexpr int kP2PTargetsPerThread = 2;
+
+// P2P kernel (GBFMM_P2P_TPT): 12 / 14 = CTA per leaf, packed FP32x2 pairs, 2 / 4 targets per
+// thread (12 is the default); 0 = warp per leaf; 1, 2, 4, 8 = CTA per leaf, scalar FP32, that
+// many targets per thread
+static int p2p_tpt()
+{
+    static const int v = [] {
+        const char *e = getenv("GBFMM_P2P_TPT");
+        const int x = e ? atoi(e) : 12;
+        return (x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 12 || x == 14) ? x : 12;
+    }();
+    return v;
+}
 constexpr int kSrcCap = 1024;
 constexpr int kRowCap = 32;
 
@@ -157,20 +171,347 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const int32_t *__res
     }
 }
 
+
+// ---- packed FP32x2 arithmetic (two lanes of one 64-bit register: targets a and b) -------------
+GB_DEV uint64_t f2_pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+GB_DEV void f2_unpack(uint64_t r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+GB_DEV uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+GB_DEV uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+GB_DEV uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+GB_DEV uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// The pair rule for two targets at once (packed X, Y, Z) and one source whose coordinates and
+// charge are staged duplicated: xy = (x, x, y, y), zq = (z, z, q, q).  Same operation order as
+// pair(); the gradient accumulates +d q / r^3 and is negated once at the end.  MASK drops pairs
+// at zero distance (only the target's own cell can hold them).
+template <bool SOFT, bool MASK>
+GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, float4 xy, float4 zq, uint64_t E2, uint64_t &P, uint64_t &GX,
+                  uint64_t &GY, uint64_t &GZ)
+{
+    const uint64_t dx = f2_sub(X, f2_pack(xy.x, xy.y));
+    const uint64_t dy = f2_sub(Y, f2_pack(xy.z, xy.w));
+    const uint64_t dz = f2_sub(Z, f2_pack(zq.x, zq.y));
+    uint64_t d2 = f2_mul(dz, dz);
+    d2 = f2_fma(dy, dy, d2);
+    d2 = f2_fma(dx, dx, d2);
+    float r0, r1;
+    f2_unpack(SOFT ? f2_add(d2, E2) : d2, r0, r1);
+    float i0 = rsqrtf(r0), i1 = rsqrtf(r1);
+    if (MASK) {
+        float a0, a1;
+        f2_unpack(d2, a0, a1);
+        i0 = a0 > 0.f ? i0 : 0.f;
+        i1 = a1 > 0.f ? i1 : 0.f;
+    }
+    const uint64_t inv = f2_pack(i0, i1);
+    const uint64_t w = f2_mul(f2_pack(zq.z, zq.w), inv);
+    P = f2_add(P, w);
+    const uint64_t w3 = f2_mul(f2_mul(w, inv), inv);
+    GX = f2_fma(dx, w3, GX);
+    GY = f2_fma(dy, w3, GY);
+    GZ = f2_fma(dz, w3, GZ);
+}
+
+constexpr int kSrcCap2 = 512;
+
+// CTA per target leaf with TPT (2 or 4) targets per thread in packed pairs; the leaf's own cell
+// is staged first so that only its sources pay for the zero-distance test
+template <bool SOFT, int TPT>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__restrict__ leaves,
+                                                      const float4 *__restrict__ sx,
+                                                      const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+                                                      const uint32_t *__restrict__ p2p_offs,
+                                                      const int32_t *__restrict__ p2p_ids,
+                                                      const float4 *__restrict__ far,
+                                                      const uint32_t *__restrict__ perm, float eps2,
+                                                      float4 *__restrict__ out)
+{
+    constexpr int NPK = TPT / 2;
+    __shared__ float4 sA[kSrcCap2], sB[kSrcCap2];
+    __shared__ float4 red[TPT][kP2PThreads];
+    __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1], s_self;
+    const int64_t leaf = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
+    const int64_t g = leaves ? leaf : level_offset(L) + leaf;
+    const int b0 = begin[g], e0 = end[g];
+    if (e0 <= b0) return;
+    const int tid = threadIdx.x;
+    const uint32_t r0 = p2p_offs[leaf];
+    const int nrow = (int)(p2p_offs[leaf + 1] - r0);
+    const int T = e0 - b0;
+    const uint64_t E2 = f2_pack(eps2, eps2);
+    for (int tc = 0; tc < T; tc += TPT * kP2PThreads) {
+        const int Tc = min(T - tc, TPT * kP2PThreads);
+        const int slots = (Tc + TPT - 1) / TPT;
+        const int G = kP2PThreads / slots;
+        const int slot = tid % slots, grp = tid / slots;
+        const bool active = grp < G;
+        uint64_t X[NPK], Y[NPK], Z[NPK], P[NPK], GX[NPK], GY[NPK], GZ[NPK];
+#pragma unroll
+        for (int k = 0; k < NPK; ++k) {
+            // a missing target repeats the slot's first one; its result is discarded
+            const int ta = TPT * slot + 2 * k, tb = ta + 1;
+            const float4 pa = __ldg(&sx[b0 + tc + (ta < Tc ? ta : TPT * slot)]);
+            const float4 pb = __ldg(&sx[b0 + tc + (tb < Tc ? tb : TPT * slot)]);
+            X[k] = f2_pack(pa.x, pb.x);
+            Y[k] = f2_pack(pa.y, pb.y);
+            Z[k] = f2_pack(pa.z, pb.z);
+            P[k] = GX[k] = GY[k] = GZ[k] = 0ull;
+        }
+        for (int rb = 0; rb < nrow; rb += kRowCap) {
+            const int nr = min(kRowCap, nrow - rb);
+            __syncthreads();
+            if (tid < nr) {
+                const int c = p2p_ids[r0 + rb + tid];
+                s_cb[tid] = begin[c];
+                s_pref[tid + 1] = end[c] - begin[c];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                // the target's own cell first
+                int self = 0;
+                for (int k = 0; k < nr; ++k)
+                    if (s_cb[k] == b0 && s_pref[k + 1] == T) {
+                        const int cb = s_cb[k], cn = s_pref[k + 1];
+                        s_cb[k] = s_cb[0];
+                        s_pref[k + 1] = s_pref[1];
+                        s_cb[0] = cb;
+                        s_pref[1] = cn;
+                        self = T;
+                        break;
+                    }
+                s_self = self;
+                s_pref[0] = 0;
+                for (int k = 0; k < nr; ++k) s_pref[k + 1] += s_pref[k];
+            }
+            __syncthreads();
+            const int S = s_pref[nr], nself = s_self;
+            for (int sc = 0; sc < S; sc += kSrcCap2) {
+                const int chunk = min(kSrcCap2, S - sc);
+                if (sc > 0) __syncthreads();
+                for (int k = tid; k < chunk; k += kP2PThreads) {
+                    const int s = sc + k;
+                    int e = 0;
+                    while (s >= s_pref[e + 1]) ++e;
+                    const float4 p = __ldg(&sx[s_cb[e] + (s - s_pref[e])]);
+                    sA[k] = make_float4(p.x, p.x, p.y, p.y);
+                    sB[k] = make_float4(p.z, p.z, p.w, p.w);
+                }
+                __syncthreads();
+                if (active) {
+                    const int mend = max(0, min(chunk, nself - sc));
+                    int j = grp;
+                    for (; j < mend; j += G) {
+                        const float4 a = sA[j], b = sB[j];
+#pragma unroll
+                        for (int k = 0; k < NPK; ++k) pair2<SOFT, true>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
+                    }
+#pragma unroll 4
+                    for (; j < chunk; j += G) {
+                        const float4 a = sA[j], b = sB[j];
+#pragma unroll
+                        for (int k = 0; k < NPK; ++k) pair2<SOFT, false>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NPK; ++k) {
+            float p0, p1, x0, x1, y0, y1, z0, z1;
+            f2_unpack(P[k], p0, p1);
+            f2_unpack(GX[k], x0, x1);
+            f2_unpack(GY[k], y0, y1);
+            f2_unpack(GZ[k], z0, z1);
+            red[2 * k][tid] = make_float4(p0, -x0, -y0, -z0);
+            red[2 * k + 1][tid] = make_float4(p1, -x1, -y1, -z1);
+        }
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int h = 0; h < TPT; ++h) {
+                const int t = TPT * slot + h;
+                if (t >= Tc) break;
+                const int i = b0 + tc + t;
+                Kahan a{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f}, bz{0.f, 0.f};
+                for (int k = 0; k < G; ++k) {
+                    const float4 v = red[h][k * slots + slot];
+                    a.add(v.x);
+                    bx.add(v.y);
+                    by.add(v.z);
+                    bz.add(v.w);
+                }
+                if (far) {
+                    const float4 f = far[i];
+                    a.add(f.x);
+                    bx.add(f.y);
+                    by.add(f.z);
+                    bz.add(f.w);
+                }
+                out[perm[i]] = make_float4(a.s, bx.s, by.s, bz.s);
+            }
+        }
+    }
+}
+
+// Warp-per-leaf variant: each warp takes one target leaf (lane = target; a second target per
+// lane for leaves of 33..64 targets, further blocks of 64 in turn) and streams the sources of
+// the leaf's list through its own shared-memory buffer: the cells of the list are appended with
+// coalesced float4 loads, 32 particles at a time, and each full buffer is swept by every lane.
+// No block-wide barrier and no cross-thread reduction; each target's FP32 sum runs over the
+// sources in list order, then the far-field value is added.
+constexpr int kP2PWarps = 4;
+constexpr int kP2PChunk = 256;  // sources per warp buffer (4 KB)
+
+template <bool SOFT>
+__global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_warp(int L, int64_t nleaves, const int32_t *__restrict__ leaves,
+                                                              const float4 *__restrict__ sx,
+                                                              const int32_t *__restrict__ begin,
+                                                              const int32_t *__restrict__ end,
+                                                              const uint32_t *__restrict__ p2p_offs,
+                                                              const int32_t *__restrict__ p2p_ids,
+                                                              const float4 *__restrict__ far,
+                                                              const uint32_t *__restrict__ perm, float eps2,
+                                                              float4 *__restrict__ out)
+{
+    __shared__ float4 sbuf[kP2PWarps][kP2PChunk];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t li = (int64_t)blockIdx.x * kP2PWarps + w;
+    if (li >= nleaves) return;
+    const int64_t leaf = leaves ? (int64_t)leaves[li] : li;
+    const int64_t g = leaves ? leaf : level_offset(L) + leaf;
+    const int b0 = begin[g], e0 = end[g];
+    if (e0 <= b0) return;
+    const uint32_t r0 = p2p_offs[leaf], r1 = p2p_offs[leaf + 1];
+    float4 *sb = sbuf[w];
+    for (int t0 = b0; t0 < e0; t0 += 64) {
+        const int ta = t0 + lane, tb = t0 + 32 + lane;
+        const bool two = e0 - t0 > 32;  // warp-uniform
+        const float4 pa = __ldg(&sx[ta < e0 ? ta : b0]);
+        const float4 pb = __ldg(&sx[tb < e0 ? tb : b0]);
+        float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f, bx = 0.f, by = 0.f, bz = 0.f, bw = 0.f;
+        auto sweep = [&](int nsrc) {
+            if (two) {
+#pragma unroll 4
+                for (int j = 0; j < nsrc; ++j) {
+                    const float4 q = sb[j];
+                    pair<SOFT>(pa.x, pa.y, pa.z, q, eps2, aw, ax, ay, az);
+                    pair<SOFT>(pb.x, pb.y, pb.z, q, eps2, bw, bx, by, bz);
+                }
+            } else {
+#pragma unroll 8
+                for (int j = 0; j < nsrc; ++j) pair<SOFT>(pa.x, pa.y, pa.z, sb[j], eps2, aw, ax, ay, az);
+            }
+        };
+        int fill = 0;
+        for (uint32_t e = r0; e < r1; ++e) {
+            const int c = p2p_ids[e];
+            const int cb = begin[c], cn = end[c] - cb;
+            for (int j0 = 0; j0 < cn; j0 += 32) {
+                if (fill > kP2PChunk - 32) {
+                    __syncwarp();
+                    sweep(fill);
+                    __syncwarp();
+                    fill = 0;
+                }
+                const int m = min(32, cn - j0);
+                if (lane < m) sb[fill + lane] = __ldg(&sx[cb + j0 + lane]);
+                fill += m;
+            }
+        }
+        __syncwarp();
+        sweep(fill);
+        __syncwarp();
+        if (ta < e0) {
+            float4 f = far ? far[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[perm[ta]] = make_float4(aw + f.x, ax + f.y, ay + f.z, az + f.w);
+        }
+        if (two && tb < e0) {
+            float4 f = far ? far[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[perm[tb]] = make_float4(bw + f.x, bx + f.y, by + f.z, bz + f.w);
+        }
+    }
+}
+
+template <int TPT>
+static void launch_p2p_t(unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
+                         const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
+                         const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
+{
+    if (eps2 > 0.f)
+        k_p2p<true, TPT><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+    else
+        k_p2p<false, TPT><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+    note_launches(1);
+}
+
+static void dispatch_p2p(unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
+                         const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
+                         const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
+{
+    if (p2p_tpt() == 12 || p2p_tpt() == 14) {
+        if (p2p_tpt() == 12) {
+            if (eps2 > 0.f)
+                k_p2p2<true, 2><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+            else
+                k_p2p2<false, 2><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        } else {
+            if (eps2 > 0.f)
+                k_p2p2<true, 4><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+            else
+                k_p2p2<false, 4><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        }
+        note_launches(1);
+        return;
+    }
+    if (p2p_tpt() == 0) {
+        const unsigned g2 = (grid + kP2PWarps - 1) / kP2PWarps;
+        if (eps2 > 0.f)
+            k_p2p_warp<true><<<g2, 32 * kP2PWarps, 0, s>>>(L, grid, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        else
+            k_p2p_warp<false><<<g2, 32 * kP2PWarps, 0, s>>>(L, grid, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        note_launches(1);
+        return;
+    }
+    switch (p2p_tpt()) {
+    case 1: launch_p2p_t<1>(grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, s); break;
+    case 2: launch_p2p_t<2>(grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, s); break;
+    case 8: launch_p2p_t<8>(grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, s); break;
+    case 4: launch_p2p_t<4>(grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, s); break;
+    }
+}
+
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs,
                 const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2, float4 *out,
                 cudaStream_t s)
 {
     if (n <= 0) return;
-    unsigned grid = (unsigned)(int64_t(1) << (3 * L));
-    constexpr int TPT = kP2PTargetsPerThread;
-    if (eps2 > 0.f)
-        k_p2p<true, TPT><<<grid, kP2PThreads, 0, s>>>(L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2,
-                                                      out);
-    else
-        k_p2p<false, TPT><<<grid, kP2PThreads, 0, s>>>(L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm,
-                                                       eps2, out);
-    note_launches(1);
+    dispatch_p2p((unsigned)(int64_t(1) << (3 * L)), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2,
+                 out, s);
 }
 
 void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
@@ -178,14 +519,7 @@ void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const f
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
 {
     if (n <= 0 || nleaves <= 0) return;
-    constexpr int TPT = kP2PTargetsPerThread;
-    if (eps2 > 0.f)
-        k_p2p<true, TPT><<<(unsigned)nleaves, kP2PThreads, 0, s>>>(0, leaves, sx, begin, end, u_offs, u_ids, far, perm,
-                                                                   eps2, out);
-    else
-        k_p2p<false, TPT><<<(unsigned)nleaves, kP2PThreads, 0, s>>>(0, leaves, sx, begin, end, u_offs, u_ids, far, perm,
-                                                                    eps2, out);
-    note_launches(1);
+    dispatch_p2p((unsigned)nleaves, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, s);
 }
 
 // Direct all-pairs sum: one thread per target, sources streamed through shared memory in
