@@ -29,7 +29,7 @@ static int p2p_tpt()
     static const int v = [] {
         const char *e = getenv("GBFMM_P2P_TPT");
         const int x = e ? atoi(e) : 12;
-        return (x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 12 || x == 14) ? x : 12;
+        return (x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 12 || x == 14 || x == 20) ? x : 12;
     }();
     return v;
 }
@@ -210,12 +210,12 @@ GB_DEV uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
 // pair(); the gradient accumulates +d q / r^3 and is negated once at the end.  MASK drops pairs
 // at zero distance (only the target's own cell can hold them).
 template <bool SOFT, bool MASK>
-GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, float4 xy, float4 zq, uint64_t E2, uint64_t &P, uint64_t &GX,
-                  uint64_t &GY, uint64_t &GZ)
+GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, ulonglong2 xy, ulonglong2 zq, uint64_t E2, uint64_t &P,
+                  uint64_t &GX, uint64_t &GY, uint64_t &GZ)
 {
-    const uint64_t dx = f2_sub(X, f2_pack(xy.x, xy.y));
-    const uint64_t dy = f2_sub(Y, f2_pack(xy.z, xy.w));
-    const uint64_t dz = f2_sub(Z, f2_pack(zq.x, zq.y));
+    const uint64_t dx = f2_sub(X, xy.x);
+    const uint64_t dy = f2_sub(Y, xy.y);
+    const uint64_t dz = f2_sub(Z, zq.x);
     uint64_t d2 = f2_mul(dz, dz);
     d2 = f2_fma(dy, dy, d2);
     d2 = f2_fma(dx, dx, d2);
@@ -229,7 +229,7 @@ GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, float4 xy, float4 zq, uint
         i1 = a1 > 0.f ? i1 : 0.f;
     }
     const uint64_t inv = f2_pack(i0, i1);
-    const uint64_t w = f2_mul(f2_pack(zq.z, zq.w), inv);
+    const uint64_t w = f2_mul(zq.y, inv);
     P = f2_add(P, w);
     const uint64_t w3 = f2_mul(f2_mul(w, inv), inv);
     GX = f2_fma(dx, w3, GX);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
                                                       float4 *__restrict__ out)
 {
     constexpr int NPK = TPT / 2;
-    __shared__ float4 sA[kSrcCap2], sB[kSrcCap2];
+    __shared__ ulonglong2 sA[kSrcCap2], sB[kSrcCap2];  // (x, x | y, y), (z, z | q, q)
     __shared__ float4 red[TPT][kP2PThreads];
     __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1], s_self;
     const int64_t leaf = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
@@ -313,26 +313,27 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
             for (int sc = 0; sc < S; sc += kSrcCap2) {
                 const int chunk = min(kSrcCap2, S - sc);
                 if (sc > 0) __syncthreads();
-                for (int k = tid; k < chunk; k += kP2PThreads) {
-                    const int s = sc + k;
-                    int e = 0;
-                    while (s >= s_pref[e + 1]) ++e;
-                    const float4 p = __ldg(&sx[s_cb[e] + (s - s_pref[e])]);
-                    sA[k] = make_float4(p.x, p.x, p.y, p.y);
-                    sB[k] = make_float4(p.z, p.z, p.w, p.w);
+                // warp w stages rows w, w + 4, ... (its lanes stride the row's particles)
+                for (int e = tid >> 5; e < nr; e += kP2PThreads / 32) {
+                    const int lo = max(s_pref[e], sc), hi = min(s_pref[e + 1], sc + chunk);
+                    for (int q = lo + (tid & 31); q < hi; q += 32) {
+                        const float4 p = __ldg(&sx[s_cb[e] + (q - s_pref[e])]);
+                        sA[q - sc] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
+                        sB[q - sc] = make_ulonglong2(f2_pack(p.z, p.z), f2_pack(p.w, p.w));
+                    }
                 }
                 __syncthreads();
                 if (active) {
                     const int mend = max(0, min(chunk, nself - sc));
                     int j = grp;
                     for (; j < mend; j += G) {
-                        const float4 a = sA[j], b = sB[j];
+                        const ulonglong2 a = sA[j], b = sB[j];
 #pragma unroll
                         for (int k = 0; k < NPK; ++k) pair2<SOFT, true>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
                     }
 #pragma unroll 4
                     for (; j < chunk; j += G) {
-                        const float4 a = sA[j], b = sB[j];
+                        const ulonglong2 a = sA[j], b = sB[j];
 #pragma unroll
                         for (int k = 0; k < NPK; ++k) pair2<SOFT, false>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
                     }
@@ -374,6 +375,126 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
                 }
                 out[perm[i]] = make_float4(a.s, bx.s, by.s, bz.s);
             }
+        }
+    }
+}
+
+// Uniform tree, CTA per parent cell ("superleaf"): the 4 x 4 x 4 leaves around the parent's 8
+// children hold every source any child needs; they are staged once in shared memory (float4,
+// cell by cell), then each thread takes two targets of one child (a packed pair) and sweeps the
+// child's 27 neighbour cells from shared memory.  No per-leaf setup, no group split and no
+// cross-thread reduction.  A block whose 64 cells hold more than kSuperCap particles sweeps
+// the same cells from global memory instead.
+constexpr int kSuperThreads = 128;
+constexpr int kSuperCap = 2304;
+
+template <bool SOFT, bool STAGED>
+GB_DEV void super_sweep(const float4 *__restrict__ src, const int *cbeg, const int *ccnt, int lc, uint64_t X, uint64_t Y,
+                        uint64_t Z, uint64_t E2, uint64_t &P, uint64_t &GX, uint64_t &GY, uint64_t &GZ)
+{
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int cell = lc + dx + 4 * dy + 16 * dz;
+                const int b = cbeg[cell], n = ccnt[cell];
+                if (dx == 0 && dy == 0 && dz == 0) {
+                    for (int j = 0; j < n; ++j) {
+                        const float4 q = STAGED ? src[b + j] : __ldg(&src[b + j]);
+                        pair2<SOFT, true>(X, Y, Z, make_ulonglong2(f2_pack(q.x, q.x), f2_pack(q.y, q.y)),
+                                          make_ulonglong2(f2_pack(q.z, q.z), f2_pack(q.w, q.w)), E2, P, GX, GY, GZ);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = 0; j < n; ++j) {
+                        const float4 q = STAGED ? src[b + j] : __ldg(&src[b + j]);
+                        pair2<SOFT, false>(X, Y, Z, make_ulonglong2(f2_pack(q.x, q.x), f2_pack(q.y, q.y)),
+                                           make_ulonglong2(f2_pack(q.z, q.z), f2_pack(q.w, q.w)), E2, P, GX, GY, GZ);
+                    }
+                }
+            }
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kSuperThreads) k_p2p_super(int L, const float4 *__restrict__ sx,
+                                                              const int32_t *__restrict__ begin,
+                                                              const int32_t *__restrict__ end,
+                                                              const float4 *__restrict__ far,
+                                                              const uint32_t *__restrict__ perm, float eps2,
+                                                              float4 *__restrict__ out)
+{
+    __shared__ float4 stage[kSuperCap];
+    __shared__ int s_gbeg[64], s_cnt[64], s_beg[64], s_pp[9];
+    __shared__ int s_total;
+    const int tid = threadIdx.x;
+    const int side = 1 << L;
+    int px, py, pz;
+    demorton3((uint32_t)blockIdx.x, px, py, pz);
+    const int64_t loff = level_offset(L);
+    if (tid < 64) {
+        const int x = 2 * px - 1 + (tid & 3), y = 2 * py - 1 + ((tid >> 2) & 3), z = 2 * pz - 1 + (tid >> 4);
+        int gb = 0, n = 0;
+        if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+            const int64_t gi = loff + morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+            gb = begin[gi];
+            n = end[gi] - gb;
+            if (n < 0) n = 0;
+        }
+        s_gbeg[tid] = gb;
+        s_cnt[tid] = n;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < 64; ++c) {
+            s_beg[c] = acc;
+            acc += s_cnt[c];
+        }
+        s_total = acc;
+        // target pairs of the 8 children (local cells (1 + (c & 1), 1 + ((c >> 1) & 1), 1 + (c >> 2)))
+        s_pp[0] = 0;
+        for (int c = 0; c < 8; ++c) {
+            const int lc = (1 + (c & 1)) + 4 * (1 + ((c >> 1) & 1)) + 16 * (1 + (c >> 2));
+            s_pp[c + 1] = s_pp[c] + (s_cnt[lc] + 1) / 2;
+        }
+    }
+    __syncthreads();
+    const bool staged = s_total <= kSuperCap;
+    if (staged) {
+        const int w = tid >> 5, lane = tid & 31;
+        for (int c = w; c < 64; c += kSuperThreads / 32) {
+            const int gb = s_gbeg[c], n = s_cnt[c], sb = s_beg[c];
+            for (int j = lane; j < n; j += 32) stage[sb + j] = __ldg(&sx[gb + j]);
+        }
+        __syncthreads();
+    }
+    const uint64_t E2 = f2_pack(eps2, eps2);
+    const int npairs = s_pp[8];
+    for (int pi = tid; pi < npairs; pi += kSuperThreads) {
+        int c = 0;
+        while (pi >= s_pp[c + 1]) ++c;
+        const int lc = (1 + (c & 1)) + 4 * (1 + ((c >> 1) & 1)) + 16 * (1 + (c >> 2));
+        const int n = s_cnt[lc];
+        const int ka = 2 * (pi - s_pp[c]), kb = ka + 1 < n ? ka + 1 : ka;
+        const int ga = s_gbeg[lc] + ka, gbi = s_gbeg[lc] + kb;
+        const float4 ta = __ldg(&sx[ga]), tb = __ldg(&sx[gbi]);
+        const uint64_t X = f2_pack(ta.x, tb.x), Y = f2_pack(ta.y, tb.y), Z = f2_pack(ta.z, tb.z);
+        uint64_t P = 0ull, GX = 0ull, GY = 0ull, GZ = 0ull;
+        if (staged)
+            super_sweep<SOFT, true>(stage, s_beg, s_cnt, lc, X, Y, Z, E2, P, GX, GY, GZ);
+        else
+            super_sweep<SOFT, false>(sx, s_gbeg, s_cnt, lc, X, Y, Z, E2, P, GX, GY, GZ);
+        float p0, p1, x0, x1, y0, y1, z0, z1;
+        f2_unpack(P, p0, p1);
+        f2_unpack(GX, x0, x1);
+        f2_unpack(GY, y0, y1);
+        f2_unpack(GZ, z0, z1);
+        {
+            const float4 f = far ? far[ga] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[perm[ga]] = make_float4(p0 + f.x, f.y - x0, f.z - y0, f.w - z0);
+        }
+        if (kb != ka) {
+            const float4 f = far ? far[gbi] : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[perm[gbi]] = make_float4(p1 + f.x, f.y - x1, f.z - y1, f.w - z1);
         }
     }
 }
@@ -473,8 +594,8 @@ static void dispatch_p2p(unsigned grid, int L, const int32_t *leaves, const floa
                          const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
                          const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
 {
-    if (p2p_tpt() == 12 || p2p_tpt() == 14) {
-        if (p2p_tpt() == 12) {
+    if (p2p_tpt() == 12 || p2p_tpt() == 14 || p2p_tpt() == 20) {
+        if (p2p_tpt() != 14) {  // 20 (superleaf, uniform tree only) takes 12 for leaf lists
             if (eps2 > 0.f)
                 k_p2p2<true, 2><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
             else
@@ -510,6 +631,15 @@ void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const 
                 cudaStream_t s)
 {
     if (n <= 0) return;
+    if (L >= 1 && p2p_tpt() == 20) {
+        const unsigned grid = (unsigned)(int64_t(1) << (3 * (L - 1)));
+        if (eps2 > 0.f)
+            k_p2p_super<true><<<grid, kSuperThreads, 0, s>>>(L, sx, begin, end, far, perm, eps2, out);
+        else
+            k_p2p_super<false><<<grid, kSuperThreads, 0, s>>>(L, sx, begin, end, far, perm, eps2, out);
+        note_launches(1);
+        return;
+    }
     dispatch_p2p((unsigned)(int64_t(1) << (3 * L)), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2,
                  out, s);
 }
