@@ -253,6 +253,19 @@ def run_gpu(args, w):
     value = n * ws / (ms_per_step / 1e3)
     stages = {k: float(np.mean(v)) for k, v in stage_acc.items()}
 
+    # the FP32 CUDA-core M2L (Eq. 4 on the same lists) measured beside the tensor-core default
+    cc_params = G.gbfmm_default_params(p=w["p"], leaf_size=w["leaf_size"],
+                                       flags=G.FLAG_STAGE_TIMING | G.FLAG_M2L_CUDA_CORES)
+    cc_ms = []
+    for i in range(4):
+        flush.zero_()
+        G.gbfmm_evaluate(fmm.ctx, cc_params, xd, out, fmm.workspace)
+        torch.cuda.synchronize()
+        if i > 0:
+            cc_ms.append(G.gbfmm_stage_times(fmm.ctx)["M2L/M2P"])
+    G.gbfmm_evaluate(fmm.ctx, fmm.params, xd, out, fmm.workspace)  # leave the default result in `out`
+    torch.cuda.synchronize()
+
     # end to end through the host-buffer ABI call (pinned host memory, copies in the timed region)
     hin = torch.from_numpy(x).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
@@ -276,6 +289,12 @@ def run_gpu(args, w):
     e2e_value = n * ws / (e2e_total / args.steps / 1e3)
 
     peak, peak_mhz = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        hbm_peak = 6800.0
+    sort_passes = -(-(3 * L) // 8)
+    sort_bytes = sort_passes * 16 + 32
     m2l_ms = stages.get("M2L/M2P", float("nan"))
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
@@ -309,9 +328,23 @@ def run_gpu(args, w):
                    "distribution": w["dist"], "parallelism": f"replicas x{ws}",
                    "l2": "flushed between steps (256 MiB write outside the per-step events)"},
         "roofline": roofline,
-        "kernels": {"p2p": {"achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
-                            "flop_per_pair": 20, "peak": peak, "bound": "alu",
-                            "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"}},
+        "kernels": {
+            "p2p": {"kernel": "k_p2p2", "achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
+                    "flop_per_pair": 20, "peak": peak, "bound": "alu",
+                    "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"},
+            "m2l_fp32_cores": {"kernel": "k_m2l", "ms": float(np.median(cc_ms)),
+                               "achieved_tflops": m2l_flops / (float(np.median(cc_ms)) / 1e3) / 1e12,
+                               "frac": m2l_flops / (float(np.median(cc_ms)) / 1e3) / 1e12 / peak, "peak": peak,
+                               "bound": "alu", "note": "same lists and Eq. 4 on the FP32 CUDA cores "
+                                                       "(GBFMM_FLAG_M2L_CUDA_CORES), timed on the same data"},
+            "box_keys": {"bytes_per_particle": 24, "achieved_gbs": 24 * n / (stages["box+keys"] / 1e3) / 1e9,
+                         "peak_gbs": hbm_peak, "bound": "hbm",
+                         "note": "read x,y,z,q (16 B) for the box and again for the keys, write key + index (8 B); "
+                                 "the box read is counted once"},
+            "sort": {"bytes_per_particle": sort_bytes, "achieved_gbs": sort_bytes * n / (stages["sort"] / 1e3) / 1e9,
+                     "peak_gbs": hbm_peak, "bound": "hbm",
+                     "note": f"{sort_passes} radix passes x (read key + index 8 B, write 8 B) + gather (16 B in, 16 B out)"},
+        },
         "stages_ms": stages,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},
         "gpu_launches": launches,
