@@ -370,6 +370,8 @@ def run_gpu(args, w):
         got = out.cpu().numpy().astype(np.float64)[tg]
         line["error_vs_fp64_direct"] = {"targets": len(tg), "phi_rel_l2": oracle.rel_l2(got[:, 0], ref[:, 0]),
                                         "grad_rel_l2": oracle.rel_l2(got[:, 1:], ref[:, 1:])}
+    if rank == 0 and ws == 1 and not args.no_serving:
+        line.update(run_next_rows(args, G, dev, local))
     if rank == 0:
         print(json.dumps(line), flush=True)
     fmm.close()
@@ -380,6 +382,55 @@ def run_gpu(args, w):
     return 0
 
 
+def run_next_rows(args, G, dev, local) -> dict:
+    """Batched uneven instances (512 sets, N log-uniform in [1e3, 2e5], half uniform cube on the
+    uniform octree and half Plummer on the adaptive one, p in {4, 8}) through the engine against
+    the plain one-at-a-time evaluation, and a served Poisson request stream (200 req/s, N
+    log-uniform in [1e3, 1e6], p in {4, 6, 10}) with latency percentiles."""
+    import torch
+
+    from paper_1010_1482_gb300 import serving
+
+    res = {}
+    inst = inputs.batch_instances()
+    x, offsets, params = serving.make_batch(inst, dev)
+    ctx = G.gbfmm_create(local)
+    serving.run_plain(ctx, x, offsets, params)  # warm-up (operator tables, workspace)
+    t_plain, out_plain = serving.run_plain(ctx, x, offsets, params)
+    G.gbfmm_destroy(ctx)
+    e = G.gbfmm_engine_create(local, args.workers, 40 << 30)
+    G.gbfmm_engine_prepare(e, [4, 6, 8, 10])
+    out = torch.empty_like(x)
+    G.gbfmm_engine_run_batch(e, offsets, params, x, out)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = G.gbfmm_engine_run_batch(e, offsets, params, x, out)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    total = int(offsets[-1])
+    res["batched"] = {
+        "instances": len(inst), "particles": total, "workers": args.workers,
+        "plain_particles_per_s": total / t_plain, "batched_particles_per_s": total / t_batch,
+        "speedup": t_plain / t_batch, "failed": int(sum(1 for v in st if v != 0)),
+        "identical_to_plain": bool(torch.equal(out, out_plain)),
+        "note": "plain = gbfmm_evaluate one instance at a time on one stream; batched = "
+                "gbfmm_engine_run_batch over the workers (their own streams and contexts), wall clock",
+    }
+    del x, out, out_plain
+    reqs = inputs.served_requests(duration=args.serve_seconds)
+    pools = {d: inputs.request_pool(d, 1 << 21) for d in ("uniform", "plummer")}
+    warm = inputs.served_requests(duration=0.5, seed=inputs.SEED_BASE + 6)
+    serving.run_stream(e, warm, pools)
+    stats = serving.run_stream(e, reqs, pools)
+    G.gbfmm_engine_destroy(e)
+    stats.update({"rate_per_s": 200.0, "duration_s": args.serve_seconds, "workers": args.workers,
+                  "budget_bytes": 40 << 30,
+                  "latency": "submit of host arrays -> result in host memory (copies included)",
+                  "inputs": "each request is a seeded contiguous slice of a 2^21-particle pool of its distribution"})
+    res["served"] = stats
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,6 +439,9 @@ def main():
     ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
     ap.add_argument("--workload", default="uniform_1m_p10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--workers", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = inputs.workload(args.workload)

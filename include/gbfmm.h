@@ -269,6 +269,52 @@ int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);
 int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_sorted_xyzq, uint32_t *d_perm,
                       uint32_t *d_sorted_leaf_keys, void *stream);
 
+/*
+ * Multi-instance engine: batched evaluation of many independent particle sets and a served
+ * request stream with continuous batching (the paper evaluates one system at a time; this is
+ * the runtime around the same single-instance evaluation).
+ *
+ * The engine owns `workers` host threads; each has its own context (operator tables, adaptive
+ * tree buffers), CUDA stream, device input/output buffers and uniform-tree workspace, kept
+ * resident and grown on demand.  Requests wait in one FIFO queue; a free worker takes the
+ * head request when the footprints of the running requests plus its own fit in
+ * memory_budget_bytes (a request larger than the whole budget runs alone).  Requests on
+ * different workers overlap on the device; each runs gbfmm_evaluate unchanged, so its result
+ * is the same alone or in a mix.  Footprint estimate: uniform tree 32 B x n (inputs and
+ * outputs, served requests only) + gbfmm_plan's workspace; adaptive tree 32 B x n + 128 B x n +
+ * (4n / leaf_size + 64) x (8p^2 + 640) B.  The workers' resident buffers are not released
+ * between requests, so the budget bounds what running requests use, not the engine's peak.
+ *
+ * gbfmm_engine_create: 1 <= workers <= 64.  ECUDA / ENOMEM / EINVAL.
+ * gbfmm_engine_destroy: stops the workers after their current request; requests still queued
+ *   are dropped (their tickets become invalid).  NULL-safe.
+ * gbfmm_engine_prepare: builds the operator tables of the listed orders on every worker (one
+ *   small evaluation each), so that no later request pays for them.  Synchronous.
+ * gbfmm_engine_submit: queues one request; h_xyzq (4n floats) and h_out (4n floats) are HOST
+ *   buffers that must stay valid until gbfmm_engine_wait returns for the ticket.  Returns at
+ *   once with *ticket.  prm is copied (GBFMM_FLAG_STAGE_TIMING is ignored).
+ * gbfmm_engine_wait: waits up to timeout_ms for the ticket; on completion returns OK and sets
+ *   *status (the request's gbfmm status), *queue_ms (submit -> start) and *latency_ms
+ *   (submit -> result in h_out), then forgets the ticket.  ETIMEOUT if it is not done yet
+ *   (the ticket stays valid); EINVAL for an unknown ticket.  Any output pointer may be NULL.
+ * gbfmm_engine_run_batch: evaluates nb instances whose particles are DEVICE arrays: instance
+ *   i is d_xyzq + 4*offsets[i] .. 4*offsets[i+1] (floats; offsets is a host array of nb + 1
+ *   ascending entries), results at the same offsets of d_out; prm[i] its parameters (host
+ *   array).  Returns when all are done; status[i] (host, may be NULL) receives each one's
+ *   status; the return value is the first error.  Must not be mixed with served requests whose
+ *   tickets another thread is waiting on.
+ */
+typedef struct gbfmm_engine gbfmm_engine;
+int gbfmm_engine_create(gbfmm_engine **out, int device, int32_t workers, size_t memory_budget_bytes);
+int gbfmm_engine_destroy(gbfmm_engine *e);
+int gbfmm_engine_prepare(gbfmm_engine *e, const int32_t *orders, int32_t norders);
+int gbfmm_engine_submit(gbfmm_engine *e, const gbfmm_params *prm, int64_t n, const float *h_xyzq, float *h_out,
+                        int64_t *ticket);
+int gbfmm_engine_wait(gbfmm_engine *e, int64_t ticket, double timeout_ms, int32_t *status, double *queue_ms,
+                      double *latency_ms);
+int gbfmm_engine_run_batch(gbfmm_engine *e, int32_t nb, const int64_t *offsets, const gbfmm_params *prm,
+                           const float *d_xyzq, float *d_out, int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,13 @@ def lib():
         "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
         "gbfmm_probe_peak": (i, [i, ctypes.POINTER(ctypes.c_double)]),
         "gbfmm_selftest_wait": (i, [P, ctypes.c_double, P]),
+        "gbfmm_engine_create": (i, [ctypes.POINTER(P), i, ctypes.c_int32, ctypes.c_size_t]),
+        "gbfmm_engine_destroy": (i, [P]),
+        "gbfmm_engine_prepare": (i, [P, P, ctypes.c_int32]),
+        "gbfmm_engine_submit": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, ctypes.POINTER(i64)]),
+        "gbfmm_engine_wait": (i, [P, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "gbfmm_engine_run_batch": (i, [P, ctypes.c_int32, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -266,6 +273,59 @@ def gbfmm_sort_static(prm: gbfmm_params, xyzq: torch.Tensor, sorted_xyzq: torch.
     assert perm.dtype == torch.int32 and sorted_leaf_keys.dtype == torch.int32  # uint32 bit patterns
     _check(None, lib().gbfmm_sort_static(ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _ptr(sorted_xyzq),
                                          _ptr(perm), _ptr(sorted_leaf_keys), _stream(stream)))
+
+
+def gbfmm_engine_create(device: int = 0, workers: int = 4, memory_budget_bytes: int = 40 << 30):
+    e = ctypes.c_void_p()
+    _check(None, lib().gbfmm_engine_create(ctypes.byref(e), int(device), int(workers), int(memory_budget_bytes)))
+    return e
+
+
+def gbfmm_engine_destroy(e) -> None:
+    lib().gbfmm_engine_destroy(e)
+
+
+def gbfmm_engine_prepare(e, orders) -> None:
+    import numpy as np
+
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    _check(None, lib().gbfmm_engine_prepare(e, _np_ptr(o), len(o)))
+
+
+def gbfmm_engine_submit(e, prm: gbfmm_params, h_xyzq, h_out) -> int:
+    """h_xyzq, h_out: host float32 (n, 4) arrays (numpy or CPU tensors) kept alive by the caller
+    until gbfmm_engine_wait returns for the ticket."""
+    t = ctypes.c_int64()
+    ptr_in = h_xyzq.ctypes.data_as(ctypes.c_void_p) if hasattr(h_xyzq, "ctypes") else _ptr(h_xyzq)
+    ptr_out = h_out.ctypes.data_as(ctypes.c_void_p) if hasattr(h_out, "ctypes") else _ptr(h_out)
+    _check(None, lib().gbfmm_engine_submit(e, ctypes.byref(prm), int(h_xyzq.shape[0]), ptr_in, ptr_out,
+                                           ctypes.byref(t)))
+    return t.value
+
+
+def gbfmm_engine_wait(e, ticket: int, timeout_ms: float = 60000.0):
+    """Returns (status, queue_ms, latency_ms); raises GbfmmError(ETIMEOUT) if not done in time."""
+    st, q, lat = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().gbfmm_engine_wait(e, int(ticket), float(timeout_ms), ctypes.byref(st), ctypes.byref(q),
+                                         ctypes.byref(lat)))
+    return st.value, q.value, lat.value
+
+
+def gbfmm_engine_run_batch(e, offsets, params, xyzq: torch.Tensor, out: torch.Tensor):
+    """offsets: nb + 1 ascending particle offsets; params: list of gbfmm_params; xyzq, out:
+    device float32 (total, 4) tensors.  Returns the per-instance status list."""
+    import numpy as np
+
+    nb = len(params)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    assert len(off) == nb + 1
+    arr = (gbfmm_params * max(nb, 1))(*params)
+    st = np.zeros(max(nb, 1), dtype=np.int32)
+    rc = lib().gbfmm_engine_run_batch(e, nb, _np_ptr(off), ctypes.cast(arr, ctypes.c_void_p), _ptr(xyzq), _ptr(out),
+                                      _np_ptr(st))
+    if rc != GBFMM_OK:
+        raise GbfmmError(rc, "batch")
+    return st[:nb].tolist()
 
 
 # ---- convenience wrapper (torch-allocated workspace) -----------------------------------------
