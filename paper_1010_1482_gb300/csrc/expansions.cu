@@ -346,11 +346,13 @@ void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *b
 // ------------------------------------------------------------------------------------------
 constexpr int kTrTN = 32, kTrCN = 8;
 
-template <int P, bool UP>
+template <int P, bool UP, int TN = kTrTN>
 struct TransCfg {
     static constexpr int PP = P * P, PR = ops_rows_padded(P), SB = staged_col_stride(P);
-    static constexpr int NCG = kTrTN / kTrCN, NRG = PR / 4, NT = ((NRG * NCG + 31) / 32) * 32;
-    static constexpr size_t kSmem = ((size_t)PP * PR + (size_t)kTrTN * SB) * sizeof(float);
+    static constexpr int NCG = TN / kTrCN, NRG = PR / 4, NT = ((NRG * NCG + 31) / 32) * 32;
+    static constexpr int AF = PP * PR, BF = TN * SB;  // floats of one operator / one column block
+    static constexpr int NBUF = UP ? 2 : 1;           // M2M walks 8 child positions: double-buffered
+    static constexpr size_t kSmem = (size_t)NBUF * (AF + BF) * sizeof(float);
 };
 
 GB_DEV int degree_of(int r)
@@ -360,20 +362,29 @@ GB_DEV int degree_of(int r)
     return d;
 }
 
-template <int P, bool UP>
-__global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate(int l, const int32_t *__restrict__ begin,
-                                                                   const int32_t *__restrict__ end,
-                                                                   const float *__restrict__ ops, float *__restrict__ X)
+GB_DEV void cp_async16_t(void *dst, const void *src, uint32_t src_bytes)
 {
-    using Cfg = TransCfg<P, UP>;
-    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// TN cells per CTA; the operator of each child position and the TN source columns are copied
+// into shared memory with cp.async (zero-filled for missing cells), the next child position's
+// copies in flight while the current one is applied
+template <int P, bool UP, int TN>
+__global__ void __launch_bounds__(TransCfg<P, UP, TN>::NT) k_translate(int l, const int32_t *__restrict__ begin,
+                                                                       const int32_t *__restrict__ end,
+                                                                       const float *__restrict__ ops,
+                                                                       float *__restrict__ X)
+{
+    using Cfg = TransCfg<P, UP, TN>;
+    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG, CN = kTrCN;
     extern __shared__ __align__(16) float tsm[];
-    float *A = tsm;            // [PP cols][PR rows]
-    float *B = tsm + PP * PR;  // [kTrTN][SB]
     // parents: level l (M2M) or l - 1 (L2L)
     const int lp = UP ? l : l - 1;
     const int64_t np = int64_t(1) << (3 * lp);
-    const int64_t q0 = blockIdx.x * (int64_t)kTrTN;
+    const int64_t q0 = blockIdx.x * (int64_t)TN;
     const int64_t offp = level_offset(lp), offc = level_offset(lp + 1);
     const int tid = threadIdx.x;
     const bool work = tid < NRG * NCG;
@@ -389,41 +400,58 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate(int l, const 
             kbeg = (d * d) / 4 * 4;
         }
     }
-    float acc[4][kTrCN];
+    auto stage = [&](int c, int buf) {
+        float *A = tsm + buf * (Cfg::AF + Cfg::BF);
+        float *B = A + Cfg::AF;
+        const float *src = ops + (size_t)c * PP * PR;
+        for (int e = tid; e < PP * PR / 4; e += blockDim.x) cp_async16_t(A + 4 * e, src + 4 * e, 16u);
+        for (int e = tid; e < TN * (PP / 4); e += blockDim.x) {
+            const int i = e / (PP / 4), k4 = e % (PP / 4);
+            const int64_t q = q0 + i;
+            const float *gsrc = X;
+            uint32_t bytes = 0;
+            if (q < np) {
+                const int64_t g = UP ? offc + 8 * q + c : offp + q;
+                if (end[g] > begin[g]) {
+                    gsrc = X + g * PP + 4 * k4;
+                    bytes = 16u;
+                }
+            }
+            cp_async16_t(B + i * SB + 4 * k4, gsrc, bytes);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float acc[4][CN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < kTrCN; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < CN; ++j) acc[i][j] = 0.f;
     const int c_first = UP ? 0 : blockIdx.y, c_last = UP ? 7 : blockIdx.y;
+    stage(c_first, 0);
     for (int c = c_first; c <= c_last; ++c) {
-        if (c != c_first) __syncthreads();
-        const float4 *src = reinterpret_cast<const float4 *>(ops + (size_t)c * PP * PR);
-        for (int e = tid; e < PP * PR / 4; e += blockDim.x) reinterpret_cast<float4 *>(A)[e] = __ldg(&src[e]);
-        for (int e = tid; e < kTrTN * (PP / 4); e += blockDim.x) {
-            const int i = e / (PP / 4), k4 = e % (PP / 4);
-            const int64_t q = q0 + i;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < np) {
-                const int64_t g = UP ? offc + 8 * q + c : offp + q;
-                if (end[g] > begin[g]) v = reinterpret_cast<const float4 *>(X + g * PP)[k4];
-            }
-            *reinterpret_cast<float4 *>(B + i * SB + 4 * k4) = v;
+        const int buf = UP ? (c - c_first) & 1 : 0;
+        if (c < c_last) {
+            stage(c + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
         if (work) {
-            const float *Ar = A + rg * 4;
-            const float *Bc = B + cg * SB;
+            const float *Ar = tsm + buf * (Cfg::AF + Cfg::BF) + rg * 4;
+            const float *Bc = tsm + buf * (Cfg::AF + Cfg::BF) + Cfg::AF + cg * SB;
 #pragma unroll 2
             for (int k = kbeg; k < kend; k += 4) {
-                Frag<kTrCN, 4> f;
+                Frag<CN, 4> f;
                 f.load(Ar, Bc, k, PR, NCG * SB);
                 f.fma(acc);
             }
         }
+        __syncthreads();  // the buffer is refilled two positions later
     }
     if (!work) return;
 #pragma unroll
-    for (int j = 0; j < kTrCN; ++j) {
+    for (int j = 0; j < CN; ++j) {
         const int64_t q = q0 + cg + j * NCG;
         if (q >= np) continue;
         const int r = rg * 4;
@@ -444,16 +472,29 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate(int l, const 
     }
 }
 
+template <int P, bool UP, int TN>
+static void launch_translate_tn(int l, const int32_t *begin, const int32_t *end, const float *ops, float *X,
+                                cudaStream_t s)
+{
+    using Cfg = TransCfg<P, UP, TN>;
+    cudaFuncSetAttribute(k_translate<P, UP, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    const int64_t np = int64_t(1) << (3 * (UP ? l : l - 1));
+    dim3 grid((unsigned)((np + TN - 1) / TN), UP ? 1 : 8);
+    k_translate<P, UP, TN><<<grid, Cfg::NT, Cfg::kSmem, s>>>(l, begin, end, ops, X);
+    note_launches(1);
+}
+
+// cells per CTA: 32 when the level has enough cells to fill the GPU twice over, else 8
 template <int P, bool UP>
 static void launch_translate_t(int l, const int32_t *begin, const int32_t *end, const float *ops, float *X,
                                cudaStream_t s)
 {
-    using Cfg = TransCfg<P, UP>;
-    cudaFuncSetAttribute(k_translate<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     const int64_t np = int64_t(1) << (3 * (UP ? l : l - 1));
-    dim3 grid((unsigned)((np + kTrTN - 1) / kTrTN), UP ? 1 : 8);
-    k_translate<P, UP><<<grid, Cfg::NT, Cfg::kSmem, s>>>(l, begin, end, ops, X);
-    note_launches(1);
+    const int64_t ctas32 = (np + 31) / 32 * (UP ? 1 : 8);
+    if (ctas32 >= 2 * 152)
+        launch_translate_tn<P, UP, 32>(l, begin, end, ops, X, s);
+    else
+        launch_translate_tn<P, UP, 8>(l, begin, end, ops, X, s);
 }
 
 void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s)
@@ -964,9 +1005,10 @@ static void translate_cells_t(int64_t lo, int64_t np, const int32_t *child_of, c
                               float *X, cudaStream_t s)
 {
     using Cfg = TransCfg<P, UP>;
-    cudaFuncSetAttribute(k_translate_cells<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    const int smem = (int)((Cfg::AF + Cfg::BF) * sizeof(float));  // one operator + one column block
+    cudaFuncSetAttribute(k_translate_cells<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     dim3 grid((unsigned)((np + kTrTN - 1) / kTrTN), UP ? 1 : 8);
-    k_translate_cells<P, UP><<<grid, Cfg::NT, Cfg::kSmem, s>>>(lo, np, child_of, nchild, ops, X);
+    k_translate_cells<P, UP><<<grid, Cfg::NT, smem, s>>>(lo, np, child_of, nchild, ops, X);
     note_launches(1);
 }
 

@@ -480,54 +480,6 @@ void launch_cells(const uint32_t *sk, int64_t n, int L, int32_t *begin, int32_t 
 // ------------------------------------------------------------------------------------------
 GB_DEV bool nonempty(const int32_t *begin, const int32_t *end, int64_t g) { return end[g] > begin[g]; }
 
-template <class F>
-GB_DEV void for_each_m2l(int l, uint32_t key, const int32_t *begin, const int32_t *end, F f)
-{
-    int x, y, z;
-    demorton3(key, x, y, z);
-    const int side = 1 << l;
-    const int cx = x & 1, cy = y & 1, cz = z & 1;
-    const int64_t off = level_offset(l);
-    for (int oz = -2 - cz; oz <= 3 - cz; ++oz) {
-        int sz = z + oz;
-        if (sz < 0 || sz >= side) continue;
-        for (int oy = -2 - cy; oy <= 3 - cy; ++oy) {
-            int sy = y + oy;
-            if (sy < 0 || sy >= side) continue;
-            for (int ox = -2 - cx; ox <= 3 - cx; ++ox) {
-                int sxx = x + ox;
-                if (sxx < 0 || sxx >= side) continue;
-                if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-                int64_t g = off + morton3((uint32_t)sxx, (uint32_t)sy, (uint32_t)sz);
-                if (nonempty(begin, end, g)) f(g, m2l_code(ox, oy, oz));
-            }
-        }
-    }
-}
-
-template <class F>
-GB_DEV void for_each_p2p(int L, uint32_t key, const int32_t *begin, const int32_t *end, F f)
-{
-    int x, y, z;
-    demorton3(key, x, y, z);
-    const int side = 1 << L;
-    const int64_t off = level_offset(L);
-    for (int oz = -1; oz <= 1; ++oz) {
-        int sz = z + oz;
-        if (sz < 0 || sz >= side) continue;
-        for (int oy = -1; oy <= 1; ++oy) {
-            int sy = y + oy;
-            if (sy < 0 || sy >= side) continue;
-            for (int ox = -1; ox <= 1; ++ox) {
-                int sxx = x + ox;
-                if (sxx < 0 || sxx >= side) continue;
-                int64_t g = off + morton3((uint32_t)sxx, (uint32_t)sy, (uint32_t)sz);
-                if (nonempty(begin, end, g)) f(g);
-            }
-        }
-    }
-}
-
 GB_DEV void cell_of(int64_t g, int &l, uint32_t &key)
 {
     l = 0;
@@ -535,64 +487,95 @@ GB_DEV void cell_of(int64_t g, int &l, uint32_t &key)
     key = (uint32_t)(g - level_offset(l));
 }
 
-__global__ void k_list_count(int L, int64_t C, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                             uint32_t *__restrict__ p2p_len, uint32_t *__restrict__ m2l_len)
-{
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= C) return;
-    int l;
-    uint32_t key;
-    cell_of(g, l, key);
-    bool ne = nonempty(begin, end, g);
-    uint32_t c = 0;
-    if (ne && l >= 2) for_each_m2l(l, key, begin, end, [&](int64_t, int) { ++c; });
-    m2l_len[g] = c;
-    if (l == L) {
-        uint32_t q = 0;
-        if (ne) for_each_p2p(L, key, begin, end, [&](int64_t) { ++q; });
-        p2p_len[key] = q;
-    }
-}
+// Warp per cell.  The lanes test the 6 x 6 x 6 box of candidate offsets around the parent's
+// neighbourhood (M2L) and the 27 neighbours (P2P) 32 at a time; a ballot keeps the candidates
+// in ascending stencil-code order (offset index = ox + 6 oy + 36 oz, with the box's corner at
+// -2 - (child bit)), the order the M2L kernels walk.
+constexpr int kListWarps = 8;
 
-__global__ void k_list_fill(int L, int64_t C, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                            const uint32_t *__restrict__ p2p_offs, int32_t *__restrict__ p2p_ids,
-                            const uint32_t *__restrict__ m2l_offs, int32_t *__restrict__ m2l_ids,
-                            uint16_t *__restrict__ m2l_code)
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, const int32_t *__restrict__ begin,
+                                                           const int32_t *__restrict__ end,
+                                                           uint32_t *__restrict__ p2p_len, uint32_t *__restrict__ m2l_len,
+                                                           const uint32_t *__restrict__ p2p_offs,
+                                                           int32_t *__restrict__ p2p_ids,
+                                                           const uint32_t *__restrict__ m2l_offs,
+                                                           int32_t *__restrict__ m2l_ids, uint16_t *__restrict__ m2l_code)
 {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = blockIdx.x * (int64_t)kListWarps + (threadIdx.x >> 5);
     if (g >= C) return;
     int l;
     uint32_t key;
     cell_of(g, l, key);
-    if (!nonempty(begin, end, g)) return;
+    const bool ne = nonempty(begin, end, g);
+    int x, y, z;
+    demorton3(key, x, y, z);
+    const int side = 1 << l;
+    const int64_t off = level_offset(l);
+    const unsigned lt = (1u << lane) - 1u;
     if (l >= 2) {
-        uint32_t e = m2l_offs[g];
-        for_each_m2l(l, key, begin, end, [&](int64_t s, int code) {
-            m2l_ids[e] = (int32_t)s;
-            m2l_code[e] = (uint16_t)code;
-            ++e;
-        });
+        uint32_t cnt = 0, e = FILL ? m2l_offs[g] : 0u;
+        if (ne) {
+            const int bx = -2 - (x & 1), by = -2 - (y & 1), bz = -2 - (z & 1);
+            for (int i0 = 0; i0 < 216; i0 += 32) {
+                const int i = i0 + lane;
+                const int ox = bx + i % 6, oy = by + (i / 6) % 6, oz = bz + i / 36;
+                const int sx = x + ox, sy = y + oy, sz = z + oz;
+                bool ok = i < 216 && sx >= 0 && sy >= 0 && sz >= 0 && sx < side && sy < side && sz < side &&
+                          !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
+                int64_t s = 0;
+                if (ok) {
+                    s = off + morton3((uint32_t)sx, (uint32_t)sy, (uint32_t)sz);
+                    ok = nonempty(begin, end, s);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (FILL && ok) {
+                    const uint32_t at = e + cnt + __popc(m & lt);
+                    m2l_ids[at] = (int32_t)s;
+                    m2l_code[at] = (uint16_t)gbfmm::m2l_code(ox, oy, oz);
+                }
+                cnt += __popc(m);
+            }
+        }
+        if (!FILL && lane == 0) m2l_len[g] = cnt;
+    } else if (!FILL && lane == 0) {
+        m2l_len[g] = 0;
     }
     if (l == L) {
-        uint32_t e = p2p_offs[key];
-        for_each_p2p(L, key, begin, end, [&](int64_t s) { p2p_ids[e++] = (int32_t)s; });
+        uint32_t cnt = 0, e = FILL ? p2p_offs[key] : 0u;
+        if (ne) {
+            const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+            const int sx = x + ox, sy = y + oy, sz = z + oz;
+            bool ok = lane < 27 && sx >= 0 && sy >= 0 && sz >= 0 && sx < side && sy < side && sz < side;
+            int64_t s = 0;
+            if (ok) {
+                s = off + morton3((uint32_t)sx, (uint32_t)sy, (uint32_t)sz);
+                ok = nonempty(begin, end, s);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (FILL && ok) p2p_ids[e + __popc(m & lt)] = (int32_t)s;
+            cnt = __popc(m);
+        }
+        if (!FILL && lane == 0) p2p_len[key] = cnt;
     }
 }
 
 void launch_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t *p2p_len, uint32_t *m2l_len,
                        cudaStream_t s)
 {
-    int64_t C = level_offset(L + 1);
-    k_list_count<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(L, C, begin, end, p2p_len, m2l_len);
+    const int64_t C = level_offset(L + 1);
+    k_lists<false><<<(unsigned)((C + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
+        L, C, begin, end, p2p_len, m2l_len, nullptr, nullptr, nullptr, nullptr, nullptr);
     note_launches(1);
 }
 
 void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
                       const uint32_t *m2l_offs, int32_t *m2l_ids, uint16_t *m2l_code, cudaStream_t s)
 {
-    int64_t C = level_offset(L + 1);
-    k_list_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(L, C, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids,
-                                                           m2l_code);
+    const int64_t C = level_offset(L + 1);
+    k_lists<true><<<(unsigned)((C + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
+        L, C, begin, end, nullptr, nullptr, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code);
     note_launches(1);
 }
 
