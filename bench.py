@@ -428,7 +428,62 @@ def run_next_rows(args, G, dev, local) -> dict:
                   "latency": "submit of host arrays -> result in host memory (copies included)",
                   "inputs": "each request is a seeded contiguous slice of a 2^21-particle pool of its distribution"})
     res["served"] = stats
+    res["crossover"] = run_crossover(G, dev, local)
     return res
+
+
+def run_crossover(G, dev, local) -> dict:
+    """Direct sum vs treecode vs FMM on the uniform cube (the paper's Fig. 4 comparison): device
+    time of one evaluation and the gradient error vs FP64 direct on 256 seeded targets, for each
+    method at p = 4, 6, 8, 10, leaf 64."""
+    import torch
+
+    import oracle
+
+    rows = []
+    ctx = G.gbfmm_create(local)
+    for n in (4096, 32768, 262144, 1048576):
+        x = inputs.uniform_cube(n, inputs.SEED_BASE + 7)
+        xd = torch.from_numpy(x).to(dev)
+        out = torch.empty_like(xd)
+        tg = inputs.sample_indices(n, 256, inputs.SEED_BASE + 7)
+        ref = oracle.direct(x, targets=tg)
+
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(reps):
+                fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        ms = timed(lambda: G.gbfmm_direct(ctx, xd, xd, out), reps=1 if n > 300000 else 3)
+        err = oracle.rel_l2(out.cpu().numpy().astype(np.float64)[tg, 1:], ref[:, 1:])
+        rows.append({"n": n, "method": "direct", "p": None, "ms": ms, "grad_err": err})
+        for method, name in ((G.METHOD_TREECODE, "treecode"), (G.METHOD_FMM, "fmm")):
+            for p in (4, 6, 8, 10):
+                prm = G.gbfmm_default_params(p=p, leaf_size=64, method=method)
+                _, wsb = G.gbfmm_plan(prm, n)
+                wsp = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+                ms = timed(lambda: G.gbfmm_evaluate(ctx, prm, xd, out, wsp))
+                G.gbfmm_sync_status(ctx)
+                err = oracle.rel_l2(out.cpu().numpy().astype(np.float64)[tg, 1:], ref[:, 1:])
+                rows.append({"n": n, "method": name, "p": p, "ms": ms, "grad_err": err})
+    G.gbfmm_destroy(ctx)
+    best = {}
+    for r in rows:
+        if r["grad_err"] <= 1e-4:
+            k = (r["n"], r["method"])
+            if k not in best or r["ms"] < best[k]["ms"]:
+                best[k] = r
+    fastest = {str(n): min((v for (m, _), v in best.items() if m == n), key=lambda v: v["ms"])["method"]
+               for n in sorted({r["n"] for r in rows})}
+    return {"rows": rows, "fastest_at_1e-4": fastest,
+            "note": "uniform cube, leaf 64, device time of one evaluation (CUDA events); the error bar is the "
+                    "gradient rel L2 <= 1e-4 vs FP64 direct on 256 seeded targets"}
 
 
 def main():
