@@ -7,10 +7,11 @@
 // p^2 output rows of T_o its N dimension (padded to a multiple of 16) and the p^2 input
 // coefficients its K dimension (padded to a multiple of 8):
 //     D[128 x N] (TMEM, FP32) += A[128 x K] (gathered source expansions) * B[N x K]^T (T_o).
-// FP32 accuracy from TF32 operands (3xTF32): every operand is split x = hi + lo with hi and lo
-// rounded to TF32, and D accumulates hi*hi + lo*hi + hi*lo; the dropped lo*lo term and the
-// rounding of lo are below 2^-21 of |x|.  The operator halves are split once, when the table
-// is built; the source halves are split by the threads that gather them.
+// FP32 accuracy from TF32 operands (3xTF32): every operand is split x = hi + lo with hi rounded
+// to TF32, and D accumulates hi*hi + lo*hi + hi*lo; the dropped lo*lo term and the TF32
+// rounding (operator table) or truncation (sources, in the tensor core) of lo are below 2^-21
+// of |x|.  The operator halves are split once, when the table is built; the source halves by
+// the threads that gather them.
 //
 // Pipeline (one CTA per tile, warp-specialised, NSTAGE stages; a stage is one K-chunk of one
 // offset).  The A operand lives in tensor memory, so shared memory carries only the operator:
@@ -143,7 +144,7 @@ struct TcTiles {
     int ntiles_level[kMaxLevel + 1];
 };
 
-template <int P, int CK, int NS>
+template <int P, int CK, int NS, int GRP>
 __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     k_m2l_tc(TcTiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     using T = TcTable<P>;
     constexpr int PP = C::PP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
     constexpr int S = 189 * NCH;
+    constexpr int NGRP = (189 + GRP - 1) / GRP;  // accumulation chains (GRP offsets each)
     constexpr uint32_t kIdesc = tc_idesc_tf32(TM, NP);
     constexpr int kMmaWarp = 8;
 
@@ -264,10 +266,10 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
         float acc[NH];
 #pragma unroll
         for (int n = 0; n < NH; ++n) acc[n] = 0.f;
-        auto drain = [&](int oc) -> bool {
-            const int b = oc & 1;
+        auto drain = [&](int gi) -> bool {
+            const int b = gi & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait_bounded(&drain_full[b], (oc >> 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait_bounded(&drain_full[b], (gi >> 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) return false;
             tc_fence_after();
@@ -310,15 +312,18 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             }
             // split into TF32 halves and store the thread's 16 columns of A_hi and A_lo (its
             // TMEM lane = its target row)
+            // hi = x rounded to TF32 (nearest, ties away: add half a TF32 unit to the magnitude's
+            // bits and clear the 13 low bits); lo = x - hi exactly, which the tensor core reads
+            // truncated to TF32 (error < 2^-21 |x|)
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float x[4] = {cur[i].x, cur[i].y, cur[i].z, cur[i].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float a = tf32_rna(x[e]);
-                    hi[4 * i + e] = __float_as_uint(a);
-                    lo[4 * i + e] = __float_as_uint(tf32_rna(x[e] - a));
+                    const uint32_t hb = (__float_as_uint(x[e]) + 0x1000u) & 0xFFFFE000u;
+                    hi[4 * i + e] = hb;
+                    lo[4 * i + e] = __float_as_uint(x[e] - __uint_as_float(hb));
                 }
             }
             const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + 16 * h);
@@ -329,8 +334,8 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_bar[st]);
             load(s + 2, cur);
-            // the previous offset's partial is complete once this one is queued
-            if (c == NCH - 1 && oc >= 1 && !drain(oc - 1)) alive = false;
+            // the previous chain's partial is complete once the next chain's first offset is queued
+            if (c == NCH - 1 && oc >= 1 && (oc - 1) % GRP == GRP - 1 && !drain((oc - 1) / GRP)) alive = false;
         };
         float4 b0[4], b1[4];
         load(0, b0);
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             step(s, b0);
             if (s + 1 < S && alive) step(s + 1, b1);
         }
-        if (alive && !drain(188)) alive = false;
+        if (alive && !drain(NGRP - 1)) alive = false;
         if (!alive && lane == 0) s_abort = 1;
         // every MMA has completed once done_bar has (bounded; needed before TMEM is freed)
         int ok = 1;
@@ -355,11 +360,12 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
                         make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
         }
     } else if (lane == 0) {
-        // ================= MMA issuer: offset oc accumulates in TMEM buffer oc & 1 =================
+        // ======= MMA issuer: chain gi (offsets GRP gi .. GRP gi + GRP - 1) accumulates in TMEM buffer gi & 1 =======
         for (int s = 0; s < S; ++s) {
-            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH, b = oc & 1;
-            if (c == 0 && oc >= 2 &&
-                !mbar_wait_bounded(&drain_empty[b], ((oc - 2) >> 1) & 1, kWaitLimitNs, &s_abort)) {
+            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH, gi = oc / GRP, b = gi & 1;
+            const bool chain_start = c == 0 && oc % GRP == 0;
+            if (chain_start && gi >= 2 &&
+                !mbar_wait_bounded(&drain_empty[b], ((gi - 2) >> 1) & 1, kWaitLimitNs, &s_abort)) {
                 s_abort = 1;
                 break;
             }
@@ -377,12 +383,12 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
                 const uint64_t bh = smem_desc(Bhi + j * 2 * NP * 4, NP * 16, 128);
                 const uint64_t bl = smem_desc(Blo + j * 2 * NP * 4, NP * 16, 128);
                 // the small cross terms first, the hi*hi term last
-                tc_mma_tf32_ta(d, alo + 8 * j, bh, kIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                tc_mma_tf32_ta(d, alo + 8 * j, bh, kIdesc, (chain_start && j == 0) ? 0u : 1u);
                 tc_mma_tf32_ta(d, ahi + 8 * j, bl, kIdesc, 1u);
                 tc_mma_tf32_ta(d, ahi + 8 * j, bh, kIdesc, 1u);
             }
             tc_commit(&empty_bar[st]);
-            if (c == NCH - 1) tc_commit(&drain_full[b]);
+            if (c == NCH - 1 && (oc % GRP == GRP - 1 || oc == 188)) tc_commit(&drain_full[b]);
         }
         tc_commit(&done_bar);  // completes once every MMA issued above has completed
     }
@@ -404,27 +410,28 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     }
 }
 
-template <int P, int CK, int NS>
+template <int P, int CK, int NS, int GRP = 1>
 static void launch_m2l_tc_t(const TcTiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                             const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                             const int32_t *m2l_ids, const uint16_t *m2l_code, const float *optc, const float *M,
                             float *Lc, int *status, cudaStream_t s)
 {
     using C = TcCfg<P, CK, NS>;
-    cudaFuncSetAttribute(k_m2l_tc<P, CK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-    k_m2l_tc<P, CK, NS><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
+    cudaFuncSetAttribute(k_m2l_tc<P, CK, NS, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+    k_m2l_tc<P, CK, NS, GRP><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
                                                                   m2l_ids, m2l_code, optc, M, Lc, status);
     note_launches(1);
 }
 
 // pipeline shape (GBFMM_M2L_TC_CFG, p = 10): 0 = chunks of <= 4 K steps, 4 stages; 1 = 4 steps,
-// 2 stages; 2 = 2 steps, 4 stages; 3 = 3 steps, 4 stages
+// 2 stages; 2 = 2 steps, 4 stages; 3 = 3 steps, 4 stages; 4, 5 = as 0 with 2, 3 offsets per
+// TMEM accumulation chain
 static int tc_variant()
 {
     static const int v = [] {
         const char *e = getenv("GBFMM_M2L_TC_CFG");
         const int x = e ? atoi(e) : 0;
-        return (x >= 0 && x <= 3) ? x : 0;
+        return (x >= 0 && x <= 5) ? x : 0;
     }();
     return v;
 }
@@ -444,6 +451,8 @@ static void dispatch_tc(int P, const TcTiles &tiles, int grid, const int4 *tdesc
         case 1: launch_m2l_tc_t<10, 4, 2>(GBFMM_TC_ARGS); break;
         case 2: launch_m2l_tc_t<10, 2, 4>(GBFMM_TC_ARGS); break;
         case 3: launch_m2l_tc_t<10, 3, 4>(GBFMM_TC_ARGS); break;
+        case 4: launch_m2l_tc_t<10, 4, 4, 2>(GBFMM_TC_ARGS); break;
+        case 5: launch_m2l_tc_t<10, 4, 4, 3>(GBFMM_TC_ARGS); break;
         default: launch_m2l_tc_t<10, 4, 4>(GBFMM_TC_ARGS); break;
         }
         break;
