@@ -56,13 +56,13 @@ void init_m2l_tc_constants()
 }
 
 // Shapes per order.  KS = K steps of 8 per offset, split into NCH chunks of (nearly) equal size
-// (at most CK steps each); NS pipeline stages.
-template <int P, int CK, int NS>
+// (at most CK steps each); NS pipeline stages; Q converter warps per TMEM lane quadrant.
+template <int P, int CK, int NS, int Q = 2>
 struct TcCfg {
     static constexpr int PP = P * P;
     static constexpr int KP = (PP + 7) / 8 * 8;      // K, padded to the MMA's K step
     static constexpr int NP = (PP + 15) / 16 * 16;   // N, padded to a multiple of 16
-    static constexpr int NH = NP / 2;                // output columns drained per thread
+    static constexpr int NH = NP / Q;                // output columns drained per thread
     static constexpr int KS = KP / 8;
     static constexpr int NCH = (KS + CK - 1) / CK;
     static constexpr int KCMAX = 8 * ((KS + NCH - 1) / NCH);  // K width of the largest chunk
@@ -76,7 +76,10 @@ struct TcCfg {
     // at least 116 KB of shared memory: one CTA per SM, so the whole of TMEM is this CTA's
     static constexpr size_t kStageBytes = (size_t)NSTAGE * B_FLOATS * sizeof(float);
     static constexpr size_t kSmemBytes = kStageBytes > 116 * 1024 ? kStageBytes : 116 * 1024;
-    static constexpr int NTHREADS = 288;             // 8 converter warps (2 per TMEM lane quadrant), 1 MMA warp
+    static constexpr int NCONV = 4 * Q;              // converter warps (Q per TMEM lane quadrant)
+    static constexpr int NF = KCMAX / 4 / Q;         // float4 columns of a chunk per converter thread
+    static constexpr int NTHREADS = 32 * NCONV + 32; // + one MMA warp
+    static_assert((KCMAX / 4) % Q == 0 && NH % 4 == 0, "converter split");
     static_assert(NP >= 16 && NP <= 128 && NP % 16 == 0, "MMA N (two accumulators below column 256)");
     static_assert(KCMAX <= 32, "a K chunk fits a 32-column TMEM slot");
     static_assert(A_COL0 + 64 * NS <= TMEM_COLS, "TMEM A stages");
@@ -144,21 +147,21 @@ struct TcTiles {
     int ntiles_level[kMaxLevel + 1];
 };
 
-template <int P, int CK, int NS, int GRP>
-__global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
+template <int P, int CK, int NS, int GRP, int Q>
+__global__ void __launch_bounds__(TcCfg<P, CK, NS, Q>::NTHREADS, 1)
     k_m2l_tc(TcTiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
              const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
              const uint16_t *__restrict__ m2l_code, const float *__restrict__ optc, const float *__restrict__ M,
              float *__restrict__ Lc, int *status)
 {
-    using C = TcCfg<P, CK, NS>;
+    using C = TcCfg<P, CK, NS, Q>;
     using T = TcTable<P>;
-    constexpr int PP = C::PP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
+    constexpr int PP = C::PP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH, NF = C::NF;
     constexpr int S = 189 * NCH;
     constexpr int NGRP = (189 + GRP - 1) / GRP;  // accumulation chains (GRP offsets each)
     constexpr uint32_t kIdesc = tc_idesc_tf32(TM, NP);
-    constexpr int kMmaWarp = 8;
+    constexpr int kMmaWarp = C::NCONV;
 
     extern __shared__ __align__(1024) float tsm[];
     __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], drain_full[2], drain_empty[2], done_bar;
@@ -198,13 +201,13 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int st = 0; st < NSTAGE; ++st) {
-            mbar_init(&full_bar[st], 9);  // 8 converter warps + the operator copies' expect_tx
+            mbar_init(&full_bar[st], C::NCONV + 1);  // converter warps + the operator copies' expect_tx
             mbar_init(&empty_bar[st], 1);  // one tcgen05.commit
             s_issued[st] = 0;
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&drain_full[b], 1);   // tcgen05.commit after an offset's last MMA
-            mbar_init(&drain_empty[b], 8);  // the 8 draining warps
+            mbar_init(&drain_empty[b], C::NCONV);  // the draining (converter) warps
         }
         mbar_init(&done_bar, 1);
         s_abort = 0;
@@ -217,7 +220,8 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     const uint32_t tmem = s_tmem;
 
     if (warp < kMmaWarp) {
-        // ============ converters / drainers: target row r, K half (and output half) h ============
+        // ====== converters / drainers: target row r; float4 columns [h NF, h NF + NF) of each
+        // chunk; output columns [h NH, h NH + NH) ======
         const int quad = warp & 3, h = warp >> 2;
         const int r = 32 * quad + lane;
         const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
@@ -236,9 +240,9 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
         }
         // source chunks are loaded into registers two steps ahead of their conversion
         const float *lsrc = nullptr;
-        auto load = [&](int s2, float4 (&buf)[4]) {
+        auto load = [&](int s2, float4 (&buf)[NF]) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < NF; ++i) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (s2 >= S) return;
             const int oc2 = s2 / NCH, c2 = s2 % NCH;
             int k0, kw;
@@ -257,8 +261,8 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             }
             if (!lsrc) return;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int kk = 16 * h + 4 * i, k = k0 + kk;
+            for (int i = 0; i < NF; ++i) {
+                const int kk = 4 * (h * NF + i), k = k0 + kk;
                 if (kk < kw && k < PP) buf[i] = __ldg(reinterpret_cast<const float4 *>(lsrc + k));
             }
         };
@@ -273,12 +277,13 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) return false;
             tc_fence_after();
+            constexpr int W = NH % 8 == 0 ? 8 : 4;
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 8) {
-                uint32_t v[8];
-                tmem_ld8(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
+            for (int c0 = 0; c0 < NH; c0 += W) {
+                uint32_t v[W];
+                tmem_ld_cols(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+                for (int j = 0; j < W; ++j) acc[c0 + j] += __uint_as_float(v[j]);
             }
             tc_fence_before();
             __syncwarp();
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             return true;
         };
         bool alive = true;
-        auto step = [&](int s, float4 (&cur)[4]) {
+        auto step = [&](int s, float4 (&cur)[NF]) {
             const int st = s % NSTAGE, oc = s / NCH, c = s % NCH;
             if (s >= NSTAGE) {
                 int ok = 1;
@@ -315,9 +320,10 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             // hi = x rounded to TF32 (nearest, ties away: add half a TF32 unit to the magnitude's
             // bits and clear the 13 low bits); lo = x - hi exactly, which the tensor core reads
             // truncated to TF32 (error < 2^-21 |x|)
-            uint32_t hi[16], lo[16];
+            const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + 4 * h * NF);
+            uint32_t hi[4 * NF], lo[4 * NF];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < NF; ++i) {
                 const float x[4] = {cur[i].x, cur[i].y, cur[i].z, cur[i].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -326,9 +332,8 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
                     lo[4 * i + e] = __float_as_uint(x[e] - __uint_as_float(hb));
                 }
             }
-            const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + 16 * h);
-            tmem_st16(tmem + lane_base + acol, hi);
-            tmem_st16(tmem + lane_base + acol + 32, lo);
+            tmem_st_cols(tmem + lane_base + acol, hi);
+            tmem_st_cols(tmem + lane_base + acol + 32, lo);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
             // the previous chain's partial is complete once the next chain's first offset is queued
             if (c == NCH - 1 && oc >= 1 && (oc - 1) % GRP == GRP - 1 && !drain((oc - 1) / GRP)) alive = false;
         };
-        float4 b0[4], b1[4];
+        float4 b0[NF], b1[NF];
         load(0, b0);
         load(1, b1);
         for (int s = 0; s < S && alive; s += 2) {
@@ -410,28 +415,29 @@ __global__ void __launch_bounds__(TcCfg<P, CK, NS>::NTHREADS, 1)
     }
 }
 
-template <int P, int CK, int NS, int GRP = 1>
+template <int P, int CK, int NS, int GRP = 1, int Q = 2>
 static void launch_m2l_tc_t(const TcTiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                             const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                             const int32_t *m2l_ids, const uint16_t *m2l_code, const float *optc, const float *M,
                             float *Lc, int *status, cudaStream_t s)
 {
-    using C = TcCfg<P, CK, NS>;
-    cudaFuncSetAttribute(k_m2l_tc<P, CK, NS, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-    k_m2l_tc<P, CK, NS, GRP><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
+    using C = TcCfg<P, CK, NS, Q>;
+    cudaFuncSetAttribute(k_m2l_tc<P, CK, NS, GRP, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)C::kSmemBytes);
+    k_m2l_tc<P, CK, NS, GRP, Q><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
                                                                   m2l_ids, m2l_code, optc, M, Lc, status);
     note_launches(1);
 }
 
 // pipeline shape (GBFMM_M2L_TC_CFG, p = 10): 0 = chunks of <= 4 K steps, 4 stages; 1 = 4 steps,
 // 2 stages; 2 = 2 steps, 4 stages; 3 = 3 steps, 4 stages; 4, 5 = as 0 with 2, 3 offsets per
-// TMEM accumulation chain
+// TMEM accumulation chain; 6, 7 = as 0 with 4, 1 converter warps per TMEM lane quadrant
 static int tc_variant()
 {
     static const int v = [] {
         const char *e = getenv("GBFMM_M2L_TC_CFG");
         const int x = e ? atoi(e) : 0;
-        return (x >= 0 && x <= 5) ? x : 0;
+        return (x >= 0 && x <= 7) ? x : 0;
     }();
     return v;
 }
@@ -453,6 +459,8 @@ static void dispatch_tc(int P, const TcTiles &tiles, int grid, const int4 *tdesc
         case 3: launch_m2l_tc_t<10, 3, 4>(GBFMM_TC_ARGS); break;
         case 4: launch_m2l_tc_t<10, 4, 4, 2>(GBFMM_TC_ARGS); break;
         case 5: launch_m2l_tc_t<10, 4, 4, 3>(GBFMM_TC_ARGS); break;
+        case 6: launch_m2l_tc_t<10, 4, 4, 1, 4>(GBFMM_TC_ARGS); break;
+        case 7: launch_m2l_tc_t<10, 4, 4, 1, 1>(GBFMM_TC_ARGS); break;
         default: launch_m2l_tc_t<10, 4, 4>(GBFMM_TC_ARGS); break;
         }
         break;

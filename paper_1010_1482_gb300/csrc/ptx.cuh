@@ -208,6 +208,55 @@ GB_DEV void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
         : "memory");
 }
 
+// whole warp: 4 consecutive 32-bit columns of TMEM lane (lane base + lane id)
+GB_DEV void tmem_ld4(uint32_t taddr, uint32_t (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// whole warp: store 4 consecutive 32-bit columns of TMEM lane (lane base + lane id)
+GB_DEV void tmem_st4(uint32_t taddr, const uint32_t (&v)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+
+// whole warp: N (4, 8 or 16) consecutive columns of the thread's TMEM lane, stored (no wait)
+// or loaded (waits for the load)
+template <int N>
+GB_DEV void tmem_st_cols(uint32_t taddr, const uint32_t (&v)[N])
+{
+    if constexpr (N == 16) {
+        tmem_st16(taddr, v);
+    } else if constexpr (N == 8) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                     "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                     : "memory");
+    } else {
+        static_assert(N % 4 == 0, "4-column groups");
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const uint32_t w[4] = {v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]};
+            tmem_st4(taddr + 4 * i, w);
+        }
+    }
+}
+
+template <int N>
+GB_DEV void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[N])
+{
+    if constexpr (N == 8) {
+        tmem_ld8(taddr, v);
+    } else {
+        static_assert(N == 4, "4 or 8 columns");
+        tmem_ld4(taddr, v);
+    }
+}
+
 GB_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 }  // namespace gbfmm
