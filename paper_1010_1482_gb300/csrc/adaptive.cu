@@ -378,7 +378,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt};
+                     &a.leaves, &a.group_cnt, &a.cscale};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -571,7 +571,9 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamSynchronize(s);
         std::vector<uint32_t> hcur(hcnt.size());
         std::vector<int4> tiles;
-        const bool tc = ops.m2l_tc != nullptr && !(prm->flags & GBFMM_FLAG_M2L_CUDA_CORES);
+        const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
+        const bool f16 = ops.m2l_f16 != nullptr && !cores;
+        const bool tc = f16 || (ops.m2l_tc != nullptr && !cores);
         const int TN = tc ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
         uint32_t acc = 0;
         for (int l = maxl; l >= 2; --l)
@@ -591,7 +593,13 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                                                               A.key.as<uint64_t>(), gcur, A.tlist.as<int32_t>());
         note_launches(1);
         cudaStreamSynchronize(s);  // the host tile vectors go out of scope
-        if (tc)
+        if (f16) {
+            if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive scales");
+            launch_cell_scale(M, ncells, P, A.cscale.as<int8_t>(), s);
+            launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
+                                 A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
+                                 A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), Lc, ctx->d_status, s);
+        } else if (tc)
             launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                 A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                                 A.vcode.as<uint16_t>(), ops.m2l_tc, M, Lc, ctx->d_status, s);

@@ -17,6 +17,7 @@ namespace gbfmm {
 void init_expansion_constants();
 void init_m2l_constants();
 void init_m2l_tc_constants();
+void init_m2l_f16_constants();
 }  // namespace gbfmm
 
 using namespace gbfmm;
@@ -158,6 +159,7 @@ Layout make_layout(int64_t n, int L, int P)
     lo.m2l_code = take(2 * (size_t)(189 * C2 + 1));
     lo.M = take(4 * (size_t)C * P * P);
     lo.Lc = take(4 * (size_t)C * P * P);
+    lo.cscale = take((size_t)C);
     lo.total = off;
     return lo;
 }
@@ -184,10 +186,14 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     if ((e = cudaMalloc(&c.l2l, 8 * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
     launch_build_operators(P, c.m2l, c.m2m, c.l2l, s);
-    if (m2l_use_tc()) {
+    if (m2l_tc_mode() == 1) {
         if ((e = cudaMalloc(&c.m2l_tc, m2l_tc_table_floats(P) * sizeof(float))) != cudaSuccess)
             return cuda_fail(ctx, e, "cudaMalloc(m2l tensor-core ops)");
         launch_build_m2l_tc(P, c.m2l, c.m2l_tc, s);
+    } else if (m2l_tc_mode() == 2) {
+        if ((e = cudaMalloc(&c.m2l_f16, m2l_f16_table_bytes(P))) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMalloc(m2l FP16 tensor-core ops)");
+        launch_build_m2l_f16(P, c.m2l, c.m2l_f16, s);
     }
     c.P = P;
     c.built = true;
@@ -238,6 +244,7 @@ int gbfmm_create(gbfmm_ctx **out, int device)
         init_expansion_constants();
         init_m2l_constants();
         init_m2l_tc_constants();
+        init_m2l_f16_constants();
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     if (!ok) {
@@ -262,6 +269,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
         cudaFree(c.m2m);
         cudaFree(c.l2l);
         cudaFree(c.m2l_tc);
+        cudaFree(c.m2l_f16);
     }
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
@@ -381,7 +389,13 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
     mark(5);
     if (L >= 2) {
-        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !(prm->flags & GBFMM_FLAG_M2L_CUDA_CORES))
+        const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
+        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_f16 && !cores) {
+            int8_t *cscale = at<int8_t>(ws, lo.cscale);
+            launch_cell_scale(M, lo.ncells, P, cscale, s);
+            launch_m2l_f16(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_f16, M, cscale, Lc, ctx->d_status,
+                           s);
+        } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !cores)
             launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
         else if (prm->method == GBFMM_METHOD_FMM)
             launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);

@@ -161,6 +161,7 @@ struct Layout {
     size_t p2p_len, p2p_offs, p2p_ids;
     size_t m2l_len, m2l_offs, m2l_ids, m2l_code;
     size_t M, Lc;
+    size_t cscale;  // int8 per cell: power-of-two scale of the FP16 tensor-core M2L
     size_t total;
 };
 
@@ -218,9 +219,21 @@ void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist
                       const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
                       const float *ops, const float *M, float *Lc, const float *zero_block, int *status,
                       cudaStream_t s);
-// M2L on the tcgen05 tensor cores (3xTF32), 128 targets per CTA
+// M2L on the tcgen05 tensor cores (3xTF32 or 3xF16), 128 targets per CTA
 constexpr int kM2LTcTargetsPerTile = 128;
+// 0 = FP32 CUDA cores, 1 = TF32 tensor cores, 2 = FP16 tensor cores (GBFMM_M2L_TC; default 2)
+int m2l_tc_mode();
 bool m2l_use_tc();
+size_t m2l_f16_table_bytes(int P);
+void launch_build_m2l_f16(int P, const float *ops, void *table, cudaStream_t s);
+void launch_cell_scale(const float *M, int64_t ncells, int P, int8_t *scale, cudaStream_t s);
+void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
+                    const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M,
+                    const int8_t *cscale, float *Lc, int *status, cudaStream_t s);
+void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
+                          const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
+                          const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
+                          float *Lc, int *status, cudaStream_t s);
 size_t m2l_tc_table_floats(int P);
 void launch_build_m2l_tc(int P, const float *ops, float *tc, cudaStream_t s);
 void launch_m2l_tc(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,

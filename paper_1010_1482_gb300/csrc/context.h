@@ -18,7 +18,8 @@ constexpr int kAdaptiveMaxLevel = 21;  // 63-bit keys: 21 bits per axis
 struct OpsCache {
     int P = 0;
     float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
-    float *m2l_tc = nullptr;  // tensor-core operator blocks (hi | lo), when the tcgen05 M2L is on
+    float *m2l_tc = nullptr;  // TF32 tensor-core operator blocks (hi | lo), tensor-core mode 1
+    void *m2l_f16 = nullptr;  // FP16 tensor-core operator blocks (hi | lo) + per-code scales, mode 2
     bool built = false;
 };
 
@@ -38,7 +39,7 @@ struct AdaptiveState {
     DevBuf keys0, keys1, idx0, idx1, sx, far, hist, scan_tmp, flags, scan, pcell, leaf_of, box;
     DevBuf level, key, begin, count, end, parent, child_begin, nchild, child_of, coll;
     DevBuf lcnt[4], loffs[4], lids[4], vcode;  // U, V, W, X
-    DevBuf M, Lc, tlist, tdesc, leaves, group_cnt;
+    DevBuf M, Lc, tlist, tdesc, leaves, group_cnt, cscale;
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
     int P = 0, max_level = 0;
     std::vector<int> level_start;

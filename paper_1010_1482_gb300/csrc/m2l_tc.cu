@@ -495,13 +495,16 @@ void launch_m2l_tc_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tl
     dispatch_tc(P, tiles, ntiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, optc, M, Lc, status, s);
 }
 
-bool m2l_use_tc()
+int m2l_tc_mode()
 {
-    static const bool on = [] {
+    static const int mode = [] {
         const char *e = getenv("GBFMM_M2L_TC");
-        return !(e && atoi(e) == 0);
+        const int v = e ? atoi(e) : 2;
+        return (v >= 0 && v <= 2) ? v : 2;
     }();
-    return on;
+    return mode;
 }
+
+bool m2l_use_tc() { return m2l_tc_mode() != 0; }
 
 }  // namespace gbfmm

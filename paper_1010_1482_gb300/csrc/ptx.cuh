@@ -169,6 +169,17 @@ GB_DEV void tc_mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uin
         : "memory");
 }
 
+// D (TMEM) = A * B^T (+ D), FP16 operands (kind::f16, FP32 accumulate), A from tensor memory
+// (two halves per 32-bit column), issued by one thread
+GB_DEV void tc_mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // the mbarrier receives one arrival when every tcgen05 operation this thread issued so far has completed
 GB_DEV void tc_commit(uint64_t *bar)
 {
