@@ -298,22 +298,34 @@ def run_gpu(args, w):
     m2l_ms = stages.get("M2L/M2P", float("nan"))
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
-    if os.environ.get("GBFMM_M2L_TC", "1") != "0":
-        # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to 8,
-        # 3 TF32 MMAs per product (3xTF32)
-        tpeak, tbasis = tf32_peak_tflops()
+    tc_mode = int(os.environ.get("GBFMM_M2L_TC", "2"))
+    if tc_mode in (1, 2):
+        # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to the
+        # MMA's K step (8 for TF32, 16 for FP16), 3 MMAs per product (hi*hi + lo*hi + hi*lo)
         tiles = sum(8 * -(-(8 ** (l - 1)) // 128) for l in range(2, L + 1))
-        npad, kpad = -(-P * P // 16) * 16, -(-P * P // 8) * 8
+        npad = -(-P * P // 16) * 16
+        if tc_mode == 2:
+            kpad = npad
+            try:
+                bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+                tpeak, tbasis = bf16, f"measured BF16 dense burst {bf16:.1f} TFLOP/s (FP16 dense has the same nominal rate; of measured)"
+            except Exception:
+                tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
+            kname, ksrc, kprof, kdt = "k_m2l_f16", "m2l_f16.cu", "m2l_f16_uniform_1m_p10.md", "FP16"
+        else:
+            kpad = -(-P * P // 8) * 8
+            tpeak, tbasis = tf32_peak_tflops()
+            kname, ksrc, kprof, kdt = "k_m2l_tc", "m2l_tc.cu", "m2l_tc_uniform_1m_p10.md", "TF32"
         tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * kpad
-        roofline = {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
+        roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": m2l_tf / tpeak,
-                    "traffic": traffic_from_profile("m2l_tc.cu", "m2l_tc_uniform_1m_p10.md"),
+                    "traffic": traffic_from_profile(ksrc, kprof),
                     "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
                     "peak_basis": tbasis,
                     "tensor_flop_issued": tensor_flops,
                     "tensor_pipe_frac": tensor_flops / (m2l_ms / 1e3) / 1e12 / tpeak,
-                    "note": "FP32-accurate products as 3 TF32 MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 "
-                            "by construction; tensor_pipe_frac counts every issued MMA flop"}
+                    "note": f"FP32-accurate products as 3 {kdt} MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 by "
+                            "construction; tensor_pipe_frac counts every issued MMA flop"}
     else:
         roofline = {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
                     "frac": m2l_tf / peak,
