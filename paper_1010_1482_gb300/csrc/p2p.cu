@@ -22,14 +22,17 @@ namespace gbfmm {
 constexpr int kP2PThreads = 128;
 
 // P2P kernel (GBFMM_P2P_TPT): 12 / 14 = CTA per leaf, packed FP32x2 pairs, 2 / 4 targets per
-// thread (12 is the default); 0 = warp per leaf; 1, 2, 4, 8 = CTA per leaf, scalar FP32, that
-// many targets per thread
+// thread (12 is the default); 16 / 17 = as 12 with 64 / 256 threads per CTA; 0 = warp per leaf;
+// 1, 2, 4, 8 = CTA per leaf, scalar FP32, that many targets per thread
 static int p2p_tpt()
 {
     static const int v = [] {
         const char *e = getenv("GBFMM_P2P_TPT");
         const int x = e ? atoi(e) : 12;
-        return (x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 12 || x == 14 || x == 20) ? x : 12;
+        return (x == 0 || x == 1 || x == 2 || x == 4 || x == 8 || x == 12 || x == 14 || x == 16 || x == 17 ||
+                x == 20)
+                   ? x
+                   : 12;
     }();
     return v;
 }
@@ -241,8 +244,8 @@ constexpr int kSrcCap2 = 512;
 
 // CTA per target leaf with TPT (2 or 4) targets per thread in packed pairs; the leaf's own cell
 // is staged first so that only its sources pay for the zero-distance test
-template <bool SOFT, int TPT>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__restrict__ leaves,
+template <bool SOFT, int TPT, int NT = kP2PThreads>
+__global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ leaves,
                                                       const float4 *__restrict__ sx,
                                                       const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                                       const uint32_t *__restrict__ p2p_offs,
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
 {
     constexpr int NPK = TPT / 2;
     __shared__ ulonglong2 sA[kSrcCap2], sB[kSrcCap2];  // (x, x | y, y), (z, z | q, q)
-    __shared__ float4 red[TPT][kP2PThreads];
+    __shared__ float4 red[TPT][NT];
     __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1], s_self;
     const int64_t leaf = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
     const int64_t g = leaves ? leaf : level_offset(L) + leaf;
@@ -264,10 +267,10 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
     const int nrow = (int)(p2p_offs[leaf + 1] - r0);
     const int T = e0 - b0;
     const uint64_t E2 = f2_pack(eps2, eps2);
-    for (int tc = 0; tc < T; tc += TPT * kP2PThreads) {
-        const int Tc = min(T - tc, TPT * kP2PThreads);
+    for (int tc = 0; tc < T; tc += TPT * NT) {
+        const int Tc = min(T - tc, TPT * NT);
         const int slots = (Tc + TPT - 1) / TPT;
-        const int G = kP2PThreads / slots;
+        const int G = NT / slots;
         const int slot = tid % slots, grp = tid / slots;
         const bool active = grp < G;
         uint64_t X[NPK], Y[NPK], Z[NPK], P[NPK], GX[NPK], GY[NPK], GZ[NPK];
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p2(int L, const int32_t *__re
                 const int chunk = min(kSrcCap2, S - sc);
                 if (sc > 0) __syncthreads();
                 // warp w stages rows w, w + 4, ... (its lanes stride the row's particles)
-                for (int e = tid >> 5; e < nr; e += kP2PThreads / 32) {
+                for (int e = tid >> 5; e < nr; e += NT / 32) {
                     const int lo = max(s_pref[e], sc), hi = min(s_pref[e + 1], sc + chunk);
                     for (int q = lo + (tid & 31); q < hi; q += 32) {
                         const float4 p = __ldg(&sx[s_cb[e] + (q - s_pref[e])]);
@@ -594,6 +597,21 @@ static void dispatch_p2p(unsigned grid, int L, const int32_t *leaves, const floa
                          const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
                          const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
 {
+    if (p2p_tpt() == 16 || p2p_tpt() == 17) {  // packed pairs, 64 / 256 threads per CTA
+        if (p2p_tpt() == 16) {
+            if (eps2 > 0.f)
+                k_p2p2<true, 2, 64><<<grid, 64, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+            else
+                k_p2p2<false, 2, 64><<<grid, 64, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        } else {
+            if (eps2 > 0.f)
+                k_p2p2<true, 2, 256><<<grid, 256, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+            else
+                k_p2p2<false, 2, 256><<<grid, 256, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
+        }
+        note_launches(1);
+        return;
+    }
     if (p2p_tpt() == 12 || p2p_tpt() == 14 || p2p_tpt() == 20) {
         if (p2p_tpt() != 14) {  // 20 (superleaf, uniform tree only) takes 12 for leaf lists
             if (eps2 > 0.f)
