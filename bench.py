@@ -44,6 +44,28 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank evaluates its own independent replica of the workload (weak scaling)."""
+    return seed + rank
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX (a no-op on one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(n_per_rank: int, world: int, total_ms: float, steps: int) -> float:
+    """Whole-job particles/s: every rank's particles over the slowest rank's time per step."""
+    return n_per_rank * world / (total_ms / steps / 1e3)
+
+
 def tf32_peak_tflops() -> tuple[float, str]:
     """Dense TF32 tensor peak: the measured BF16 dense burst figure x the nominal TF32/BF16
     ratio (1.1 / 2.25 PFLOP/s)."""
@@ -191,7 +213,7 @@ def run_gpu(args, w):
     G.lib()
 
     n = w["n"]
-    x = inputs.make_particles(n, w["dist"], w["seed"] + rank)
+    x = inputs.make_particles(n, w["dist"], replica_seed(w["seed"], rank))
     fmm = G.FMM(local, p=w["p"], leaf_size=w["leaf_size"], flags=G.FLAG_STAGE_TIMING)
     L, ws_bytes = fmm.plan(n)
     xd = torch.from_numpy(x).to(dev)
@@ -241,16 +263,13 @@ def run_gpu(args, w):
     if clock_ctx:
         clock_ctx.__exit__()
     G.gbfmm_sync_status(fmm.ctx)
-    total_ms = float(sum(step_ms))
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
     if ws > 1:
         import torch.distributed as dist
 
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = n * ws / (ms_per_step / 1e3)
+    value = job_rate(n, ws, total_ms, args.steps)
     stages = {k: float(np.mean(v)) for k, v in stage_acc.items()}
 
     # the FP32 CUDA-core M2L (Eq. 4 on the same lists) measured beside the tensor-core default
@@ -279,14 +298,8 @@ def run_gpu(args, w):
         t0 = time.perf_counter()
         G.gbfmm_evaluate_host(fmm.ctx, fmm.params, hin, hout)  # waits for the result on the host
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = float(sum(e2e_ms))
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * ws / (e2e_total / args.steps / 1e3)
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), dev)
+    e2e_value = job_rate(n, ws, e2e_total, args.steps)
 
     peak, peak_mhz = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
     try:
