@@ -288,16 +288,32 @@ GB_DEV void p2x_particles(float (&acc)[P * P], const float4 *__restrict__ sx, in
     }
 }
 
-// warp-wide butterfly sum of acc; lane (i mod 32) adds / stores coefficient i
+// Warp-wide sum of acc over the lanes, stored to (or added into) dst: a transpose through the
+// warp's shared-memory scratch in two halves of the coefficients (each lane writes its row,
+// then lane j sums column j over the 32 rows).  scr holds 32 x (WS_H + 1) floats.
 template <int P>
-GB_DEV void warp_store(float (&acc)[P * P], float *dst, int lane, bool add)
+struct WarpSum {
+    static constexpr int PP = P * P, H = (PP + 1) / 2, LD = H + 1;
+};
+
+template <int P>
+GB_DEV void warp_store(float (&acc)[P * P], float *dst, int lane, bool add, float *scr)
 {
+    using W = WarpSum<P>;
 #pragma unroll
-    for (int i = 0; i < P * P; ++i) {
-        float v = acc[i];
+    for (int part = 0; part < 2; ++part) {
+        __syncwarp();
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((i & 31) == lane) dst[i] = add ? dst[i] + v : v;
+        for (int i = 0; i < W::H; ++i)
+            if (part * W::H + i < W::PP) scr[lane * W::LD + i] = acc[part * W::H + i];
+        __syncwarp();
+        for (int i = lane; i < W::H && part * W::H + i < W::PP; i += 32) {
+            float v = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) v += scr[r * W::LD + i];
+            float *d = dst + part * W::H + i;
+            *d = add ? *d + v : v;
+        }
     }
 }
 
@@ -306,6 +322,7 @@ __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box,
                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                              float *__restrict__ M)
 {
+    __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
     const int64_t leaf = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (leaf >= (int64_t(1) << (3 * L))) return;
@@ -318,7 +335,7 @@ __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box,
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
     p2x_particles<P, false>(acc, sx, b0, e0, lane, cg);
-    warp_store<P>(acc, M + g * (P * P), lane, false);
+    warp_store<P>(acc, M + g * (P * P), lane, false, scr[threadIdx.x >> 5]);
 }
 
 void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
@@ -756,6 +773,7 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
                                                    const Box *__restrict__ box, const float4 *__restrict__ sx,
                                                    float *__restrict__ M)
 {
+    __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
     const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= nleaves) return;
@@ -767,7 +785,7 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
     p2x_particles<P, false>(acc, sx, begin[c], begin[c] + count[c], lane, cg);
-    warp_store<P>(acc, M + (int64_t)c * (P * P), lane, false);
+    warp_store<P>(acc, M + (int64_t)c * (P * P), lane, false, scr[threadIdx.x >> 5]);
 }
 
 // P2L over the X list (Eq. 3's L from the particles of each X leaf), one warp per cell; adds
@@ -780,6 +798,7 @@ __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t
                                                    const int32_t *__restrict__ x_ids, const Box *__restrict__ box,
                                                    const float4 *__restrict__ sx, float *__restrict__ Lc)
 {
+    __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
     const int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= ncells) return;
@@ -794,7 +813,7 @@ __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t
         const int32_t c = x_ids[e];
         p2x_particles<P, true>(acc, sx, begin[c], begin[c] + count[c], lane, cg);
     }
-    warp_store<P>(acc, Lc + b * (P * P), lane, true);
+    warp_store<P>(acc, Lc + b * (P * P), lane, true, scr[threadIdx.x >> 5]);
 }
 
 // L2P at every particle's leaf (leaves above level 2 carry no local expansion)
