@@ -363,10 +363,10 @@ void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *b
 // ------------------------------------------------------------------------------------------
 constexpr int kTrTN = 32, kTrCN = 8;
 
-template <int P, bool UP, int TN = kTrTN>
+template <int P, bool UP, int TN = kTrTN, int CN = kTrCN>
 struct TransCfg {
     static constexpr int PP = P * P, PR = ops_rows_padded(P), SB = staged_col_stride(P);
-    static constexpr int NCG = TN / kTrCN, NRG = PR / 4, NT = ((NRG * NCG + 31) / 32) * 32;
+    static constexpr int NCG = TN / CN, NRG = PR / 4, NT = ((NRG * NCG + 31) / 32) * 32;
     static constexpr int AF = PP * PR, BF = TN * SB;  // floats of one operator / one column block
     static constexpr int NBUF = UP ? 2 : 1;           // M2M walks 8 child positions: double-buffered
     static constexpr size_t kSmem = (size_t)NBUF * (AF + BF) * sizeof(float);
@@ -389,14 +389,14 @@ GB_DEV void cp_async16_t(void *dst, const void *src, uint32_t src_bytes)
 // TN cells per CTA; the operator of each child position and the TN source columns are copied
 // into shared memory with cp.async (zero-filled for missing cells), the next child position's
 // copies in flight while the current one is applied
-template <int P, bool UP, int TN>
-__global__ void __launch_bounds__(TransCfg<P, UP, TN>::NT) k_translate(int l, const int32_t *__restrict__ begin,
+template <int P, bool UP, int TN, int CN>
+__global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate(int l, const int32_t *__restrict__ begin,
                                                                        const int32_t *__restrict__ end,
                                                                        const float *__restrict__ ops,
                                                                        float *__restrict__ X)
 {
-    using Cfg = TransCfg<P, UP, TN>;
-    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG, CN = kTrCN;
+    using Cfg = TransCfg<P, UP, TN, CN>;
+    constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
     extern __shared__ __align__(16) float tsm[];
     // parents: level l (M2M) or l - 1 (L2L)
     const int lp = UP ? l : l - 1;
@@ -489,19 +489,22 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN>::NT) k_translate(int l, co
     }
 }
 
-template <int P, bool UP, int TN>
+template <int P, bool UP, int TN, int CN>
 static void launch_translate_tn(int l, const int32_t *begin, const int32_t *end, const float *ops, float *X,
                                 cudaStream_t s)
 {
-    using Cfg = TransCfg<P, UP, TN>;
-    cudaFuncSetAttribute(k_translate<P, UP, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    using Cfg = TransCfg<P, UP, TN, CN>;
+    cudaFuncSetAttribute(k_translate<P, UP, TN, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     const int64_t np = int64_t(1) << (3 * (UP ? l : l - 1));
     dim3 grid((unsigned)((np + TN - 1) / TN), UP ? 1 : 8);
-    k_translate<P, UP, TN><<<grid, Cfg::NT, Cfg::kSmem, s>>>(l, begin, end, ops, X);
+    k_translate<P, UP, TN, CN><<<grid, Cfg::NT, Cfg::kSmem, s>>>(l, begin, end, ops, X);
     note_launches(1);
 }
 
-// cells per CTA: 32 when the level has enough cells to fill the GPU twice over, else 8
+// cells per CTA: 32 (8 per thread) when the level has enough cells to fill the GPU twice over,
+// else 16 (2 per thread): small levels are bound by the latency of staging the operators, and
+// seven times the threads per cell cut it (M2M levels 2-4 of a 2^20-particle p = 10 tree:
+// 150 us -> 68 us)
 template <int P, bool UP>
 static void launch_translate_t(int l, const int32_t *begin, const int32_t *end, const float *ops, float *X,
                                cudaStream_t s)
@@ -509,9 +512,9 @@ static void launch_translate_t(int l, const int32_t *begin, const int32_t *end, 
     const int64_t np = int64_t(1) << (3 * (UP ? l : l - 1));
     const int64_t ctas32 = (np + 31) / 32 * (UP ? 1 : 8);
     if (ctas32 >= 2 * 152)
-        launch_translate_tn<P, UP, 32>(l, begin, end, ops, X, s);
+        launch_translate_tn<P, UP, 32, 8>(l, begin, end, ops, X, s);
     else
-        launch_translate_tn<P, UP, 8>(l, begin, end, ops, X, s);
+        launch_translate_tn<P, UP, 16, 2>(l, begin, end, ops, X, s);
 }
 
 void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s)
