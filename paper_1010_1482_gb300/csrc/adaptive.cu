@@ -378,7 +378,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -507,6 +507,9 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     k_cell_end<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.begin.as<int32_t>(), A.count.as<int32_t>(),
                                                  A.end.as<int32_t>());
     note_launches(1);
+    if (grow(A.geom, 16 * (size_t)ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
+    const float4 *geom = A.geom.as<float4>();
+    launch_cell_geom(ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(), box, A.geom.as<float4>(), s);
     for (int l = 0; l <= maxl; ++l) {
         const int64_t lo = ls[l], hi = ls[l + 1];
         k_colleagues<<<blocks_for(hi - lo), 256, 0, s>>>(lo, hi, l, A.key.as<uint64_t>(), A.parent.as<int32_t>(),
@@ -552,8 +555,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     float *M = A.M.as<float>(), *Lc = A.Lc.as<float>();
     float4 *far = A.far.as<float4>();
     const bool deep = maxl >= 2;
-    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), A.key.as<uint64_t>(),
-                               A.begin.as<int32_t>(), A.count.as<int32_t>(), box, A.sx.as<float4>(), M, s);
+    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), geom,
+                               A.begin.as<int32_t>(), A.count.as<int32_t>(), A.sx.as<float4>(), M, s);
     mark(4);
     for (int l = maxl - 1; l >= 2; --l)
         launch_translate_cells(P, true, ls[l], ls[l + 1] - ls[l], A.child_of.as<int32_t>(), A.nchild.as<int32_t>(),
@@ -607,21 +610,18 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                              A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                              A.vcode.as<uint16_t>(), ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
-        launch_p2l_cells(P, ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(),
-                         A.count.as<int32_t>(), A.loffs[kListX].as<uint32_t>(), A.lids[kListX].as<int32_t>(), box,
-                         A.sx.as<float4>(), Lc, s);
+        launch_p2l_cells(P, ncells, A.level.as<int32_t>(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                         A.loffs[kListX].as<uint32_t>(), A.lids[kListX].as<int32_t>(), A.sx.as<float4>(), Lc, s);
     }
     mark(6);
     for (int l = 3; l <= maxl; ++l)
         launch_translate_cells(P, false, ls[l - 1], ls[l] - ls[l - 1], A.child_of.as<int32_t>(),
                                A.nchild.as<int32_t>(), ops.l2l, Lc, s);
     mark(7);
-    launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), A.key.as<uint64_t>(), box,
-                     A.sx.as<float4>(), Lc, far, s);
+    launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s);
     if (deep)
-        launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), A.key.as<uint64_t>(),
-                         A.begin.as<int32_t>(), A.count.as<int32_t>(), A.loffs[kListW].as<uint32_t>(),
-                         A.lids[kListW].as<int32_t>(), box, A.sx.as<float4>(), M, far, s);
+        launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                         A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far, s);
     mark(8);
     launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                      A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(), far, perm,

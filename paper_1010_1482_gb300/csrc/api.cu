@@ -160,6 +160,7 @@ Layout make_layout(int64_t n, int L, int P)
     lo.M = take(4 * (size_t)C * P * P);
     lo.Lc = take(4 * (size_t)C * P * P);
     lo.cscale = take((size_t)C);
+    lo.geo = take(4 * geo_floats(L));
     lo.total = off;
     return lo;
 }
@@ -358,6 +359,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     int32_t *m2l_ids = at<int32_t>(ws, lo.m2l_ids);
     uint16_t *m2l_code = at<uint16_t>(ws, lo.m2l_code);
     float *M = at<float>(ws, lo.M), *Lc = at<float>(ws, lo.Lc);
+    float *geo = at<float>(ws, lo.geo);
 
     // operator tables (once per order and context)
     bool built_now = false;
@@ -373,6 +375,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, ctx->d_partials, ctx->d_counter,
                 ctx->d_status, s);
     launch_keys(x, n, box, L, k0, v0, s);
+    if (L >= 2) launch_geo_levels(box, L, geo, s);
     mark(1);
     uint32_t *skeys = nullptr, *perm = nullptr;
     launch_sort_gather(k0, k1, v0, v1, n, 3 * L, hist, lo.rs_blocks, scan_tmp, x, sx, &skeys, &perm, s);
@@ -383,7 +386,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, scan_tmp, s);
     launch_list_fill(L, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code, s);
     mark(3);
-    if (L >= 2) launch_p2m(P, L, box, sx, begin, end, M, s);
+    if (L >= 2) launch_p2m(P, L, geo, sx, begin, end, M, s);
     mark(4);
     if (L >= 2)
         for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
@@ -400,13 +403,13 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         else if (prm->method == GBFMM_METHOD_FMM)
             launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
         else
-            launch_m2p(P, L, box, sx, begin, end, m2l_offs, m2l_ids, M, far, s);
+            launch_m2p(P, L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far, s);
     }
     mark(6);
     if (L >= 2 && prm->method == GBFMM_METHOD_FMM)
         for (int l = 3; l <= L; ++l) launch_l2l(P, l, begin, end, ops.l2l, Lc, s);
     mark(7);
-    if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, box, n, sx, skeys, Lc, far, s);
+    if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s);
     mark(8);
     launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out, s);
     mark(9);

@@ -145,6 +145,11 @@ struct Box {
     double key_scale;  // 2^21 / side, one IEEE FP64 division
 };
 
+// Cell geometry table of the uniform tree (expansions.cu, k_geo_levels): 1/h_l for
+// l < kGeoLevels, then the 2^l cell-centre coordinates of every level l = 0..L along x, y, z.
+constexpr int kGeoLevels = 22;
+inline size_t geo_floats(int L) { return kGeoLevels + 3 * ((size_t(2) << L) - 1); }
+
 // Layout of one evaluation's workspace (byte offsets from the workspace base).
 struct Layout {
     int64_t n;
@@ -162,6 +167,7 @@ struct Layout {
     size_t m2l_len, m2l_offs, m2l_ids, m2l_code;
     size_t M, Lc;
     size_t cscale;  // int8 per cell: power-of-two scale of the FP16 tensor-core M2L
+    size_t geo;     // float: cell geometry table per level and axis (geo_floats(L))
     size_t total;
 };
 
@@ -189,13 +195,14 @@ void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uin
 
 // expansions.cu
 void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_ops, cudaStream_t s);
-void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
+void launch_geo_levels(const Box *box, int L, float *geo, cudaStream_t s);
+void launch_p2m(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
                 cudaStream_t s);
 void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s);
 void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *Lc, cudaStream_t s);
-void launch_l2p(int P, int L, const Box *box, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
+void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
                 float4 *far, cudaStream_t s);
-void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end,
+void launch_m2p(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s);
 
 // m2l.cu
@@ -210,9 +217,10 @@ void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s);
 void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
                           uint32_t *hist, int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx,
                           uint64_t **keys_out, uint32_t **idx_out, cudaStream_t s);
-void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
-                      const int32_t *begin, const int32_t *count, const Box *box, const float4 *sx, float *M,
+void launch_cell_geom(int64_t nc, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
                       cudaStream_t s);
+void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,
+                      const int32_t *begin, const int32_t *count, const float4 *sx, float *M, cudaStream_t s);
 void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,
                             const int32_t *nchild, const float *ops, float *X, cudaStream_t s);
 void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
@@ -243,14 +251,14 @@ void launch_m2l_tc_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tl
                          const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                          const uint16_t *m2l_code, const float *optc, const float *M, float *Lc, int *status,
                          cudaStream_t s);
-void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *begin,
-                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const Box *box,
-                      const float4 *sx, float *Lc, cudaStream_t s);
-void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const uint64_t *key,
-                      const Box *box, const float4 *sx, const float *Lc, float4 *far, cudaStream_t s);
-void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
-                      const int32_t *begin, const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids,
-                      const Box *box, const float4 *sx, const float *M, float4 *far, cudaStream_t s);
+void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
+                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
+                      cudaStream_t s);
+void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
+                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s);
+void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float4 *geom, const int32_t *begin,
+                      const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
+                      const float *M, float4 *far, cudaStream_t s);
 void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);

@@ -224,20 +224,69 @@ void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_op
 // FP32 helpers
 // ------------------------------------------------------------------------------------------
 struct CellGeom {
-    float cx, cy, cz, inv_h, h;
+    float cx, cy, cz, inv_h;
 };
 
-GB_DEV CellGeom cell_geom(const Box &b, int l, uint32_t key)
+// ------------------------------------------------------------------------------------------
+// Cell geometry tables.  The centre of a level-l cell with integer coordinates (ix, iy, iz) is
+// origin + (i + 1/2) h_l per axis, h_l = side / 2^l, and its inverse side 1 / h_l: FP64
+// expressions rounded to FP32.  FP64 runs at a small fraction of the FP32 rate, so they are
+// evaluated once per level and axis (uniform tree) or once per cell (adaptive tree) into a
+// table that the expansion kernels read, instead of once per particle or per (particle, cell)
+// pair.
+//   uniform: geo[l] = 1/h_l for l < kGeoLevels, then for l = 0..L the 2^l centre coordinates
+//            along x, then y, then z, at offset kGeoLevels + 3 (2^l - 1)
+//   adaptive: geom[c] = (cx, cy, cz, 1/h) of cell c
+// ------------------------------------------------------------------------------------------
+__global__ void k_geo_levels(const Box *__restrict__ box, int L, float *__restrict__ geo)
+{
+    const Box b = *box;
+    const int64_t total = kGeoLevels + 3 * ((int64_t(2) << L) - 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < kGeoLevels) {
+            const double h = b.side / (double)(int64_t(1) << t);
+            geo[t] = (float)(1.0 / h);
+            continue;
+        }
+        const int64_t u = t - kGeoLevels;
+        int l = 0;
+        while (3 * ((int64_t(2) << l) - 1) <= u) ++l;
+        const int64_t r = u - 3 * ((int64_t(1) << l) - 1);
+        const int d = (int)(r >> l);
+        const int i = (int)(r - ((int64_t)d << l));
+        const double h = b.side / (double)(int64_t(1) << l);
+        geo[t] = (float)(b.origin[d] + (i + 0.5) * h);
+    }
+}
+
+void launch_geo_levels(const Box *box, int L, float *geo, cudaStream_t s)
+{
+    const int64_t total = kGeoLevels + 3 * ((int64_t(2) << L) - 1);
+    k_geo_levels<<<(unsigned)std::min<int64_t>((total + 255) / 256, 1024), 256, 0, s>>>(box, L, geo);
+    note_launches(1);
+}
+
+GB_DEV CellGeom geo_level_cell(const float *__restrict__ geo, int l, uint32_t key)
 {
     int ix, iy, iz;
     demorton3(key, ix, iy, iz);
-    double h = b.side / (double)(1 << l);
+    const float *a = geo + kGeoLevels + 3 * ((1 << l) - 1);
     CellGeom g;
-    g.cx = (float)(b.origin[0] + (ix + 0.5) * h);
-    g.cy = (float)(b.origin[1] + (iy + 0.5) * h);
-    g.cz = (float)(b.origin[2] + (iz + 0.5) * h);
-    g.h = (float)h;
-    g.inv_h = (float)(1.0 / h);
+    g.cx = __ldg(a + ix);
+    g.cy = __ldg(a + (1 << l) + iy);
+    g.cz = __ldg(a + (2 << l) + iz);
+    g.inv_h = __ldg(geo + l);
+    return g;
+}
+
+GB_DEV CellGeom geo_cell(const float4 *__restrict__ geom, int64_t c)
+{
+    const float4 v = __ldg(&geom[c]);
+    CellGeom g;
+    g.cx = v.x;
+    g.cy = v.y;
+    g.cz = v.z;
+    g.inv_h = v.w;
     return g;
 }
 
@@ -318,7 +367,7 @@ GB_DEV void warp_store(float (&acc)[P * P], float *dst, int lane, bool add, floa
 }
 
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box, const float4 *__restrict__ sx,
+__global__ void __launch_bounds__(128) k_p2m(int L, const float *__restrict__ geo, const float4 *__restrict__ sx,
                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                              float *__restrict__ M)
 {
@@ -329,8 +378,7 @@ __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box,
     const int64_t g = level_offset(L) + leaf;
     const int b0 = begin[g], e0 = end[g];
     if (e0 <= b0) return;
-    const Box bx = *box;
-    const CellGeom cg = cell_geom(bx, L, (uint32_t)leaf);
+    const CellGeom cg = geo_level_cell(geo, L, (uint32_t)leaf);
     float acc[P * P];
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
@@ -338,16 +386,16 @@ __global__ void __launch_bounds__(128) k_p2m(int L, const Box *__restrict__ box,
     warp_store<P>(acc, M + g * (P * P), lane, false, scr[threadIdx.x >> 5]);
 }
 
-void launch_p2m(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
+void launch_p2m(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end, float *M,
                 cudaStream_t s)
 {
     int64_t nl = int64_t(1) << (3 * L);
     unsigned grid = (unsigned)((nl + 3) / 4);
     switch (P) {
-    case 4: k_p2m<4><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
-    case 6: k_p2m<6><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
-    case 8: k_p2m<8><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
-    case 10: k_p2m<10><<<grid, 128, 0, s>>>(L, box, sx, begin, end, M); break;
+    case 4: k_p2m<4><<<grid, 128, 0, s>>>(L, geo, sx, begin, end, M); break;
+    case 6: k_p2m<6><<<grid, 128, 0, s>>>(L, geo, sx, begin, end, M); break;
+    case 8: k_p2m<8><<<grid, 128, 0, s>>>(L, geo, sx, begin, end, M); break;
+    case 10: k_p2m<10><<<grid, 128, 0, s>>>(L, geo, sx, begin, end, M); break;
     }
     note_launches(1);
 }
@@ -609,7 +657,7 @@ GB_DEV float4 l2p_eval(const float *__restrict__ Lg, float x, float y, float z, 
 }
 
 template <int P>
-__global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box, int64_t n,
+__global__ void __launch_bounds__(128) k_l2p(int L, const float *__restrict__ geo, int64_t n,
                                              const float4 *__restrict__ sx, const uint32_t *__restrict__ leafkey,
                                              const float *__restrict__ Lc, float4 *__restrict__ far)
 {
@@ -618,23 +666,22 @@ __global__ void __launch_bounds__(128) k_l2p(int L, const Box *__restrict__ box,
     if (i >= n) return;
     const uint32_t key = leafkey[i];
     const int64_t g = level_offset(L) + key;
-    const Box bx = *box;
-    const CellGeom cg = cell_geom(bx, L, key);
+    const CellGeom cg = geo_level_cell(geo, L, key);
     float4 p = __ldg(&sx[i]);
     far[i] = l2p_eval<P>(Lc + g * PP, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
                          cg.inv_h);
 }
 
-void launch_l2p(int P, int L, const Box *box, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
+void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
                 float4 *far, cudaStream_t s)
 {
     if (n <= 0) return;
     unsigned grid = (unsigned)((n + 127) / 128);
     switch (P) {
-    case 4: k_l2p<4><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
-    case 6: k_l2p<6><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
-    case 8: k_l2p<8><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
-    case 10: k_l2p<10><<<grid, 128, 0, s>>>(L, box, n, sx, leafkey, Lc, far); break;
+    case 4: k_l2p<4><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
+    case 6: k_l2p<6><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
+    case 8: k_l2p<8><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
+    case 10: k_l2p<10><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
     }
     note_launches(1);
 }
@@ -704,7 +751,7 @@ GB_DEV void m2p_accumulate(const float *__restrict__ Ms, float x, float y, float
 }
 
 template <int P>
-__global__ void __launch_bounds__(128) k_m2p(int L, const Box *__restrict__ box, const float4 *__restrict__ sx,
+__global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ geo, const float4 *__restrict__ sx,
                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                                              const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
                                              const float *__restrict__ M, float4 *__restrict__ far)
@@ -715,7 +762,6 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const Box *__restrict__ box,
     const int64_t g = level_offset(L) + leaf;
     const int b0 = begin[g], e0 = end[g];
     if (e0 <= b0) return;
-    const Box bx = *box;
     for (int t0 = b0; t0 < e0; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
         const bool act = t < e0;
@@ -728,7 +774,7 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const Box *__restrict__ box,
                 __syncthreads();
                 for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[s * PP + k];
                 __syncthreads();
-                const CellGeom cg = cell_geom(bx, l, (uint32_t)(s - level_offset(l)));
+                const CellGeom cg = geo_level_cell(geo, l, (uint32_t)(s - level_offset(l)));
                 if (act)
                     m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
                                       (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
@@ -738,15 +784,15 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const Box *__restrict__ box,
     }
 }
 
-void launch_m2p(int P, int L, const Box *box, const float4 *sx, const int32_t *begin, const int32_t *end,
+void launch_m2p(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s)
 {
     unsigned grid = (unsigned)(int64_t(1) << (3 * L));
     switch (P) {
-    case 4: k_m2p<4><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 6: k_m2p<6><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 8: k_m2p<8><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 10: k_m2p<10><<<grid, 64, 0, s>>>(L, box, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 4: k_m2p<4><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 6: k_m2p<6><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 8: k_m2p<8><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
+    case 10: k_m2p<10><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
     }
     note_launches(1);
 }
@@ -763,18 +809,33 @@ GB_DEV CellGeom cell_geom63(const Box &b, int l, uint64_t key)
     g.cx = (float)(b.origin[0] + (ix + 0.5) * h);
     g.cy = (float)(b.origin[1] + (iy + 0.5) * h);
     g.cz = (float)(b.origin[2] + (iz + 0.5) * h);
-    g.h = (float)h;
     g.inv_h = (float)(1.0 / h);
     return g;
+}
+
+__global__ void k_cell_geom(int64_t nc, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                            const Box *__restrict__ box, float4 *__restrict__ geom)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const CellGeom g = cell_geom63(*box, level[c], key[c]);
+    geom[c] = make_float4(g.cx, g.cy, g.cz, g.inv_h);
+}
+
+void launch_cell_geom(int64_t nc, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
+                      cudaStream_t s)
+{
+    if (nc <= 0) return;
+    k_cell_geom<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, level, key, box, geom);
+    note_launches(1);
 }
 
 // P2M at the listed leaves (levels >= 2), one warp per leaf
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ leaves, int64_t nleaves,
-                                                   const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                                                   const int32_t *__restrict__ level, const float4 *__restrict__ geom,
                                                    const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-                                                   const Box *__restrict__ box, const float4 *__restrict__ sx,
-                                                   float *__restrict__ M)
+                                                   const float4 *__restrict__ sx, float *__restrict__ M)
 {
     __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
@@ -782,8 +843,7 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
     if (w >= nleaves) return;
     const int32_t c = leaves[w];
     if (level[c] < 2) return;
-    const Box bx = *box;
-    const CellGeom cg = cell_geom63(bx, level[c], key[c]);
+    const CellGeom cg = geo_cell(geom, c);
     float acc[P * P];
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
@@ -795,11 +855,11 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
 // into the cell's local expansion
 template <int P>
 __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t *__restrict__ level,
-                                                   const uint64_t *__restrict__ key, const int32_t *__restrict__ begin,
+                                                   const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
                                                    const int32_t *__restrict__ count,
                                                    const uint32_t *__restrict__ x_offs,
-                                                   const int32_t *__restrict__ x_ids, const Box *__restrict__ box,
-                                                   const float4 *__restrict__ sx, float *__restrict__ Lc)
+                                                   const int32_t *__restrict__ x_ids, const float4 *__restrict__ sx,
+                                                   float *__restrict__ Lc)
 {
     __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
@@ -807,8 +867,7 @@ __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t
     if (b >= ncells) return;
     const uint32_t e0 = x_offs[b], e1 = x_offs[b + 1];
     if (e0 == e1 || level[b] < 2) return;
-    const Box bx = *box;
-    const CellGeom cg = cell_geom63(bx, level[b], key[b]);
+    const CellGeom cg = geo_cell(geom, b);
     float acc[P * P];
 #pragma unroll
     for (int i = 0; i < P * P; ++i) acc[i] = 0.f;
@@ -822,9 +881,9 @@ __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t
 // L2P at every particle's leaf (leaves above level 2 carry no local expansion)
 template <int P>
 __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__restrict__ leaf_of,
-                                                   const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
-                                                   const Box *__restrict__ box, const float4 *__restrict__ sx,
-                                                   const float *__restrict__ Lc, float4 *__restrict__ far)
+                                                   const int32_t *__restrict__ level, const float4 *__restrict__ geom,
+                                                   const float4 *__restrict__ sx, const float *__restrict__ Lc,
+                                                   float4 *__restrict__ far)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -833,8 +892,7 @@ __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__r
         far[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    const Box bx = *box;
-    const CellGeom cg = cell_geom63(bx, level[c], key[c]);
+    const CellGeom cg = geo_cell(geom, c);
     float4 p = __ldg(&sx[i]);
     far[i] = l2p_eval<P>(Lc + (int64_t)c * (P * P), (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
                          (p.z - cg.cz) * cg.inv_h, cg.inv_h);
@@ -843,19 +901,17 @@ __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__r
 // M2P over the W list, one CTA per listed leaf; adds into the far-field accumulator
 template <int P>
 __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ leaves,
-                                                  const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
-                                                  const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                                  const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
+                                                  const int32_t *__restrict__ count,
                                                   const uint32_t *__restrict__ w_offs,
-                                                  const int32_t *__restrict__ w_ids, const Box *__restrict__ box,
-                                                  const float4 *__restrict__ sx, const float *__restrict__ M,
-                                                  float4 *__restrict__ far)
+                                                  const int32_t *__restrict__ w_ids, const float4 *__restrict__ sx,
+                                                  const float *__restrict__ M, float4 *__restrict__ far)
 {
     constexpr int PP = P * P;
     __shared__ float sM[PP];
     const int32_t b = leaves[blockIdx.x];
     const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
     if (e0 == e1) return;
-    const Box bx = *box;
     const int b0 = begin[b], bend = begin[b] + count[b];
     for (int t0 = b0; t0 < bend; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
@@ -867,7 +923,7 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
             __syncthreads();
             for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[(int64_t)sc * PP + k];
             __syncthreads();
-            const CellGeom cg = cell_geom63(bx, level[sc], key[sc]);
+            const CellGeom cg = geo_cell(geom, sc);
             if (act)
                 m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
                                   cg.inv_h, o);
@@ -982,43 +1038,42 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t
     case 10: { constexpr int PQ = 10; CALL; } break; \
     }
 
-void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
-                      const int32_t *begin, const int32_t *count, const Box *box, const float4 *sx, float *M,
-                      cudaStream_t s)
+void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,
+                      const int32_t *begin, const int32_t *count, const float4 *sx, float *M, cudaStream_t s)
 {
     if (nleaves <= 0) return;
     const unsigned grid = (unsigned)((nleaves + 3) / 4);
-    GBFMM_DISPATCH_P(P, (k_p2m_cells<PQ><<<grid, 128, 0, s>>>(leaves, nleaves, level, key, begin, count, box, sx, M)));
+    GBFMM_DISPATCH_P(P, (k_p2m_cells<PQ><<<grid, 128, 0, s>>>(leaves, nleaves, level, geom, begin, count, sx, M)));
     note_launches(1);
 }
 
-void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const uint64_t *key, const int32_t *begin,
-                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const Box *box,
-                      const float4 *sx, float *Lc, cudaStream_t s)
+void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
+                      const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
+                      cudaStream_t s)
 {
     if (ncells <= 0) return;
     const unsigned grid = (unsigned)((ncells + 3) / 4);
-    GBFMM_DISPATCH_P(P, (k_p2l_cells<PQ><<<grid, 128, 0, s>>>(ncells, level, key, begin, count, x_offs, x_ids, box,
-                                                              sx, Lc)));
+    GBFMM_DISPATCH_P(P, (k_p2l_cells<PQ><<<grid, 128, 0, s>>>(ncells, level, geom, begin, count, x_offs, x_ids, sx,
+                                                              Lc)));
     note_launches(1);
 }
 
-void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const uint64_t *key,
-                      const Box *box, const float4 *sx, const float *Lc, float4 *far, cudaStream_t s)
+void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
+                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s)
 {
     if (n <= 0) return;
     const unsigned grid = (unsigned)((n + 127) / 128);
-    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, key, box, sx, Lc, far)));
+    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, geom, sx, Lc, far)));
     note_launches(1);
 }
 
-void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const uint64_t *key,
-                      const int32_t *begin, const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids,
-                      const Box *box, const float4 *sx, const float *M, float4 *far, cudaStream_t s)
+void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float4 *geom, const int32_t *begin,
+                      const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
+                      const float *M, float4 *far, cudaStream_t s)
 {
     if (nleaves <= 0) return;
-    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)nleaves, 64, 0, s>>>(leaves, level, key, begin, count, w_offs,
-                                                                          w_ids, box, sx, M, far)));
+    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)nleaves, 64, 0, s>>>(leaves, geom, begin, count, w_offs, w_ids,
+                                                                          sx, M, far)));
     note_launches(1);
 }
 
