@@ -139,6 +139,217 @@ __global__ void k_tree_pcell(int64_t n, const uint32_t *__restrict__ flags, cons
     pcell[i] = (int32_t)(base + scan[i] + flags[i] - 1);
 }
 
+// ---- one-pass construction ------------------------------------------------------------------
+// With the particles sorted by key, let cpl(a, b) be the deepest level d at which keys a and b
+// have the same level-d prefix (21 for equal keys).  For a window of leaf_size + 1 consecutive
+// particles j..j+leaf_size, w_j = cpl(key_j, key_{j+leaf_size}) is the deepest level whose cell
+// holds the whole window.  The level-d cell of particle i holds more than leaf_size particles
+// exactly when some window containing i lies inside it, so
+//   D_i = max over j in [i - leaf_size, i] of w_j      (-1 if no window fits in [0, n))
+// is the deepest level at which i's cell would split by count, and i's leaf is at level
+//   lambda_i = D_i < 0 ? 0 : min(D_i, 20) + 1.
+// Particle i is the first particle of its level-l cell for l >= a_i = cpl(key_{i-1}, key_i) + 1
+// (a_0 = 0), and that cell exists when l <= lambda_i (every ancestor splits).  So i starts the
+// cells of levels a_i..lambda_i, and the cells of level l, numbered level by level in key
+// order, are ranked by a per-level count over the particles: the same cells, numbering and
+// fields as the level-by-level rounds, with one host read (the level sizes) instead of one
+// per level.
+constexpr int kTreeB = 256;                      // particles per block
+constexpr int kTreeBins = kAdaptMaxLevel + 2;    // levels 0..21, then leaf starts
+constexpr int kTreeMaxWindow = 16384;            // leaf sizes above this take the level rounds
+
+GB_DEV int cpl63(uint64_t a, uint64_t b)
+{
+    const uint64_t x = a ^ b;
+    if (x == 0) return kAdaptMaxLevel;
+    return kAdaptMaxLevel - 1 - (63 - __clzll((long long)x)) / 3;
+}
+
+GB_DEV bool tree_bin(int bin, int a, int lam) { return bin < kTreeBins - 1 ? (a <= bin && bin <= lam) : (a <= lam); }
+
+// per particle: (a_i, lambda_i) packed as a | lambda << 8, and per block the count of each bin;
+// the window maxima come from a sparse table in shared memory over w_j, j in [i0 - leaf, i0 + B)
+__global__ void __launch_bounds__(kTreeB) k_tree_ranges(int64_t n, const uint64_t *__restrict__ sk, int leaf,
+                                                        int64_t nblk, uint16_t *__restrict__ range,
+                                                        uint32_t *__restrict__ hist)
+{
+    extern __shared__ int8_t wbuf[];  // 2 (B + leaf): ping-pong
+    __shared__ uint32_t wc[kTreeB / 32][kTreeBins];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = blockIdx.x * (int64_t)kTreeB;
+    const int size = kTreeB + leaf;
+    int8_t *src = wbuf, *dst = wbuf + size;
+    for (int jj = tid; jj < size; jj += kTreeB) {
+        const int64_t j = i0 - leaf + jj;
+        int w = -1;
+        if (j >= 0 && j + leaf < n) w = cpl63(sk[j], sk[j + leaf]);
+        src[jj] = (int8_t)w;
+    }
+    __syncthreads();
+    int k = 0;
+    while ((2 << k) <= leaf + 1) ++k;  // 2^k <= leaf + 1 < 2^(k+1)
+    for (int t = 0; t < k; ++t) {
+        const int d = 1 << t;
+        for (int jj = tid; jj < size; jj += kTreeB) {
+            int8_t v = src[jj];
+            if (jj + d < size) v = max(v, src[jj + d]);
+            dst[jj] = v;
+        }
+        __syncthreads();
+        int8_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    const int64_t i = i0 + tid;
+    int a = kAdaptMaxLevel + 1, lam = -1;
+    if (i < n) {
+        const int dm = max((int)src[tid], (int)src[tid + leaf + 1 - (1 << k)]);
+        lam = dm < 0 ? 0 : min(dm, kAdaptMaxLevel - 1) + 1;
+        a = i == 0 ? 0 : cpl63(sk[i - 1], sk[i]) + 1;
+        range[i] = (uint16_t)(a | (lam << 8));
+    }
+    for (int b = 0; b < kTreeBins; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, tree_bin(b, a, lam));
+        if (lane == 0) wc[warp][b] = __popc(bal);
+    }
+    __syncthreads();
+    if (tid < kTreeBins) {
+        uint32_t sum = 0;
+        for (int w = 0; w < kTreeB / 32; ++w) sum += wc[w][tid];
+        hist[(int64_t)tid * nblk + blockIdx.x] = sum;
+    }
+}
+
+// info[b] = first index of bin b (level starts, then the number of cells), info[kTreeBins] =
+// cells + leaves
+__global__ void k_tree_starts(int64_t nblk, const uint32_t *__restrict__ base, int32_t *__restrict__ info)
+{
+    const int t = threadIdx.x;
+    if (t <= kTreeBins) info[t] = (int32_t)base[(int64_t)t * nblk];
+}
+
+// writes every cell a particle starts (level, key, begin, parent when it starts there too),
+// the leaf list in key order and every particle's leaf ordinal (into leaf_ord)
+__global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t *__restrict__ sk, int64_t nblk,
+                                                       const uint16_t *__restrict__ range,
+                                                       const uint32_t *__restrict__ base, int32_t *__restrict__ level,
+                                                       uint64_t *__restrict__ key, int32_t *__restrict__ begin,
+                                                       int32_t *__restrict__ parent, int32_t *__restrict__ child_begin,
+                                                       int32_t *__restrict__ nchild, int32_t *__restrict__ child_of,
+                                                       int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_ord)
+{
+    __shared__ uint32_t wc[kTreeB / 32][kTreeBins];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = blockIdx.x * (int64_t)kTreeB + tid;
+    int a = kAdaptMaxLevel + 1, lam = -1;
+    uint64_t kk = 0;
+    if (i < n) {
+        const uint16_t r = range[i];
+        a = r & 0xff;
+        lam = r >> 8;
+        kk = sk[i];
+    }
+    for (int b = 0; b < kTreeBins; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, tree_bin(b, a, lam));
+        if (lane == 0) wc[warp][b] = __popc(bal);
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t prev = -1;
+    for (int b = 0; b < kTreeBins; ++b) {
+        const bool p = tree_bin(b, a, lam);
+        const unsigned bal = __ballot_sync(0xffffffffu, p);
+        uint32_t off = __popc(bal & lt);
+        for (int w = 0; w < warp; ++w) off += wc[w][b];
+        const uint32_t b0 = base[(int64_t)b * nblk + blockIdx.x];
+        if (b < kTreeBins - 1) {
+            if (!p) continue;
+            const int32_t id = (int32_t)(b0 + off);
+            level[id] = b;
+            key[id] = kk >> (3 * (kAdaptMaxLevel - b));
+            begin[id] = (int32_t)i;
+            parent[id] = b == 0 ? -1 : (b > a ? prev : -2);
+            child_begin[id] = 0x7fffffff;
+            nchild[id] = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) child_of[(int64_t)id * 8 + q] = -1;
+            prev = id;
+        } else if (i < n) {
+            const int64_t ord = (int64_t)b0 - (int64_t)base[(int64_t)b * nblk] + off + (p ? 1 : 0) - 1;
+            leaf_ord[i] = (int32_t)ord;
+            if (p) leaves[ord] = prev;  // the cell of level lambda_i
+        }
+    }
+}
+
+// per cell: particle count (end of its key prefix in the sorted keys), the parent of a cell
+// whose parent starts at an earlier particle (key search within the parent level), and the
+// parent's child links
+__global__ void k_tree_links(int64_t nc, int64_t n, const uint64_t *__restrict__ sk, const int32_t *__restrict__ info,
+                             const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                             const int32_t *__restrict__ begin, int32_t *__restrict__ count, int32_t *__restrict__ end,
+                             int32_t *__restrict__ parent, int32_t *__restrict__ child_begin,
+                             int32_t *__restrict__ nchild, int32_t *__restrict__ child_of)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int l = level[c];
+    const uint64_t kk = key[c];
+    const int64_t b = begin[c];
+    int64_t e = n;
+    if (l > 0) {
+        const int sh = 3 * (kAdaptMaxLevel - l);
+        int64_t lo = b + 1, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((sk[mid] >> sh) == kk)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        e = lo;
+    }
+    count[c] = (int32_t)(e - b);
+    end[c] = (int32_t)e;
+    int32_t p = parent[c];
+    if (p == -2) {
+        const uint64_t pk = kk >> 3;
+        int32_t lo = info[l - 1], hi = info[l] - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (key[mid] < pk)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        p = lo;
+        parent[c] = p;
+    }
+    if (p >= 0) {
+        child_of[(int64_t)p * 8 + (int)(kk & 7)] = (int32_t)c;
+        atomicAdd(&nchild[p], 1);
+        atomicMin(&child_begin[p], (int32_t)c);
+    }
+}
+
+__global__ void k_tree_leaf_of(int64_t n, const int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_of)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) leaf_of[i] = leaves[leaf_of[i]];
+}
+
+// list sizes of the four kinds into info[0..3]
+__global__ void k_list_totals(int64_t nc, const uint32_t *o0, const uint32_t *o1, const uint32_t *o2,
+                              const uint32_t *o3, int32_t *info)
+{
+    if (threadIdx.x == 0) {
+        info[0] = (int32_t)o0[nc];
+        info[1] = (int32_t)o1[nc];
+        info[2] = (int32_t)o2[nc];
+        info[3] = (int32_t)o3[nc];
+    }
+}
+
 __global__ void k_cell_end(int64_t nc, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                            int32_t *__restrict__ end)
 {
@@ -314,6 +525,48 @@ __global__ void k_alist_fill(int kind, int64_t nc, TreeView t, const uint32_t *_
     });
 }
 
+// V list, one warp per cell: lane j takes the candidate offsets t = j, j + 32, ... of the
+// 6x6x6 block of the parent's colleagues' children (t = 36 (oz + 2 + cz) + 6 (oy + 2 + cy) +
+// (ox + 2 + cx), the order of for_each_entry), and a ballot compacts the hits so that a row is
+// written in that order with coalesced stores.
+template <bool FILL>
+__global__ void k_vlist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+                             int32_t *__restrict__ ids, uint16_t *__restrict__ codes)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nc) return;
+    const int l = t.level[b];
+    if (l < 2) {
+        if (!FILL && lane == 0) cnt[b] = 0;
+        return;
+    }
+    int x, y, z;
+    demorton63(t.key[b], x, y, z);
+    const int side = 1 << l, cx = x & 1, cy = y & 1, cz = z & 1;
+    const int32_t *pc = t.coll + (int64_t)t.parent[b] * 27;
+    uint32_t e = FILL ? offs[b] : 0u;
+    for (int t0 = 0; t0 < 216; t0 += 32) {
+        const int u = t0 + lane;
+        const int ox = u % 6 - 2 - cx, oy = (u / 6) % 6 - 2 - cy, oz = u / 36 - 2 - cz;
+        const int nx = x + ox, ny = y + oy, nz = z + oz;
+        int32_t src = -1;
+        if (u < 216 && !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) && nx >= 0 && ny >= 0 &&
+            nz >= 0 && nx < side && ny < side && nz < side) {
+            const int32_t a = pc[slot27((nx >> 1) - (x >> 1), (ny >> 1) - (y >> 1), (nz >> 1) - (z >> 1))];
+            if (a >= 0) src = t.child_of[(int64_t)a * 8 + ((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2))];
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, src >= 0);
+        if (FILL && src >= 0) {
+            const uint32_t at = e + __popc(hit & ((1u << lane) - 1u));
+            ids[at] = src;
+            codes[at] = (uint16_t)m2l_code(ox, oy, oz);
+        }
+        e += __popc(hit);
+    }
+    if (!FILL && lane == 0) cnt[b] = e;
+}
+
 // ---- M2L targets grouped by (level, child position) ----------------------------------------
 __global__ void k_group_count(int64_t lo, int64_t nc, const int32_t *__restrict__ level,
                               const uint64_t *__restrict__ key, uint32_t *__restrict__ gcnt)
@@ -378,7 +631,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -415,10 +668,14 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     need(A.sx, 16 * n);
     need(A.far, 16 * n);
     need(A.hist, 4 * (256 * nblk + 1));
-    need(A.scan_tmp, 4 * (exclusive_scan_tmp_words(n + 1) + exclusive_scan_tmp_words(256 * nblk) + 64));
+    const int64_t tb = (n + kTreeB - 1) / kTreeB;  // one-pass tree blocks
+    const int64_t hb = kTreeBins * tb + 1;
+    need(A.scan_tmp, 4 * (exclusive_scan_tmp_words(std::max<int64_t>(n + 1, hb)) + exclusive_scan_tmp_words(256 * nblk) +
+                          64));
     need(A.flags, 4 * (n + 1));
-    need(A.scan, 4 * (n + 1));
-    need(A.pcell, 4 * n);
+    need(A.scan, 4 * std::max<int64_t>(n + 1, hb));
+    need(A.pcell, 4 * std::max<int64_t>(n, hb));
+    need(A.info, 4 * 64);
     need(A.leaf_of, 4 * n);
     need(A.box, sizeof(Box));
     need(A.group_cnt, 4 * 2 * 8 * (kAdaptMaxLevel + 2));
@@ -446,7 +703,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                          A.sx.as<float4>(), &skeys, &perm, s);
     mark(2);
 
-    // ---- tree, level by level ----
+    // ---- tree ----
     int64_t cap = std::max<int64_t>(64, 2 * n / std::max(1, leaf_size) + 64);
     auto cell_bufs = [&](int64_t c, bool keep, int64_t used) {
         struct {
@@ -458,55 +715,101 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             if (grow(*e.b, e.per * c, keep, e.per * used, s) != 0) return false;
         return true;
     };
-    if (!cell_bufs(cap, false, 0)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
-    k_tree_root<<<1, 1, 0, s>>>(n, A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(),
-                                A.count.as<int32_t>(), A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
-                                A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
-    k_tree_pcell_init<<<blocks_for(n), 256, 0, s>>>(n, A.pcell.as<int32_t>());
-    note_launches(2);
-    std::vector<int> ls = {0, 1};
-    int64_t ncells = 1;
+    std::vector<int> ls;
+    int64_t ncells = 0;
     int maxl = 0;
-    for (int l = 0; l < kAdaptMaxLevel + 1; ++l) {
-        k_tree_flags<<<blocks_for(n), 256, 0, s>>>(n, skeys, l, leaf_size, kAdaptMaxLevel, A.pcell.as<int32_t>(),
-                                                   A.count.as<int32_t>(), A.begin.as<int32_t>(),
+    const int64_t window = std::min<int64_t>(leaf_size, n);
+    int32_t *info = A.info.as<int32_t>();
+    if (n > 0 && window <= kTreeMaxWindow) {
+        // one pass: per-particle level ranges, per-level ranks, one host read of the level sizes
+        uint16_t *range = A.flags.as<uint16_t>();
+        uint32_t *hist = A.scan.as<uint32_t>(), *hbase = reinterpret_cast<uint32_t *>(A.pcell.p);
+        k_tree_ranges<<<(unsigned)tb, kTreeB, 2 * (kTreeB + (int)window), s>>>(n, skeys, (int)window, tb, range,
+                                                                              hist);
+        launch_exclusive_scan(hist, hbase, kTreeBins * tb, A.scan_tmp.as<uint32_t>(), s);
+        k_tree_starts<<<1, 32, 0, s>>>(tb, hbase, info);
+        note_launches(2);
+        int32_t hinfo[kTreeBins + 1];
+        cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        ncells = hinfo[kTreeBins - 1];
+        A.nleaves = (uint32_t)(hinfo[kTreeBins] - hinfo[kTreeBins - 1]);
+        for (int l = 0; l <= kAdaptMaxLevel; ++l)
+            if (hinfo[l + 1] > hinfo[l]) maxl = l;
+        for (int l = 0; l <= maxl + 1; ++l) ls.push_back(hinfo[l]);
+        if (!cell_bufs(ncells, false, 0) || grow(A.end, 4 * ncells, false, 0, s) ||
+            grow(A.leaves, 4 * ncells + 4, false, 0, s))
+            return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
+        k_tree_cells<<<(unsigned)tb, kTreeB, 0, s>>>(n, skeys, tb, range, hbase, A.level.as<int32_t>(),
+                                                     A.key.as<uint64_t>(), A.begin.as<int32_t>(),
+                                                     A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
+                                                     A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
+                                                     A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>());
+        k_tree_links<<<blocks_for(ncells), 256, 0, s>>>(ncells, n, skeys, info, A.level.as<int32_t>(),
+                                                       A.key.as<uint64_t>(), A.begin.as<int32_t>(),
+                                                       A.count.as<int32_t>(), A.end.as<int32_t>(),
+                                                       A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
+                                                       A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
+        k_tree_leaf_of<<<blocks_for(n), 256, 0, s>>>(n, A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>());
+        note_launches(3);
+    } else {
+        // level by level (leaf sizes beyond the one-pass window, or no particles): one flag /
+        // scan / compact round per level, the host reading the number of new cells after each
+        if (!cell_bufs(cap, false, 0)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
+        k_tree_root<<<1, 1, 0, s>>>(n, A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(),
+                                    A.count.as<int32_t>(), A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
+                                    A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
+        k_tree_pcell_init<<<blocks_for(n), 256, 0, s>>>(n, A.pcell.as<int32_t>());
+        note_launches(2);
+        ls = {0, 1};
+        ncells = 1;
+        for (int l = 0; l < kAdaptMaxLevel + 1; ++l) {
+            k_tree_flags<<<blocks_for(n), 256, 0, s>>>(n, skeys, l, leaf_size, kAdaptMaxLevel, A.pcell.as<int32_t>(),
+                                                       A.count.as<int32_t>(), A.begin.as<int32_t>(),
+                                                       A.flags.as<uint32_t>(), A.leaf_of.as<int32_t>());
+            note_launches(1);
+            launch_exclusive_scan(A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), n, A.scan_tmp.as<uint32_t>(), s);
+            const uint32_t nnew = read1<uint32_t>(A.scan.as<uint32_t>() + n, s);
+            if (nnew == 0) break;
+            if (ncells + nnew > cap) {
+                int64_t ncap = std::max<int64_t>(2 * cap, ncells + nnew + 64);
+                if (!cell_bufs(ncap, true, ncells)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
+                cap = ncap;
+            }
+            k_tree_new_cells<<<blocks_for(n), 256, 0, s>>>(
+                n, skeys, l, A.pcell.as<int32_t>(), A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), ncells,
+                A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(), A.parent.as<int32_t>(),
+                A.child_begin.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
+            k_tree_counts<<<blocks_for(nnew), 256, 0, s>>>(ncells, nnew, A.begin.as<int32_t>(),
+                                                          A.parent.as<int32_t>(), A.count.as<int32_t>());
+            k_tree_pcell<<<blocks_for(n), 256, 0, s>>>(n, A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), ncells,
+                                                      A.pcell.as<int32_t>());
+            note_launches(3);
+            ncells += nnew;
+            ls.push_back((int)ncells);
+            maxl = l + 1;
+        }
+        // particles still in a cell after the last level are in leaves of that level
+        k_tree_flags<<<blocks_for(n), 256, 0, s>>>(n, skeys, kAdaptMaxLevel, leaf_size, kAdaptMaxLevel,
+                                                   A.pcell.as<int32_t>(), A.count.as<int32_t>(), A.begin.as<int32_t>(),
                                                    A.flags.as<uint32_t>(), A.leaf_of.as<int32_t>());
         note_launches(1);
-        launch_exclusive_scan(A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), n, A.scan_tmp.as<uint32_t>(), s);
-        const uint32_t nnew = read1<uint32_t>(A.scan.as<uint32_t>() + n, s);
-        if (nnew == 0) break;
-        if (ncells + nnew > cap) {
-            int64_t ncap = std::max<int64_t>(2 * cap, ncells + nnew + 64);
-            if (!cell_bufs(ncap, true, ncells)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
-            cap = ncap;
-        }
-        k_tree_new_cells<<<blocks_for(n), 256, 0, s>>>(
-            n, skeys, l, A.pcell.as<int32_t>(), A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), ncells,
-            A.level.as<int32_t>(), A.key.as<uint64_t>(), A.begin.as<int32_t>(), A.parent.as<int32_t>(),
-            A.child_begin.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
-        k_tree_counts<<<blocks_for(nnew), 256, 0, s>>>(ncells, nnew, A.begin.as<int32_t>(), A.parent.as<int32_t>(),
-                                                      A.count.as<int32_t>());
-        k_tree_pcell<<<blocks_for(n), 256, 0, s>>>(n, A.flags.as<uint32_t>(), A.scan.as<uint32_t>(), ncells,
-                                                  A.pcell.as<int32_t>());
-        note_launches(3);
-        ncells += nnew;
-        ls.push_back((int)ncells);
-        maxl = l + 1;
+        if (grow(A.end, 4 * ncells, false, 0, s) || grow(A.leaves, 4 * ncells + 4, false, 0, s))
+            return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
+        k_cell_end<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                                                     A.end.as<int32_t>());
+        note_launches(1);
+        cudaMemsetAsync(A.group_cnt.p, 0, A.group_cnt.cap, s);
+        uint32_t *leaf_cursor = A.group_cnt.as<uint32_t>() + 8 * (kAdaptMaxLevel + 2) * 2 - 1;
+        k_leaf_list<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.nchild.as<int32_t>(), leaf_cursor,
+                                                      A.leaves.as<int32_t>());
+        note_launches(1);
+        A.nleaves = read1<uint32_t>(leaf_cursor, s);
     }
-    // particles still in a cell after the last level are in leaves of that level
-    k_tree_flags<<<blocks_for(n), 256, 0, s>>>(n, skeys, kAdaptMaxLevel, leaf_size, kAdaptMaxLevel,
-                                               A.pcell.as<int32_t>(), A.count.as<int32_t>(), A.begin.as<int32_t>(),
-                                               A.flags.as<uint32_t>(), A.leaf_of.as<int32_t>());
-    note_launches(1);
     A.ncells = ncells;
     A.max_level = maxl;
     A.level_start = ls;
-    if (grow(A.end, 4 * ncells, false, 0, s) || grow(A.coll, 4 * 27 * ncells, false, 0, s) ||
-        grow(A.leaves, 4 * ncells + 4, false, 0, s))
-        return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
-    k_cell_end<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.begin.as<int32_t>(), A.count.as<int32_t>(),
-                                                 A.end.as<int32_t>());
-    note_launches(1);
+    if (grow(A.coll, 4 * 27 * ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
     if (grow(A.geom, 16 * (size_t)ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
     const float4 *geom = A.geom.as<float4>();
     launch_cell_geom(ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(), box, A.geom.as<float4>(), s);
@@ -516,15 +819,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                                                         A.child_of.as<int32_t>(), A.coll.as<int32_t>());
         note_launches(1);
     }
-    // leaf list
-    cudaMemsetAsync(A.group_cnt.p, 0, A.group_cnt.cap, s);
-    uint32_t *leaf_cursor = A.group_cnt.as<uint32_t>() + 8 * (kAdaptMaxLevel + 2) * 2 - 1;
-    k_leaf_list<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.nchild.as<int32_t>(), leaf_cursor,
-                                                  A.leaves.as<int32_t>());
-    note_launches(1);
-    A.nleaves = read1<uint32_t>(leaf_cursor, s);
 
-    // ---- lists ----
+    // ---- lists: counts and offsets of the four kinds, one host read of their sizes, fills ----
     if (grow(A.scan_tmp, 4 * (exclusive_scan_tmp_words(ncells + 1) + 64), false, 0, s))
         return fail(ctx, GBFMM_ENOMEM, "adaptive scan");
     TreeView tv{A.level.as<int32_t>(), A.parent.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
@@ -532,19 +828,34 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     for (int k = 0; k < 4; ++k) {
         if (grow(A.lcnt[k], 4 * (ncells + 1), false, 0, s) || grow(A.loffs[k], 4 * (ncells + 1), false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
-        k_alist_count<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.lcnt[k].as<uint32_t>(),
-                                                             ctx->d_status);
+        if (k == kListV)
+            k_vlist_warp<false><<<blocks_for(ncells, 8), 256, 0, s>>>(ncells, tv, A.lcnt[k].as<uint32_t>(), nullptr,
+                                                                      nullptr, nullptr);
+        else
+            k_alist_count<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.lcnt[k].as<uint32_t>(),
+                                                                 ctx->d_status);
         note_launches(1);
         launch_exclusive_scan(A.lcnt[k].as<uint32_t>(), A.loffs[k].as<uint32_t>(), ncells,
                               A.scan_tmp.as<uint32_t>(), s);
-        const uint32_t ne = read1<uint32_t>(A.loffs[k].as<uint32_t>() + ncells, s);
+    }
+    k_list_totals<<<1, 32, 0, s>>>(ncells, A.loffs[0].as<uint32_t>(), A.loffs[1].as<uint32_t>(),
+                                   A.loffs[2].as<uint32_t>(), A.loffs[3].as<uint32_t>(), info + 32);
+    note_launches(1);
+    int32_t ltot[4];
+    cudaMemcpyAsync(ltot, info + 32, sizeof(ltot), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t ne = (uint32_t)ltot[k];
         A.entries[k] = ne;
         if (grow(A.lids[k], 4 * (size_t)ne + 4, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
         if (k == kListV && grow(A.vcode, 2 * (size_t)ne + 4, false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
-        k_alist_fill<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.loffs[k].as<uint32_t>(),
-                                                            A.lids[k].as<int32_t>(),
-                                                            k == kListV ? A.vcode.as<uint16_t>() : nullptr);
+        if (k == kListV)
+            k_vlist_warp<true><<<blocks_for(ncells, 8), 256, 0, s>>>(ncells, tv, nullptr, A.loffs[k].as<uint32_t>(),
+                                                                     A.lids[k].as<int32_t>(), A.vcode.as<uint16_t>());
+        else
+            k_alist_fill<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.loffs[k].as<uint32_t>(),
+                                                                A.lids[k].as<int32_t>(), nullptr);
         note_launches(1);
     }
     mark(3);
@@ -566,6 +877,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         // M2L targets: every cell at levels >= 2, grouped by (level, child position)
         const int64_t lo2 = ls[2];
         uint32_t *gcnt = A.group_cnt.as<uint32_t>();
+        cudaMemsetAsync(gcnt, 0, 4 * 8 * (kAdaptMaxLevel + 2), s);
         k_group_count<<<blocks_for(ncells - lo2), 256, 0, s>>>(lo2, ncells, A.level.as<int32_t>(),
                                                                A.key.as<uint64_t>(), gcnt);
         note_launches(1);
