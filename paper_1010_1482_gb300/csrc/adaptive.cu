@@ -1,11 +1,11 @@
 // Adaptive octree FMM on the device (the adaptive FMM of Cheng, Greengard & Rokhlin 1999,
 // which the paper cites for its translation operators).
 //
-// Tree: the particles are sorted by their full 63-bit Morton key (stable radix sort), then
-// the tree is built level by level: a cell splits while it holds more than leaf_size particles
-// (and is above level 21); only nonempty children exist.  Cells are numbered level by level,
-// in key order within a level.  Every level is one flag / scan / compact round over the
-// particles; the host reads the number of new cells after each round to size the cell arrays.
+// Tree: the particles are sorted by their full 63-bit Morton key (stable radix sort); a cell
+// splits while it holds more than leaf_size particles (and is above level 21); only nonempty
+// children exist.  Cells are numbered level by level, in key order within a level.  The cells
+// are found in one pass over the sorted keys (every particle learns the levels at which it
+// starts a cell); leaf sizes beyond the one-pass window take level-by-level rounds.
 //
 // Lists (every cell B):
 //   colleagues(B)  cells of B's level adjacent to B (B included), stored by position (27 slots)
@@ -30,6 +30,7 @@ namespace gbfmm {
 constexpr int kAdaptMaxLevel = kAdaptiveMaxLevel;
 constexpr int kListU = 0, kListV = 1, kListW = 2, kListX = 3;
 constexpr int kDescentStack = 256;
+constexpr int64_t kListWarpCells = 1 << 17;  // below this many cells the U/W/X rows take a warp per cell
 
 // ---- keys ---------------------------------------------------------------------------------
 __global__ void k_keys64(const float4 *__restrict__ x, int64_t n, const Box *__restrict__ box,
@@ -393,141 +394,168 @@ __global__ void k_colleagues(int64_t lo, int64_t hi, int l, const uint64_t *__re
 struct TreeView {
     const int32_t *level, *parent, *nchild, *child_of, *coll;
     const uint64_t *key;
+    const int4 *anc;  // integer box at depth 21: anchor x, y, z and log2 of the side
 };
 
-GB_DEV void cell_box(const TreeView &t, int32_t c, int64_t lo[3], int64_t &size)
+// integer box of every cell at depth 21 (the adjacency tests read it instead of decoding keys)
+__global__ void k_cell_anchor(int64_t nc, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                              int4 *__restrict__ anc)
 {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
     int x, y, z;
-    const int l = t.level[c];
-    demorton63(t.key[c], x, y, z);
-    size = int64_t(1) << (kAdaptMaxLevel - l);
-    lo[0] = x * size;
-    lo[1] = y * size;
-    lo[2] = z * size;
+    demorton63(key[c], x, y, z);
+    const int sh = kAdaptMaxLevel - level[c];
+    anc[c] = make_int4(x << sh, y << sh, z << sh, sh);
 }
 
+// boxes that touch or overlap in all three dimensions
 GB_DEV bool adjacent(const TreeView &t, int32_t a, int32_t b)
 {
-    int64_t la[3], lb[3], sa, sb;
-    cell_box(t, a, la, sa);
-    cell_box(t, b, lb, sb);
-    for (int d = 0; d < 3; ++d)
-        if (la[d] > lb[d] + sb || lb[d] > la[d] + sa) return false;
-    return true;
+    const int4 la = t.anc[a], lb = t.anc[b];
+    const int sa = 1 << la.w, sb = 1 << lb.w;
+    return !(la.x > lb.x + sb || lb.x > la.x + sa || la.y > lb.y + sb || lb.y > la.y + sa || la.z > lb.z + sb ||
+             lb.z > la.z + sa);
 }
 
-// Calls f(id, code) for every entry of list `kind` of cell b; returns false if a descent
-// exceeded its stack (the row is then incomplete and the caller raises the status word).
-template <class F>
-GB_DEV bool for_each_entry(const TreeView &t, int kind, int32_t b, F f)
+// Descent below colleague a of leaf b (U and W lists): a leaf colleague is a U entry; below a
+// split colleague, descendants adjacent to b are opened (leaves among them are U entries) and
+// the first non-adjacent ones on each path are W entries.  Calls f(id) for the entries of the
+// list kind; returns false if the stack overflowed.
+template <bool U, class F>
+GB_DEV bool descend(const TreeView &t, int32_t b, int32_t a, F f)
 {
-    const int l = t.level[b];
-    if (kind == kListV) {
-        if (l < 2) return true;
-        int x, y, z;
-        demorton63(t.key[b], x, y, z);
-        const int side = 1 << l, cx = x & 1, cy = y & 1, cz = z & 1;
-        const int32_t *pc = t.coll + (int64_t)t.parent[b] * 27;
-        for (int oz = -2 - cz; oz <= 3 - cz; ++oz)
-            for (int oy = -2 - cy; oy <= 3 - cy; ++oy)
-                for (int ox = -2 - cx; ox <= 3 - cx; ++ox) {
-                    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-                    const int nx = x + ox, ny = y + oy, nz = z + oz;
-                    if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side) continue;
-                    const int32_t a = pc[slot27((nx >> 1) - (x >> 1), (ny >> 1) - (y >> 1), (nz >> 1) - (z >> 1))];
-                    if (a < 0) continue;
-                    const int32_t s = t.child_of[(int64_t)a * 8 + ((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2))];
-                    if (s >= 0) f(s, m2l_code(ox, oy, oz));
-                }
+    if (a < 0) return true;
+    if (t.nchild[a] == 0) {
+        if (U) f(a);
         return true;
     }
-    if (kind == kListX) {
-        const int32_t pb = t.parent[b];
-        if (pb < 0) return true;
-        for (int32_t anc = pb; anc >= 0; anc = t.parent[anc]) {
-            const int32_t *ac = t.coll + (int64_t)anc * 27;
-            for (int s = 0; s < 27; ++s) {
-                const int32_t c = ac[s];
-                if (c < 0 || c == anc || t.nchild[c] != 0) continue;
-                if (adjacent(t, pb, c) && !adjacent(t, b, c)) f(c, 0);
-            }
-        }
-        return true;
-    }
-    // U and W: leaves only
-    if (t.nchild[b] != 0) return true;
     bool ok = true;
-    const int32_t *bc = t.coll + (int64_t)b * 27;
-    for (int s = 0; s < 27; ++s) {
-        const int32_t a = bc[s];
-        if (a < 0) continue;
-        if (t.nchild[a] == 0) {
-            if (kind == kListU) f(a, 0);
-            continue;
-        }
-        int32_t stack[kDescentStack];
-        int sp = 0;
-        for (int q = 0; q < 8; ++q) {
-            const int32_t c = t.child_of[(int64_t)a * 8 + q];
-            if (c >= 0) stack[sp++] = c;
-        }
-        while (sp > 0) {
-            const int32_t d = stack[--sp];
-            if (adjacent(t, b, d)) {
-                if (t.nchild[d] == 0) {
-                    if (kind == kListU) f(d, 0);
-                } else {
-                    for (int q = 0; q < 8; ++q) {
-                        const int32_t c = t.child_of[(int64_t)d * 8 + q];
-                        if (c < 0) continue;
-                        if (sp < kDescentStack)
-                            stack[sp++] = c;
-                        else
-                            ok = false;
-                    }
+    int32_t stack[kDescentStack];
+    int sp = 0;
+    for (int q = 0; q < 8; ++q) {
+        const int32_t c = t.child_of[(int64_t)a * 8 + q];
+        if (c >= 0) stack[sp++] = c;
+    }
+    while (sp > 0) {
+        const int32_t d = stack[--sp];
+        if (adjacent(t, b, d)) {
+            if (t.nchild[d] == 0) {
+                if (U) f(d);
+            } else {
+                for (int q = 0; q < 8; ++q) {
+                    const int32_t c = t.child_of[(int64_t)d * 8 + q];
+                    if (c < 0) continue;
+                    if (sp < kDescentStack)
+                        stack[sp++] = c;
+                    else
+                        ok = false;
                 }
-            } else if (kind == kListW) {
-                f(d, 0);
             }
+        } else if (!U) {
+            f(d);
         }
     }
-    if (kind == kListU)
-        for (int32_t anc = t.parent[b]; anc >= 0; anc = t.parent[anc]) {
-            const int32_t *ac = t.coll + (int64_t)anc * 27;
-            for (int s = 0; s < 27; ++s) {
-                const int32_t c = ac[s];
-                if (c < 0 || c == anc || t.nchild[c] != 0) continue;
-                if (adjacent(t, b, c)) f(c, 0);
-            }
-        }
     return ok;
 }
 
-__global__ void k_alist_count(int kind, int64_t nc, TreeView t, uint32_t *__restrict__ cnt, int *status)
+GB_DEV uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t &total)
 {
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nc) return;
-    uint32_t k = 0;
-    if (!for_each_entry(t, kind, (int32_t)b, [&](int32_t, int) { ++k; })) atomicOr(status, kStatusTimeout);
-    cnt[b] = k;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
 }
 
-__global__ void k_alist_fill(int kind, int64_t nc, TreeView t, const uint32_t *__restrict__ offs,
-                             int32_t *__restrict__ ids, uint16_t *__restrict__ codes)
+// U, W and X lists, one warp per cell.  Entries come in the order: colleague slot (lane), the
+// descent below it, then (U, X) ancestors from the parent up, colleague slot within each.  The
+// count pass (FILL = false) writes the row lengths; the fill pass writes the rows at `offs`.
+template <int KIND, bool FILL>
+__global__ void k_alist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+                             int32_t *__restrict__ ids, int *status)
 {
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nc) return;
-    uint32_t e = offs[b];
-    for_each_entry(t, kind, (int32_t)b, [&](int32_t s, int code) {
-        ids[e] = s;
-        if (codes) codes[e] = (uint16_t)code;
+    const int lane = threadIdx.x & 31;
+    const int64_t bb = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (bb >= nc) return;
+    const int32_t b = (int32_t)bb;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t e = FILL ? offs[b] : 0u;
+    if (KIND == kListU || KIND == kListW) {
+        if (t.nchild[b] != 0) {
+            if (!FILL && lane == 0) cnt[b] = 0;
+            return;
+        }
+        const int32_t a = lane < 27 ? t.coll[(int64_t)b * 27 + lane] : -1;
+        uint32_t mine = 0;
+        const bool ok = descend<KIND == kListU>(t, b, a, [&](int32_t) { ++mine; });
+        if (!FILL && !ok) atomicOr(status, kStatusTimeout);
+        uint32_t total;
+        const uint32_t excl = warp_excl_scan(mine, lane, total);
+        if (FILL) {
+            uint32_t w = e + excl;
+            descend<KIND == kListU>(t, b, a, [&](int32_t d) { ids[w++] = d; });
+        }
+        e += total;
+    }
+    if (KIND == kListU || KIND == kListX) {
+        const int32_t ref = KIND == kListU ? b : t.parent[b];  // adjacency reference
+        if (ref >= 0)
+            for (int32_t anc = t.parent[b]; anc >= 0; anc = t.parent[anc]) {
+                const int32_t c = lane < 27 ? t.coll[(int64_t)anc * 27 + lane] : -1;
+                bool hit = c >= 0 && c != anc && t.nchild[c] == 0 && adjacent(t, ref, c);
+                if (KIND == kListX && hit) hit = !adjacent(t, b, c);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (FILL && hit) ids[e + __popc(bal & lt)] = c;
+                e += __popc(bal);
+            }
+    }
+    if (!FILL && lane == 0) cnt[b] = e;
+}
+
+// The same U, W and X rows, one thread per cell (slots in sequence): on large trees the warp
+// form leaves most lanes idle while one descends, and its fill repeats the descents.
+template <int KIND, bool FILL>
+__global__ void k_alist_thread(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+                               int32_t *__restrict__ ids, int *status)
+{
+    const int64_t bb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (bb >= nc) return;
+    const int32_t b = (int32_t)bb;
+    uint32_t e = FILL ? offs[b] : 0u;
+    auto emit = [&](int32_t d) {
+        if (FILL) ids[e] = d;
         ++e;
-    });
+    };
+    if (KIND == kListU || KIND == kListW) {
+        if (t.nchild[b] != 0) {
+            if (!FILL) cnt[b] = 0;
+            return;
+        }
+        bool ok = true;
+        for (int sl = 0; sl < 27; ++sl) ok &= descend<KIND == kListU>(t, b, t.coll[(int64_t)b * 27 + sl], emit);
+        if (!FILL && !ok) atomicOr(status, kStatusTimeout);
+    }
+    if (KIND == kListU || KIND == kListX) {
+        const int32_t ref = KIND == kListU ? b : t.parent[b];
+        if (ref >= 0)
+            for (int32_t anc = t.parent[b]; anc >= 0; anc = t.parent[anc])
+                for (int sl = 0; sl < 27; ++sl) {
+                    const int32_t c = t.coll[(int64_t)anc * 27 + sl];
+                    if (c < 0 || c == anc || t.nchild[c] != 0 || !adjacent(t, ref, c)) continue;
+                    if (KIND == kListX && adjacent(t, b, c)) continue;
+                    emit(c);
+                }
+    }
+    if (!FILL) cnt[b] = e;
 }
 
 // V list, one warp per cell: lane j takes the candidate offsets t = j, j + 32, ... of the
 // 6x6x6 block of the parent's colleagues' children (t = 36 (oz + 2 + cz) + 6 (oy + 2 + cy) +
-// (ox + 2 + cx), the order of for_each_entry), and a ballot compacts the hits so that a row is
+// (ox + 2 + cx): oz slowest, ox fastest), and a ballot compacts the hits so that a row is
 // written in that order with coalesced stores.
 template <bool FILL>
 __global__ void k_vlist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
@@ -631,7 +659,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -823,18 +851,39 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     // ---- lists: counts and offsets of the four kinds, one host read of their sizes, fills ----
     if (grow(A.scan_tmp, 4 * (exclusive_scan_tmp_words(ncells + 1) + 64), false, 0, s))
         return fail(ctx, GBFMM_ENOMEM, "adaptive scan");
+    if (grow(A.anchor, 16 * (size_t)ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
+    k_cell_anchor<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(),
+                                                    A.anchor.as<int4>());
+    note_launches(1);
     TreeView tv{A.level.as<int32_t>(), A.parent.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
-                A.coll.as<int32_t>(), A.key.as<uint64_t>()};
+                A.coll.as<int32_t>(), A.key.as<uint64_t>(), A.anchor.as<int4>()};
+    const unsigned g8 = blocks_for(ncells, 8);
+    // U, W, X rows: a warp per cell while the tree is small (latency: the 27 colleague slots in
+    // parallel), a thread per cell on large trees (throughput)
+    const bool warp_rows = ncells < kListWarpCells;
+    auto launch_alist = [&](int k, bool fill, uint32_t *cnt, const uint32_t *offs, int32_t *ids) {
+        const unsigned gt = blocks_for(ncells, 128);
+#define GB_ALIST(KIND, FILL)                                                                               \
+    (warp_rows ? k_alist_warp<KIND, FILL><<<g8, 256, 0, s>>>(ncells, tv, cnt, offs, ids, ctx->d_status)    \
+               : k_alist_thread<KIND, FILL><<<gt, 128, 0, s>>>(ncells, tv, cnt, offs, ids, ctx->d_status))
+        if (k == kListU) {
+            if (fill) GB_ALIST(kListU, true); else GB_ALIST(kListU, false);
+        } else if (k == kListW) {
+            if (fill) GB_ALIST(kListW, true); else GB_ALIST(kListW, false);
+        } else {
+            if (fill) GB_ALIST(kListX, true); else GB_ALIST(kListX, false);
+        }
+#undef GB_ALIST
+        note_launches(1);
+    };
     for (int k = 0; k < 4; ++k) {
         if (grow(A.lcnt[k], 4 * (ncells + 1), false, 0, s) || grow(A.loffs[k], 4 * (ncells + 1), false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
+        uint32_t *cnt = A.lcnt[k].as<uint32_t>();
         if (k == kListV)
-            k_vlist_warp<false><<<blocks_for(ncells, 8), 256, 0, s>>>(ncells, tv, A.lcnt[k].as<uint32_t>(), nullptr,
-                                                                      nullptr, nullptr);
+            k_vlist_warp<false><<<g8, 256, 0, s>>>(ncells, tv, cnt, nullptr, nullptr, nullptr);
         else
-            k_alist_count<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.lcnt[k].as<uint32_t>(),
-                                                                 ctx->d_status);
-        note_launches(1);
+            launch_alist(k, false, cnt, nullptr, nullptr);
         launch_exclusive_scan(A.lcnt[k].as<uint32_t>(), A.loffs[k].as<uint32_t>(), ncells,
                               A.scan_tmp.as<uint32_t>(), s);
     }
@@ -850,13 +899,12 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         if (grow(A.lids[k], 4 * (size_t)ne + 4, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
         if (k == kListV && grow(A.vcode, 2 * (size_t)ne + 4, false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
+        const uint32_t *offs = A.loffs[k].as<uint32_t>();
+        int32_t *ids = A.lids[k].as<int32_t>();
         if (k == kListV)
-            k_vlist_warp<true><<<blocks_for(ncells, 8), 256, 0, s>>>(ncells, tv, nullptr, A.loffs[k].as<uint32_t>(),
-                                                                     A.lids[k].as<int32_t>(), A.vcode.as<uint16_t>());
+            k_vlist_warp<true><<<g8, 256, 0, s>>>(ncells, tv, nullptr, offs, ids, A.vcode.as<uint16_t>());
         else
-            k_alist_fill<<<blocks_for(ncells, 128), 128, 0, s>>>(k, ncells, tv, A.loffs[k].as<uint32_t>(),
-                                                                A.lids[k].as<int32_t>(), nullptr);
-        note_launches(1);
+            launch_alist(k, true, nullptr, offs, ids);
     }
     mark(3);
 

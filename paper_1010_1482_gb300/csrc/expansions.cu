@@ -940,19 +940,19 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
 }
 
 // M2M (up) / L2L (down) over cells given by their parents' index range; children by position
-template <int P, bool UP>
-__global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t lo, int64_t np,
+template <int P, bool UP, int TN, int CN>
+__global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells(int64_t lo, int64_t np,
                                                                          const int32_t *__restrict__ child_of,
                                                                          const int32_t *__restrict__ nchild,
                                                                          const float *__restrict__ ops,
                                                                          float *__restrict__ X)
 {
-    using Cfg = TransCfg<P, UP>;
+    using Cfg = TransCfg<P, UP, TN, CN>;
     constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
     extern __shared__ __align__(16) float tsm[];
     float *A = tsm;
     float *B = tsm + PP * PR;
-    const int64_t q0 = blockIdx.x * (int64_t)kTrTN;
+    const int64_t q0 = blockIdx.x * (int64_t)TN;
     const int tid = threadIdx.x;
     const bool work = tid < NRG * NCG;
     const int cg = tid % NCG, rg = tid / NCG;
@@ -967,17 +967,17 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t
             kbeg = (d * d) / 4 * 4;
         }
     }
-    float acc[4][kTrCN];
+    float acc[4][CN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < kTrCN; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < CN; ++j) acc[i][j] = 0.f;
     const int c_first = UP ? 0 : blockIdx.y, c_last = UP ? 7 : blockIdx.y;
     for (int c = c_first; c <= c_last; ++c) {
         if (c != c_first) __syncthreads();
         const float4 *src = reinterpret_cast<const float4 *>(ops + (size_t)c * PP * PR);
         for (int e = tid; e < PP * PR / 4; e += blockDim.x) reinterpret_cast<float4 *>(A)[e] = __ldg(&src[e]);
-        for (int e = tid; e < kTrTN * (PP / 4); e += blockDim.x) {
+        for (int e = tid; e < TN * (PP / 4); e += blockDim.x) {
             const int i = e / (PP / 4), k4 = e % (PP / 4);
             const int64_t q = q0 + i;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -994,7 +994,7 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t
             const float *Bc = B + cg * SB;
 #pragma unroll 2
             for (int k = kbeg; k < kend; k += 4) {
-                Frag<kTrCN, 4> f;
+                Frag<CN, 4> f;
                 f.load(Ar, Bc, k, PR, NCG * SB);
                 f.fma(acc);
             }
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(TransCfg<P, UP>::NT) k_translate_cells(int64_t
     }
     if (!work) return;
 #pragma unroll
-    for (int j = 0; j < kTrCN; ++j) {
+    for (int j = 0; j < CN; ++j) {
         const int64_t q = q0 + cg + j * NCG;
         if (q >= np) continue;
         const int r = rg * 4;
@@ -1077,16 +1077,28 @@ void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float
     note_launches(1);
 }
 
+template <int P, bool UP, int TN, int CN>
+static void translate_cells_tn(int64_t lo, int64_t np, const int32_t *child_of, const int32_t *nchild,
+                               const float *ops, float *X, cudaStream_t s)
+{
+    using Cfg = TransCfg<P, UP, TN, CN>;
+    const int smem = (int)((Cfg::AF + Cfg::BF) * sizeof(float));  // one operator + one column block
+    cudaFuncSetAttribute(k_translate_cells<P, UP, TN, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 grid((unsigned)((np + TN - 1) / TN), UP ? 1 : 8);
+    k_translate_cells<P, UP, TN, CN><<<grid, Cfg::NT, smem, s>>>(lo, np, child_of, nchild, ops, X);
+    note_launches(1);
+}
+
+// the cells-per-CTA choice of the uniform tree's translations (launch_translate_t)
 template <int P, bool UP>
 static void translate_cells_t(int64_t lo, int64_t np, const int32_t *child_of, const int32_t *nchild, const float *ops,
                               float *X, cudaStream_t s)
 {
-    using Cfg = TransCfg<P, UP>;
-    const int smem = (int)((Cfg::AF + Cfg::BF) * sizeof(float));  // one operator + one column block
-    cudaFuncSetAttribute(k_translate_cells<P, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    dim3 grid((unsigned)((np + kTrTN - 1) / kTrTN), UP ? 1 : 8);
-    k_translate_cells<P, UP><<<grid, Cfg::NT, smem, s>>>(lo, np, child_of, nchild, ops, X);
-    note_launches(1);
+    const int64_t ctas32 = (np + 31) / 32 * (UP ? 1 : 8);
+    if (ctas32 >= 2 * 152)
+        translate_cells_tn<P, UP, 32, 8>(lo, np, child_of, nchild, ops, X, s);
+    else
+        translate_cells_tn<P, UP, 16, 2>(lo, np, child_of, nchild, ops, X, s);
 }
 
 void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,

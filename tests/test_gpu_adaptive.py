@@ -45,14 +45,14 @@ def run(G, ctx, x, **kw):
 
 
 def sorted_rows(offs, ids):
-    ids = ids.copy()
-    for r in range(len(offs) - 1):
-        ids[offs[r]:offs[r + 1]] = np.sort(ids[offs[r]:offs[r + 1]])
-    return ids
+    row = np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+    return ids[np.lexsort((ids, row))]
 
 
-# the last case has a leaf size beyond the one-pass construction's window: level-by-level rounds
-TREE_CASES = [("plummer", 30000, 32), ("plummer", 100000, 64), ("uniform", 20000, 16), ("plummer", 60000, 20000)]
+# ("plummer", 1000000, 8) has more than 2^17 cells (list rows a thread per cell); the last case
+# has a leaf size beyond the one-pass construction's window (level-by-level rounds)
+TREE_CASES = [("plummer", 30000, 32), ("plummer", 100000, 64), ("uniform", 20000, 16), ("plummer", 1000000, 8),
+              ("plummer", 60000, 20000)]
 
 
 @pytest.mark.parametrize("dist,n,leaf", TREE_CASES)
