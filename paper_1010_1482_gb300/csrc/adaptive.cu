@@ -695,11 +695,10 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     need(A.idx1, 4 * n);
     need(A.sx, 16 * n);
     need(A.far, 16 * n);
-    need(A.hist, 4 * (256 * nblk + 1));
+    need(A.hist, sort_scratch_bytes(n, 63));
     const int64_t tb = (n + kTreeB - 1) / kTreeB;  // one-pass tree blocks
     const int64_t hb = kTreeBins * tb + 1;
-    need(A.scan_tmp, 4 * (exclusive_scan_tmp_words(std::max<int64_t>(n + 1, hb)) + exclusive_scan_tmp_words(256 * nblk) +
-                          64));
+    need(A.scan_tmp, 4 * (exclusive_scan_tmp_words(std::max<int64_t>(n + 1, hb)) + 64));
     need(A.flags, 4 * (n + 1));
     need(A.scan, 4 * std::max<int64_t>(n + 1, hb));
     need(A.pcell, 4 * std::max<int64_t>(n, hb));
@@ -727,8 +726,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     uint64_t *skeys = nullptr;
     uint32_t *perm = nullptr;
     launch_sort_gather64(A.keys0.as<uint64_t>(), A.keys1.as<uint64_t>(), A.idx0.as<uint32_t>(),
-                         A.idx1.as<uint32_t>(), n, 63, A.hist.as<uint32_t>(), nblk, A.scan_tmp.as<uint32_t>(), x,
-                         A.sx.as<float4>(), &skeys, &perm, s);
+                         A.idx1.as<uint32_t>(), n, 63, A.hist.p, ctx->d_status, x, A.sx.as<float4>(), &skeys, &perm,
+                         s);
     mark(2);
 
     // ---- tree ----

@@ -144,7 +144,7 @@ Layout make_layout(int64_t n, int L, int P)
     lo.idx1 = take(4 * (size_t)n);
     lo.sx = take(16 * (size_t)n);
     lo.far = take(16 * (size_t)n);
-    lo.rs_hist = take(4 * (size_t)(256 * lo.rs_blocks + 1));
+    lo.rs_hist = take(sort_scratch_bytes(n, 3 * L));
     size_t tmpw = std::max({exclusive_scan_tmp_words(256 * lo.rs_blocks), exclusive_scan_tmp_words(C),
                             exclusive_scan_tmp_words(NL)});
     lo.scan_tmp = take(4 * tmpw);
@@ -378,7 +378,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     if (L >= 2) launch_geo_levels(box, L, geo, s);
     mark(1);
     uint32_t *skeys = nullptr, *perm = nullptr;
-    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, hist, lo.rs_blocks, scan_tmp, x, sx, &skeys, &perm, s);
+    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, hist, ctx->d_status, x, sx, &skeys, &perm, s);
     mark(2);
     launch_cells(skeys, n, L, begin, end, s);
     launch_list_count(L, begin, end, p2p_len, m2l_len, s);

@@ -180,11 +180,20 @@ void note_launches(int k);
 void launch_bbox(const float4 *x, int64_t n, int has_box, const double *box_origin, double box_side, Box *box_out,
                  float *partials, unsigned *counter, int *status, cudaStream_t s);
 void launch_keys(const float4 *x, int64_t n, const Box *box, int L, uint32_t *leafkey, uint32_t *idx, cudaStream_t s);
-// sorts (keys, idx) by key (stable) over `bits` low bits; on return the sorted pair is in
-// (*keys_out, *idx_out) (one of the two buffers); also gathers sx[i] = x[idx[i]].
-void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
-                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
-                        uint32_t **idx_out, cudaStream_t s);
+// Radix-sort scratch (tree.cu): per-pass tile counters, the histograms of every 8-bit digit
+// position, and one 64-bit look-back word per (pass, tile of 4096 keys, digit).
+constexpr size_t kRsCounterBytes = 256, kRsHistBytes = 8 * 256 * 4;
+constexpr size_t sort_scratch_bytes(int64_t n, int bits)
+{
+    return kRsCounterBytes + kRsHistBytes + 8 * 256 * (size_t)((bits + 7) / 8) * (size_t)((n + 4095) / 4096);
+}
+// sorts (keys, idx) by key (stable) over `bits` low bits (keys < 2^bits); on return the sorted
+// pair is in (*keys_out, *idx_out) (one of the two buffers); also gathers sx[i] = x[idx[i]].
+// `scratch` holds sort_scratch_bytes(n, bits); a look-back wait that runs out raises
+// kStatusTimeout in *err.
+void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, void *scratch,
+                        int *err, const float4 *x, float4 *sx, uint32_t **keys_out, uint32_t **idx_out,
+                        cudaStream_t s);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t s);
 size_t exclusive_scan_tmp_words(int64_t n);
 void launch_cells(const uint32_t *sorted_leaf_keys, int64_t n, int L, int32_t *begin, int32_t *end, cudaStream_t s);
@@ -215,8 +224,8 @@ void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s);
 
 // adaptive tree (targets and sources given as cell lists; cells carry level and 63-bit key)
 void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
-                          uint32_t *hist, int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx,
-                          uint64_t **keys_out, uint32_t **idx_out, cudaStream_t s);
+                          void *scratch, int *err, const float4 *x, float4 *sx, uint64_t **keys_out,
+                          uint32_t **idx_out, cudaStream_t s);
 void launch_cell_geom(int64_t nc, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
                       cudaStream_t s);
 void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,

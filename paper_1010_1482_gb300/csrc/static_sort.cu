@@ -4,7 +4,7 @@
 // Some callers cannot call cudaMalloc at all: code running inside a host framework whose
 // allocator owns every device byte, plug-ins that are handed only the buffers they read and
 // write, or hooks that run while the application forbids allocation.  For them this entry
-// point takes its scratch (ping-pong key / index buffers, digit histograms, scan partials,
+// point takes its scratch (ping-pong key / index buffers, the radix-sort histograms and look-back words,
 // the root-box partials and completion counter) from one file-scope __device__ array of
 // kStaticSortBytes.  Every GPU that loads the library holds that array until the process
 // exits.  The caller still passes the input particles and the three outputs.
@@ -23,7 +23,6 @@
 namespace gbfmm {
 
 constexpr int64_t kStaticSortMaxN = int64_t(1) << 20;
-constexpr int64_t kStaticSortBlocks = (kStaticSortMaxN + 4095) / 4096;
 
 // scratch layout (byte offsets, each 256-aligned)
 constexpr size_t kSsBox = 0;
@@ -32,9 +31,8 @@ constexpr size_t kSsStatus = 512;
 constexpr size_t kSsPartials = 768;                                   // 304 x 8 floats
 constexpr size_t kSsKeys = kSsPartials + 10240;                       // uint32[max n]
 constexpr size_t kSsIdx = kSsKeys + 4 * kStaticSortMaxN;              // uint32[max n]
-constexpr size_t kSsHist = kSsIdx + 4 * kStaticSortMaxN;              // uint32[256 x blocks + 1]
-constexpr size_t kSsScan = kSsHist + 4 * (256 * kStaticSortBlocks + 256);
-constexpr size_t kStaticSortBytes = kSsScan + 4 * 1024;
+constexpr size_t kSsHist = kSsIdx + 4 * kStaticSortMaxN;              // radix-sort scratch (32-bit keys)
+constexpr size_t kStaticSortBytes = kSsHist + sort_scratch_bytes(kStaticSortMaxN, 32);
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kStaticSortBytes];
 
@@ -89,8 +87,7 @@ extern "C" int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float
                 reinterpret_cast<float *>(base + kSsPartials), counter, status, s);
     launch_keys(x, n, box, L, k0, v0, s);
     uint32_t *kout = nullptr, *vout = nullptr;
-    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, reinterpret_cast<uint32_t *>(base + kSsHist), (n + 4095) / 4096,
-                       reinterpret_cast<uint32_t *>(base + kSsScan), x, reinterpret_cast<float4 *>(d_sorted_xyzq),
+    launch_sort_gather(k0, k1, v0, v1, n, 3 * L, base + kSsHist, status, x, reinterpret_cast<float4 *>(d_sorted_xyzq),
                        &kout, &vout, s);
     if (kout != k_caller || vout != v_caller) return GBFMM_ECUDA;  // buffer parity bookkeeping failed
     return cudaGetLastError() == cudaSuccess ? GBFMM_OK : GBFMM_ECUDA;

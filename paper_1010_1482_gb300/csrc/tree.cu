@@ -11,6 +11,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace gbfmm {
 
 // ------------------------------------------------------------------------------------------
@@ -307,78 +309,173 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 }
 
 // ------------------------------------------------------------------------------------------
-// Stable LSD radix sort of (key, index) pairs, 8-bit digits.  Per pass: tile histograms,
-// an exclusive scan of the digit-major histogram, and a scatter that ranks keys stably
-// inside each tile (warp match + per-warp digit counts).  The last pass also gathers the
-// particles into sorted order.
+// Stable LSD radix sort of (key, index) pairs, 8-bit digits: one kernel counts every digit
+// position's histogram, then one kernel per digit position ranks and scatters the keys.
+// Tiles of 4096 keys are taken in launch order (a counter), each ranks its keys stably in
+// shared memory (per-warp counts over a blocked layout, warp match within a round), publishes
+// its per-digit count and looks back over the earlier tiles' counts (decoupled look-back: an
+// earlier tile publishes its count at once and its inclusive prefix when it has one) to find
+// where its keys of each digit start.  The keys are staged in shared memory in tile-sorted
+// order and written out in runs per digit.  The last pass also gathers the particles.
+// Scratch: per-pass tile counters, the digit histograms, and one 64-bit status word per
+// (pass, tile, digit): flag (bits 62-63: 1 = count, 2 = inclusive prefix) | value.
 // ------------------------------------------------------------------------------------------
 constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
+constexpr int kRsWarps = kRsThreads / 32, kRsWarpKeys = kRsTile / kRsWarps;
+constexpr uint64_t kRsAgg = 1ull << 62, kRsInc = 2ull << 62, kRsFlags = 3ull << 62;
 
-template <class KeyT>
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const KeyT *__restrict__ keys, int64_t n, int shift,
-                                                        uint32_t mask, uint32_t *__restrict__ hist, int64_t nblk)
+static_assert(kRsWarpKeys == 32 * kRsItems, "blocked layout: a warp owns kRsItems rounds of 32 keys");
+
+GB_DEV void st_release_u64(uint64_t *p, uint64_t v)
 {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t base = blockIdx.x * (int64_t)kRsTile;
-#pragma unroll 4
-    for (int r = 0; r < kRsItems; ++r) {
-        int64_t i = base + r * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & mask], 1u);
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+GB_DEV uint64_t ld_acquire_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+GB_DEV uint64_t timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// exclusive scan of one value per thread over a 256-thread block
+GB_DEV uint32_t block_excl_scan256(uint32_t v, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+    uint32_t off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    __syncthreads();
+    return off + x - v;
 }
 
 template <class KeyT>
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const KeyT *__restrict__ kin,
-                                                           const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
-                                                           uint32_t *__restrict__ vout, int64_t n, int shift,
-                                                           uint32_t mask, const uint32_t *__restrict__ hist_scan,
-                                                           int64_t nblk, const float4 *__restrict__ gx,
-                                                           float4 *__restrict__ gsx)
+__global__ void __launch_bounds__(kRsThreads) k_rs_ghist(const KeyT *__restrict__ keys, int64_t n, int passes,
+                                                         uint32_t *__restrict__ ghist)
 {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[kRsThreads / 32][256];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    base[tid] = hist_scan[(int64_t)tid * nblk + blockIdx.x];
-#pragma unroll
-    for (int w = 0; w < kRsThreads / 32; ++w) wcnt[w][tid] = 0;
+    __shared__ uint32_t h[sizeof(KeyT)][256];
+    for (int d = 0; d < passes; ++d) h[d][threadIdx.x] = 0;
     __syncthreads();
-    const int64_t tbase = blockIdx.x * (int64_t)kRsTile;
+    for (int64_t i = blockIdx.x * (int64_t)kRsThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRsThreads) {
+        const KeyT k = keys[i];
+        for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(uint32_t)(k >> (8 * d)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int d = 0; d < passes; ++d)
+        if (h[d][threadIdx.x]) atomicAdd(&ghist[d * 256 + threadIdx.x], h[d][threadIdx.x]);
+}
+
+template <class KeyT>
+__global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                        KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                        int64_t n, int pass, int64_t nblk,
+                                                        const uint32_t *__restrict__ ghist, uint64_t *status,
+                                                        uint32_t *counter, const float4 *__restrict__ gx,
+                                                        float4 *__restrict__ gsx, int *err)
+{
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    KeyT *skey = reinterpret_cast<KeyT *>(rs_smem);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kRsTile);
+    __shared__ uint32_t wcnt[kRsWarps][256];
+    __shared__ uint32_t dstart[256], gbase[256], wsum[kRsWarps];
+    __shared__ uint32_t tile_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int shift = 8 * pass;
+    if (tid == 0) tile_sh = atomicAdd(&counter[pass], 1u);
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int64_t tile = tile_sh;
+    const int64_t base = tile * kRsTile + (int64_t)warp * kRsWarpKeys;
+    KeyT k[kRsItems];
+    uint32_t v[kRsItems], rk[kRsItems];
+#pragma unroll
     for (int r = 0; r < kRsItems; ++r) {
-        int64_t i = tbase + r * kRsThreads + tid;
-        bool valid = i < n;
-        const KeyT key = valid ? kin[i] : KeyT(0);
-        const uint32_t val = valid ? vin[i] : 0u;
-        uint32_t d = valid ? ((uint32_t)(key >> shift) & mask) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = base[tid];
+        const int64_t i = base + 32 * r + lane;
+        const bool valid = i < n;
+        k[r] = valid ? kin[i] : KeyT(0);
+        v[r] = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & 0xffu) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rk[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // digit tid: offsets of the warps' runs inside the tile's run, and the tile's count
+    uint32_t cnt = 0;
 #pragma unroll
-            for (int w = 0; w < kRsThreads / 32; ++w) {
-                uint32_t t = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += t;
+    for (int w = 0; w < kRsWarps; ++w) {
+        const uint32_t t = wcnt[w][tid];
+        wcnt[w][tid] = cnt;
+        cnt += t;
+    }
+    dstart[tid] = block_excl_scan256(cnt, wsum);
+    // look back over the earlier tiles' counts of digit tid
+    uint64_t *st = status + (size_t)pass * nblk * 256;
+    uint32_t excl = 0;
+    if (tile == 0) {
+        st_release_u64(&st[tid], kRsInc | cnt);
+    } else {
+        st_release_u64(&st[tile * 256 + tid], kRsAgg | cnt);
+        const uint64_t t0 = timer_ns();
+        for (int64_t t = tile - 1; t >= 0;) {
+            const uint64_t w = ld_acquire_u64(&st[t * 256 + tid]);
+            if ((w & kRsFlags) == 0) {
+                if (timer_ns() - t0 > 1000000000ull) {  // 1 s: report and give up
+                    atomicOr(err, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
             }
-            base[tid] = run;
+            excl += (uint32_t)w;
+            if ((w & kRsFlags) == kRsInc) break;
+            --t;
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = wcnt[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
-            if (gsx) gsx[pos] = __ldg(&gx[val]);
-        }
-        __syncthreads();
+        st_release_u64(&st[tile * 256 + tid], kRsInc | (excl + cnt));
+    }
+    gbase[tid] = block_excl_scan256(ghist[pass * 256 + tid], wsum) + excl;
+    __syncthreads();
+    // stage in tile-sorted order, then write the runs of each digit
 #pragma unroll
-        for (int w = 0; w < kRsThreads / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
+    for (int r = 0; r < kRsItems; ++r) {
+        const int64_t i = base + 32 * r + lane;
+        if (i < n) {
+            const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+            const uint32_t pos = dstart[d] + wcnt[warp][d] + rk[r];
+            skey[pos] = k[r];
+            sval[pos] = v[r];
+        }
+    }
+    __syncthreads();
+    const int64_t t0 = tile * kRsTile;
+    const int tn = (int)(n - t0 < kRsTile ? n - t0 : kRsTile);
+    for (int jj = tid; jj < tn; jj += kRsThreads) {
+        const KeyT key = skey[jj];
+        const uint32_t val = sval[jj];
+        const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+        const uint32_t gp = gbase[d] + (uint32_t)jj - dstart[d];
+        kout[gp] = key;
+        vout[gp] = val;
+        if (gsx) gsx[gp] = __ldg(&gx[val]);
     }
 }
 
@@ -389,9 +486,9 @@ __global__ void k_gather_identity(const float4 *__restrict__ x, float4 *__restri
 }
 
 template <class KeyT>
-static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
-                          int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, KeyT **keys_out,
-                          uint32_t **idx_out, cudaStream_t s)
+static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, void *scratch,
+                          int *err, const float4 *x, float4 *sx, KeyT **keys_out, uint32_t **idx_out,
+                          cudaStream_t s)
 {
     KeyT *kin = k0, *kout = k1;
     uint32_t *vin = v0, *vout = v1;
@@ -404,15 +501,21 @@ static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_
         *idx_out = v0;
         return;
     }
-    for (int shift = 0; shift < bits; shift += 8) {
-        int nb = bits - shift < 8 ? bits - shift : 8;
-        uint32_t mask = (1u << nb) - 1u;
-        bool last = shift + 8 >= bits;
-        k_rs_hist<KeyT><<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, n, shift, mask, hist, nblk);
-        launch_exclusive_scan(hist, hist, 256 * nblk, scan_tmp, s);
-        k_rs_scatter<KeyT><<<(unsigned)nblk, kRsThreads, 0, s>>>(kin, vin, kout, vout, n, shift, mask, hist, nblk,
-                                                                 x, last ? sx : nullptr);
-        note_launches(2);
+    const int passes = (bits + 7) / 8;
+    const int64_t nblk = (n + kRsTile - 1) / kRsTile;
+    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    uint32_t *counter = reinterpret_cast<uint32_t *>(sc);
+    uint32_t *ghist = reinterpret_cast<uint32_t *>(sc + kRsCounterBytes);
+    uint64_t *status = reinterpret_cast<uint64_t *>(sc + kRsCounterBytes + kRsHistBytes);
+    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s);
+    const unsigned hgrid = (unsigned)std::min<int64_t>(nblk * (kRsTile / kRsThreads) / 4 + 1, 1216);
+    k_rs_ghist<KeyT><<<hgrid, kRsThreads, 0, s>>>(kin, n, passes, ghist);
+    const int smem = kRsTile * (int)(sizeof(KeyT) + sizeof(uint32_t));
+    cudaFuncSetAttribute(k_rs_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    for (int pass = 0; pass < passes; ++pass) {
+        const bool last = pass + 1 == passes;
+        k_rs_pass<KeyT><<<(unsigned)nblk, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, pass, nblk, ghist, status,
+                                                                 counter, x, last ? sx : nullptr, err);
         KeyT *t = kin;
         kin = kout;
         kout = t;
@@ -420,22 +523,23 @@ static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_
         vin = vout;
         vout = u;
     }
+    note_launches(1 + passes);
     *keys_out = kin;
     *idx_out = vin;
 }
 
-void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, uint32_t *hist,
-                        int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx, uint32_t **keys_out,
-                        uint32_t **idx_out, cudaStream_t s)
+void launch_sort_gather(uint32_t *k0, uint32_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits, void *scratch,
+                        int *err, const float4 *x, float4 *sx, uint32_t **keys_out, uint32_t **idx_out,
+                        cudaStream_t s)
 {
-    sort_gather_t<uint32_t>(k0, k1, v0, v1, n, bits, hist, nblk, scan_tmp, x, sx, keys_out, idx_out, s);
+    sort_gather_t<uint32_t>(k0, k1, v0, v1, n, bits, scratch, err, x, sx, keys_out, idx_out, s);
 }
 
 void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
-                          uint32_t *hist, int64_t nblk, uint32_t *scan_tmp, const float4 *x, float4 *sx,
-                          uint64_t **keys_out, uint32_t **idx_out, cudaStream_t s)
+                          void *scratch, int *err, const float4 *x, float4 *sx, uint64_t **keys_out,
+                          uint32_t **idx_out, cudaStream_t s)
 {
-    sort_gather_t<uint64_t>(k0, k1, v0, v1, n, bits, hist, nblk, scan_tmp, x, sx, keys_out, idx_out, s);
+    sort_gather_t<uint64_t>(k0, k1, v0, v1, n, bits, scratch, err, x, sx, keys_out, idx_out, s);
 }
 
 // ------------------------------------------------------------------------------------------
