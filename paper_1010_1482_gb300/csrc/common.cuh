@@ -143,6 +143,11 @@ struct Box {
     double origin[3];
     double side;
     double key_scale;  // 2^21 / side, one IEEE FP64 division
+    // FP32 roundings of origin and key_scale, and the slack of the FP32 key estimate (k_keys):
+    // |FP32 estimate - FP64 value| <= |estimate| 2^-21 + key_slack
+    float origin_f[3];
+    float key_scale_f;
+    float key_slack;
 };
 
 // Cell geometry table of the uniform tree (expansions.cu, k_geo_levels): 1/h_l for

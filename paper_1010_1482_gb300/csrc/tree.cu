@@ -135,6 +135,14 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox(const float4 *__restrict__
             b.side = S;
         }
         b.key_scale = __ddiv_rn(2097152.0, b.side);
+        double m = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            b.origin_f[d] = __double2float_rn(b.origin[d]);
+            m = fmax(m, fabs(b.origin[d]));
+        }
+        b.key_scale_f = __double2float_rn(b.key_scale);
+        // twice the bound 2^-22 (|o| s + |v|) + 2^-40 of the FP32 estimate's error (see k_keys)
+        b.key_slack = __double2float_ru(__dmul_ru(__dmul_ru(m, b.key_scale), 0x1p-21) + 0x1p-20);
         *box_out = b;
         *counter = 0u;  // ready for the next launch on this stream
     }
@@ -155,6 +163,32 @@ void launch_bbox(const float4 *x, int64_t n, int has_box, const double *box_orig
 // s = 2^21 / side (one IEEE FP64 division, in the box kernel), every step one IEEE FP64
 // rounding; then the 3L-bit key of the depth-L cell = interleave(k_d >> (21 - L)).
 // ------------------------------------------------------------------------------------------
+//
+// The uniform tree needs only the top L bits of each k_d, and those are found in FP32 for all
+// but the particles within a few grid units of a leaf-cell face.  With o_f, s_f the FP32
+// roundings of origin and scale, the estimate v_f = (x - o_f) s_f (two FP32 roundings) is
+// within 2^-22 (|o| s + |v_f|) + 2^-40 of the FP64 value v, so v lies in [v_f - e, v_f + e]
+// with e = |v_f| 2^-21 + key_slack (twice that bound).  The leaf index clamp(floor(v), 0,
+// 2^21 - 1) >> (21 - L) is monotone in v: where it agrees at both ends of the interval it is
+// the FP64 result; otherwise the particle takes the FP64 steps above.
+GB_DEV uint32_t leaf_coord_f(float v, int sh)
+{
+    float f = floorf(v);
+    if (!(f >= 0.f)) f = 0.f;  // also maps NaN to 0
+    if (f > 2097151.f) f = 2097151.f;
+    return (uint32_t)f >> sh;
+}
+
+GB_DEV uint32_t grid_coord_fp64(float c, double origin, double scale)
+{
+    double t = __dsub_rn((double)c, origin);
+    double v = __dmul_rn(t, scale);
+    double f = floor(v);
+    if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
+    if (f > 2097151.0) f = 2097151.0;
+    return (uint32_t)f;
+}
+
 __global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__restrict__ box, int L,
                        uint32_t *__restrict__ leafkey, uint32_t *__restrict__ idx)
 {
@@ -163,18 +197,16 @@ __global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__res
     const Box b = *box;
     float4 p = __ldg(&x[i]);
     float c[3] = {p.x, p.y, p.z};
+    const int sh = 21 - L;
     uint32_t k[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double t = __dsub_rn((double)c[d], b.origin[d]);
-        double v = __dmul_rn(t, b.key_scale);
-        double f = floor(v);
-        if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
-        if (f > 2097151.0) f = 2097151.0;
-        k[d] = (uint32_t)f;
+        const float vf = __fmul_rn(__fsub_rn(c[d], b.origin_f[d]), b.key_scale_f);
+        const float e = __fadd_ru(__fmul_ru(fabsf(vf), 0x1p-21f), b.key_slack);
+        const uint32_t lo = leaf_coord_f(__fsub_rd(vf, e), sh), hi = leaf_coord_f(__fadd_ru(vf, e), sh);
+        k[d] = lo == hi ? lo : grid_coord_fp64(c[d], b.origin[d], b.key_scale) >> sh;
     }
-    const int sh = 21 - L;
-    leafkey[i] = morton3(k[0] >> sh, k[1] >> sh, k[2] >> sh);
+    leafkey[i] = morton3(k[0], k[1], k[2]);
     idx[i] = (uint32_t)i;
 }
 
@@ -621,23 +653,36 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, con
     if (l >= 2) {
         uint32_t cnt = 0, e = FILL ? m2l_offs[g] : 0u;
         if (ne) {
+            // all seven rounds' candidates first, so that their begin/end loads are in flight
+            // together, then the ballots in order
+            constexpr int kRounds = (216 + 31) / 32;
             const int bx = -2 - (x & 1), by = -2 - (y & 1), bz = -2 - (z & 1);
-            for (int i0 = 0; i0 < 216; i0 += 32) {
-                const int i = i0 + lane;
+            int32_t src[kRounds];
+            bool ok[kRounds];
+#pragma unroll
+            for (int r = 0; r < kRounds; ++r) {
+                const int i = 32 * r + lane;
                 const int ox = bx + i % 6, oy = by + (i / 6) % 6, oz = bz + i / 36;
                 const int sx = x + ox, sy = y + oy, sz = z + oz;
-                bool ok = i < 216 && sx >= 0 && sy >= 0 && sz >= 0 && sx < side && sy < side && sz < side &&
-                          !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
-                int64_t s = 0;
-                if (ok) {
-                    s = off + morton3((uint32_t)sx, (uint32_t)sy, (uint32_t)sz);
-                    ok = nonempty(begin, end, s);
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, ok);
-                if (FILL && ok) {
+                ok[r] = i < 216 && sx >= 0 && sy >= 0 && sz >= 0 && sx < side && sy < side && sz < side &&
+                        !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
+                src[r] = ok[r] ? (int32_t)(off + morton3((uint32_t)sx, (uint32_t)sy, (uint32_t)sz)) : 0;
+            }
+            int32_t b[kRounds], en[kRounds];
+#pragma unroll
+            for (int r = 0; r < kRounds; ++r) {
+                b[r] = ok[r] ? __ldg(&begin[src[r]]) : 0;
+                en[r] = ok[r] ? __ldg(&end[src[r]]) : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < kRounds; ++r) {
+                const bool hit = ok[r] && en[r] > b[r];
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (FILL && hit) {
+                    const int i = 32 * r + lane;
                     const uint32_t at = e + cnt + __popc(m & lt);
-                    m2l_ids[at] = (int32_t)s;
-                    m2l_code[at] = (uint16_t)gbfmm::m2l_code(ox, oy, oz);
+                    m2l_ids[at] = src[r];
+                    m2l_code[at] = (uint16_t)gbfmm::m2l_code(bx + i % 6, by + (i / 6) % 6, bz + i / 36);
                 }
                 cnt += __popc(m);
             }

@@ -87,6 +87,28 @@ def test_tree_and_lists_bit_exact(G, ctx, dist, n, leaf):
     assert np.array_equal(offs, ls["m2l_offs"]) and np.array_equal(ids, ls["m2l_ids"])
 
 
+def test_keys_on_leaf_cell_faces(G, ctx):
+    """Coordinates exactly on leaf-cell faces (j / 32 in the unit box, depth 5) and one float step
+    to either side: the key kernel's FP32 estimate cannot decide these and takes the FP64 steps;
+    keys, permutation and cells must still equal the oracle's bit for bit."""
+    g = np.arange(33, dtype=np.float64) / 32.0
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float32)
+    lo = np.nextafter(pts, np.float32(-1)).astype(np.float32)
+    hi = np.nextafter(pts, np.float32(2)).astype(np.float32)
+    xyz = np.concatenate([pts, np.clip(lo, 0, 1), np.clip(hi, 0, 1)])
+    q = inputs.uniform_cube(len(xyz), 12)[:, 3:4]
+    x = np.concatenate([xyz, q], axis=1).astype(np.float32)
+    leaf = 16
+    _, L = run(G, ctx, x, p=4, leaf_size=leaf)
+    t = O.build_tree(x, leaf)
+    assert L == t["L"] == 5
+    g_ = G.gbfmm_export_tree(ctx, len(x), O.level_offset(L + 1))
+    assert np.array_equal(g_["sorted_leaf_keys"].astype(np.uint64), t["sorted_leaf_keys"])
+    assert np.array_equal(g_["perm"].astype(np.int64), t["perm"])
+    assert np.array_equal(g_["count"], t["count"])
+
+
 @pytest.mark.parametrize("kind", ["duplicates", "one", "two", "below_leaf", "line"])
 def test_degenerate_inputs(G, ctx, kind):
     x, leaf = degenerate(kind)
