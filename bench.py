@@ -161,6 +161,22 @@ def traffic_from_profile(kernel_file: str, summary: str):
 # reference arm: the FP64 oracle on the host cores
 # ------------------------------------------------------------------------------------------
 
+def oracle_fmm(oracle, x, w):
+    """The oracle FMM on the workload's tree kind."""
+    if w["tree"] == "adaptive":
+        return oracle.fmm_adaptive(x, w["p"], w["leaf_size"])
+    return oracle.fmm(x, w["p"], w["leaf_size"])
+
+
+def oracle_sample_text(oracle, n_sample, w):
+    if w["tree"] == "adaptive":
+        return (f"oracle FP64 adaptive FMM, full evaluation of {n_sample} particles of the same distribution, "
+                f"p={w['p']}, leaf {w['leaf_size']}")
+    return (f"oracle FP64 FMM, full evaluation of {n_sample} particles of the same distribution, p={w['p']}, "
+            f"leaf {w['leaf_size']} (depth {oracle.uniform_depth(n_sample, w['leaf_size'])}, mean leaf occupancy "
+            f"32 as in the full workload)")
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -169,15 +185,13 @@ def run_reference(args, w):
 
     x = inputs.make_particles(REF_SAMPLE_N, w["dist"], w["seed"])
     for _ in range(args.warmup):
-        oracle.fmm(x, w["p"], w["leaf_size"])
+        oracle_fmm(oracle, x, w)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fmm(x, w["p"], w["leaf_size"])
+        oracle_fmm(oracle, x, w)
     dt = time.perf_counter() - t0
     value = REF_SAMPLE_N * args.steps / dt
-    sample = (f"oracle FP64 FMM, full evaluation of {REF_SAMPLE_N} particles of the same distribution, "
-              f"p={w['p']}, leaf {w['leaf_size']} (depth {oracle.uniform_depth(REF_SAMPLE_N, w['leaf_size'])}, "
-              "mean leaf occupancy 32 as in the full workload) per step")
+    sample = oracle_sample_text(oracle, REF_SAMPLE_N, w) + " per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -213,8 +227,10 @@ def run_gpu(args, w):
     G.lib()
 
     n = w["n"]
+    adaptive = w["tree"] == "adaptive"
+    tree_kind = G.TREE_ADAPTIVE if adaptive else G.TREE_UNIFORM
     x = inputs.make_particles(n, w["dist"], replica_seed(w["seed"], rank))
-    fmm = G.FMM(local, p=w["p"], leaf_size=w["leaf_size"], flags=G.FLAG_STAGE_TIMING)
+    fmm = G.FMM(local, p=w["p"], leaf_size=w["leaf_size"], tree=tree_kind, flags=G.FLAG_STAGE_TIMING)
     L, ws_bytes = fmm.plan(n)
     xd = torch.from_numpy(x).to(dev)
     out = torch.empty_like(xd)
@@ -226,13 +242,26 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
 
     # algorithmic work of the dominant kernels (from this evaluation's own lists)
-    C = G.level_offset(L + 1)
-    m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_M2L, C)
+    if adaptive:
+        tree = G.gbfmm_export_adaptive_tree(fmm.ctx, n)
+        C = tree["ncells"]
+        L = int(tree["level"].max())
+        m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_V, C)
+        p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_U, C)
+        cnt_leaf = tree["count"].astype(np.int64)  # U rows of non-leaves are empty
+        # M2L tiles: targets grouped by (level, child position), 128 per tile
+        deep = tree["level"] >= 2
+        grp = tree["level"][deep].astype(np.int64) * 8 + (tree["key"][deep] & np.uint64(7)).astype(np.int64)
+        tiles = int(np.sum(-(-np.bincount(grp) // 128)))
+    else:
+        C = G.level_offset(L + 1)
+        m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_M2L, C)
+        tree = G.gbfmm_export_tree(fmm.ctx, n, C)
+        p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_P2P, 8 ** L)
+        cnt_leaf = tree["count"][G.level_offset(L): G.level_offset(L) + 8 ** L].astype(np.int64)
+        tiles = sum(8 * -(-(8 ** (l - 1)) // 128) for l in range(2, L + 1))
     m2l_pairs = int(m2l_offs[-1])
-    tree = G.gbfmm_export_tree(fmm.ctx, n, C)
-    p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_P2P, 8 ** L)
-    cnt_leaf = tree["count"][G.level_offset(L): G.level_offset(L) + 8 ** L].astype(np.int64)
-    cs = np.concatenate([[0], np.cumsum(tree["count"][p2p_ids].astype(np.int64))])
+    cs = np.concatenate([[0], np.cumsum(tree["count"][p2p_ids[:p2p_offs[-1]]].astype(np.int64))])
     src_per_leaf = cs[p2p_offs[1:]] - cs[p2p_offs[:-1]]
     p2p_pairs = int(np.sum(cnt_leaf * src_per_leaf))
     P = w["p"]
@@ -273,7 +302,7 @@ def run_gpu(args, w):
     stages = {k: float(np.mean(v)) for k, v in stage_acc.items()}
 
     # the FP32 CUDA-core M2L (Eq. 4 on the same lists) measured beside the tensor-core default
-    cc_params = G.gbfmm_default_params(p=w["p"], leaf_size=w["leaf_size"],
+    cc_params = G.gbfmm_default_params(p=w["p"], leaf_size=w["leaf_size"], tree=tree_kind,
                                        flags=G.FLAG_STAGE_TIMING | G.FLAG_M2L_CUDA_CORES)
     cc_ms = []
     for i in range(4):
@@ -306,8 +335,11 @@ def run_gpu(args, w):
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
         hbm_peak = 6800.0
-    sort_passes = -(-(3 * L) // 8)
-    sort_bytes = sort_passes * 16 + 32
+    # keys: 32-bit leaf keys (uniform tree) or 63-bit keys at depth 21 (adaptive tree)
+    kb = 8 if adaptive else 4
+    sort_passes = 8 if adaptive else -(-(3 * L) // 8)
+    sort_bytes = sort_passes * 2 * (kb + 4) + kb + 32
+    box_bytes = 16 + kb + 4
     m2l_ms = stages.get("M2L/M2P", float("nan"))
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
@@ -315,7 +347,6 @@ def run_gpu(args, w):
     if tc_mode in (1, 2):
         # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to the
         # MMA's K step (8 for TF32, 16 for FP16), 3 MMAs per product (hi*hi + lo*hi + hi*lo)
-        tiles = sum(8 * -(-(8 ** (l - 1)) // 128) for l in range(2, L + 1))
         npad = -(-P * P // 16) * 16
         if tc_mode == 2:
             kpad = npad
@@ -324,11 +355,11 @@ def run_gpu(args, w):
                 tpeak, tbasis = bf16, f"measured BF16 dense burst {bf16:.1f} TFLOP/s (FP16 dense has the same nominal rate; of measured)"
             except Exception:
                 tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
-            kname, ksrc, kprof, kdt = "k_m2l_f16", "m2l_f16.cu", "m2l_f16_uniform_1m_p10.md", "FP16"
+            kname, ksrc, kprof, kdt = "k_m2l_f16", "m2l_f16.cu", f"m2l_f16_{w['name']}.md", "FP16"
         else:
             kpad = -(-P * P // 8) * 8
             tpeak, tbasis = tf32_peak_tflops()
-            kname, ksrc, kprof, kdt = "k_m2l_tc", "m2l_tc.cu", "m2l_tc_uniform_1m_p10.md", "TF32"
+            kname, ksrc, kprof, kdt = "k_m2l_tc", "m2l_tc.cu", f"m2l_tc_{w['name']}.md", "TF32"
         tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * kpad
         roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": m2l_tf / tpeak,
@@ -342,7 +373,7 @@ def run_gpu(args, w):
     else:
         roofline = {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
                     "frac": m2l_tf / peak,
-                    "traffic": traffic_from_profile("m2l.cu", "m2l_uniform_1m_p10.md"),
+                    "traffic": traffic_from_profile("m2l.cu", f"m2l_{w['name']}.md"),
                     "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
                     "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"}
     line = {
@@ -350,7 +381,7 @@ def run_gpu(args, w):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "p": P, "leaf_size": w["leaf_size"], "levels": L,
-                   "distribution": w["dist"], "parallelism": f"replicas x{ws}",
+                   "tree": w["tree"], "cells": int(C), "distribution": w["dist"], "parallelism": f"replicas x{ws}",
                    "l2": "flushed between steps (256 MiB write outside the per-step events)"},
         "roofline": roofline,
         "kernels": {
@@ -362,13 +393,15 @@ def run_gpu(args, w):
                                "frac": m2l_flops / (float(np.median(cc_ms)) / 1e3) / 1e12 / peak, "peak": peak,
                                "bound": "alu", "note": "same lists and Eq. 4 on the FP32 CUDA cores "
                                                        "(GBFMM_FLAG_M2L_CUDA_CORES), timed on the same data"},
-            "box_keys": {"bytes_per_particle": 24, "achieved_gbs": 24 * n / (stages["box+keys"] / 1e3) / 1e9,
+            "box_keys": {"bytes_per_particle": box_bytes,
+                         "achieved_gbs": box_bytes * n / (stages["box+keys"] / 1e3) / 1e9,
                          "peak_gbs": hbm_peak, "bound": "hbm",
-                         "note": "read x,y,z,q (16 B) for the box and again for the keys, write key + index (8 B); "
-                                 "the box read is counted once"},
+                         "note": f"read x,y,z,q (16 B) for the box and again for the keys, write key + index "
+                                 f"({kb + 4} B); the box read is counted once"},
             "sort": {"bytes_per_particle": sort_bytes, "achieved_gbs": sort_bytes * n / (stages["sort"] / 1e3) / 1e9,
                      "peak_gbs": hbm_peak, "bound": "hbm",
-                     "note": f"{sort_passes} radix passes x (read key + index 8 B, write 8 B) + gather (16 B in, 16 B out)"},
+                     "note": f"one histogram read of the keys (4 B), {sort_passes} radix passes x (read key + index 8 B, "
+                             "write 8 B), gather (16 B in, 16 B out)"},
         },
         "stages_ms": stages,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},
@@ -381,13 +414,11 @@ def run_gpu(args, w):
 
         xs = inputs.make_particles(CPU_BASELINE_N, w["dist"], w["seed"])
         t0 = time.perf_counter()
-        oracle.fmm(xs, P, w["leaf_size"])
+        oracle_fmm(oracle, xs, w)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {
             "value": CPU_BASELINE_N / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": (f"oracle FP64 FMM, full evaluation of {CPU_BASELINE_N} particles of the same distribution, "
-                       f"p={P}, leaf {w['leaf_size']} (depth {oracle.uniform_depth(CPU_BASELINE_N, w['leaf_size'])}, "
-                       f"mean leaf occupancy 32 as in the full workload), {dt:.1f} s"),
+            "sample": oracle_sample_text(oracle, CPU_BASELINE_N, w) + f", {dt:.1f} s",
         }
         # accuracy of the timed result on seeded targets against the FP64 direct sum
         tg = inputs.sample_indices(n, ERROR_TARGETS, w["seed"])

@@ -101,10 +101,14 @@ def workload(name: str) -> dict:
         "uniform_1m_p10": dict(n=1 << 20, dist="uniform", p=10, leaf_size=64, seed=SEED_BASE + 1),
         # same distribution, p and mean leaf occupancy (32) at depth 4: the small profiling case
         "uniform_128k_p10": dict(n=1 << 17, dist="uniform", p=10, leaf_size=64, seed=SEED_BASE + 1),
-        # clustered single instance
+        # clustered single instance (adaptive octree)
         "plummer_16m_p8": dict(n=1 << 24, dist="plummer", p=8, leaf_size=64, seed=SEED_BASE + 2),
+        # same distribution, p and leaf size at 2^21 particles: the small profiling case
+        "plummer_2m_p8": dict(n=1 << 21, dist="plummer", p=8, leaf_size=64, seed=SEED_BASE + 2),
     }
-    return dict(table[name], name=name)
+    w = dict(table[name], name=name)
+    w["tree"] = "adaptive" if w["dist"] == "plummer" else "uniform"
+    return w
 
 
 def make_particles(n: int, dist: str, seed: int) -> np.ndarray:
