@@ -344,11 +344,11 @@ def run_gpu(args, w):
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
     tc_mode = int(os.environ.get("GBFMM_M2L_TC", "2"))
-    if tc_mode in (1, 2):
+    if tc_mode in (1, 2, 3, 4):
         # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to the
         # MMA's K step (8 for TF32, 16 for FP16), 3 MMAs per product (hi*hi + lo*hi + hi*lo)
         npad = -(-P * P // 16) * 16
-        if tc_mode == 2:
+        if tc_mode >= 2:
             kpad = npad
             try:
                 bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])

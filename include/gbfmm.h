@@ -64,10 +64,12 @@ enum {
 
 /* flags */
 #define GBFMM_FLAG_STAGE_TIMING 1 /* record CUDA events between stages (gbfmm_stage_times) */
-/* run M2L on the FP32 CUDA cores instead of the tcgen05 tensor cores (3xTF32 with FP32
- * accumulation; the default).  Both compute Eq. 4 over the same lists; they differ by
- * rounding only.  Setting the environment variable GBFMM_M2L_TC=0 before the first
- * evaluation of an order p disables the tensor-core path for the whole process. */
+/* run M2L on the FP32 CUDA cores instead of the tcgen05 tensor cores (FP16 operands split in
+ * three products with FP32 accumulation; the default).  Both compute Eq. 4 over the same
+ * lists; they differ by rounding only.  The environment variable GBFMM_M2L_TC, read once per
+ * process, picks the tensor-core form: 2 = FP16 (default; sources pre-split per cell for
+ * p <= 8), 3 = FP16 with pre-split sources, 4 = FP16 converted in the kernel, 1 = TF32,
+ * 0 = none (CUDA cores). */
 #define GBFMM_FLAG_M2L_CUDA_CORES 2
 
 /*

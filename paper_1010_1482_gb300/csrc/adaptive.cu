@@ -659,7 +659,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -957,10 +957,19 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamSynchronize(s);  // the host tile vectors go out of scope
         if (f16) {
             if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive scales");
-            launch_cell_scale(M, ncells, P, A.cscale.as<int8_t>(), s);
+            void *ps = nullptr;
+            if (m2l_f16_presplit(P)) {  // sources split once per cell
+                if (grow(A.presplit, presplit_bytes(P, ncells), false, 0, s))
+                    return fail(ctx, GBFMM_ENOMEM, "adaptive pre-split sources");
+                ps = A.presplit.p;
+                launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s);
+            } else {
+                launch_cell_scale(M, ncells, P, A.cscale.as<int8_t>(), s);
+            }
             launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                  A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
-                                 A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), Lc, ctx->d_status, s);
+                                 A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc, ctx->d_status,
+                                 s);
         } else if (tc)
             launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                 A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),

@@ -161,6 +161,7 @@ Layout make_layout(int64_t n, int L, int P)
     lo.Lc = take(4 * (size_t)C * P * P);
     lo.cscale = take((size_t)C);
     lo.geo = take(4 * geo_floats(L));
+    lo.presplit = take(presplit_bytes(P, C));
     lo.total = off;
     return lo;
 }
@@ -191,7 +192,7 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
         if ((e = cudaMalloc(&c.m2l_tc, m2l_tc_table_floats(P) * sizeof(float))) != cudaSuccess)
             return cuda_fail(ctx, e, "cudaMalloc(m2l tensor-core ops)");
         launch_build_m2l_tc(P, c.m2l, c.m2l_tc, s);
-    } else if (m2l_tc_mode() == 2) {
+    } else if (m2l_tc_mode() >= 2) {
         if ((e = cudaMalloc(&c.m2l_f16, m2l_f16_table_bytes(P))) != cudaSuccess)
             return cuda_fail(ctx, e, "cudaMalloc(m2l FP16 tensor-core ops)");
         launch_build_m2l_f16(P, c.m2l, c.m2l_f16, s);
@@ -395,9 +396,15 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
         if (prm->method == GBFMM_METHOD_FMM && ops.m2l_f16 && !cores) {
             int8_t *cscale = at<int8_t>(ws, lo.cscale);
-            launch_cell_scale(M, lo.ncells, P, cscale, s);
-            launch_m2l_f16(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_f16, M, cscale, Lc, ctx->d_status,
-                           s);
+            void *ps = nullptr;
+            if (m2l_f16_presplit(P)) {  // sources split once per cell
+                ps = at<void>(ws, lo.presplit);
+                launch_presplit(P, M, lo.ncells, cscale, ps, s);
+            } else {
+                launch_cell_scale(M, lo.ncells, P, cscale, s);
+            }
+            launch_m2l_f16(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_f16, M, cscale, ps, Lc,
+                           ctx->d_status, s);
         } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !cores)
             launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
         else if (prm->method == GBFMM_METHOD_FMM)

@@ -172,7 +172,8 @@ struct Layout {
     size_t m2l_len, m2l_offs, m2l_ids, m2l_code;
     size_t M, Lc;
     size_t cscale;  // int8 per cell: power-of-two scale of the FP16 tensor-core M2L
-    size_t geo;     // float: cell geometry table per level and axis (geo_floats(L))
+    size_t geo;       // float: cell geometry table per level and axis (geo_floats(L))
+    size_t presplit;  // FP16 pre-split source rows of the gathered tensor-core M2L
     size_t total;
 };
 
@@ -251,11 +252,16 @@ void launch_build_m2l_f16(int P, const float *ops, void *table, cudaStream_t s);
 void launch_cell_scale(const float *M, int64_t ncells, int P, int8_t *scale, cudaStream_t s);
 void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                     const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M,
-                    const int8_t *cscale, float *Lc, int *status, cudaStream_t s);
+                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s);
 void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
                           const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                           const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                          float *Lc, int *status, cudaStream_t s);
+                          const void *ps, float *Lc, int *status, cudaStream_t s);
+// per cell: the FP16 scale s_c and the pre-split halves of M~_c 2^s_c (KP / 8 pieces of 8 hi
+// then 8 lo halves); m2l_f16_presplit(P): whether the FP16 M2L of order P takes them
+bool m2l_f16_presplit(int P);
+size_t presplit_bytes(int P, int64_t ncells);
+void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s);
 size_t m2l_tc_table_floats(int P);
 void launch_build_m2l_tc(int P, const float *ops, float *tc, cudaStream_t s);
 void launch_m2l_tc(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,

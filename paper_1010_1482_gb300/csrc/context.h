@@ -42,6 +42,7 @@ struct AdaptiveState {
     DevBuf M, Lc, tlist, tdesc, leaves, group_cnt, cscale, geom;  // geom: float4 (centre, 1/h) per cell
     DevBuf info;                                                   // small device-side totals read by the host
     DevBuf anchor;                                                 // int4 integer box per cell (depth 21)
+    DevBuf presplit;                                               // FP16 pre-split source rows (gathered M2L)
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
     int P = 0, max_level = 0;
     std::vector<int> level_start;

@@ -160,13 +160,15 @@ struct F16Tiles {
     int ntiles_level[kMaxLevel + 1];
 };
 
-template <int P>
+// PRE: the sources come pre-split (ps, KP halves hi then lo per cell) instead of as FP32 (M)
+template <int P, bool PRE>
 __global__ void __launch_bounds__(288, 1)
     k_m2l_f16(F16Tiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
               const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
               const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
               const uint16_t *__restrict__ m2l_code, const __half *__restrict__ tab, const int *__restrict__ gexp,
-              const float *__restrict__ M, const int8_t *__restrict__ cscale, float *__restrict__ Lc, int *status)
+              const float *__restrict__ M, const __half *__restrict__ ps, const int8_t *__restrict__ cscale,
+              float *__restrict__ Lc, int *status)
 {
     using C = F16Cfg<P>;
     using T = F16Table<P>;
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(288, 1)
             nxt_id = m2l_ids[ptr];
         }
         const float *lsrc = nullptr;
+        const __half *lps = nullptr;
         int lscale = 0;
         // per offset, in step order: the source's scale exponent (applied when converting)
         auto load = [&](int s2, float4 (&buf)[8], int &sc) {
@@ -260,8 +263,12 @@ __global__ void __launch_bounds__(288, 1)
             chunk16(c2, C::KS, NCH, k0, kw);
             if (c2 == 0) {
                 lsrc = nullptr;
+                lps = nullptr;
                 if (nxt_code == (int)c_f16_codes[tau][oc2]) {
-                    lsrc = M + (size_t)nxt_id * PP;
+                    if (PRE)
+                        lps = ps + (size_t)nxt_id * (2 * C::KP);
+                    else
+                        lsrc = M + (size_t)nxt_id * PP;
                     lscale = cscale[nxt_id];
                     ++ptr;
                     nxt_code = 0xffff;
@@ -272,6 +279,19 @@ __global__ void __launch_bounds__(288, 1)
                 }
             }
             sc = lscale;
+            if (PRE) {
+                // pieces (k0 + 32h) / 8 + i, i < 4: hi halves to buf[i], lo halves to buf[4 + i]
+                if (!lps) return;
+                const __half *pc = lps + 2 * (k0 + 32 * h);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (32 * h + 8 * i < kw) {
+                        buf[i] = __ldg(reinterpret_cast<const float4 *>(pc + 16 * i));
+                        buf[4 + i] = __ldg(reinterpret_cast<const float4 *>(pc + 16 * i + 8));
+                    }
+                }
+                return;
+            }
             if (!lsrc) return;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -328,10 +348,24 @@ __global__ void __launch_bounds__(288, 1)
                 s_issued[st] += 1;
             }
             // scale by 2^sc, split into FP16 halves hi = fp16(x), lo = fp16(x - hi), two per column
+            // (pre-split sources arrive as those halves)
             const float up = pow2f(sc);
             uint32_t hi[16], lo[16];
+            if (PRE) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 4; ++i) {
+                    hi[4 * i] = __float_as_uint(cur[i].x);
+                    hi[4 * i + 1] = __float_as_uint(cur[i].y);
+                    hi[4 * i + 2] = __float_as_uint(cur[i].z);
+                    hi[4 * i + 3] = __float_as_uint(cur[i].w);
+                    lo[4 * i] = __float_as_uint(cur[4 + i].x);
+                    lo[4 * i + 1] = __float_as_uint(cur[4 + i].y);
+                    lo[4 * i + 2] = __float_as_uint(cur[4 + i].z);
+                    lo[4 * i + 3] = __float_as_uint(cur[4 + i].w);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8 && !PRE; ++i) {
                 const float x0 = cur[i].x * up, x1 = cur[i].y * up, x2 = cur[i].z * up, x3 = cur[i].w * up;
                 const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
                 const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
@@ -429,28 +463,112 @@ __global__ void __launch_bounds__(288, 1)
     }
 }
 
+// ---- pre-split sources ------------------------------------------------------------------
+// The sources can be converted once per cell instead of once per (target, offset): after the
+// upward pass every cell's expansion is scaled by 2^s_c and split into FP16 halves, stored per
+// piece of 8 coefficients as 8 hi halves then 8 lo halves (KP / 8 pieces, zero-padded), so a
+// converter thread's hi and lo halves of a chunk are one contiguous 128-byte line.  With them
+// the converter warps only load their target's source and store it into TMEM (the same bits
+// the conversion produces, so the result is identical).
+template <int P>
+__global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, int64_t ncells,
+                                                  int8_t *__restrict__ scale, __half *__restrict__ ps)
+{
+    constexpr int PP = P * P, KP = F16Cfg<P>::KP, PER = (KP + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncells) return;
+    float v[PER];
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = lane + 32 * i;
+        v[i] = k < PP ? M[c * PP + k] : 0.f;
+        m = fmaxf(m, fabsf(v[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // the scale of k_cell_scale: max |M~_c| = f 2^e, f in [0.5, 1) -> s_c = 10 - e
+    const bool fin = m > 0.f && m <= 3.0e38f;
+    int ex = 0;
+    if (fin) frexpf(m, &ex);
+    int sc = fin ? 10 - ex : 0;
+    sc = sc < -100 ? -100 : (sc > 100 ? 100 : sc);
+    if (lane == 0) scale[c] = (int8_t)sc;
+    const float up = pow2f(sc);
+    __half *row = ps + c * (2 * KP);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = lane + 32 * i;
+        if (k < KP) {
+            const float x = v[i] * up;
+            const __half hi = __float2half_rn(x);
+            row[(k >> 3) * 16 + (k & 7)] = hi;
+            row[(k >> 3) * 16 + 8 + (k & 7)] = __float2half_rn(x - __half2float(hi));
+        }
+    }
+}
+
+// FP16 M2L modes (GBFMM_M2L_TC): 2 = pre-split sources for p <= 8 and converted in the kernel
+// at p = 10 (the faster form of each, measured on the GB300), 3 = always pre-split, 4 = never
+bool m2l_f16_presplit(int P)
+{
+    const int mode = m2l_tc_mode();
+    return mode == 3 || (mode == 2 && P <= 8);
+}
+
+size_t presplit_bytes(int P, int64_t ncells)
+{
+    const int KP = (P * P + 15) / 16 * 16;
+    return (size_t)ncells * 4 * KP;
+}
+
+void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s)
+{
+    if (ncells <= 0) return;
+    const unsigned grid = (unsigned)((ncells + 7) / 8);
+    __half *h = static_cast<__half *>(ps);
+    switch (P) {
+    case 4: k_presplit<4><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
+    case 6: k_presplit<6><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
+    case 8: k_presplit<8><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
+    case 10: k_presplit<10><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
+    }
+    note_launches(1);
+}
+
 template <int P>
 static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist, const int32_t *begin,
                          const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
-                         const void *table, const float *M, const int8_t *cscale, float *Lc, int *status,
-                         cudaStream_t s)
+                         const void *table, const float *M, const int8_t *cscale, const void *ps, float *Lc,
+                         int *status, cudaStream_t s)
 {
     using C = F16Cfg<P>;
     using T = F16Table<P>;
     const __half *tab = static_cast<const __half *>(table);
     const int *gexp = reinterpret_cast<const int *>(tab + (size_t)kM2LCodes * T::CODE_HALVES);
-    cudaFuncSetAttribute(k_m2l_f16<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-    k_m2l_f16<P><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code,
-                                                          tab, gexp, M, cscale, Lc, status);
+    const __half *h = static_cast<const __half *>(ps);
+    if (ps) {
+        cudaFuncSetAttribute(k_m2l_f16<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+        k_m2l_f16<P, true><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
+                                                                    m2l_ids, m2l_code, tab, gexp, M, h, cscale, Lc,
+                                                                    status);
+    } else {
+        cudaFuncSetAttribute(k_m2l_f16<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+        k_m2l_f16<P, false><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
+                                                                     m2l_ids, m2l_code, tab, gexp, M, h, cscale, Lc,
+                                                                     status);
+    }
     note_launches(1);
 }
 
+// ps != nullptr: the sources come pre-split (launch_presplit)
 static void dispatch_f16(int P, const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                          const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                          const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                         float *Lc, int *status, cudaStream_t s)
+                         const void *ps, float *Lc, int *status, cudaStream_t s)
 {
-#define GBFMM_F16_ARGS tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, Lc, status, s
+#define GBFMM_F16_ARGS tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc, status, s
     switch (P) {
     case 4: launch_f16_t<4>(GBFMM_F16_ARGS); break;
     case 6: launch_f16_t<6>(GBFMM_F16_ARGS); break;
@@ -462,7 +580,7 @@ static void dispatch_f16(int P, const F16Tiles &tiles, int grid, const int4 *tde
 
 void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                     const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M,
-                    const int8_t *cscale, float *Lc, int *status, cudaStream_t s)
+                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s)
 {
     if (L < 2) return;
     F16Tiles tiles{};
@@ -474,19 +592,19 @@ void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, cons
         total += tiles.ntiles_level[l];
     }
     if (total == 0) return;
-    dispatch_f16(P, tiles, total, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, Lc,
-                 status, s);
+    dispatch_f16(P, tiles, total, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps,
+                 Lc, status, s);
 }
 
 void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
                           const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                           const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                          float *Lc, int *status, cudaStream_t s)
+                          const void *ps, float *Lc, int *status, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     F16Tiles tiles{};
-    dispatch_f16(P, tiles, ntiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, Lc, status,
-                 s);
+    dispatch_f16(P, tiles, ntiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc,
+                 status, s);
 }
 
 }  // namespace gbfmm
