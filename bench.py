@@ -355,7 +355,8 @@ def run_gpu(args, w):
                 tpeak, tbasis = bf16, f"measured BF16 dense burst {bf16:.1f} TFLOP/s (FP16 dense has the same nominal rate; of measured)"
             except Exception:
                 tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
-            kname, ksrc, kprof, kdt = "k_m2l_f16", "m2l_f16.cu", f"m2l_f16_{w['name']}.md", "FP16"
+            kname = "k_m2l_f16s" if tc_mode == 2 else "k_m2l_f16"
+            ksrc, kprof, kdt = "m2l_f16.cu", f"{kname[2:]}_{w['name']}.md", "FP16"
         else:
             kpad = -(-P * P // 8) * 8
             tpeak, tbasis = tf32_peak_tflops()

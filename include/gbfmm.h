@@ -67,9 +67,9 @@ enum {
 /* run M2L on the FP32 CUDA cores instead of the tcgen05 tensor cores (FP16 operands split in
  * three products with FP32 accumulation; the default).  Both compute Eq. 4 over the same
  * lists; they differ by rounding only.  The environment variable GBFMM_M2L_TC, read once per
- * process, picks the tensor-core form: 2 = FP16 (default; sources pre-split per cell for
- * p <= 8), 3 = FP16 with pre-split sources, 4 = FP16 converted in the kernel, 1 = TF32,
- * 0 = none (CUDA cores). */
+ * process, picks the tensor-core form: 2 = FP16 with the sources split once per cell and
+ * staged through shared memory (default), 4 = FP16 with the sources converted in the kernel,
+ * 1 = TF32, 0 = none (CUDA cores). */
 #define GBFMM_FLAG_M2L_CUDA_CORES 2
 
 /*

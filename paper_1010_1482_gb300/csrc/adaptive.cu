@@ -968,8 +968,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             }
             launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                  A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
-                                 A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc, ctx->d_status,
-                                 s);
+                                 A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc,
+                                 ctx->d_status, s);
         } else if (tc)
             launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                 A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),

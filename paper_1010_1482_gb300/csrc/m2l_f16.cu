@@ -160,15 +160,13 @@ struct F16Tiles {
     int ntiles_level[kMaxLevel + 1];
 };
 
-// PRE: the sources come pre-split (ps, KP halves hi then lo per cell) instead of as FP32 (M)
-template <int P, bool PRE>
+template <int P>
 __global__ void __launch_bounds__(288, 1)
     k_m2l_f16(F16Tiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
               const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
               const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
               const uint16_t *__restrict__ m2l_code, const __half *__restrict__ tab, const int *__restrict__ gexp,
-              const float *__restrict__ M, const __half *__restrict__ ps, const int8_t *__restrict__ cscale,
-              float *__restrict__ Lc, int *status)
+              const float *__restrict__ M, const int8_t *__restrict__ cscale, float *__restrict__ Lc, int *status)
 {
     using C = F16Cfg<P>;
     using T = F16Table<P>;
@@ -251,7 +249,6 @@ __global__ void __launch_bounds__(288, 1)
             nxt_id = m2l_ids[ptr];
         }
         const float *lsrc = nullptr;
-        const __half *lps = nullptr;
         int lscale = 0;
         // per offset, in step order: the source's scale exponent (applied when converting)
         auto load = [&](int s2, float4 (&buf)[8], int &sc) {
@@ -263,12 +260,8 @@ __global__ void __launch_bounds__(288, 1)
             chunk16(c2, C::KS, NCH, k0, kw);
             if (c2 == 0) {
                 lsrc = nullptr;
-                lps = nullptr;
                 if (nxt_code == (int)c_f16_codes[tau][oc2]) {
-                    if (PRE)
-                        lps = ps + (size_t)nxt_id * (2 * C::KP);
-                    else
-                        lsrc = M + (size_t)nxt_id * PP;
+                    lsrc = M + (size_t)nxt_id * PP;
                     lscale = cscale[nxt_id];
                     ++ptr;
                     nxt_code = 0xffff;
@@ -279,19 +272,6 @@ __global__ void __launch_bounds__(288, 1)
                 }
             }
             sc = lscale;
-            if (PRE) {
-                // pieces (k0 + 32h) / 8 + i, i < 4: hi halves to buf[i], lo halves to buf[4 + i]
-                if (!lps) return;
-                const __half *pc = lps + 2 * (k0 + 32 * h);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (32 * h + 8 * i < kw) {
-                        buf[i] = __ldg(reinterpret_cast<const float4 *>(pc + 16 * i));
-                        buf[4 + i] = __ldg(reinterpret_cast<const float4 *>(pc + 16 * i + 8));
-                    }
-                }
-                return;
-            }
             if (!lsrc) return;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -348,24 +328,10 @@ __global__ void __launch_bounds__(288, 1)
                 s_issued[st] += 1;
             }
             // scale by 2^sc, split into FP16 halves hi = fp16(x), lo = fp16(x - hi), two per column
-            // (pre-split sources arrive as those halves)
             const float up = pow2f(sc);
             uint32_t hi[16], lo[16];
-            if (PRE) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    hi[4 * i] = __float_as_uint(cur[i].x);
-                    hi[4 * i + 1] = __float_as_uint(cur[i].y);
-                    hi[4 * i + 2] = __float_as_uint(cur[i].z);
-                    hi[4 * i + 3] = __float_as_uint(cur[i].w);
-                    lo[4 * i] = __float_as_uint(cur[4 + i].x);
-                    lo[4 * i + 1] = __float_as_uint(cur[4 + i].y);
-                    lo[4 * i + 2] = __float_as_uint(cur[4 + i].z);
-                    lo[4 * i + 3] = __float_as_uint(cur[4 + i].w);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 8 && !PRE; ++i) {
+            for (int i = 0; i < 8; ++i) {
                 const float x0 = cur[i].x * up, x1 = cur[i].y * up, x2 = cur[i].z * up, x3 = cur[i].w * up;
                 const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
                 const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
@@ -470,6 +436,7 @@ __global__ void __launch_bounds__(288, 1)
 // converter thread's hi and lo halves of a chunk are one contiguous 128-byte line.  With them
 // the converter warps only load their target's source and store it into TMEM (the same bits
 // the conversion produces, so the result is identical).
+// one warp per cell
 template <int P>
 __global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, int64_t ncells,
                                                   int8_t *__restrict__ scale, __half *__restrict__ ps)
@@ -509,13 +476,9 @@ __global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, i
     }
 }
 
-// FP16 M2L modes (GBFMM_M2L_TC): 2 = pre-split sources for p <= 8 and converted in the kernel
-// at p = 10 (the faster form of each, measured on the GB300), 3 = always pre-split, 4 = never
-bool m2l_f16_presplit(int P)
-{
-    const int mode = m2l_tc_mode();
-    return mode == 3 || (mode == 2 && P <= 8);
-}
+// FP16 M2L modes (GBFMM_M2L_TC): 2 = pre-split sources staged by the converter warps
+// (k_m2l_f16s, default), 4 = FP32 sources converted in the kernel (k_m2l_f16)
+bool m2l_f16_presplit(int) { return m2l_tc_mode() == 2; }
 
 size_t presplit_bytes(int P, int64_t ncells)
 {
@@ -537,27 +500,338 @@ void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void 
     note_launches(1);
 }
 
+// ---- staged variant: coalesced copies of the pre-split sources --------------------------------
+// The converter warps' scattered 16-byte loads (every lane a different source row) kept the L1
+// data pipe near its peak while the tensor pipe idled.  Here each converter warp first copies
+// the chunk pieces of its 32 rows into a warp-private shared-memory slot with cp.async, 8 lanes
+// per row (each instruction reads 4 rows x 128 contiguous bytes of the pre-split sources: 8 hi
+// then 8 lo halves per 8 coefficients), one step ahead; then every lane reads its own row back
+// (conflict-free 16-byte shared loads) and stores it into TMEM.  Only warp-local
+// synchronisation: a warp reads only what it copied.
+template <int P, int CW_>
+struct F16SCfg {
+    static constexpr int PP = P * P, KP = F16Cfg<P>::KP, NP = F16Cfg<P>::NP, KS = KP / 16;
+    static constexpr int NCH = (KS + 3) / 4, TM = 128, CW = CW_;
+    static constexpr int HW = CW / 4;                         // converter warps per TMEM lane quadrant
+    static constexpr int SEG = 64 / HW;                       // halves of a chunk per warp
+    static constexpr int UPR = SEG / 4;                       // 16-byte units per row (hi + lo)
+    static constexpr int RSW = 4 * SEG + 16;                  // bytes per staged row (padded)
+    static constexpr int SLOT_BYTES = 32 * RSW;               // one warp, one step
+    static constexpr int STAGING_BYTES = CW * 2 * SLOT_BYTES; // two slots per warp
+    static constexpr int B_BYTES = 2 * NP * 64 * 2;           // operator: B_hi | B_lo
+    static constexpr int NSTAGE = STAGING_BYTES + 4 * B_BYTES <= 210 * 1024 ? 4 : 3;
+    static constexpr size_t kBytes = (size_t)NSTAGE * B_BYTES + STAGING_BYTES;
+    static constexpr size_t kSmemBytes = kBytes > 116 * 1024 ? kBytes : 116 * 1024;
+    static constexpr int TMEM_COLS = 512, A_COL0 = 256;      // D ping-pong, then A stages (64 columns each)
+    static constexpr int NTHREADS = 32 * (CW + 1);
+    static constexpr int NH = NP / HW;                        // output columns drained per thread
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+    static_assert(A_COL0 + 64 * NSTAGE <= TMEM_COLS, "TMEM A stages");
+    static_assert(B_BYTES % 1024 == 0, "stage alignment");
+    static_assert(NH % 4 == 0 && SEG % 8 == 0, "converter split");
+};
+
+template <int P, int CW_>
+__global__ void __launch_bounds__(F16SCfg<P, CW_>::NTHREADS, 1)
+    k_m2l_f16s(F16Tiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
+               const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+               const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
+               const uint16_t *__restrict__ m2l_code, const __half *__restrict__ tab, const int *__restrict__ gexp,
+               const __half *__restrict__ ps, const int8_t *__restrict__ cscale, float *__restrict__ Lc, int *status)
+{
+    using C = F16SCfg<P, CW_>;
+    using T = F16Table<P>;
+    constexpr int PP = C::PP, KP = C::KP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
+    constexpr int S = 189 * NCH, CW = C::CW, SEG = C::SEG, UPR = C::UPR;
+    constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);  // F32 += F16 x F16
+    constexpr int kMmaWarp = CW;
+
+    extern __shared__ __align__(1024) unsigned char f16ssm[];
+    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], drain_full[2], drain_empty[2], done_bar;
+    __shared__ int s_issued[NSTAGE];
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    int tau;
+    int64_t q0 = 0, nq = 0, off = 0, tstart = 0;
+    int tcount = 0;
+    if (tdesc) {
+        const int4 d = tdesc[blockIdx.x];
+        tau = d.y;
+        tstart = d.z;
+        tcount = d.w;
+    } else {
+        int rem = blockIdx.x;
+        int l = tiles.L;
+        while (l >= 2 && rem >= tiles.ntiles_level[l]) {
+            rem -= tiles.ntiles_level[l];
+            --l;
+        }
+        if (l < 2) return;
+        nq = int64_t(1) << (3 * (l - 1));
+        const int64_t qtiles = (nq + TM - 1) / TM;
+        tau = (int)(rem / qtiles);
+        q0 = (rem % qtiles) * TM;
+        off = level_offset(l);
+    }
+    auto target = [&](int t) -> int64_t {
+        if (tdesc) return t < tcount ? (int64_t)tlist[tstart + t] : -1;
+        const int64_t q = q0 + t;
+        return q < nq ? off + 8 * q + tau : -1;
+    };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < NSTAGE; ++st) {
+            mbar_init(&full_bar[st], CW + 1);  // the converter warps + the operator copies' expect_tx
+            mbar_init(&empty_bar[st], 1);      // one tcgen05.commit
+            s_issued[st] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&drain_full[b], 1);
+            mbar_init(&drain_empty[b], CW);
+        }
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == kMmaWarp) tmem_alloc(&s_tmem, C::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    unsigned char *bstages = f16ssm;
+    unsigned char *staging = f16ssm + (size_t)NSTAGE * C::B_BYTES;
+
+    if (warp < CW) {
+        // ===== converters / drainers: target row r; halves [SEG h, SEG h + SEG) of each chunk;
+        // output columns [h NH, h NH + NH) =====
+        const int quad = warp & 3, h = warp >> 2;
+        const int r = 32 * quad + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        const int64_t g = target(r);
+        uint32_t ptr = 0, pend = 0;
+        if (g >= 0 && end[g] > begin[g]) {
+            ptr = m2l_offs[g];
+            pend = m2l_offs[g + 1];
+        }
+        int nxt_code = 0xffff, nxt_id = 0;
+        if (ptr < pend) {
+            nxt_code = m2l_code[ptr];
+            nxt_id = m2l_ids[ptr];
+        }
+        float acc[NH];
+#pragma unroll
+        for (int n = 0; n < NH; ++n) acc[n] = 0.f;
+        auto drain = [&](int oc, float factor) -> bool {
+            const int b = oc & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_bounded(&drain_full[b], (oc >> 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) return false;
+            tc_fence_after();
+            constexpr int LD = NH % 8 == 0 ? 8 : 4;
+#pragma unroll
+            for (int c0 = 0; c0 < NH; c0 += LD) {
+                uint32_t v[LD];
+                tmem_ld_cols<LD>(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
+#pragma unroll
+                for (int j = 0; j < LD; ++j) acc[c0 + j] = fmaf(__uint_as_float(v[j]), factor, acc[c0 + j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drain_empty[b]);
+            return true;
+        };
+        // copies of step s2 into slot s2 & 1: this warp's 32 rows, UPR lanes per row (16 bytes
+        // each: unit u = 2 i + {hi, lo} of coefficient piece SEG h / 8 + i); the offset's source
+        // and unscaling factor are taken from the list at its first chunk
+        const __half *mysrc = ps;
+        int myok = 0;
+        float fac[2] = {0.f, 0.f};
+        auto issue = [&](int s2) {
+            const int oc2 = s2 / NCH, c2 = s2 % NCH;
+            if (c2 == 0) {
+                const int code = c_f16_codes[tau][oc2];
+                myok = 0;
+                float f = 0.f;
+                if (nxt_code == code) {
+                    mysrc = ps + (size_t)nxt_id * (2 * KP);
+                    myok = 1;
+                    f = pow2f(-((int)cscale[nxt_id] + gexp[code]));
+                    ++ptr;
+                    nxt_code = 0xffff;
+                    if (ptr < pend) {
+                        nxt_code = m2l_code[ptr];
+                        nxt_id = m2l_ids[ptr];
+                    }
+                }
+                if (oc2 & 1)
+                    fac[1] = f;
+                else
+                    fac[0] = f;
+            }
+            int k0, kw;
+            chunk16(c2, C::KS, NCH, k0, kw);
+            unsigned char *slot = staging + (size_t)(warp * 2 + (s2 & 1)) * C::SLOT_BYTES;
+            const int u = lane % UPR;
+            const bool uok = SEG * h + 8 * (u >> 1) < kw;
+#pragma unroll
+            for (int it = 0; it < UPR; ++it) {
+                const int rl = (32 / UPR) * it + lane / UPR;
+                const __half *sp = reinterpret_cast<const __half *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(mysrc), rl));
+                const int ok = __shfl_sync(0xffffffffu, myok, rl);
+                cp_async16(slot + (size_t)rl * C::RSW + 16 * u, sp + 2 * k0 + 2 * SEG * h + 8 * u,
+                           (ok && uok) ? 16u : 0u);
+            }
+            cp_async_commit();
+        };
+        bool alive = true;
+        float pend_factor = 0.f;
+        issue(0);
+        for (int s = 0; s < S && alive; ++s) {
+            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH;
+            const float cur_factor = (oc & 1) ? fac[1] : fac[0];
+            if (s + 1 < S) {
+                issue(s + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            uint32_t hi[SEG / 2], lo[SEG / 2];
+            const uint4 *rp = reinterpret_cast<const uint4 *>(staging + (size_t)(warp * 2 + (s & 1)) * C::SLOT_BYTES +
+                                                              (size_t)lane * C::RSW);
+#pragma unroll
+            for (int i = 0; i < SEG / 8; ++i) {
+                const uint4 a = rp[2 * i], b = rp[2 * i + 1];
+                hi[4 * i] = a.x;
+                hi[4 * i + 1] = a.y;
+                hi[4 * i + 2] = a.z;
+                hi[4 * i + 3] = a.w;
+                lo[4 * i] = b.x;
+                lo[4 * i + 1] = b.y;
+                lo[4 * i + 2] = b.z;
+                lo[4 * i + 3] = b.w;
+            }
+            __syncwarp();  // the slot is refilled by the next step's copies
+            if (s >= NSTAGE) {
+                int ok = 1;
+                if (lane == 0)
+                    ok = mbar_wait_bounded(&empty_bar[st], ((s / NSTAGE) - 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    alive = false;
+                    break;
+                }
+            }
+            int k0, kw;
+            chunk16(c, C::KS, NCH, k0, kw);
+            if (tid == 0) {
+                const uint32_t half = (uint32_t)NP * kw * 2u;
+                const int code = c_f16_codes[tau][oc];
+                const __half *tb = tab + (size_t)code * T::CODE_HALVES + (size_t)k0 * NP;
+                __half *B = reinterpret_cast<__half *>(bstages + (size_t)st * C::B_BYTES);
+                mbar_expect_tx(&full_bar[st], 2u * half);
+                tma_bulk_g2s(B, tb, half, &full_bar[st]);
+                tma_bulk_g2s(B + NP * kw, tb + T::HALF, half, &full_bar[st]);
+                s_issued[st] += 1;
+            }
+            const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + (SEG / 2) * h);
+            tmem_st_cols<SEG / 2>(tmem + lane_base + acol, hi);
+            tmem_st_cols<SEG / 2>(tmem + lane_base + acol + 32, lo);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[st]);
+            // the previous offset's partial is complete once this one is queued
+            if (c == NCH - 1 && oc >= 1 && !drain(oc - 1, pend_factor)) alive = false;
+            if (c == NCH - 1) pend_factor = cur_factor;
+        }
+        cp_async_wait<0>();
+        if (alive && !drain(188, pend_factor)) alive = false;
+        if (!alive && lane == 0) s_abort = 1;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&done_bar, 0u, kWaitLimitNs, nullptr) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok && lane == 0) s_abort = 1;
+        __syncwarp();
+        if (ok && alive && !s_abort && g >= 0 && end[g] > begin[g]) {
+#pragma unroll
+            for (int n = 0; n < NH; n += 4)
+                if (h * NH + n < PP)
+                    *reinterpret_cast<float4 *>(Lc + g * PP + h * NH + n) =
+                        make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
+        }
+    } else if (lane == 0) {
+        // ================= MMA issuer: offset oc accumulates in TMEM buffer oc & 1 =================
+        for (int s = 0; s < S; ++s) {
+            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH, b = oc & 1;
+            if (c == 0 && oc >= 2 &&
+                !mbar_wait_bounded(&drain_empty[b], ((oc - 2) >> 1) & 1, kWaitLimitNs, &s_abort)) {
+                s_abort = 1;
+                break;
+            }
+            if (!mbar_wait_bounded(&full_bar[st], (s / NSTAGE) & 1, kWaitLimitNs, &s_abort)) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            int k0, kw;
+            chunk16(c, C::KS, NCH, k0, kw);
+            const __half *Bhi = reinterpret_cast<const __half *>(bstages + (size_t)st * C::B_BYTES), *Blo = Bhi + NP * kw;
+            const uint32_t d = tmem + (uint32_t)(b * NP);
+            const uint32_t ahi = tmem + (uint32_t)(C::A_COL0 + 64 * st), alo = ahi + 32;
+            for (int j = 0; j < kw / 16; ++j) {
+                const uint64_t bh = smem_desc(Bhi + j * 2 * NP * 8, NP * 16, 128);
+                const uint64_t bl = smem_desc(Blo + j * 2 * NP * 8, NP * 16, 128);
+                tc_mma_f16_ta(d, alo + 8 * j, bh, kIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                tc_mma_f16_ta(d, ahi + 8 * j, bl, kIdesc, 1u);
+                tc_mma_f16_ta(d, ahi + 8 * j, bh, kIdesc, 1u);
+            }
+            tc_commit(&empty_bar[st]);
+            if (c == NCH - 1) tc_commit(&drain_full[b]);
+        }
+        tc_commit(&done_bar);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            atomicOr(status, kStatusTimeout);
+            for (int st = 0; st < NSTAGE; ++st)
+                if (s_issued[st] > 0) mbar_wait_bounded(&full_bar[st], (s_issued[st] - 1) & 1, kWaitLimitNs, nullptr);
+        }
+        __syncthreads();
+    }
+    if (warp == kMmaWarp) {
+        __syncwarp();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
 template <int P>
 static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist, const int32_t *begin,
                          const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
                          const void *table, const float *M, const int8_t *cscale, const void *ps, float *Lc,
                          int *status, cudaStream_t s)
 {
-    using C = F16Cfg<P>;
     using T = F16Table<P>;
     const __half *tab = static_cast<const __half *>(table);
     const int *gexp = reinterpret_cast<const int *>(tab + (size_t)kM2LCodes * T::CODE_HALVES);
-    const __half *h = static_cast<const __half *>(ps);
     if (ps) {
-        cudaFuncSetAttribute(k_m2l_f16<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-        k_m2l_f16<P, true><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
-                                                                    m2l_ids, m2l_code, tab, gexp, M, h, cscale, Lc,
+        using CS = F16SCfg<P, 8>;
+        cudaFuncSetAttribute(k_m2l_f16s<P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS::kSmemBytes);
+        k_m2l_f16s<P, 8><<<grid, CS::NTHREADS, CS::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
+                                                                    m2l_code, tab, gexp,
+                                                                    static_cast<const __half *>(ps), cscale, Lc,
                                                                     status);
     } else {
-        cudaFuncSetAttribute(k_m2l_f16<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-        k_m2l_f16<P, false><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs,
-                                                                     m2l_ids, m2l_code, tab, gexp, M, h, cscale, Lc,
-                                                                     status);
+        using C = F16Cfg<P>;
+        cudaFuncSetAttribute(k_m2l_f16<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+        k_m2l_f16<P><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
+                                                              m2l_code, tab, gexp, M, cscale, Lc, status);
     }
     note_launches(1);
 }
@@ -592,8 +866,8 @@ void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, cons
         total += tiles.ntiles_level[l];
     }
     if (total == 0) return;
-    dispatch_f16(P, tiles, total, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps,
-                 Lc, status, s);
+    dispatch_f16(P, tiles, total, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc,
+                 status, s);
 }
 
 void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,

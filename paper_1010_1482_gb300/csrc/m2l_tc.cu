@@ -500,7 +500,7 @@ int m2l_tc_mode()
     static const int mode = [] {
         const char *e = getenv("GBFMM_M2L_TC");
         const int v = e ? atoi(e) : 2;
-        return (v >= 0 && v <= 4) ? v : 2;
+        return (v == 0 || v == 1 || v == 2 || v == 4) ? v : 2;
     }();
     return mode;
 }
