@@ -458,12 +458,16 @@ def run_next_rows(args, G, dev, local) -> dict:
     e = G.gbfmm_engine_create(local, args.workers, 40 << 30)
     G.gbfmm_engine_prepare(e, [4, 6, 8, 10])
     out = torch.empty_like(x)
-    G.gbfmm_engine_run_batch(e, offsets, params, x, out)  # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = G.gbfmm_engine_run_batch(e, offsets, params, x, out)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+
+    def batched(prms):
+        G.gbfmm_engine_run_batch(e, offsets, prms, x, out)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = G.gbfmm_engine_run_batch(e, offsets, prms, x, out)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st
+
+    t_batch, st = batched(params)
     total = int(offsets[-1])
     res["batched"] = {
         "instances": len(inst), "particles": total, "workers": args.workers,
@@ -473,7 +477,36 @@ def run_next_rows(args, G, dev, local) -> dict:
         "note": "plain = gbfmm_evaluate one instance at a time on one stream; batched = "
                 "gbfmm_engine_run_batch over the workers (their own streams and contexts), wall clock",
     }
-    del x, out, out_plain
+    # the same batch with leaf sizes from the autotuner (gbfmm_tune_leaf per (distribution, p,
+    # log2 N) bucket, candidates 32 / 64 / 128 / 256), plain and batched
+    ctx = G.gbfmm_create(local)
+    leaves = serving.tune_leaves(ctx, x, offsets, inst)
+    tparams = serving.tuned_params(inst, leaves)
+    serving.run_plain(ctx, x, offsets, tparams)
+    t_plain_t, out_plain_t = serving.run_plain(ctx, x, offsets, tparams)
+    G.gbfmm_destroy(ctx)
+    t_batch_t, st_t = batched(tparams)
+    # accuracy of both leaf choices on 8 instances, 256 seeded targets each, vs FP64 direct
+    import oracle
+
+    errs = {"leaf_64": [], "tuned": []}
+    for i in range(0, len(inst), len(inst) // 8)[:8]:
+        a, b = int(offsets[i]), int(offsets[i + 1])
+        xs = x[a:b].cpu().numpy()
+        tg = inputs.sample_indices(b - a, min(256, b - a), inputs.SEED_BASE + 9)
+        ref = oracle.direct(xs, targets=tg)
+        for name, o in (("leaf_64", out_plain), ("tuned", out_plain_t)):
+            got = o[a:b].cpu().numpy().astype(np.float64)[tg]
+            errs[name].append(oracle.rel_l2(got[:, 1:], ref[:, 1:]))
+    res["batched_tuned"] = {
+        "leaf_sizes": {f"{d}/p{p}/2^{k}": v for (d, p, k), v in sorted(leaves.items())},
+        "plain_particles_per_s": total / t_plain_t, "batched_particles_per_s": total / t_batch_t,
+        "speedup_vs_leaf64_batched": t_batch / t_batch_t, "failed": int(sum(1 for v in st_t if v != 0)),
+        "identical_to_plain": bool(torch.equal(out, out_plain_t)),
+        "grad_err_max": {k: float(max(v)) for k, v in errs.items()},
+    }
+    del x, out, out_plain, out_plain_t
+    res["graph"] = run_graph(G, dev, local)
     reqs = inputs.served_requests(duration=args.serve_seconds)
     pools = {d: inputs.request_pool(d, 1 << 21) for d in ("uniform", "plummer")}
     warm = inputs.served_requests(duration=0.5, seed=inputs.SEED_BASE + 6)
@@ -487,6 +520,45 @@ def run_next_rows(args, G, dev, local) -> dict:
     res["served"] = stats
     res["crossover"] = run_crossover(G, dev, local)
     return res
+
+
+def run_graph(G, dev, local) -> dict:
+    """The bench workload evaluated repeatedly in the same buffers: eager gbfmm_evaluate calls
+    against replays of one captured CUDA graph (device time per evaluation, L2 not flushed)."""
+    import torch
+
+    w = inputs.workload("uniform_1m_p10")
+    x = inputs.make_particles(w["n"], w["dist"], w["seed"])
+    prm = G.gbfmm_default_params(p=w["p"], leaf_size=w["leaf_size"])
+    _, wsb = G.gbfmm_plan(prm, w["n"])
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    xd = torch.from_numpy(x).to(dev)
+    out = torch.empty_like(xd)
+    ctx = G.gbfmm_create(local)
+    g = G.gbfmm_graph_create(ctx, prm, xd, out, ws)
+    reps = 20
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    eager = timed(lambda: G.gbfmm_evaluate(ctx, prm, xd, out, ws))
+    ref = out.clone()
+    graph = timed(lambda: G.gbfmm_graph_launch(g))
+    G.gbfmm_sync_status(ctx)
+    same = bool(torch.equal(out, ref))
+    G.gbfmm_graph_destroy(g)
+    G.gbfmm_destroy(ctx)
+    return {"workload": w["name"], "eager_ms": eager, "graph_ms": graph, "identical": same,
+            "note": "back-to-back evaluations of the same buffers on one stream (inputs resident)"}
 
 
 def run_crossover(G, dev, local) -> dict:

@@ -317,6 +317,33 @@ int gbfmm_engine_wait(gbfmm_engine *e, int64_t ticket, double timeout_ms, int32_
 int gbfmm_engine_run_batch(gbfmm_engine *e, int32_t nb, const int64_t *offsets, const gbfmm_params *prm,
                            const float *d_xyzq, float *d_out, int32_t *status);
 
+/*
+ * Repeated evaluations and tuning (no counterpart in the paper; for time-stepping codes and
+ * for the batched and served forms).
+ *
+ * gbfmm_graph_create: captures one uniform-tree gbfmm_evaluate (same arguments) into a CUDA
+ *   graph and instantiates it; an eager evaluation runs first (it builds the order's operator
+ *   tables and checks the arguments) and must succeed.  The graph replays the evaluation of the
+ *   same buffers: the caller may change the contents of d_xyzq (n, the pointers and prm stay)
+ *   between launches.  It uses the context's operator tables, status word and scratch: destroy
+ *   it before the context, and read errors with gbfmm_sync_status as after gbfmm_evaluate.
+ *   EUNSUPPORTED for the adaptive tree (its evaluation reads counts back from the device).
+ * gbfmm_graph_launch: one replay, asynchronous on `stream`.
+ * gbfmm_graph_destroy: NULL-safe.
+ * gbfmm_tune_leaf: leaf-size autotuner.  For each of the ncand leaf sizes in candidates (host
+ *   array) it times one evaluation of the caller's particles d_xyzq (device, 4n floats; read
+ *   only) after one warm-up, with prm's other fields, into the context's own device buffers;
+ *   *best_leaf receives the fastest candidate and *best_ms (may be NULL) its time.
+ *   Synchronous.  Candidates that gbfmm_plan rejects are skipped; EINVAL if none is valid.
+ */
+typedef struct gbfmm_graph gbfmm_graph;
+int gbfmm_graph_create(gbfmm_graph **out, gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq,
+                       float *d_out, void *d_workspace, size_t workspace_bytes);
+int gbfmm_graph_launch(gbfmm_graph *g, void *stream);
+int gbfmm_graph_destroy(gbfmm_graph *g);
+int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
+                    int32_t ncand, int32_t *best_leaf, float *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,12 @@ def lib():
         "gbfmm_engine_wait": (i, [P, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "gbfmm_engine_run_batch": (i, [P, ctypes.c_int32, P, P, P, P, P]),
+        "gbfmm_graph_create": (i, [ctypes.POINTER(P), P, ctypes.POINTER(gbfmm_params), i64, P, P, P,
+                                   ctypes.c_size_t]),
+        "gbfmm_graph_launch": (i, [P, P]),
+        "gbfmm_graph_destroy": (i, [P]),
+        "gbfmm_tune_leaf": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -326,6 +332,38 @@ def gbfmm_engine_run_batch(e, offsets, params, xyzq: torch.Tensor, out: torch.Te
     if rc != GBFMM_OK:
         raise GbfmmError(rc, "batch")
     return st[:nb].tolist()
+
+
+def gbfmm_graph_create(ctx, prm: gbfmm_params, xyzq: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor):
+    """Captures one uniform-tree evaluation of these buffers into a CUDA graph; returns its handle."""
+    assert xyzq.is_cuda and out.is_cuda and xyzq.shape == out.shape
+    g = ctypes.c_void_p()
+    _check(ctx, lib().gbfmm_graph_create(ctypes.byref(g), ctx, ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _ptr(out),
+                                         _ptr(workspace), workspace.numel() * workspace.element_size()))
+    return g
+
+
+def gbfmm_graph_launch(g, stream=None) -> None:
+    rc = lib().gbfmm_graph_launch(g, _stream(stream))
+    if rc != GBFMM_OK:
+        raise GbfmmError(rc, "graph launch")
+
+
+def gbfmm_graph_destroy(g) -> None:
+    lib().gbfmm_graph_destroy(g)
+
+
+def gbfmm_tune_leaf(ctx, prm: gbfmm_params, xyzq: torch.Tensor, candidates) -> tuple:
+    """Leaf-size autotuner: (fastest candidate, its evaluation time in ms)."""
+    import numpy as np
+
+    assert xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous()
+    c = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = ctypes.c_int32()
+    ms = ctypes.c_float()
+    _check(ctx, lib().gbfmm_tune_leaf(ctx, ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _np_ptr(c), len(c),
+                                      ctypes.byref(best), ctypes.byref(ms)))
+    return int(best.value), float(ms.value)
 
 
 # ---- convenience wrapper (torch-allocated workspace) -----------------------------------------

@@ -69,6 +69,28 @@ def run_stream(engine, requests: list[dict], pools: dict, timeout_s: float = 120
     }
 
 
+def tune_leaves(ctx, x, offsets, instances: list[dict], candidates=(32, 64, 128, 256)) -> dict:
+    """Leaf size per (distribution, p, floor(log2 N)) bucket, chosen by gbfmm_tune_leaf on the
+    bucket's first instance."""
+    import math
+
+    chosen = {}
+    for i, r in enumerate(instances):
+        key = (r["dist"], r["p"], int(math.log2(max(r["n"], 1))))
+        if key in chosen:
+            continue
+        a, b = int(offsets[i]), int(offsets[i + 1])
+        chosen[key], _ = G.gbfmm_tune_leaf(ctx, params_for(r["dist"], r["p"]), x[a:b], list(candidates))
+    return chosen
+
+
+def tuned_params(instances: list[dict], leaves: dict) -> list:
+    import math
+
+    return [params_for(r["dist"], r["p"], leaves[(r["dist"], r["p"], int(math.log2(max(r["n"], 1))))])
+            for r in instances]
+
+
 def make_batch(instances: list[dict], device) -> tuple:
     """Concatenated device particles of the instances, their offsets and parameters."""
     xs = [inputs.make_particles(r["n"], r["dist"], r["seed"]) for r in instances]
