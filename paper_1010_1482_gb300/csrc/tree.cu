@@ -352,8 +352,9 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 // Scratch: per-pass tile counters, the digit histograms, and one 64-bit status word per
 // (pass, tile, digit): flag (bits 62-63: 1 = count, 2 = inclusive prefix) | value.
 // ------------------------------------------------------------------------------------------
-constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;
+constexpr int kRsThreads = 512, kRsItems = 8, kRsTile = kRsThreads * kRsItems;  // tile of 4096 keys
 constexpr int kRsWarps = kRsThreads / 32, kRsWarpKeys = kRsTile / kRsWarps;
+constexpr int kRsHistThreads = 256;  // one per digit
 constexpr uint64_t kRsAgg = 1ull << 62, kRsInc = 2ull << 62, kRsFlags = 3ull << 62;
 
 static_assert(kRsWarpKeys == 32 * kRsItems, "blocked layout: a warp owns kRsItems rounds of 32 keys");
@@ -377,8 +378,8 @@ GB_DEV uint64_t timer_ns()
     return t;
 }
 
-// exclusive scan of one value per thread over a 256-thread block
-GB_DEV uint32_t block_excl_scan256(uint32_t v, uint32_t *wsum)
+// exclusive scan of one value per thread over the block (wsum: one word per warp)
+GB_DEV uint32_t block_excl_scan(uint32_t v, uint32_t *wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -396,13 +397,14 @@ GB_DEV uint32_t block_excl_scan256(uint32_t v, uint32_t *wsum)
 }
 
 template <class KeyT>
-__global__ void __launch_bounds__(kRsThreads) k_rs_ghist(const KeyT *__restrict__ keys, int64_t n, int passes,
-                                                         uint32_t *__restrict__ ghist)
+__global__ void __launch_bounds__(kRsHistThreads) k_rs_ghist(const KeyT *__restrict__ keys, int64_t n, int passes,
+                                                             uint32_t *__restrict__ ghist)
 {
     __shared__ uint32_t h[sizeof(KeyT)][256];
     for (int d = 0; d < passes; ++d) h[d][threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)kRsThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRsThreads) {
+    for (int64_t i = blockIdx.x * (int64_t)kRsHistThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kRsHistThreads) {
         const KeyT k = keys[i];
         for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(uint32_t)(k >> (8 * d)) & 0xffu], 1u);
     }
@@ -428,9 +430,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int shift = 8 * pass;
+    const bool dig = tid < 256;  // the per-digit work: thread tid, digit tid
     if (tid == 0) tile_sh = atomicAdd(&counter[pass], 1u);
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) wcnt[w][tid] = 0;
+    for (int e = tid; e < kRsWarps * 256; e += kRsThreads) (&wcnt[0][0])[e] = 0;
     __syncthreads();
     const int64_t tile = tile_sh;
     const int64_t base = tile * kRsTile + (int64_t)warp * kRsWarpKeys;
@@ -453,17 +455,21 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
     __syncthreads();
     // digit tid: offsets of the warps' runs inside the tile's run, and the tile's count
     uint32_t cnt = 0;
+    if (dig) {
 #pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) {
-        const uint32_t t = wcnt[w][tid];
-        wcnt[w][tid] = cnt;
-        cnt += t;
+        for (int w = 0; w < kRsWarps; ++w) {
+            const uint32_t t = wcnt[w][tid];
+            wcnt[w][tid] = cnt;
+            cnt += t;
+        }
     }
-    dstart[tid] = block_excl_scan256(cnt, wsum);
+    const uint32_t ds = block_excl_scan(cnt, wsum);  // threads >= 256 add zeros after the digits
+    if (dig) dstart[tid] = ds;
     // look back over the earlier tiles' counts of digit tid
     uint64_t *st = status + (size_t)pass * nblk * 256;
     uint32_t excl = 0;
-    if (tile == 0) {
+    if (!dig) {
+    } else if (tile == 0) {
         st_release_u64(&st[tid], kRsInc | cnt);
     } else {
         st_release_u64(&st[tile * 256 + tid], kRsAgg | cnt);
@@ -484,7 +490,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
         }
         st_release_u64(&st[tile * 256 + tid], kRsInc | (excl + cnt));
     }
-    gbase[tid] = block_excl_scan256(ghist[pass * 256 + tid], wsum) + excl;
+    const uint32_t gb = block_excl_scan(dig ? ghist[pass * 256 + tid] : 0u, wsum);
+    if (dig) gbase[tid] = gb + excl;
     __syncthreads();
     // stage in tile-sorted order, then write the runs of each digit
 #pragma unroll
@@ -540,8 +547,8 @@ static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_
     uint32_t *ghist = reinterpret_cast<uint32_t *>(sc + kRsCounterBytes);
     uint64_t *status = reinterpret_cast<uint64_t *>(sc + kRsCounterBytes + kRsHistBytes);
     cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s);
-    const unsigned hgrid = (unsigned)std::min<int64_t>(nblk * (kRsTile / kRsThreads) / 4 + 1, 1216);
-    k_rs_ghist<KeyT><<<hgrid, kRsThreads, 0, s>>>(kin, n, passes, ghist);
+    const unsigned hgrid = (unsigned)std::min<int64_t>(nblk * (kRsTile / kRsHistThreads) / 4 + 1, 1216);
+    k_rs_ghist<KeyT><<<hgrid, kRsHistThreads, 0, s>>>(kin, n, passes, ghist);
     const int smem = kRsTile * (int)(sizeof(KeyT) + sizeof(uint32_t));
     cudaFuncSetAttribute(k_rs_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     for (int pass = 0; pass < passes; ++pass) {
