@@ -939,7 +939,10 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
     }
 }
 
-// M2M (up) / L2L (down) over cells given by their parents' index range; children by position
+// M2M (up) / L2L (down) over cells given by their parents' index range; children by position.
+// As k_translate: the operator of each child position and the TN source columns are copied into
+// shared memory with cp.async (zero-filled for missing children), the next child position's
+// copies in flight while the current one is applied.
 template <int P, bool UP, int TN, int CN>
 __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells(int64_t lo, int64_t np,
                                                                          const int32_t *__restrict__ child_of,
@@ -950,8 +953,6 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
     using Cfg = TransCfg<P, UP, TN, CN>;
     constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
     extern __shared__ __align__(16) float tsm[];
-    float *A = tsm;
-    float *B = tsm + PP * PR;
     const int64_t q0 = blockIdx.x * (int64_t)TN;
     const int tid = threadIdx.x;
     const bool work = tid < NRG * NCG;
@@ -967,31 +968,47 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
             kbeg = (d * d) / 4 * 4;
         }
     }
+    auto stage = [&](int c, int buf) {
+        float *A = tsm + buf * (Cfg::AF + Cfg::BF);
+        float *B = A + Cfg::AF;
+        const float *src = ops + (size_t)c * PP * PR;
+        for (int e = tid; e < PP * PR / 4; e += blockDim.x) cp_async16_t(A + 4 * e, src + 4 * e, 16u);
+        for (int e = tid; e < TN * (PP / 4); e += blockDim.x) {
+            const int i = e / (PP / 4), k4 = e % (PP / 4);
+            const int64_t q = q0 + i;
+            const float *gsrc = X;
+            uint32_t bytes = 0;
+            if (q < np) {
+                const int64_t pcell = lo + q;
+                const int64_t g = UP ? child_of[pcell * 8 + c] : (child_of[pcell * 8 + c] >= 0 ? pcell : -1);
+                if (g >= 0) {
+                    gsrc = X + g * PP + 4 * k4;
+                    bytes = 16u;
+                }
+            }
+            cp_async16_t(B + i * SB + 4 * k4, gsrc, bytes);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     float acc[4][CN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < CN; ++j) acc[i][j] = 0.f;
     const int c_first = UP ? 0 : blockIdx.y, c_last = UP ? 7 : blockIdx.y;
+    stage(c_first, 0);
     for (int c = c_first; c <= c_last; ++c) {
-        if (c != c_first) __syncthreads();
-        const float4 *src = reinterpret_cast<const float4 *>(ops + (size_t)c * PP * PR);
-        for (int e = tid; e < PP * PR / 4; e += blockDim.x) reinterpret_cast<float4 *>(A)[e] = __ldg(&src[e]);
-        for (int e = tid; e < TN * (PP / 4); e += blockDim.x) {
-            const int i = e / (PP / 4), k4 = e % (PP / 4);
-            const int64_t q = q0 + i;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < np) {
-                const int64_t pcell = lo + q;
-                const int64_t g = UP ? child_of[pcell * 8 + c] : (child_of[pcell * 8 + c] >= 0 ? pcell : -1);
-                if (g >= 0) v = reinterpret_cast<const float4 *>(X + g * PP)[k4];
-            }
-            *reinterpret_cast<float4 *>(B + i * SB + 4 * k4) = v;
+        const int buf = UP ? (c - c_first) & 1 : 0;
+        if (c < c_last) {
+            stage(c + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
         if (work) {
-            const float *Ar = A + rg * 4;
-            const float *Bc = B + cg * SB;
+            const float *Ar = tsm + buf * (Cfg::AF + Cfg::BF) + rg * 4;
+            const float *Bc = tsm + buf * (Cfg::AF + Cfg::BF) + Cfg::AF + cg * SB;
 #pragma unroll 2
             for (int k = kbeg; k < kend; k += 4) {
                 Frag<CN, 4> f;
@@ -999,6 +1016,7 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
                 f.fma(acc);
             }
         }
+        __syncthreads();  // the buffer is refilled two positions later
     }
     if (!work) return;
 #pragma unroll
@@ -1082,7 +1100,7 @@ static void translate_cells_tn(int64_t lo, int64_t np, const int32_t *child_of, 
                                const float *ops, float *X, cudaStream_t s)
 {
     using Cfg = TransCfg<P, UP, TN, CN>;
-    const int smem = (int)((Cfg::AF + Cfg::BF) * sizeof(float));  // one operator + one column block
+    const int smem = (int)Cfg::kSmem;  // operator + column block, double-buffered for M2M
     cudaFuncSetAttribute(k_translate_cells<P, UP, TN, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     dim3 grid((unsigned)((np + TN - 1) / TN), UP ? 1 : 8);
     k_translate_cells<P, UP, TN, CN><<<grid, Cfg::NT, smem, s>>>(lo, np, child_of, nchild, ops, X);
