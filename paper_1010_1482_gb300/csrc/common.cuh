@@ -138,6 +138,16 @@ struct Frag {
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 
+// The hardware reciprocal square root (rsqrt.approx.ftz: relative error about 2^-23, subnormal
+// inputs flushed).  The pair rules and the far-field series take it on squared distances that
+// are either zero (masked by the caller) or far above the subnormal range.
+GB_DEV float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Root box as computed on the device: origin xyz and side, FP64.
 struct Box {
     double origin[3];

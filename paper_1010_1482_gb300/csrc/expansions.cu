@@ -305,8 +305,9 @@ GB_DEV void p2x_particles(float (&acc)[P * P], const float4 *__restrict__ sx, in
         float4 p = __ldg(&sx[j]);
         const float x = (p.x - cg.cx) * cg.inv_h, y = (p.y - cg.cy) * cg.inv_h, z = (p.z - cg.cz) * cg.inv_h;
         const float q = p.w, r2 = x * x + y * y + z * z;
-        const float ir2 = IRREG ? 1.f / r2 : 1.f;
-        float mre = IRREG ? rsqrtf(r2) : 1.f, mim = 0.f;  // H_m^m
+        const float ir = IRREG ? rsqrt_ftz(r2) : 1.f;
+        const float ir2 = ir * ir;
+        float mre = ir, mim = 0.f;  // H_m^m
 #pragma unroll
         for (int m = 0; m < P; ++m) {
             if (m > 0) {
@@ -698,9 +699,10 @@ template <int P>
 GB_DEV void m2p_accumulate(const float *__restrict__ Ms, float x, float y, float z, float ih, float *o)
 {
     const float r2 = x * x + y * y + z * z;
-    const float ir2 = 1.f / r2;
+    const float ir = rsqrt_ftz(r2);
+    const float ir2 = ir * ir;
     float phi = 0.f, gz = 0.f, gpr = 0.f, gpi = 0.f;
-    float mre = rsqrtf(r2), mim = 0.f;  // I_0^0 = 1/r
+    float mre = ir, mim = 0.f;  // I_0^0 = 1/r
 #pragma unroll
     for (int m = 0; m <= P; ++m) {
         if (m > 0) {

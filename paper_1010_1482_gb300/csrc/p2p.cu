@@ -44,7 +44,7 @@ GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi,
 {
     const float dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float inv = rsqrtf(SOFT ? d2 + eps2 : d2);
+    float inv = rsqrt_ftz(SOFT ? d2 + eps2 : d2);
     inv = d2 > 0.f ? inv : 0.f;
     const float qi = s.w * inv;
     phi += qi;
@@ -224,7 +224,7 @@ GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, ulonglong2 xy, ulonglong2 
     d2 = f2_fma(dx, dx, d2);
     float r0, r1;
     f2_unpack(SOFT ? f2_add(d2, E2) : d2, r0, r1);
-    float i0 = rsqrtf(r0), i1 = rsqrtf(r1);
+    float i0 = rsqrt_ftz(r0), i1 = rsqrt_ftz(r1);
     if (MASK) {
         float a0, a1;
         f2_unpack(d2, a0, a1);
