@@ -630,14 +630,14 @@ __global__ void __launch_bounds__(F16SCfg<P, CW_>::NTHREADS, 1)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) return false;
             tc_fence_after();
-            constexpr int LD = NH % 8 == 0 ? 8 : 4;
+            // all the row's columns in flight at once, one wait
+            static_assert(NH % 8 == 0, "drain in 8-column loads");
+            uint32_t v[NH];
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += LD) {
-                uint32_t v[LD];
-                tmem_ld_cols<LD>(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
+            for (int c0 = 0; c0 < NH; c0 += 8) tmem_ld8_nowait(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v + c0);
+            tmem_wait_ld_regs(v);
 #pragma unroll
-                for (int j = 0; j < LD; ++j) acc[c0 + j] = fmaf(__uint_as_float(v[j]), factor, acc[c0 + j]);
-            }
+            for (int n = 0; n < NH; ++n) acc[n] = fmaf(__uint_as_float(v[n]), factor, acc[n]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&drain_empty[b]);

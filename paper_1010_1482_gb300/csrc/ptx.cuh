@@ -207,6 +207,25 @@ GB_DEV void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// whole warp: 8 consecutive 32-bit columns of TMEM lane (lane base + lane id) into v[0..7]
+// without waiting: the values are valid after tmem_wait_ld_regs (which also keeps the compiler
+// from reading them earlier)
+GB_DEV void tmem_ld8_nowait(uint32_t taddr, uint32_t *v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+// wait for this thread's outstanding tcgen05.ld and make v[0..N) depend on the wait
+template <int N>
+GB_DEV void tmem_wait_ld_regs(uint32_t (&v)[N])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
+}
+
 // whole warp: store 16 consecutive 32-bit columns of TMEM lane (lane base + lane id); the
 // stores are complete for this thread after tmem_wait_st()
 GB_DEV void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
