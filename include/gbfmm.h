@@ -71,6 +71,12 @@ enum {
  * staged through shared memory (default), 4 = FP16 with the sources converted in the kernel,
  * 1 = TF32, 0 = none (CUDA cores). */
 #define GBFMM_FLAG_M2L_CUDA_CORES 2
+/* run every stage on the caller's stream, one after another.  By default an FMM evaluation
+ * runs the near field (P2P, Listings 1-2) on a low-priority stream of the context while the
+ * expansions (P2M .. L2L) run on a high-priority one, both forked from and joined back into the
+ * caller's stream (event waits only, so stream capture sees one graph); the output is the same
+ * bit for bit. */
+#define GBFMM_FLAG_SERIAL 4
 
 /*
  * Parameters of one evaluation (Section "Fast N-body simulation").
@@ -224,8 +230,11 @@ int gbfmm_export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *nce
 /*
  * Per-stage device times (ms) of the last evaluate run with
  * GBFMM_FLAG_STAGE_TIMING, in this order: 0 box+keys, 1 sort, 2 cells+lists,
- * 3 P2M, 4 M2M, 5 M2L (or M2P), 6 L2L, 7 L2P, 8 P2P(+output), 9 operator build
- * (0 when cached).  Waits for the device.  *count = stages written (<= max).
+ * 3 P2M, 4 M2M, 5 M2L (or M2P), 6 L2L, 7 L2P(+output), 8 P2P, 9 operator build
+ * (0 when cached).  When P2P ran on the context's second stream (the default for the FMM),
+ * stage 8 is its own duration, overlapping stages 3-6, and the stages add up to more than the
+ * evaluation took; with GBFMM_FLAG_SERIAL they are consecutive.  Waits for the device.
+ * *count = stages written (<= max).
  */
 int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
 

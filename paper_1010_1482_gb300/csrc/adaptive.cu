@@ -659,7 +659,7 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit, &a.near};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -907,6 +907,31 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     }
     mark(3);
 
+    // near field beside the far field: P2P (U lists) writes its compensated sums on the
+    // context's low-priority stream while the expansions run on its high-priority one (unless
+    // the evaluation is timed or serial); L2P adds the far field to them and writes the output
+    const bool split = p2p_near_supported();
+    const bool fork = split && (prm->flags & GBFMM_FLAG_SERIAL) == 0;
+    ctx->stage_order_last = fork ? 2 : (split ? 1 : 0);
+    float4 *near = nullptr;
+    if (split) {
+        if (grow(A.near, 32 * (size_t)n, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive near field");
+        near = A.near.as<float4>();
+    }
+    const cudaStream_t s_main = s;
+    if (fork) {
+        cudaEventRecord(ctx->ev_fork, s_main);
+        cudaStreamWaitEvent(ctx->s_far, ctx->ev_fork, 0);
+        cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0);
+        s = ctx->s_far;
+        if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
+        launch_p2p_cells_near(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+                              A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
+                              (float)prm->eps2, near, ctx->s_near);
+        if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
+        cudaEventRecord(ctx->ev_near, ctx->s_near);
+    }
+
     // ---- expansions ----
     if (grow(A.M, 4 * (size_t)ncells * PP, false, 0, s) || grow(A.Lc, 4 * (size_t)ncells * PP, false, 0, s))
         return fail(ctx, GBFMM_ENOMEM, "adaptive expansions");
@@ -969,7 +994,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                  A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                                  A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc,
-                                 ctx->d_status, s);
+                                 ctx->d_status, s, fork ? sm_count() : 0);
         } else if (tc)
             launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                 A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
@@ -986,15 +1011,45 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         launch_translate_cells(P, false, ls[l - 1], ls[l] - ls[l - 1], A.child_of.as<int32_t>(),
                                A.nchild.as<int32_t>(), ops.l2l, Lc, s);
     mark(7);
-    launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s);
-    if (deep)
-        launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
-                         A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far, s);
-    mark(8);
-    launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
-                     A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(), far, perm,
-                     (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
-    mark(9);
+    if (split) {
+        // M2P into the zeroed far field, then L2P adds the local expansion's value and the
+        // near-field sums (the same rounding as L2P then M2P: one addition each)
+        if (!fork) {
+            launch_p2p_cells_near(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+                                  A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
+                                  (float)prm->eps2, near, s);
+            mark(8);
+        }
+        cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
+        if (deep)
+            launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                             A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far,
+                             s);
+        if (fork) {
+            mark(8);
+            cudaStreamWaitEvent(s, ctx->ev_near, 0);
+            if (timing) cudaEventRecord(ctx->ev_aux[2], s);
+        }
+        launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s,
+                         near, perm, reinterpret_cast<float4 *>(d_out));
+        mark(9);
+        if (fork) {
+            cudaEventRecord(ctx->ev_join, s);
+            cudaStreamWaitEvent(s_main, ctx->ev_join, 0);
+            s = s_main;
+        }
+    } else {
+        launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s);
+        if (deep)
+            launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                             A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far,
+                             s);
+        mark(8);
+        launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+                         A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(), far, perm,
+                         (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
+        mark(9);
+    }
     A.n = n;
     A.P = P;
     A.skeys = skeys;

@@ -26,6 +26,17 @@ namespace gbfmm {
 static thread_local int64_t tl_launches = 0;
 void note_launches(int k) { tl_launches += k; }
 int64_t launch_count() { return tl_launches; }
+
+int sm_count()
+{
+    static const int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 0;
+    }();
+    return n;
+}
 }  // namespace gbfmm
 
 #include "context.h"
@@ -143,7 +154,7 @@ Layout make_layout(int64_t n, int L, int P)
     lo.idx0 = take(4 * (size_t)n);
     lo.idx1 = take(4 * (size_t)n);
     lo.sx = take(16 * (size_t)n);
-    lo.far = take(16 * (size_t)n);
+    lo.far = take(32 * (size_t)n);  // far field (16 B), or the near-field sums (32 B)
     lo.rs_hist = take(sort_scratch_bytes(n, 3 * L));
     size_t tmpw = std::max({exclusive_scan_tmp_words(256 * lo.rs_blocks), exclusive_scan_tmp_words(C),
                             exclusive_scan_tmp_words(NL)});
@@ -242,6 +253,15 @@ int gbfmm_create(gbfmm_ctx **out, int device)
              cudaMemset(ctx->d_counter, 0, sizeof(unsigned)) == cudaSuccess &&
              cudaMemset(ctx->d_zero, 0, 128 * sizeof(float)) == cudaSuccess;
     for (int i = 0; ok && i <= kStages; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    for (int i = 0; ok && i < 3; ++i) ok = cudaEventCreate(&ctx->ev_aux[i]) == cudaSuccess;
+    if (ok) {
+        int least = 0, greatest = 0;
+        ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&ctx->s_far, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&ctx->s_near, cudaStreamNonBlocking, least) == cudaSuccess;
+        for (cudaEvent_t *e : {&ctx->ev_fork, &ctx->ev_near, &ctx->ev_join})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    }
     if (ok) {
         init_expansion_constants();
         init_m2l_constants();
@@ -279,6 +299,10 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
     free_adaptive(ctx->ad);
     for (int i = 0; i <= kStages; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_near, ctx->ev_join, ctx->ev_aux[0], ctx->ev_aux[1], ctx->ev_aux[2]})
+        if (e) cudaEventDestroy(e);
+    if (ctx->s_far) cudaStreamDestroy(ctx->s_far);
+    if (ctx->s_near) cudaStreamDestroy(ctx->s_near);
     delete ctx;
     return GBFMM_OK;
 }
@@ -387,6 +411,23 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, scan_tmp, s);
     launch_list_fill(L, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code, s);
     mark(3);
+    // near field beside the far field (FMM): P2P writes its compensated sums, L2P adds the far
+    // field to them and writes the output; concurrently on the context's two streams unless the
+    // evaluation is timed or serial
+    const bool split = L >= 2 && prm->method == GBFMM_METHOD_FMM && p2p_near_supported();
+    const bool fork = split && (prm->flags & GBFMM_FLAG_SERIAL) == 0;
+    float4 *near = split ? far : nullptr;
+    const cudaStream_t s_main = s;
+    if (fork) {
+        cudaEventRecord(ctx->ev_fork, s_main);
+        cudaStreamWaitEvent(ctx->s_far, ctx->ev_fork, 0);
+        cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0);
+        s = ctx->s_far;
+        if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
+        launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, ctx->s_near);
+        if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
+        cudaEventRecord(ctx->ev_near, ctx->s_near);
+    }
     if (L >= 2) launch_p2m(P, L, geo, sx, begin, end, M, s);
     mark(4);
     if (L >= 2)
@@ -404,7 +445,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
                 launch_cell_scale(M, lo.ncells, P, cscale, s);
             }
             launch_m2l_f16(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_f16, M, cscale, ps, Lc,
-                           ctx->d_status, s);
+                           ctx->d_status, s, fork ? sm_count() : 0);
         } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !cores)
             launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
         else if (prm->method == GBFMM_METHOD_FMM)
@@ -416,10 +457,28 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     if (L >= 2 && prm->method == GBFMM_METHOD_FMM)
         for (int l = 3; l <= L; ++l) launch_l2l(P, l, begin, end, ops.l2l, Lc, s);
     mark(7);
-    if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s);
-    mark(8);
-    launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out, s);
-    mark(9);
+    if (split) {
+        if (fork) {
+            mark(8);
+            cudaStreamWaitEvent(s, ctx->ev_near, 0);
+            if (timing) cudaEventRecord(ctx->ev_aux[2], s);
+        } else {
+            launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, s);
+            mark(8);
+        }
+        launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s, near, perm, out);
+        mark(9);
+        if (fork) {
+            cudaEventRecord(ctx->ev_join, s);
+            cudaStreamWaitEvent(s_main, ctx->ev_join, 0);
+            s = s_main;
+        }
+    } else {
+        if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s);
+        mark(8);
+        launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out, s);
+        mark(9);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
 
@@ -432,6 +491,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     ctx->last_idx = (size_t)(reinterpret_cast<unsigned char *>(perm) - ctx->last_ws);
     ctx->last_method = prm->method;
     ctx->timed_last = timing;
+    ctx->stage_order_last = fork ? 2 : (split ? 1 : 0);
     ctx->ops_built_last = built_now;
     return GBFMM_OK;
 }
@@ -650,12 +710,21 @@ int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count)
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaEventSynchronize(ctx->ev[9]);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event sync");
-    int k = 0;
-    for (; k < 9 && k < max; ++k) {
-        float t = 0.f;
-        cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]);
-        ms[k] = t;
+    float t9[9];
+    for (int k = 0; k < 9; ++k) {
+        t9[k] = 0.f;
+        cudaEventElapsedTime(&t9[k], ctx->ev[k], ctx->ev[k + 1]);
     }
+    if (ctx->stage_order_last == 1) std::swap(t9[7], t9[8]);  // reported as 7 L2P, 8 P2P
+    if (ctx->stage_order_last == 2) {
+        float l2p = 0.f, p2p = 0.f;
+        cudaEventElapsedTime(&l2p, ctx->ev_aux[2], ctx->ev[9]);
+        cudaEventElapsedTime(&p2p, ctx->ev_aux[0], ctx->ev_aux[1]);
+        t9[7] += l2p;  // ev 7 -> 8: what ran on the far stream before the join (adaptive: M2P)
+        t9[8] = p2p;
+    }
+    int k = 0;
+    for (; k < 9 && k < max; ++k) ms[k] = t9[k];
     if (k < max) {
         float t = 0.f;
         if (ctx->ops_built_last) cudaEventElapsedTime(&t, ctx->ev[kStages], ctx->ev[0]);

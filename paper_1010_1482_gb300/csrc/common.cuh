@@ -138,6 +138,18 @@ struct Frag {
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 
+// compensated (Kahan) summation: s the running sum, c the lost low-order part
+struct Kahan {
+    float s, c;
+    GB_DEV void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 // The hardware reciprocal square root (rsqrt.approx.ftz: relative error about 2^-23, subnormal
 // inputs flushed).  The pair rules and the far-field series take it on squared distances that
 // are either zero (masked by the caller) or far above the subnormal range.
@@ -225,8 +237,11 @@ void launch_p2m(int P, int L, const float *geo, const float4 *sx, const int32_t 
                 cudaStream_t s);
 void launch_m2m(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *M, cudaStream_t s);
 void launch_l2l(int P, int l, const int32_t *begin, const int32_t *end, const float *ops, float *Lc, cudaStream_t s);
+// near != nullptr: add the P2P kernel's compensated near-field sums (launch_p2p_near) and write
+// the total to out[perm[i]] instead of far[i]
 void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
-                float4 *far, cudaStream_t s);
+                float4 *far, cudaStream_t s, const float4 *near = nullptr, const uint32_t *perm = nullptr,
+                float4 *out = nullptr);
 void launch_m2p(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s);
 
@@ -260,13 +275,18 @@ bool m2l_use_tc();
 size_t m2l_f16_table_bytes(int P);
 void launch_build_m2l_f16(int P, const float *ops, void *table, cudaStream_t s);
 void launch_cell_scale(const float *M, int64_t ncells, int P, int8_t *scale, cudaStream_t s);
+// max_ctas > 0: the tiles are launched max_ctas at a time (one wave of one CTA per SM), so that
+// no CTA of the M2L waits for an SM while a kernel on another stream (the near field) could use
+// the room left beside the running ones
 void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                     const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M,
-                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s);
+                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s, int max_ctas = 0);
 void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
                           const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                           const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                          const void *ps, float *Lc, int *status, cudaStream_t s);
+                          const void *ps, float *Lc, int *status, cudaStream_t s, int max_ctas = 0);
+// number of SMs of the current device (cached per process)
+int sm_count();
 // per cell: the FP16 scale s_c and the pre-split halves of M~_c 2^s_c (KP / 8 pieces of 8 hi
 // then 8 lo halves); m2l_f16_presplit(P): whether the FP16 M2L of order P takes them
 bool m2l_f16_presplit(int P);
@@ -284,8 +304,11 @@ void launch_m2l_tc_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tl
 void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
                       cudaStream_t s);
+// near != nullptr: far holds the M2P sums; the local expansion's value, those and the near-field
+// sums are added and written to out[perm[i]]
 void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
-                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s);
+                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s, const float4 *near = nullptr,
+                      const uint32_t *perm = nullptr, float4 *out = nullptr);
 void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
                       const float *M, float4 *far, cudaStream_t s);
@@ -294,6 +317,15 @@ void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const f
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);
 
 // p2p.cu
+// P2P without the far field: the compensated near-field sums of every particle in sorted order,
+// near[2 i] = sums (phi, dphi/dx, dphi/dy, dphi/dz), near[2 i + 1] = their compensations (the
+// packed-pair kernels only: p2p_near_supported())
+bool p2p_near_supported();
+void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
+                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, cudaStream_t s);
+void launch_p2p_cells_near(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+                           const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
+                           cudaStream_t s);
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *p2p_offs, const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2,
                 float4 *out, cudaStream_t s);

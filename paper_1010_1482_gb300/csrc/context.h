@@ -43,6 +43,7 @@ struct AdaptiveState {
     DevBuf info;                                                   // small device-side totals read by the host
     DevBuf anchor;                                                 // int4 integer box per cell (depth 21)
     DevBuf presplit;                                               // FP16 pre-split source rows (gathered M2L)
+    DevBuf near;                                                   // P2P's compensated sums, 2 float4 per particle
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
     int P = 0, max_level = 0;
     std::vector<int> level_start;
@@ -76,6 +77,15 @@ struct gbfmm_ctx {
     // stage timing
     cudaEvent_t ev[gbfmm::kStages + 1] = {};
     bool timed_last = false;
+    // order of the last timed evaluation's stages 7 (L2P) and 8 (P2P): 0 = L2P then P2P (ev 7, 8,
+    // 9); 1 = P2P then L2P, serial; 2 = P2P on s_near between ev_aux[0] and ev_aux[1] while the
+    // far field ran on s_far, whose L2P (after the join on ev_aux[2]) ends at ev[9]
+    int stage_order_last = 0;
+    // the near field runs beside the far field: P2P on s_near (lowest priority), M2L .. L2P on
+    // s_far (highest), forked from and joined into the caller's stream by events
+    cudaStream_t s_far = nullptr, s_near = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_near = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_aux[3] = {};
     bool ops_built_last = false;
     int64_t launches_last = 0;
 };

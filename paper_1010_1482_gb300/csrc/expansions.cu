@@ -23,6 +23,14 @@
 
 namespace gbfmm {
 
+#define GBFMM_DISPATCH_P(P, CALL)      \
+    switch (P) {                       \
+    case 4: { constexpr int PQ = 4; CALL; } break;   \
+    case 6: { constexpr int PQ = 6; CALL; } break;   \
+    case 8: { constexpr int PQ = 8; CALL; } break;   \
+    case 10: { constexpr int PQ = 10; CALL; } break; \
+    }
+
 constexpr int kMaxP = 10;
 constexpr int kMaxDeg = 2 * kMaxP;  // harmonics up to degree 2P-2 (M2L) and P (M2P gradient)
 
@@ -657,10 +665,25 @@ GB_DEV float4 l2p_eval(const float *__restrict__ Lg, float x, float y, float z, 
     return make_float4(phi * ih, gpr * ih2, gpi * ih2, gz * ih2);
 }
 
+// the near-field compensated sums of particle i (sorted order: the sums, then their
+// compensations) completed with the far field, in the order the P2P kernel adds it
+GB_DEV float4 near_plus_far(const float4 *__restrict__ near, int64_t i, float4 f)
+{
+    const float4 s = near[2 * i], c = near[2 * i + 1];
+    Kahan a{s.x, c.x}, bx{s.y, c.y}, by{s.z, c.z}, bz{s.w, c.w};
+    a.add(f.x);
+    bx.add(f.y);
+    by.add(f.z);
+    bz.add(f.w);
+    return make_float4(a.s, bx.s, by.s, bz.s);
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_l2p(int L, const float *__restrict__ geo, int64_t n,
                                              const float4 *__restrict__ sx, const uint32_t *__restrict__ leafkey,
-                                             const float *__restrict__ Lc, float4 *__restrict__ far)
+                                             const float *__restrict__ Lc, float4 *__restrict__ far,
+                                             const float4 *__restrict__ near, const uint32_t *__restrict__ perm,
+                                             float4 *__restrict__ out)
 {
     constexpr int PP = P * P;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -669,21 +692,20 @@ __global__ void __launch_bounds__(128) k_l2p(int L, const float *__restrict__ ge
     const int64_t g = level_offset(L) + key;
     const CellGeom cg = geo_level_cell(geo, L, key);
     float4 p = __ldg(&sx[i]);
-    far[i] = l2p_eval<P>(Lc + g * PP, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
-                         cg.inv_h);
+    const float4 f = l2p_eval<P>(Lc + g * PP, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                                 (p.z - cg.cz) * cg.inv_h, cg.inv_h);
+    if (near)
+        out[perm[i]] = near_plus_far(near, i, f);
+    else
+        far[i] = f;
 }
 
 void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, const uint32_t *leafkey, const float *Lc,
-                float4 *far, cudaStream_t s)
+                float4 *far, cudaStream_t s, const float4 *near, const uint32_t *perm, float4 *out)
 {
     if (n <= 0) return;
     unsigned grid = (unsigned)((n + 127) / 128);
-    switch (P) {
-    case 4: k_l2p<4><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
-    case 6: k_l2p<6><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
-    case 8: k_l2p<8><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
-    case 10: k_l2p<10><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far); break;
-    }
+    GBFMM_DISPATCH_P(P, (k_l2p<PQ><<<grid, 128, 0, s>>>(L, geo, n, sx, leafkey, Lc, far, near, perm, out)));
     note_launches(1);
 }
 
@@ -885,19 +907,29 @@ template <int P>
 __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__restrict__ leaf_of,
                                                    const int32_t *__restrict__ level, const float4 *__restrict__ geom,
                                                    const float4 *__restrict__ sx, const float *__restrict__ Lc,
-                                                   float4 *__restrict__ far)
+                                                   float4 *__restrict__ far, const float4 *__restrict__ near,
+                                                   const uint32_t *__restrict__ perm, float4 *__restrict__ out)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t c = leaf_of[i];
-    if (level[c] < 2) {
-        far[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (level[c] >= 2) {
+        const CellGeom cg = geo_cell(geom, c);
+        float4 p = __ldg(&sx[i]);
+        f = l2p_eval<P>(Lc + (int64_t)c * (P * P), (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                        (p.z - cg.cz) * cg.inv_h, cg.inv_h);
     }
-    const CellGeom cg = geo_cell(geom, c);
-    float4 p = __ldg(&sx[i]);
-    far[i] = l2p_eval<P>(Lc + (int64_t)c * (P * P), (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
-                         (p.z - cg.cz) * cg.inv_h, cg.inv_h);
+    if (near) {  // far holds the M2P (W list) sums
+        const float4 w = far[i];
+        f.x += w.x;
+        f.y += w.y;
+        f.z += w.z;
+        f.w += w.w;
+        out[perm[i]] = near_plus_far(near, i, f);
+    } else {
+        far[i] = f;
+    }
 }
 
 // M2P over the W list, one CTA per listed leaf; adds into the far-field accumulator
@@ -1050,14 +1082,6 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
     }
 }
 
-#define GBFMM_DISPATCH_P(P, CALL)      \
-    switch (P) {                       \
-    case 4: { constexpr int PQ = 4; CALL; } break;   \
-    case 6: { constexpr int PQ = 6; CALL; } break;   \
-    case 8: { constexpr int PQ = 8; CALL; } break;   \
-    case 10: { constexpr int PQ = 10; CALL; } break; \
-    }
-
 void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,
                       const int32_t *begin, const int32_t *count, const float4 *sx, float *M, cudaStream_t s)
 {
@@ -1079,11 +1103,12 @@ void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 
 }
 
 void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
-                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s)
+                      const float4 *sx, const float *Lc, float4 *far, cudaStream_t s, const float4 *near,
+                      const uint32_t *perm, float4 *out)
 {
     if (n <= 0) return;
     const unsigned grid = (unsigned)((n + 127) / 128);
-    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, geom, sx, Lc, far)));
+    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, geom, sx, Lc, far, near, perm, out)));
     note_launches(1);
 }
 

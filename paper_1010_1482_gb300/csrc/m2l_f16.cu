@@ -157,6 +157,7 @@ GB_DEV void chunk16(int c, int KS, int NCH, int &k0, int &kw)
 
 struct F16Tiles {
     int L;
+    int tile0;  // tile of block 0 (a launch may cover a range of the tiles)
     int ntiles_level[kMaxLevel + 1];
 };
 
@@ -186,12 +187,12 @@ __global__ void __launch_bounds__(288, 1)
     int64_t q0 = 0, nq = 0, off = 0, tstart = 0;
     int tcount = 0;
     if (tdesc) {
-        const int4 d = tdesc[blockIdx.x];
+        const int4 d = tdesc[tiles.tile0 + blockIdx.x];
         tau = d.y;
         tstart = d.z;
         tcount = d.w;
     } else {
-        int rem = blockIdx.x;
+        int rem = tiles.tile0 + blockIdx.x;
         int l = tiles.L;
         while (l >= 2 && rem >= tiles.ntiles_level[l]) {
             rem -= tiles.ntiles_level[l];
@@ -556,12 +557,12 @@ __global__ void __launch_bounds__(F16SCfg<P, CW_>::NTHREADS, 1)
     int64_t q0 = 0, nq = 0, off = 0, tstart = 0;
     int tcount = 0;
     if (tdesc) {
-        const int4 d = tdesc[blockIdx.x];
+        const int4 d = tdesc[tiles.tile0 + blockIdx.x];
         tau = d.y;
         tstart = d.z;
         tcount = d.w;
     } else {
-        int rem = blockIdx.x;
+        int rem = tiles.tile0 + blockIdx.x;
         int l = tiles.L;
         while (l >= 2 && rem >= tiles.ntiles_level[l]) {
             rem -= tiles.ntiles_level[l];
@@ -815,7 +816,7 @@ template <int P>
 static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist, const int32_t *begin,
                          const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
                          const void *table, const float *M, const int8_t *cscale, const void *ps, float *Lc,
-                         int *status, cudaStream_t s)
+                         int *status, cudaStream_t s, int max_ctas)
 {
     using T = F16Table<P>;
     const __half *tab = static_cast<const __half *>(table);
@@ -823,10 +824,18 @@ static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, con
     if (ps) {
         using CS = F16SCfg<P, 8>;
         cudaFuncSetAttribute(k_m2l_f16s<P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS::kSmemBytes);
-        k_m2l_f16s<P, 8><<<grid, CS::NTHREADS, CS::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
-                                                                    m2l_code, tab, gexp,
-                                                                    static_cast<const __half *>(ps), cscale, Lc,
-                                                                    status);
+        const int step = max_ctas > 0 ? max_ctas : grid;
+        for (int t0 = 0; t0 < grid; t0 += step) {
+            F16Tiles tt = tiles;
+            tt.tile0 = t0;
+            const int g = grid - t0 < step ? grid - t0 : step;
+            k_m2l_f16s<P, 8><<<g, CS::NTHREADS, CS::kSmemBytes, s>>>(tt, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
+                                                                     m2l_code, tab, gexp,
+                                                                     static_cast<const __half *>(ps), cscale, Lc,
+                                                                     status);
+            note_launches(1);
+        }
+        return;
     } else {
         using C = F16Cfg<P>;
         cudaFuncSetAttribute(k_m2l_f16<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
@@ -840,9 +849,9 @@ static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, con
 static void dispatch_f16(int P, const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                          const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                          const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                         const void *ps, float *Lc, int *status, cudaStream_t s)
+                         const void *ps, float *Lc, int *status, cudaStream_t s, int max_ctas)
 {
-#define GBFMM_F16_ARGS tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc, status, s
+#define GBFMM_F16_ARGS tiles, grid, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc, status, s, max_ctas
     switch (P) {
     case 4: launch_f16_t<4>(GBFMM_F16_ARGS); break;
     case 6: launch_f16_t<6>(GBFMM_F16_ARGS); break;
@@ -854,7 +863,7 @@ static void dispatch_f16(int P, const F16Tiles &tiles, int grid, const int4 *tde
 
 void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
                     const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M,
-                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s)
+                    const int8_t *cscale, const void *ps, float *Lc, int *status, cudaStream_t s, int max_ctas)
 {
     if (L < 2) return;
     F16Tiles tiles{};
@@ -867,18 +876,18 @@ void launch_m2l_f16(int P, int L, const int32_t *begin, const int32_t *end, cons
     }
     if (total == 0) return;
     dispatch_f16(P, tiles, total, nullptr, nullptr, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc,
-                 status, s);
+                 status, s, max_ctas);
 }
 
 void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
                           const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                           const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
-                          const void *ps, float *Lc, int *status, cudaStream_t s)
+                          const void *ps, float *Lc, int *status, cudaStream_t s, int max_ctas)
 {
     if (ntiles <= 0) return;
     F16Tiles tiles{};
     dispatch_f16(P, tiles, ntiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids, m2l_code, table, M, cscale, ps, Lc,
-                 status, s);
+                 status, s, max_ctas);
 }
 
 }  // namespace gbfmm

@@ -54,17 +54,6 @@ GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi,
     gz = fmaf(-dz, qi3, gz);
 }
 
-struct Kahan {
-    float s, c;
-    GB_DEV void add(float x)
-    {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
 template <bool SOFT, int TPT>
 __global__ void __launch_bounds__(kP2PThreads) k_p2p(int L, const int32_t *__restrict__ leaves,
                                                      const float4 *__restrict__ sx,
@@ -252,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ 
                                                       const int32_t *__restrict__ p2p_ids,
                                                       const float4 *__restrict__ far,
                                                       const uint32_t *__restrict__ perm, float eps2,
-                                                      float4 *__restrict__ out)
+                                                      float4 *__restrict__ out, float4 *__restrict__ near)
 {
     constexpr int NPK = TPT / 2;
     __shared__ ulonglong2 sA[kSrcCap2], sB[kSrcCap2];  // (x, x | y, y), (z, z | q, q)
@@ -368,6 +357,11 @@ __global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ 
                     bx.add(v.y);
                     by.add(v.z);
                     bz.add(v.w);
+                }
+                if (near) {  // the compensated sums so far; the far field is added by L2P
+                    near[2 * (int64_t)i] = make_float4(a.s, bx.s, by.s, bz.s);
+                    near[2 * (int64_t)i + 1] = make_float4(a.c, bx.c, by.c, bz.c);
+                    continue;
                 }
                 if (far) {
                     const float4 f = far[i];
@@ -593,38 +587,51 @@ static void launch_p2p_t(unsigned grid, int L, const int32_t *leaves, const floa
     note_launches(1);
 }
 
+// near != nullptr: write the compensated near-field sums (sorted order, 2 float4 per particle:
+// the sums, then their compensations) instead of adding `far` and scattering to `out`; only the
+// packed-pair kernels have this output (p2p_has_near)
+static bool p2p_has_near()
+{
+    const int t = p2p_tpt();
+    return t == 12 || t == 14 || t == 16 || t == 17;
+}
+
+// the packed-pair kernel, with the shared-memory carveout of the tensor-core M2L (the largest)
+// so that its CTAs can share an SM with the M2L's when both run at once
+template <int TPT, int NT>
+static void launch_pk(bool soft, unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
+                      const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
+                      const uint32_t *perm, float eps2, float4 *out, float4 *near, cudaStream_t s)
+{
+    static const bool carve = [] {
+        cudaFuncSetAttribute(k_p2p2<true, TPT, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_p2p2<false, TPT, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        return true;
+    }();
+    (void)carve;
+    if (soft)
+        k_p2p2<true, TPT, NT><<<grid, NT, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near);
+    else
+        k_p2p2<false, TPT, NT><<<grid, NT, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near);
+    note_launches(1);
+}
+
 static void dispatch_p2p(unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
                          const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
-                         const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
+                         const uint32_t *perm, float eps2, float4 *out, cudaStream_t s, float4 *near = nullptr)
 {
-    if (p2p_tpt() == 16 || p2p_tpt() == 17) {  // packed pairs, 64 / 256 threads per CTA
-        if (p2p_tpt() == 16) {
-            if (eps2 > 0.f)
-                k_p2p2<true, 2, 64><<<grid, 64, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-            else
-                k_p2p2<false, 2, 64><<<grid, 64, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-        } else {
-            if (eps2 > 0.f)
-                k_p2p2<true, 2, 256><<<grid, 256, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-            else
-                k_p2p2<false, 2, 256><<<grid, 256, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-        }
-        note_launches(1);
+    if (p2p_has_near()) {  // packed pairs: 12 / 14 = 2 / 4 targets per thread; 16 / 17 = 64 / 256 threads
+        const int t = p2p_tpt();
+        if (t == 12) launch_pk<2, kP2PThreads>(eps2 > 0.f, grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near, s);
+        if (t == 14) launch_pk<4, kP2PThreads>(eps2 > 0.f, grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near, s);
+        if (t == 16) launch_pk<2, 64>(eps2 > 0.f, grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near, s);
+        if (t == 17) launch_pk<2, 256>(eps2 > 0.f, grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near, s);
         return;
     }
-    if (p2p_tpt() == 12 || p2p_tpt() == 14 || p2p_tpt() == 20) {
-        if (p2p_tpt() != 14) {  // 20 (superleaf, uniform tree only) takes 12 for leaf lists
-            if (eps2 > 0.f)
-                k_p2p2<true, 2><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-            else
-                k_p2p2<false, 2><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-        } else {
-            if (eps2 > 0.f)
-                k_p2p2<true, 4><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-            else
-                k_p2p2<false, 4><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out);
-        }
-        note_launches(1);
+    if (p2p_tpt() == 20) {  // superleaf (uniform tree only) takes 12 for leaf lists
+        launch_pk<2, kP2PThreads>(eps2 > 0.f, grid, L, leaves, sx, begin, end, offs, ids, far, perm, eps2, out, near, s);
         return;
     }
     if (p2p_tpt() == 0) {
@@ -668,6 +675,24 @@ void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const f
 {
     if (n <= 0 || nleaves <= 0) return;
     dispatch_p2p((unsigned)nleaves, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, s);
+}
+
+bool p2p_near_supported() { return p2p_has_near(); }
+
+void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
+                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, cudaStream_t s)
+{
+    if (n <= 0 || !p2p_has_near()) return;
+    dispatch_p2p((unsigned)(int64_t(1) << (3 * L)), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, nullptr, nullptr,
+                 eps2, nullptr, s, near);
+}
+
+void launch_p2p_cells_near(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+                           const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
+                           cudaStream_t s)
+{
+    if (n <= 0 || nleaves <= 0 || !p2p_has_near()) return;
+    dispatch_p2p((unsigned)nleaves, 0, leaves, sx, begin, end, u_offs, u_ids, nullptr, nullptr, eps2, nullptr, s, near);
 }
 
 // Direct all-pairs sum: one thread per target, sources streamed through shared memory in

@@ -167,6 +167,22 @@ def test_adaptive_uniform_lattice_reduces_to_uniform_tree(G, ctx):
     assert O.rel_l2(ad, un) <= 1e-6
 
 
+@pytest.mark.parametrize("n,leaf", [(50000, 32), (3000, 64)])
+def test_adaptive_concurrent_near_field_equals_serial(G, ctx, n, leaf):
+    """P2P over the U lists on a second stream beside the expansions gives the serial output
+    (all stages on the caller's stream; the timed evaluation) bit for bit; the small case has
+    no level-2 cells below the root's children (no far field)."""
+    x = inputs.plummer(n, 515)
+    a = run(G, ctx, x, p=8, leaf_size=leaf)
+    b = run(G, ctx, x, p=8, leaf_size=leaf, flags=G.FLAG_SERIAL)
+    c = run(G, ctx, x, p=8, leaf_size=leaf, flags=G.FLAG_STAGE_TIMING)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    for _ in range(2):
+        assert np.array_equal(a, run(G, ctx, x, p=8, leaf_size=leaf))
+    ref = O.fmm_adaptive(x, 8, leaf)["out"]
+    assert O.rel_l2(a, ref) <= TOL_FMM
+
+
 def test_adaptive_host_path_timing_and_treecode_rejected(G, ctx):
     x = inputs.plummer(10000, 31)
     prm = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, p=4, leaf_size=32, flags=G.FLAG_STAGE_TIMING)

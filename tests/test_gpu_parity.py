@@ -257,6 +257,24 @@ def test_host_path_and_determinism(G, ctx):
     assert np.array_equal(hout.numpy().astype(np.float64), a)
 
 
+@pytest.mark.parametrize("p,leaf", [(8, 32), (10, 64)])
+def test_concurrent_near_field_equals_serial(G, ctx, p, leaf):
+    """The default FMM evaluation runs P2P on a second stream beside M2L / L2L; its output is
+    the serial one (all stages on the caller's stream, and the timed evaluation) bit for bit,
+    and both agree with the oracle."""
+    x = inputs.uniform_cube(60000, 21)
+    a, _ = run(G, ctx, x, p=p, leaf_size=leaf)
+    b, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_SERIAL)
+    c, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_STAGE_TIMING)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    for _ in range(3):  # back-to-back evaluations reuse the workspace: each waits for the last
+        d, _ = run(G, ctx, x, p=p, leaf_size=leaf)
+        assert np.array_equal(a, d)
+    if p == 8:
+        ref = O.fmm(x, p, leaf)["out"]
+        assert O.rel_l2(a, ref) <= TOL_FMM
+
+
 def test_stage_timing(G, ctx):
     x = inputs.uniform_cube(40000, 2)
     run(G, ctx, x, p=6, leaf_size=32, flags=G.FLAG_STAGE_TIMING)
