@@ -379,10 +379,18 @@ def run_gpu(args, w):
             tpeak, tbasis = tf32_peak_tflops()
             kname, ksrc, kprof, kdt = "k_m2l_tc", "m2l_tc.cu", f"m2l_tc_{w['name']}.md", "TF32"
         tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * kpad
+        # the default (forked) evaluation launches the staged M2L one wave of one CTA per SM at a
+        # time; flop and DRAM traffic per launch are the evaluation's over that many launches
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        m2l_launches = -(-tiles // sms) if kname == "k_m2l_f16s" else 1
+        traffic = traffic_from_profile(ksrc, kprof)
         roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": m2l_tf / tpeak,
-                    "traffic": traffic_from_profile(ksrc, kprof),
-                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
+                    "traffic": traffic,
+                    "launches_per_evaluation": m2l_launches,
+                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per evaluation, "
+                            f"{m2l_flops / m2l_launches:.4g} per launch ({m2l_launches} launches of <= {sms} tiles); "
+                            "achieved = flop / the launches' summed duration; traffic per launch (ncu, cold L2)",
                     "peak_basis": tbasis,
                     "tensor_flop_issued": tensor_flops,
                     "tensor_pipe_frac": tensor_flops / (m2l_ms / 1e3) / 1e12 / tpeak,

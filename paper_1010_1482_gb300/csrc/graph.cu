@@ -51,7 +51,10 @@ int gbfmm_graph_create(gbfmm_graph **out, gbfmm_ctx *ctx, const gbfmm_params *pr
         }
     }
     cudaGraphExec_t exec = nullptr;
-    if (rc == GBFMM_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+    // the kernel nodes keep the priorities of the streams they were captured from (the near
+    // field's low-priority stream beside the expansions' high-priority one)
+    if (rc == GBFMM_OK &&
+        (e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority)) != cudaSuccess)
         rc = cuda_fail(ctx, e, "cudaGraphInstantiate");
     cudaStreamDestroy(s);
     if (rc != GBFMM_OK) {

@@ -10,9 +10,10 @@
 // so one staged source feeds TPT pair interactions; when the leaf has fewer target slots than
 // the CTA has threads, the threads form G groups that split the sources round-robin, so the
 // lanes stay busy for leaves of any occupancy (the paper instead pads targets to the block
-// size).  Each thread sums its share in FP32; the group partials, and then the far-field
-// value, are combined per target with compensated (Kahan) summation and written to the
-// caller's original particle order.
+// size).  Each thread sums its share in FP32; the group partials are combined per target with
+// compensated (Kahan) summation.  Then either the far-field value is added the same way and the
+// result written to the caller's original particle order, or (FMM, the packed-pair kernels) the
+// compensated sums are stored for L2P, which adds the far field and writes the output.
 #include "common.cuh"
 
 #include <stdlib.h>
