@@ -63,3 +63,20 @@ def test_workspace_grows_linearly(lib):
     _, a = G.gbfmm_plan(prm, 1 << 20)
     _, b = G.gbfmm_plan(prm, 1 << 23)
     assert 6 < b / a < 10
+
+
+def test_header_constants_match_binding():
+    """Every enumerator and GBFMM_FLAG_* macro of the header has the value the Python binding
+    uses (GBFMM_X in the header is X in the binding, error codes keep their prefix)."""
+    import os
+    import re
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "gbfmm.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (GBFMM_FLAG_\w+)\s+(\d+)", text, re.M)}
+    consts.update({m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GBFMM_[A-Z0-9_]+)\s*=\s*(\d+)", text)})
+    assert {"GBFMM_FLAG_STAGE_TIMING", "GBFMM_FLAG_M2L_CUDA_CORES", "GBFMM_FLAG_SERIAL", "GBFMM_OK",
+            "GBFMM_LIST_X", "GBFMM_TREE_ADAPTIVE", "GBFMM_METHOD_TREECODE"} <= set(consts)
+    for name, value in consts.items():
+        py = name if (name == "GBFMM_OK" or name.startswith("GBFMM_E")) else name[len("GBFMM_"):]
+        assert getattr(G, py) == value, name
