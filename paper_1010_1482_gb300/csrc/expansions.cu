@@ -717,8 +717,64 @@ void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, con
 //   dphi/dx + i dphi/dy =  (1/h^2) sum s(m) sqrt((n+m+2)(n+m+1)) M~_n^m I_{n+1}^{m+1},
 //   s(m) = +1 for m >= 0, -1 for m < 0.
 // ------------------------------------------------------------------------------------------
+// The constants of these sums are folded into the source cell's coefficients once per cell
+// (staged in shared memory), so that each (particle, cell) evaluation spends two FMAs per real
+// term: per (N, m), 0 <= m <= N <= P, two float4
+//   {w M_N^m (re, im), -w sqrt((N-m)(N+m)) M_{N-1}^m (re, im)},
+//   {A - B (re, im), A + B (re, im)},  A = sqrt((N+m)(N+m-1)) M_{N-1}^{m-1},
+//                                      B = sqrt((N-m)(N-m-1)) M_{N-1}^{m+1},
+// w = 2 for m > 0; dphi/dx + i dphi/dy = sum A I - conj(B I), so its real part takes A - B
+// against (Re I, -Im I) and its imaginary part A + B against (Im I, Re I).
 template <int P>
-GB_DEV void m2p_accumulate(const float *__restrict__ Ms, float x, float y, float z, float ih, float *o)
+struct M2PFold {
+    static constexpr int NM = (P + 1) * (P + 2) / 2;
+};
+
+GB_HD constexpr int nm_idx(int N, int m) { return N * (N + 1) / 2 + m; }
+
+// the block stages the cell's coefficients M[P^2] (coalesced) in sM, then threads t, t + nt,
+// ... fill F[2 NM]; the square roots of the integer products (exact in FP32) are taken in place,
+// so the lanes read no table at lane-dependent addresses
+template <int P>
+GB_DEV void m2p_fold(const float *__restrict__ M, float *__restrict__ sM, float4 *__restrict__ F, int t, int nt)
+{
+    for (int k = t; k < P * P; k += nt) sM[k] = M[k];
+    __syncthreads();
+    for (int q = t; q < M2PFold<P>::NM; q += nt) {
+        int N = 0;
+        while ((N + 1) * (N + 2) / 2 <= q) ++N;
+        const int m = q - N * (N + 1) / 2;
+        const float w = m > 0 ? 2.f : 1.f;
+        auto cre = [&](int n, int k) { return sM[re_idx(n, k)]; };
+        auto cim = [&](int n, int k) { return k > 0 ? sM[im_idx(n, k)] : 0.f; };
+        auto root = [](int a, int b) { return sqrtf((float)(a * b)); };
+        float pr = 0.f, pi = 0.f, zr = 0.f, zi = 0.f, ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+        if (N <= P - 1) {
+            pr = w * cre(N, m);
+            pi = w * cim(N, m);
+        }
+        if (N >= 1 && m <= N - 1) {
+            const float c = -w * root(N - m, N + m);
+            zr = c * cre(N - 1, m);
+            zi = c * cim(N - 1, m);
+        }
+        if (N >= 1 && m >= 1) {
+            const float c = root(N + m, N + m - 1);
+            ar = c * cre(N - 1, m - 1);
+            ai = c * cim(N - 1, m - 1);
+        }
+        if (N >= 1 && m + 1 <= N - 1) {
+            const float c = root(N - m, N - m - 1);
+            br = c * cre(N - 1, m + 1);
+            bi = c * cim(N - 1, m + 1);
+        }
+        F[2 * q] = make_float4(pr, pi, zr, zi);
+        F[2 * q + 1] = make_float4(ar - br, ai - bi, ar + br, ai + bi);
+    }
+}
+
+template <int P>
+GB_DEV void m2p_accumulate_folded(const float4 *__restrict__ F, float x, float y, float z, float ih, float *o)
 {
     const float r2 = x * x + y * y + z * z;
     const float ir = rsqrt_ftz(r2);
@@ -744,26 +800,16 @@ GB_DEV void m2p_accumulate(const float *__restrict__ Ms, float x, float y, float
                 are = nre;
                 aim = nim;
             }
-            const float w = (m > 0) ? 2.f : 1.f;
-            if (N <= P - 1) {  // phi: M_N^m I_N^m
-                const float lre = Ms[re_idx(N, m)], lim = (m > 0) ? Ms[im_idx(N, m)] : 0.f;
-                phi += w * (lre * are - lim * aim);
+            const int q = nm_idx(N, m);
+            if (N <= P - 1 || (N >= 1 && m <= N - 1)) {
+                const float4 a = F[2 * q];
+                if (N <= P - 1) phi = fmaf(a.x, are, fmaf(-a.y, aim, phi));
+                if (N >= 1 && m <= N - 1) gz = fmaf(a.z, are, fmaf(-a.w, aim, gz));
             }
-            if (N >= 1 && m <= N - 1) {  // d/dz: -sqrt((N-m)(N+m)) M_{N-1}^m I_N^m
-                const float lre = Ms[re_idx(N - 1, m)], lim = (m > 0) ? Ms[im_idx(N - 1, m)] : 0.f;
-                gz -= w * c_sq[N - m][N + m] * (lre * are - lim * aim);
-            }
-            if (N >= 1 && m >= 1) {  // mu = m >= 1: + sqrt((N+m)(N+m-1)) M_{N-1}^{m-1} I_N^m
-                const float lre = Ms[re_idx(N - 1, m - 1)], lim = (m - 1 > 0) ? Ms[im_idx(N - 1, m - 1)] : 0.f;
-                const float c = c_sq[N + m][N + m - 1];
-                gpr += c * (lre * are - lim * aim);
-                gpi += c * (lre * aim + lim * are);
-            }
-            if (N >= 1 && m + 1 <= N - 1) {  // mu = -m: - sqrt((N-m)(N-m-1)) conj(M_{N-1}^{m+1} I_N^m)
-                const float lre = Ms[re_idx(N - 1, m + 1)], lim = Ms[im_idx(N - 1, m + 1)];
-                const float c = c_sq[N - m][N - m - 1];
-                gpr -= c * (lre * are - lim * aim);
-                gpi += c * (lre * aim + lim * are);
+            if (N >= 1 && (m >= 1 || m + 1 <= N - 1)) {
+                const float4 b = F[2 * q + 1];
+                gpr = fmaf(b.x, are, fmaf(-b.y, aim, gpr));
+                gpi = fmaf(b.z, aim, fmaf(b.w, are, gpi));
             }
         }
     }
@@ -780,8 +826,8 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ ge
                                              const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
                                              const float *__restrict__ M, float4 *__restrict__ far)
 {
-    constexpr int PP = P * P;
-    __shared__ float sM[PP];
+    __shared__ float4 sF[2 * M2PFold<P>::NM];
+    __shared__ float sM[P * P];
     const int64_t leaf = blockIdx.x;
     const int64_t g = level_offset(L) + leaf;
     const int b0 = begin[g], e0 = end[g];
@@ -796,12 +842,12 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ ge
             for (uint32_t e = m2l_offs[a]; e < m2l_offs[a + 1]; ++e) {
                 const int64_t s = m2l_ids[e];
                 __syncthreads();
-                for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[s * PP + k];
+                m2p_fold<P>(M + s * (P * P), sM, sF, threadIdx.x, blockDim.x);
                 __syncthreads();
                 const CellGeom cg = geo_level_cell(geo, l, (uint32_t)(s - level_offset(l)));
                 if (act)
-                    m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
-                                      (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
+                    m2p_accumulate_folded<P>(sF, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                                             (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
             }
         }
         if (act) far[t] = make_float4(o[0], o[1], o[2], o[3]);
@@ -941,8 +987,8 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
                                                   const int32_t *__restrict__ w_ids, const float4 *__restrict__ sx,
                                                   const float *__restrict__ M, float4 *__restrict__ far)
 {
-    constexpr int PP = P * P;
-    __shared__ float sM[PP];
+    __shared__ float4 sF[2 * M2PFold<P>::NM];
+    __shared__ float sM[P * P];
     const int32_t b = leaves[blockIdx.x];
     const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
     if (e0 == e1) return;
@@ -955,12 +1001,12 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
         for (uint32_t e = e0; e < e1; ++e) {
             const int32_t sc = w_ids[e];
             __syncthreads();
-            for (int k = threadIdx.x; k < PP; k += blockDim.x) sM[k] = M[(int64_t)sc * PP + k];
+            m2p_fold<P>(M + (int64_t)sc * (P * P), sM, sF, threadIdx.x, blockDim.x);
             __syncthreads();
             const CellGeom cg = geo_cell(geom, sc);
             if (act)
-                m2p_accumulate<P>(sM, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h, (p.z - cg.cz) * cg.inv_h,
-                                  cg.inv_h, o);
+                m2p_accumulate_folded<P>(sF, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
+                                         (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
         }
         if (act) {
             float4 f = far[t];
