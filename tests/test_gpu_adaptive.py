@@ -170,8 +170,9 @@ def test_adaptive_uniform_lattice_reduces_to_uniform_tree(G, ctx):
 @pytest.mark.parametrize("n,leaf", [(50000, 32), (3000, 64)])
 def test_adaptive_concurrent_near_field_equals_serial(G, ctx, n, leaf):
     """P2P over the U lists on a second stream beside the expansions gives the serial output
-    (all stages on the caller's stream; the timed evaluation) bit for bit; the small case has
-    no level-2 cells below the root's children (no far field)."""
+    (all stages on the caller's stream; the timed evaluation) bit for bit.  Trees without a
+    far field (fewer particles than a leaf holds) take the same path in
+    test_adaptive_degenerate_inputs."""
     x = inputs.plummer(n, 515)
     a = run(G, ctx, x, p=8, leaf_size=leaf)
     b = run(G, ctx, x, p=8, leaf_size=leaf, flags=G.FLAG_SERIAL)
