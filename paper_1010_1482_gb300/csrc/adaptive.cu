@@ -919,6 +919,15 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         near = A.near.as<float4>();
     }
     const cudaStream_t s_main = s;
+    // an error after the fork still joins both streams back into the caller's
+    auto fail_joined = [&](int code, const char *msg) {
+        if (fork) {
+            cudaEventRecord(ctx->ev_join, ctx->s_far);
+            cudaStreamWaitEvent(s_main, ctx->ev_join, 0);
+            cudaStreamWaitEvent(s_main, ctx->ev_near, 0);
+        }
+        return fail(ctx, code, msg);
+    };
     if (fork) {
         cudaEventRecord(ctx->ev_fork, s_main);
         cudaStreamWaitEvent(ctx->s_far, ctx->ev_fork, 0);
@@ -934,7 +943,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
 
     // ---- expansions ----
     if (grow(A.M, 4 * (size_t)ncells * PP, false, 0, s) || grow(A.Lc, 4 * (size_t)ncells * PP, false, 0, s))
-        return fail(ctx, GBFMM_ENOMEM, "adaptive expansions");
+        return fail_joined(GBFMM_ENOMEM, "adaptive expansions");
     float *M = A.M.as<float>(), *Lc = A.Lc.as<float>();
     float4 *far = A.far.as<float4>();
     const bool deep = maxl >= 2;
@@ -972,7 +981,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                 acc += hcnt[gi];
             }
         if (grow(A.tlist, 4 * (size_t)acc + 4, false, 0, s) || grow(A.tdesc, sizeof(int4) * tiles.size() + 16, false, 0, s))
-            return fail(ctx, GBFMM_ENOMEM, "adaptive tiles");
+            return fail_joined(GBFMM_ENOMEM, "adaptive tiles");
         uint32_t *gcur = gcnt + 8 * (kAdaptMaxLevel + 2);
         cudaMemcpyAsync(gcur, hcur.data(), 4 * hcur.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(A.tdesc.p, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s);
@@ -981,11 +990,11 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         note_launches(1);
         cudaStreamSynchronize(s);  // the host tile vectors go out of scope
         if (f16) {
-            if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive scales");
+            if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail_joined(GBFMM_ENOMEM, "adaptive scales");
             void *ps = nullptr;
             if (m2l_f16_presplit(P)) {  // sources split once per cell
                 if (grow(A.presplit, presplit_bytes(P, ncells), false, 0, s))
-                    return fail(ctx, GBFMM_ENOMEM, "adaptive pre-split sources");
+                    return fail_joined(GBFMM_ENOMEM, "adaptive pre-split sources");
                 ps = A.presplit.p;
                 launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s);
             } else {
