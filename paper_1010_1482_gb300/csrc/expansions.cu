@@ -732,42 +732,66 @@ struct M2PFold {
 
 GB_HD constexpr int nm_idx(int N, int m) { return N * (N + 1) / 2 + m; }
 
-// the block stages the cell's coefficients M[P^2] (coalesced) in sM, then threads t, t + nt,
-// ... fill F[2 NM]; the square roots of the integer products (exact in FP32) are taken in place,
-// so the lanes read no table at lane-dependent addresses
+// per (N, m) of the folded coefficients: where its four source coefficients sit in M (re and im
+// index each, -1 for none) and their factors; built once per CTA by m2p_fold_table
 template <int P>
-GB_DEV void m2p_fold(const float *__restrict__ M, float *__restrict__ sM, float4 *__restrict__ F, int t, int nt)
+struct M2PFoldTab {
+    int4 re, im;   // source coefficient of {phi, dz, A, B}: real / imaginary part index, -1: zero
+    float4 c;      // factors of {phi, dz, A, B}
+};
+
+template <int P>
+GB_DEV void m2p_fold_table(M2PFoldTab<P> *__restrict__ T, int t, int nt)
 {
-    for (int k = t; k < P * P; k += nt) sM[k] = M[k];
-    __syncthreads();
+    auto root = [](int a, int b) { return sqrtf((float)(a * b)); };
     for (int q = t; q < M2PFold<P>::NM; q += nt) {
         int N = 0;
         while ((N + 1) * (N + 2) / 2 <= q) ++N;
         const int m = q - N * (N + 1) / 2;
         const float w = m > 0 ? 2.f : 1.f;
-        auto cre = [&](int n, int k) { return sM[re_idx(n, k)]; };
-        auto cim = [&](int n, int k) { return k > 0 ? sM[im_idx(n, k)] : 0.f; };
-        auto root = [](int a, int b) { return sqrtf((float)(a * b)); };
-        float pr = 0.f, pi = 0.f, zr = 0.f, zi = 0.f, ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+        M2PFoldTab<P> e;
+        e.re = make_int4(-1, -1, -1, -1);
+        e.im = make_int4(-1, -1, -1, -1);
+        e.c = make_float4(0.f, 0.f, 0.f, 0.f);
         if (N <= P - 1) {
-            pr = w * cre(N, m);
-            pi = w * cim(N, m);
+            e.re.x = re_idx(N, m);
+            e.im.x = m > 0 ? im_idx(N, m) : -1;
+            e.c.x = w;
         }
         if (N >= 1 && m <= N - 1) {
-            const float c = -w * root(N - m, N + m);
-            zr = c * cre(N - 1, m);
-            zi = c * cim(N - 1, m);
+            e.re.y = re_idx(N - 1, m);
+            e.im.y = m > 0 ? im_idx(N - 1, m) : -1;
+            e.c.y = -w * root(N - m, N + m);
         }
         if (N >= 1 && m >= 1) {
-            const float c = root(N + m, N + m - 1);
-            ar = c * cre(N - 1, m - 1);
-            ai = c * cim(N - 1, m - 1);
+            e.re.z = re_idx(N - 1, m - 1);
+            e.im.z = m - 1 > 0 ? im_idx(N - 1, m - 1) : -1;
+            e.c.z = root(N + m, N + m - 1);
         }
         if (N >= 1 && m + 1 <= N - 1) {
-            const float c = root(N - m, N - m - 1);
-            br = c * cre(N - 1, m + 1);
-            bi = c * cim(N - 1, m + 1);
+            e.re.w = re_idx(N - 1, m + 1);
+            e.im.w = im_idx(N - 1, m + 1);
+            e.c.w = root(N - m, N - m - 1);
         }
+        T[q] = e;
+    }
+}
+
+// the block stages the cell's coefficients M[P^2] (coalesced) in sM, then threads t, t + nt,
+// ... fill F[2 NM] through the table
+template <int P>
+GB_DEV void m2p_fold(const float *__restrict__ M, float *__restrict__ sM, const M2PFoldTab<P> *__restrict__ T,
+                     float4 *__restrict__ F, int t, int nt)
+{
+    for (int k = t; k < P * P; k += nt) sM[k] = M[k];
+    __syncthreads();
+    auto at = [&](int k) { return k >= 0 ? sM[k] : 0.f; };
+    for (int q = t; q < M2PFold<P>::NM; q += nt) {
+        const M2PFoldTab<P> e = T[q];
+        const float pr = e.c.x * at(e.re.x), pi = e.c.x * at(e.im.x);
+        const float zr = e.c.y * at(e.re.y), zi = e.c.y * at(e.im.y);
+        const float ar = e.c.z * at(e.re.z), ai = e.c.z * at(e.im.z);
+        const float br = e.c.w * at(e.re.w), bi = e.c.w * at(e.im.w);
         F[2 * q] = make_float4(pr, pi, zr, zi);
         F[2 * q + 1] = make_float4(ar - br, ai - bi, ar + br, ai + bi);
     }
@@ -828,6 +852,8 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ ge
 {
     __shared__ float4 sF[2 * M2PFold<P>::NM];
     __shared__ float sM[P * P];
+    __shared__ M2PFoldTab<P> sT[M2PFold<P>::NM];
+    m2p_fold_table<P>(sT, threadIdx.x, blockDim.x);  // read after the first fold's barrier
     const int64_t leaf = blockIdx.x;
     const int64_t g = level_offset(L) + leaf;
     const int b0 = begin[g], e0 = end[g];
@@ -842,7 +868,7 @@ __global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ ge
             for (uint32_t e = m2l_offs[a]; e < m2l_offs[a + 1]; ++e) {
                 const int64_t s = m2l_ids[e];
                 __syncthreads();
-                m2p_fold<P>(M + s * (P * P), sM, sF, threadIdx.x, blockDim.x);
+                m2p_fold<P>(M + s * (P * P), sM, sT, sF, threadIdx.x, blockDim.x);
                 __syncthreads();
                 const CellGeom cg = geo_level_cell(geo, l, (uint32_t)(s - level_offset(l)));
                 if (act)
@@ -989,9 +1015,11 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
 {
     __shared__ float4 sF[2 * M2PFold<P>::NM];
     __shared__ float sM[P * P];
+    __shared__ M2PFoldTab<P> sT[M2PFold<P>::NM];
     const int32_t b = leaves[blockIdx.x];
     const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
     if (e0 == e1) return;
+    m2p_fold_table<P>(sT, threadIdx.x, blockDim.x);  // read after the first fold's barrier
     const int b0 = begin[b], bend = begin[b] + count[b];
     for (int t0 = b0; t0 < bend; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
@@ -1001,7 +1029,7 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
         for (uint32_t e = e0; e < e1; ++e) {
             const int32_t sc = w_ids[e];
             __syncthreads();
-            m2p_fold<P>(M + (int64_t)sc * (P * P), sM, sF, threadIdx.x, blockDim.x);
+            m2p_fold<P>(M + (int64_t)sc * (P * P), sM, sT, sF, threadIdx.x, blockDim.x);
             __syncthreads();
             const CellGeom cg = geo_cell(geom, sc);
             if (act)
