@@ -22,7 +22,7 @@
  * paper cites for its translation operators (Section "Overview of Advanced
  * Techniques").
  *
- * Readings taken where the paper is silent or garbled (each also in the design doc):
+ * Readings taken where the paper is silent or garbled:
  *   - Eq. 8 prints (2m-1)!; the Legendre recurrence needs the double factorial
  *     (2m-1)!! -- used here, with the Condon-Shortley phase (-1)^m.
  *   - Eq. 4 carries (-1)^j in the denominator; that is the textbook M2L for the
