@@ -268,17 +268,26 @@ int gbfmm_last_launch_count(const gbfmm_ctx *ctx, int64_t *count);
  *   d_sorted_xyzq       device, 4*n floats, 16-byte aligned: particles in sorted order
  *   d_perm              device, n uint32: original index of each sorted position
  *   d_sorted_leaf_keys  device, n uint32: depth-L Morton key of each sorted position
- * These equal what gbfmm_export_tree reports after gbfmm_evaluate with the same prm.
+ *   d_status            device, one int32, or NULL: cleared by the call, then raised by its
+ *                       kernels -- bit 0 (value 1) a non-finite coordinate was seen (it is
+ *                       clamped into a boundary cell), bit 1 (value 2) a bounded device wait
+ *                       gave up (the outputs are then invalid).  Read it after the stream
+ *                       completes.  With NULL these conditions are not reported.
+ * The outputs equal what gbfmm_export_tree reports after gbfmm_evaluate with the same prm.
+ * No two of the five buffers may share a byte (EINVAL otherwise).
+ * Uniform tree only (prm->tree == GBFMM_TREE_UNIFORM; EUNSUPPORTED otherwise, before any
+ * launch): its keys have 3L <= 30 bits.
  * Scratch: one static device array (about 8.4 MB) per GPU that loads the library, held
  * until the process exits; n is limited to 1,048,576 (EUNSUPPORTED beyond).  The first call
  * on a device looks the array's address up (cudaGetSymbolAddress) with that device current:
- * make that first call before any stream capture.  Every call clears the scratch words that
- * must start at zero; calls that overlap on the GPU share the array and race.  Non-finite
- * coordinates are not reported (they are clamped into boundary cells).  Asynchronous on
- * `stream`; EINVAL / EUNSUPPORTED / ECUDA.
+ * make that first call before any stream capture.  The address is cached for the life of the
+ * process: calls after cudaDeviceReset on that device are not supported.  Every call clears
+ * the scratch words that must start at zero; calls that overlap on the GPU share the array
+ * and race.  n = 0 returns OK without work (d_status untouched).  Asynchronous on `stream`;
+ * EINVAL / EUNSUPPORTED / ECUDA.
  */
 int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_sorted_xyzq, uint32_t *d_perm,
-                      uint32_t *d_sorted_leaf_keys, void *stream);
+                      uint32_t *d_sorted_leaf_keys, int32_t *d_status, void *stream);
 
 /*
  * Multi-instance engine: batched evaluation of many independent particle sets and a served

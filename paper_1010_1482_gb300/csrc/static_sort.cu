@@ -11,10 +11,14 @@
 //
 // The array's name is only a host-side stand-in in host code, so its device address is looked
 // up with cudaGetSymbolAddress once per device (with that device current) on the first call
-// there; that first call should therefore come before any stream capture.  All calls share
-// the one array and it keeps the last call's contents: the completion counter and the status
-// word are cleared at the start of every call, and calls that overlap on the GPU (two streams,
-// or two host threads) race on the array.
+// there; that first call should therefore come before any stream capture.  The address is
+// cached for the life of the process, so calls after cudaDeviceReset on that device are not
+// supported.  All calls share the one array and it keeps the last call's contents: the
+// completion counter and the status word are cleared at the start of every call, and calls
+// that overlap on the GPU (two streams, or two host threads) race on the array.
+//
+// Only the uniform tree's keys (3L <= 30 bits, at most 4 radix passes of 8 bits) fit the
+// array; the adaptive tree's 63-bit keys are refused before anything is launched.
 #include "common.cuh"
 #include "gbfmm.h"
 
@@ -46,18 +50,42 @@ unsigned char *g_addr[kMaxDevices] = {};
 
 using namespace gbfmm;
 
+namespace {
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+}  // namespace
+
 extern "C" int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_sorted_xyzq,
-                                 uint32_t *d_perm, uint32_t *d_sorted_leaf_keys, void *stream)
+                                 uint32_t *d_perm, uint32_t *d_sorted_leaf_keys, int32_t *d_status, void *stream)
 {
     if (!prm || n < 0) return GBFMM_EINVAL;
     if (n > kStaticSortMaxN) return GBFMM_EUNSUPPORTED;
     int32_t L = 0;
     int rc = gbfmm_plan(prm, n, &L, nullptr);
     if (rc != GBFMM_OK) return rc;
+    // the static array holds the 32-bit leaf keys of the uniform tree only
+    if (prm->tree != GBFMM_TREE_UNIFORM) return GBFMM_EUNSUPPORTED;
+    if (L < 0 || 3 * L > 30 || kSsHist + sort_scratch_bytes(n, 3 * L) > kStaticSortBytes) return GBFMM_EUNSUPPORTED;
     if (n == 0) return GBFMM_OK;
     if (!d_xyzq || !d_sorted_xyzq || !d_perm || !d_sorted_leaf_keys) return GBFMM_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 || reinterpret_cast<uintptr_t>(d_sorted_xyzq) % 16)
         return GBFMM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_perm) % 4 || reinterpret_cast<uintptr_t>(d_sorted_leaf_keys) % 4 ||
+        reinterpret_cast<uintptr_t>(d_status) % 4)
+        return GBFMM_EINVAL;
+    {
+        // every output is written while the input (and the other outputs, used as ping-pong
+        // buffers) are read: no two of them may share a byte
+        const size_t b16 = 16 * (size_t)n, b4 = 4 * (size_t)n;
+        const void *ptr[5] = {d_xyzq, d_sorted_xyzq, d_perm, d_sorted_leaf_keys, d_status};
+        const size_t len[5] = {b16, b16, b4, b4, d_status ? sizeof(int32_t) : 0};
+        for (int i = 0; i < 5; ++i)
+            for (int j = i + 1; j < 5; ++j)
+                if (len[i] && len[j] && overlaps(ptr[i], len[i], ptr[j], len[j])) return GBFMM_EINVAL;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GBFMM_ECUDA;
     unsigned char *base;
@@ -73,8 +101,11 @@ extern "C" int gbfmm_sort_static(const gbfmm_params *prm, int64_t n, const float
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Box *box = reinterpret_cast<Box *>(base + kSsBox);
     unsigned *counter = reinterpret_cast<unsigned *>(base + kSsCounter);
-    int *status = reinterpret_cast<int *>(base + kSsStatus);
+    // the status word the kernels raise: the caller's when given (so that it can be read
+    // back), else the one in the static array
+    int *status = d_status ? reinterpret_cast<int *>(d_status) : reinterpret_cast<int *>(base + kSsStatus);
     if (cudaMemsetAsync(base + kSsCounter, 0, 512, s) != cudaSuccess) return GBFMM_ECUDA;  // counter, status
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return GBFMM_ECUDA;
     const int passes = (3 * L + 7) / 8;
     // the sort ends in its first buffer pair after an even number of passes: start there with
     // the caller's outputs so the result lands in them

@@ -86,7 +86,7 @@ def lib():
         "gbfmm_export_adaptive_tree": (i, [P, P, ctypes.POINTER(i64), P, P, P, P, P, P]),
         "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
-        "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P]),
+        "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P, P]),
         "gbfmm_probe_peak": (i, [i, ctypes.POINTER(ctypes.c_double)]),
         "gbfmm_selftest_wait": (i, [P, ctypes.c_double, P]),
         "gbfmm_engine_create": (i, [ctypes.POINTER(P), i, ctypes.c_int32, ctypes.c_size_t]),
@@ -275,11 +275,16 @@ def gbfmm_probe_peak(kind: int) -> float:
 
 
 def gbfmm_sort_static(prm: gbfmm_params, xyzq: torch.Tensor, sorted_xyzq: torch.Tensor, perm: torch.Tensor,
-                      sorted_leaf_keys: torch.Tensor, stream=None) -> None:
-    """Allocation-free Morton sort (library-owned static scratch; see include/gbfmm.h)."""
+                      sorted_leaf_keys: torch.Tensor, status: torch.Tensor = None, stream=None) -> None:
+    """Allocation-free Morton sort (library-owned static scratch; see include/gbfmm.h).
+
+    `status`, if given, is a one-element int32 device tensor the call clears and its kernels
+    raise (1: non-finite coordinate, 2: a bounded wait gave up)."""
     assert perm.dtype == torch.int32 and sorted_leaf_keys.dtype == torch.int32  # uint32 bit patterns
+    assert status is None or (status.dtype == torch.int32 and status.numel() >= 1)
     _check(None, lib().gbfmm_sort_static(ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _ptr(sorted_xyzq),
-                                         _ptr(perm), _ptr(sorted_leaf_keys), _stream(stream)))
+                                         _ptr(perm), _ptr(sorted_leaf_keys),
+                                         _ptr(status), _stream(stream)))
 
 
 def gbfmm_engine_create(device: int = 0, workers: int = 4, memory_budget_bytes: int = 40 << 30):

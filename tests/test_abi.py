@@ -80,3 +80,23 @@ def test_header_constants_match_binding():
     for name, value in consts.items():
         py = name if (name == "GBFMM_OK" or name.startswith("GBFMM_E")) else name[len("GBFMM_"):]
         assert getattr(G, py) == value, name
+
+
+def test_sort_static_rejects_before_any_launch(lib):
+    """The allocation-free sort refuses, on the host and before any CUDA call, what its static
+    scratch cannot hold (the adaptive tree's 63-bit keys, n > 2^20) and outputs that share
+    bytes with its input or with each other.  The pointers are never dereferenced."""
+    P = ctypes.c_void_p
+    f = lib.gbfmm_sort_static
+    n = 4096
+    a, b, c, d, s = 1 << 20, 2 << 20, 3 << 20, 4 << 20, 5 << 20  # disjoint, aligned, never touched
+    adaptive = G.gbfmm_default_params(p=4, leaf_size=64, tree=G.TREE_ADAPTIVE)
+    assert f(ctypes.byref(adaptive), n, P(a), P(b), P(c), P(d), P(s), None) == G.GBFMM_EUNSUPPORTED
+    uniform = G.gbfmm_default_params(p=4, leaf_size=64)
+    assert f(ctypes.byref(uniform), (1 << 20) + 1, P(a), P(b), P(c), P(d), None, None) == G.GBFMM_EUNSUPPORTED
+    for bad in [(a, a, c, d, s), (a, a + 16 * n - 16, c, d, s), (a, b, c, c, s), (a, b, c, d, d + 8),
+                (a, b, a + 64, d, s), (a, b, c, b + 4 * n, s)]:
+        assert f(ctypes.byref(uniform), n, *map(P, bad), None) == G.GBFMM_EINVAL, bad
+    assert f(ctypes.byref(uniform), n, P(a), P(b), P(c + 2), P(d), None, None) == G.GBFMM_EINVAL  # misaligned
+    assert f(None, n, P(a), P(b), P(c), P(d), None, None) == G.GBFMM_EINVAL
+    assert f(ctypes.byref(uniform), -1, P(a), P(b), P(c), P(d), None, None) == G.GBFMM_EINVAL
