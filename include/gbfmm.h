@@ -77,6 +77,11 @@ enum {
  * caller's stream (event waits only, so stream capture sees one graph); the output is the same
  * bit for bit. */
 #define GBFMM_FLAG_SERIAL 4
+/* uniform tree: run the M2L as the list-based tensor-core kernel of the adaptive tree (128
+ * target cells per CTA, sources gathered through the M2L list) instead of the default block
+ * form (one dense GEMM per parent offset over all parents of a level).  Same Eq. 4, same
+ * precision scheme; they differ by rounding only. */
+#define GBFMM_FLAG_M2L_GATHERED 8
 
 /*
  * Parameters of one evaluation (Section "Fast N-body simulation").

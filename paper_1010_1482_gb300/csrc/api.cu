@@ -170,9 +170,10 @@ Layout make_layout(int64_t n, int L, int P)
     lo.m2l_code = take(2 * (size_t)(189 * C2 + 1));
     lo.M = take(4 * (size_t)C * P * P);
     lo.Lc = take(4 * (size_t)C * P * P);
-    lo.cscale = take((size_t)C);
+    lo.cscale = take(std::max((size_t)C, m2l_blk_scale_bytes(L)));
     lo.geo = take(4 * geo_floats(L));
-    lo.presplit = take(presplit_bytes(P, C));
+    lo.presplit = take(std::max(presplit_bytes(P, C), m2l_blk_presplit_bytes(P, L)));
+    lo.lpart = take(m2l_blk_part_bytes(P, L));
     lo.total = off;
     return lo;
 }
@@ -211,6 +212,20 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     c.P = P;
     c.built = true;
     *built_now = true;
+    return GBFMM_OK;
+}
+
+// the block operators of the uniform tree's M2L (built on the stream at first use of order P)
+static int ensure_blk(gbfmm_ctx *ctx, int P, cudaStream_t s)
+{
+    OpsCache &c = ctx->ops[order_slot(P)];
+    if (c.m2l_blk) return GBFMM_OK;
+    cudaError_t e = cudaMalloc(&c.m2l_blk, m2l_blk_table_bytes(P));
+    if (e != cudaSuccess) {
+        c.m2l_blk = nullptr;
+        return cuda_fail(ctx, e, "cudaMalloc(m2l block operators)");
+    }
+    launch_build_m2l_blk(P, c.m2l, c.m2l_blk, s);
     return GBFMM_OK;
 }
 
@@ -292,6 +307,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
         cudaFree(c.l2l);
         cudaFree(c.m2l_tc);
         cudaFree(c.m2l_f16);
+        cudaFree(c.m2l_blk);
     }
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
@@ -435,7 +451,17 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     mark(5);
     if (L >= 2) {
         const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
-        if (prm->method == GBFMM_METHOD_FMM && ops.m2l_f16 && !cores) {
+        const bool gathered = (prm->flags & GBFMM_FLAG_M2L_GATHERED) != 0;
+        if (prm->method == GBFMM_METHOD_FMM && !cores && !gathered) {
+            rc = ensure_blk(ctx, P, s);
+            if (rc != GBFMM_OK) return rc;
+            int8_t *pscale = at<int8_t>(ws, lo.cscale);
+            void *ps = at<void>(ws, lo.presplit);
+            launch_blk_presplit(P, L, begin, end, M, ps, pscale, s);
+            if (launch_m2l_blk(P, L, begin, end, ps, pscale, ops.m2l_blk, Lc, at<float>(ws, lo.lpart), ctx->d_status,
+                               s, fork ? sm_count() : 0) != 0)
+                return fail(ctx, GBFMM_ECUDA, "TMA tensor map encoding failed");
+        } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_f16 && !cores) {
             int8_t *cscale = at<int8_t>(ws, lo.cscale);
             void *ps = nullptr;
             if (m2l_f16_presplit(P)) {  // sources split once per cell

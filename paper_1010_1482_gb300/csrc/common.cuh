@@ -195,7 +195,8 @@ struct Layout {
     size_t M, Lc;
     size_t cscale;  // int8 per cell: power-of-two scale of the FP16 tensor-core M2L
     size_t geo;       // float: cell geometry table per level and axis (geo_floats(L))
-    size_t presplit;  // FP16 pre-split source rows of the gathered tensor-core M2L
+    size_t presplit;  // FP16 pre-split source rows of the tensor-core M2L (gathered or block form)
+    size_t lpart;     // block M2L of small trees: partial local expansions of the offset ranges
     size_t total;
 };
 
@@ -315,6 +316,21 @@ void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float
 void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);
+
+// m2l_blk.cu: the uniform tree's M2L as one dense GEMM per parent offset on the tensor cores
+size_t m2l_blk_table_bytes(int P);
+void launch_build_m2l_blk(int P, const float *ops, void *table, cudaStream_t s);
+size_t m2l_blk_presplit_bytes(int P, int L);
+size_t m2l_blk_scale_bytes(int L);
+void launch_blk_presplit(int P, int L, const int32_t *begin, const int32_t *end, const float *M, void *presplit,
+                         int8_t *pscale, cudaStream_t s);
+// small trees split the 26 parent offsets over several CTAs per tile; their partial sums take
+// m2l_blk_part_bytes of workspace and are added in a fixed order
+int m2l_blk_ksplit(int P, int L);
+size_t m2l_blk_part_bytes(int P, int L);
+// -1 if the TMA tensor maps cannot be encoded (nothing launched)
+int launch_m2l_blk(int P, int L, const int32_t *begin, const int32_t *end, const void *presplit, const int8_t *pscale,
+                   const void *table, float *Lc, float *Lpart, int *status, cudaStream_t s, int max_ctas);
 
 // p2p.cu
 // P2P without the far field: the compensated near-field sums of every particle in sorted order,

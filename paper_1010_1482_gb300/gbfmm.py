@@ -25,6 +25,7 @@ LIST_P2P, LIST_M2L, LIST_U, LIST_V, LIST_W, LIST_X = range(6)
 FLAG_STAGE_TIMING = 1
 FLAG_M2L_CUDA_CORES = 2
 FLAG_SERIAL = 4
+FLAG_M2L_GATHERED = 8
 STAGES = ["box+keys", "sort", "cells+lists", "P2M", "M2M", "M2L/M2P", "L2L", "L2P", "P2P", "operators"]
 
 

@@ -162,18 +162,44 @@ def test_fmm_matches_oracle(G, ctx, p):
 
 @pytest.mark.parametrize("p", [4, 6, 8, 10])
 def test_m2l_tensor_cores_and_cuda_cores_agree(G, ctx, p):
-    """The tcgen05 M2L (3xTF32, the default) and the FP32 CUDA-core M2L compute Eq. 4 over the
-    same lists: both match the oracle, and each other to rounding."""
+    """The three M2L forms compute Eq. 4 over the same admissible pairs: the block form (one
+    GEMM per parent offset on the tensor cores, the default; at this size the offsets are split
+    over several CTAs per tile), the list-based tensor-core kernel (FLAG_M2L_GATHERED) and the
+    FP32 CUDA-core kernel.  All match the oracle, and each other to rounding."""
     n, leaf = 30000, 16
     x = inputs.uniform_cube(n, 123 + p)
-    tc, L = run(G, ctx, x, p=p, leaf_size=leaf)
+    blk, L = run(G, ctx, x, p=p, leaf_size=leaf)
+    gat, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_GATHERED)
     cc, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_CUDA_CORES)
     assert L == 4
     ref = O.fmm(x, p, leaf)["out"]
-    for out in (tc, cc):
+    for out in (blk, gat, cc):
         assert O.rel_l2(out[:, 0], ref[:, 0]) <= TOL_FMM
         assert O.rel_l2(out[:, 1:], ref[:, 1:]) <= TOL_FMM
-    assert O.rel_l2(tc, cc) <= 5e-6
+    assert O.rel_l2(blk, cc) <= 5e-6
+    assert O.rel_l2(gat, cc) <= 5e-6
+
+
+@pytest.mark.parametrize("p,n,leaf", [(8, 40000, 8), (10, 30000, 16), (4, 5000, 64), (6, 300000, 64)])
+def test_m2l_block_local_expansions(G, ctx, p, n, leaf):
+    """Local expansions after the M2L and L2L of the block form against the FP32 CUDA-core M2L,
+    level by level (relative L2 of the scaled coefficients).  The cases split the 26 parent
+    offsets over 4 (depth 5) and 13 or 26 (depths 3 and 4) CTAs per tile; every tree has level 2
+    (one 2 x 2 x 2 parent box, 8 of the 128 MMA rows used) and level 3 (a 4 x 4 x 4 box)."""
+    x = inputs.uniform_cube(n, 4242 + p)
+    _, L = run(G, ctx, x, p=p, leaf_size=leaf)
+    C = O.level_offset(L + 1)
+    Lb = G.gbfmm_export_expansions(ctx, 1, C, p)
+    _, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_CUDA_CORES)
+    Lcc = G.gbfmm_export_expansions(ctx, 1, C, p)
+    side = float(np.max(x[:, :3].max(0).astype(np.float64) - x[:, :3].min(0)))
+    deg = np.concatenate([np.full(k + 1, k) for k in range(p)])  # degree of each complex coefficient
+    for l in range(2, L + 1):
+        sl = slice(O.level_offset(l), O.level_offset(l + 1))
+        sc = (side / 2**l) ** (deg + 1.0)  # the scaled coefficients h^(n+1) L_n^m
+        num = np.linalg.norm((Lb[sl] - Lcc[sl]) * sc)
+        den = np.linalg.norm(Lcc[sl] * sc)
+        assert num <= 1e-5 * den, (l, num / den)
 
 
 def test_fmm_clustered_input(G, ctx):
