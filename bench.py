@@ -32,8 +32,8 @@ from paper_1010_1482_gb300 import inputs  # noqa: E402
 METRIC = "FMM particles/s at rel L2 err<=1e-4 on 1 GB300; served p50/p99 latency"
 UNIT = "particles/s"
 L2_FLUSH_BYTES = 256 << 20
-REF_SAMPLE_N = 16384       # oracle step: same distribution, p and mean leaf occupancy (32), depth 3
-CPU_BASELINE_N = 131072    # cpu_baseline sample: same distribution, p and mean leaf occupancy, depth 4
+CPU_SAMPLE_N = 131072      # oracle sample (reference arm and cpu_baseline): same distribution, p and mean leaf occupancy, depth 4
+CPU_ONE_CORE_N = 16384     # single-thread oracle sample (the paper's one-core CPU convention), depth 3
 ERROR_TARGETS = 4096
 
 
@@ -64,17 +64,6 @@ def max_over_ranks(value: float, device) -> float:
 def job_rate(n_per_rank: int, world: int, total_ms: float, steps: int) -> float:
     """Whole-job particles/s: every rank's particles over the slowest rank's time per step."""
     return n_per_rank * world / (total_ms / steps / 1e3)
-
-
-def tf32_peak_tflops() -> tuple[float, str]:
-    """Dense TF32 tensor peak: the measured BF16 dense burst figure x the nominal TF32/BF16
-    ratio (1.1 / 2.25 PFLOP/s)."""
-    try:
-        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        bf16 = float(mp["bf16_tflops"])
-        return bf16 * 1.1 / 2.25, f"measured BF16 dense burst {bf16:.1f} TFLOP/s x nominal TF32/BF16 1.1/2.25 (of measured)"
-    except Exception:
-        return 1900.0 * 1.1 / 2.25, "fallback BF16 1900 TFLOP/s x nominal TF32/BF16 1.1/2.25 (of fallback)"
 
 
 def fp32_peak_tflops(sm_count: int) -> tuple[float, float]:
@@ -177,27 +166,51 @@ def oracle_sample_text(oracle, n_sample, w):
             f"32 as in the full workload)")
 
 
+def oracle_one_thread(w) -> dict:
+    """The oracle FMM on one host thread (the paper's single-core CPU convention), in a fresh
+    interpreter with OMP_NUM_THREADS=1 (OpenMP reads it at start-up)."""
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import oracle\n"
+        "from paper_1010_1482_gb300 import inputs\n"
+        "w = inputs.workload(%r)\n"
+        "x = inputs.make_particles(%d, w['dist'], w['seed'])\n"
+        "t0 = time.perf_counter()\n"
+        "(oracle.fmm_adaptive(x, w['p'], w['leaf_size']) if w['tree'] == 'adaptive' else oracle.fmm(x, w['p'], w['leaf_size']))\n"
+        "print(json.dumps({'dt': time.perf_counter() - t0, 'threads': oracle.threads()}))\n"
+    ) % (ROOT, w["name"], CPU_ONE_CORE_N)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the GPU line stands without it
+        return {"error": str(e)[:200]}
+    return {"value": CPU_ONE_CORE_N / d["dt"], "unit": UNIT, "cores": d["threads"],
+            "sample": f"oracle FP64 FMM of {CPU_ONE_CORE_N} particles of the same distribution, p={w['p']}, "
+                      f"leaf {w['leaf_size']}, one thread, {d['dt']:.1f} s"}
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
 
-    x = inputs.make_particles(REF_SAMPLE_N, w["dist"], w["seed"])
+    x = inputs.make_particles(CPU_SAMPLE_N, w["dist"], w["seed"])
     for _ in range(args.warmup):
         oracle_fmm(oracle, x, w)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle_fmm(oracle, x, w)
     dt = time.perf_counter() - t0
-    value = REF_SAMPLE_N * args.steps / dt
-    sample = oracle_sample_text(oracle, REF_SAMPLE_N, w) + " per step"
+    value = CPU_SAMPLE_N * args.steps / dt
+    sample = oracle_sample_text(oracle, CPU_SAMPLE_N, w) + " per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "leaf_size": w["leaf_size"],
-                   "distribution": w["dist"], "sample_n": REF_SAMPLE_N},
+                   "distribution": w["dist"], "sample_n": CPU_SAMPLE_N},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -360,52 +373,55 @@ def run_gpu(args, w):
     m2l_ms = stages.get("M2L/M2P", float("nan"))
     m2l_tf = m2l_flops / (m2l_ms / 1e3) / 1e12
     p2p_tf = p2p_flops / (stages["P2P"] / 1e3) / 1e12
-    tc_mode = int(os.environ.get("GBFMM_M2L_TC", "2"))
-    if tc_mode in (1, 2, 3, 4):
-        # tcgen05 M2L: 128 targets per tile (MMA M), N = p^2 padded to 16, K = p^2 padded to the
-        # MMA's K step (8 for TF32, 16 for FP16), 3 MMAs per product (hi*hi + lo*hi + hi*lo)
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        tpeak, tbasis = bf16, f"measured BF16 dense burst {bf16:.1f} TFLOP/s (FP16 dense has the same nominal rate; of measured)"
+    except Exception:
+        tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if adaptive:
+        # list-based kernel: 128 targets per tile (MMA M), N = K = p^2 padded to 16, 189 offsets
+        # per tile, 3 MMAs per product (hi*hi + lo*hi + hi*lo)
         npad = -(-P * P // 16) * 16
-        if tc_mode >= 2:
-            kpad = npad
-            try:
-                bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
-                tpeak, tbasis = bf16, f"measured BF16 dense burst {bf16:.1f} TFLOP/s (FP16 dense has the same nominal rate; of measured)"
-            except Exception:
-                tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
-            kname = "k_m2l_f16s" if tc_mode == 2 else "k_m2l_f16"
-            ksrc, kprof, kdt = "m2l_f16.cu", f"{kname[2:]}_{w['name']}.md", "FP16"
-        else:
-            kpad = -(-P * P // 8) * 8
-            tpeak, tbasis = tf32_peak_tflops()
-            kname, ksrc, kprof, kdt = "k_m2l_tc", "m2l_tc.cu", f"m2l_tc_{w['name']}.md", "TF32"
-        tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * kpad
-        # the default (forked) evaluation launches the staged M2L one wave of one CTA per SM at a
-        # time; flop and DRAM traffic per launch are the evaluation's over that many launches
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        m2l_launches = -(-tiles // sms) if kname == "k_m2l_f16s" else 1
-        traffic = traffic_from_profile(ksrc, kprof)
-        roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
-                    "frac": m2l_tf / tpeak,
-                    "traffic": traffic,
-                    "launches_per_evaluation": m2l_launches,
-                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per evaluation, "
-                            f"{m2l_flops / m2l_launches:.4g} per launch ({m2l_launches} launches of <= {sms} tiles); "
-                            "achieved = flop / the launches' summed duration; traffic per launch (ncu, cold L2)",
-                    "peak_basis": tbasis,
-                    "tensor_flop_issued": tensor_flops,
-                    "tensor_pipe_frac": tensor_flops / (m2l_ms / 1e3) / 1e12 / tpeak,
-                    "achieved_alone": m2l_flops / (ser_stages["M2L/M2P"] / 1e3) / 1e12,
-                    "frac_alone": m2l_flops / (ser_stages["M2L/M2P"] / 1e3) / 1e12 / tpeak,
-                    "measured": "achieved: CUDA events around the M2L launches on their stream in the timed "
-                                "steps (P2P runs beside it on a second stream); alone: the serial evaluation",
-                    "note": f"FP32-accurate products as 3 {kdt} MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 by "
-                            "construction; tensor_pipe_frac counts every issued MMA flop"}
+        kname, ksrc, kprof = "k_m2l_f16s", "m2l_f16.cu", f"m2l_f16s_{w['name']}.md"
+        tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * npad
+        m2l_launches = -(-tiles // sms)
+        kshape = "128 target cells x p^2 (padded to 16) per MMA, 189 offsets per tile"
     else:
-        roofline = {"kernel": "k_m2l", "bound": "alu", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
-                    "frac": m2l_tf / peak,
-                    "traffic": traffic_from_profile("m2l.cu", f"m2l_{w['name']}.md"),
-                    "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per launch",
-                    "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"}
+        # block kernel: per tile 128 target parents (MMA M) x NT outputs (MMA N) over the 26 parent
+        # offsets, K = 8 p^2 per offset; 3 MMAs per product
+        nt = {4: 128, 6: 144, 8: 256, 10: 208}[P]
+        nstride = 200 if P == 10 else nt
+        kd = 8 * P * P
+        ntiles_n = -(-kd // nstride)
+        blk_tiles = sum(max(1, 8 ** (l - 1) // 128) * ntiles_n for l in range(2, L + 1))
+        ksplit = 1 if blk_tiles >= 152 else min(26, -(-304 // blk_tiles))
+        kname, ksrc, kprof = "k_m2l_blk", "m2l_blk.cu", f"m2l_blk_{w['name']}.md"
+        tensor_flops = blk_tiles * 26 * kd * 3 * 2 * 128 * nt
+        m2l_launches = -(-(blk_tiles * ksplit) // sms)
+        kshape = (f"{blk_tiles} tiles of 128 target parents x {nt} outputs (of 8p^2 = {kd}), K = {kd} per parent "
+                  f"offset, 26 offsets, offsets split over {ksplit} CTA(s) per tile")
+    traffic = traffic_from_profile(ksrc, kprof)
+    roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": m2l_tf / tpeak,
+                "traffic": traffic,
+                "launches_per_evaluation": m2l_launches,
+                "work": f"{m2l_pairs} M2L pairs x 2p^4 = {m2l_flops:.4g} flop per evaluation, "
+                        f"{m2l_flops / m2l_launches:.4g} per launch ({m2l_launches} launch(es) of <= {sms} CTAs); "
+                        "achieved = flop / the launches' summed duration",
+                "shape": kshape,
+                "peak_basis": tbasis,
+                "tensor_flop_issued": tensor_flops,
+                "tensor_pipe_frac": tensor_flops / (m2l_ms / 1e3) / 1e12 / tpeak,
+                "achieved_alone": m2l_flops / (ser_stages["M2L/M2P"] / 1e3) / 1e12,
+                "frac_alone": m2l_flops / (ser_stages["M2L/M2P"] / 1e3) / 1e12 / tpeak,
+                "tensor_pipe_frac_alone": tensor_flops / (ser_stages["M2L/M2P"] / 1e3) / 1e12 / tpeak,
+                "measured": "achieved: CUDA events around the M2L launches on their stream in the timed "
+                            "steps (P2P runs beside it on a second stream); alone: the serial evaluation",
+                "traffic_basis": "DRAM bytes per launch from the ncu capture in profiles/ (ncu starts each "
+                                 "launch from a cold L2); null if the kernel source changed since",
+                "note": "FP32-accurate products as 3 FP16 MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 by "
+                        "construction; tensor_pipe_frac counts every issued MMA flop"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -450,20 +466,28 @@ def run_gpu(args, w):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
 
-        xs = inputs.make_particles(CPU_BASELINE_N, w["dist"], w["seed"])
+        xs = inputs.make_particles(CPU_SAMPLE_N, w["dist"], w["seed"])
         t0 = time.perf_counter()
         oracle_fmm(oracle, xs, w)
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {
-            "value": CPU_BASELINE_N / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": oracle_sample_text(oracle, CPU_BASELINE_N, w) + f", {dt:.1f} s",
-        }
-        # accuracy of the timed result on seeded targets against the FP64 direct sum
+        # accuracy of the timed result on seeded targets against the FP64 direct sum (the O(N^2)
+        # oracle, timed: its full-N cost is extrapolated x N / targets)
         tg = inputs.sample_indices(n, ERROR_TARGETS, w["seed"])
+        t1 = time.perf_counter()
         ref = oracle.direct(x, targets=tg)
+        dt_direct = time.perf_counter() - t1
         got = out.cpu().numpy().astype(np.float64)[tg]
         line["error_vs_fp64_direct"] = {"targets": len(tg), "phi_rel_l2": oracle.rel_l2(got[:, 0], ref[:, 0]),
                                         "grad_rel_l2": oracle.rel_l2(got[:, 1:], ref[:, 1:])}
+        line["cpu_baseline"] = {
+            "value": CPU_SAMPLE_N / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": oracle_sample_text(oracle, CPU_SAMPLE_N, w) + f", {dt:.1f} s (the reference arm's sample)",
+            "one_core": oracle_one_thread(w),
+            "direct": {"value": n / (dt_direct * n / len(tg)), "unit": UNIT, "cores": oracle.threads(),
+                       "extrapolated": True,
+                       "sample": f"oracle FP64 O(N^2) direct sum: {len(tg)} seeded targets over all {n} sources in "
+                                 f"{dt_direct:.2f} s, full-N time extrapolated x N/{len(tg)}"},
+        }
     if rank == 0 and ws == 1 and not args.no_serving:
         line.update(run_next_rows(args, G, dev, local))
     if rank == 0:

@@ -66,10 +66,7 @@ enum {
 #define GBFMM_FLAG_STAGE_TIMING 1 /* record CUDA events between stages (gbfmm_stage_times) */
 /* run M2L on the FP32 CUDA cores instead of the tcgen05 tensor cores (FP16 operands split in
  * three products with FP32 accumulation; the default).  Both compute Eq. 4 over the same
- * lists; they differ by rounding only.  The environment variable GBFMM_M2L_TC, read once per
- * process, picks the tensor-core form: 2 = FP16 with the sources split once per cell and
- * staged through shared memory (default), 4 = FP16 with the sources converted in the kernel,
- * 1 = TF32, 0 = none (CUDA cores). */
+ * admissible pairs; they differ by rounding only. */
 #define GBFMM_FLAG_M2L_CUDA_CORES 2
 /* run every stage on the caller's stream, one after another.  By default an FMM evaluation
  * runs the near field (P2P, Listings 1-2) on a low-priority stream of the context while the

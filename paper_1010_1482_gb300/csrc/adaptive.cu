@@ -968,9 +968,8 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         std::vector<uint32_t> hcur(hcnt.size());
         std::vector<int4> tiles;
         const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
-        const bool f16 = ops.m2l_f16 != nullptr && !cores;
-        const bool tc = f16 || (ops.m2l_tc != nullptr && !cores);
-        const int TN = tc ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
+        const bool f16 = !cores;
+        const int TN = f16 ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
         uint32_t acc = 0;
         for (int l = maxl; l >= 2; --l)
             for (int tau = 0; tau < 8; ++tau) {
@@ -991,24 +990,15 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamSynchronize(s);  // the host tile vectors go out of scope
         if (f16) {
             if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail_joined(GBFMM_ENOMEM, "adaptive scales");
-            void *ps = nullptr;
-            if (m2l_f16_presplit(P)) {  // sources split once per cell
-                if (grow(A.presplit, presplit_bytes(P, ncells), false, 0, s))
-                    return fail_joined(GBFMM_ENOMEM, "adaptive pre-split sources");
-                ps = A.presplit.p;
-                launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s);
-            } else {
-                launch_cell_scale(M, ncells, P, A.cscale.as<int8_t>(), s);
-            }
+            if (grow(A.presplit, presplit_bytes(P, ncells), false, 0, s))
+                return fail_joined(GBFMM_ENOMEM, "adaptive pre-split sources");
+            void *ps = A.presplit.p;
+            launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s);  // sources split once per cell
             launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                  A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                                  A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc,
                                  ctx->d_status, s, fork ? sm_count() : 0);
-        } else if (tc)
-            launch_m2l_tc_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
-                                A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
-                                A.vcode.as<uint16_t>(), ops.m2l_tc, M, Lc, ctx->d_status, s);
-        else
+        } else
             launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                              A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                              A.vcode.as<uint16_t>(), ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);

@@ -16,7 +16,6 @@
 namespace gbfmm {
 void init_expansion_constants();
 void init_m2l_constants();
-void init_m2l_tc_constants();
 void init_m2l_f16_constants();
 }  // namespace gbfmm
 
@@ -200,15 +199,9 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     if ((e = cudaMalloc(&c.l2l, 8 * (size_t)P * P * PR * sizeof(float))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(l2l ops)");
     launch_build_operators(P, c.m2l, c.m2m, c.l2l, s);
-    if (m2l_tc_mode() == 1) {
-        if ((e = cudaMalloc(&c.m2l_tc, m2l_tc_table_floats(P) * sizeof(float))) != cudaSuccess)
-            return cuda_fail(ctx, e, "cudaMalloc(m2l tensor-core ops)");
-        launch_build_m2l_tc(P, c.m2l, c.m2l_tc, s);
-    } else if (m2l_tc_mode() >= 2) {
-        if ((e = cudaMalloc(&c.m2l_f16, m2l_f16_table_bytes(P))) != cudaSuccess)
-            return cuda_fail(ctx, e, "cudaMalloc(m2l FP16 tensor-core ops)");
-        launch_build_m2l_f16(P, c.m2l, c.m2l_f16, s);
-    }
+    if ((e = cudaMalloc(&c.m2l_f16, m2l_f16_table_bytes(P))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(m2l FP16 tensor-core ops)");
+    launch_build_m2l_f16(P, c.m2l, c.m2l_f16, s);
     c.P = P;
     c.built = true;
     *built_now = true;
@@ -280,7 +273,6 @@ int gbfmm_create(gbfmm_ctx **out, int device)
     if (ok) {
         init_expansion_constants();
         init_m2l_constants();
-        init_m2l_tc_constants();
         init_m2l_f16_constants();
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
@@ -305,7 +297,6 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
         cudaFree(c.m2l);
         cudaFree(c.m2m);
         cudaFree(c.l2l);
-        cudaFree(c.m2l_tc);
         cudaFree(c.m2l_f16);
         cudaFree(c.m2l_blk);
     }
@@ -461,20 +452,13 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
             if (launch_m2l_blk(P, L, begin, end, ps, pscale, ops.m2l_blk, Lc, at<float>(ws, lo.lpart), ctx->d_status,
                                s, fork ? sm_count() : 0) != 0)
                 return fail(ctx, GBFMM_ECUDA, "TMA tensor map encoding failed");
-        } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_f16 && !cores) {
+        } else if (prm->method == GBFMM_METHOD_FMM && !cores) {
             int8_t *cscale = at<int8_t>(ws, lo.cscale);
-            void *ps = nullptr;
-            if (m2l_f16_presplit(P)) {  // sources split once per cell
-                ps = at<void>(ws, lo.presplit);
-                launch_presplit(P, M, lo.ncells, cscale, ps, s);
-            } else {
-                launch_cell_scale(M, lo.ncells, P, cscale, s);
-            }
+            void *ps = at<void>(ws, lo.presplit);
+            launch_presplit(P, M, lo.ncells, cscale, ps, s);  // sources split once per cell
             launch_m2l_f16(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_f16, M, cscale, ps, Lc,
                            ctx->d_status, s, fork ? sm_count() : 0);
-        } else if (prm->method == GBFMM_METHOD_FMM && ops.m2l_tc && !cores)
-            launch_m2l_tc(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_tc, M, Lc, ctx->d_status, s);
-        else if (prm->method == GBFMM_METHOD_FMM)
+        } else if (prm->method == GBFMM_METHOD_FMM)
             launch_m2l(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
         else
             launch_m2p(P, L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far, s);

@@ -270,12 +270,8 @@ void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist
                       cudaStream_t s);
 // M2L on the tcgen05 tensor cores (3xTF32 or 3xF16), 128 targets per CTA
 constexpr int kM2LTcTargetsPerTile = 128;
-// 0 = FP32 CUDA cores, 1 = TF32 tensor cores, 2 = FP16 tensor cores (GBFMM_M2L_TC; default 2)
-int m2l_tc_mode();
-bool m2l_use_tc();
 size_t m2l_f16_table_bytes(int P);
 void launch_build_m2l_f16(int P, const float *ops, void *table, cudaStream_t s);
-void launch_cell_scale(const float *M, int64_t ncells, int P, int8_t *scale, cudaStream_t s);
 // max_ctas > 0: the tiles are launched max_ctas at a time (one wave of one CTA per SM), so that
 // no CTA of the M2L waits for an SM while a kernel on another stream (the near field) could use
 // the room left beside the running ones
@@ -289,19 +285,9 @@ void launch_m2l_f16_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *t
 // number of SMs of the current device (cached per process)
 int sm_count();
 // per cell: the FP16 scale s_c and the pre-split halves of M~_c 2^s_c (KP / 8 pieces of 8 hi
-// then 8 lo halves); m2l_f16_presplit(P): whether the FP16 M2L of order P takes them
-bool m2l_f16_presplit(int P);
+// then 8 lo halves), the sources of the list-based FP16 M2L
 size_t presplit_bytes(int P, int64_t ncells);
 void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s);
-size_t m2l_tc_table_floats(int P);
-void launch_build_m2l_tc(int P, const float *ops, float *tc, cudaStream_t s);
-void launch_m2l_tc(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
-                   const int32_t *m2l_ids, const uint16_t *m2l_code, const float *optc, const float *M, float *Lc,
-                   int *status, cudaStream_t s);
-void launch_m2l_tc_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
-                         const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
-                         const uint16_t *m2l_code, const float *optc, const float *M, float *Lc, int *status,
-                         cudaStream_t s);
 void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
                       cudaStream_t s);

@@ -18,8 +18,7 @@ constexpr int kAdaptiveMaxLevel = 21;  // 63-bit keys: 21 bits per axis
 struct OpsCache {
     int P = 0;
     float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
-    float *m2l_tc = nullptr;  // TF32 tensor-core operator blocks (hi | lo), tensor-core mode 1
-    void *m2l_f16 = nullptr;  // FP16 tensor-core operator blocks (hi | lo) + per-code scales, mode 2
+    void *m2l_f16 = nullptr;  // FP16 tensor-core operator blocks (hi | lo) + per-code scales (list-based M2L)
     void *m2l_blk = nullptr;  // uniform tree: per parent offset, the 8p^2 x 8p^2 FP16 blocks (hi | lo) + scale
     bool built = false;
 };

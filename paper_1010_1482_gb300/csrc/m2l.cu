@@ -318,35 +318,13 @@ void launch_m2l(int P, int L, const int32_t *begin, const int32_t *end, const ui
                 const float *zero_block, int *status, cudaStream_t s)
 {
     if (L < 2) return;
-    // tile shape (GBFMM_M2L_TILE): 0 = 64 targets x (4 rows x 8 targets per thread), 3 stages;
-    // 1 = 64 targets x (8 x 8), 3 stages; 2 = 32 targets x (4 x 8), 2 stages, 2 CTAs per SM
-    static const int variant = [] {
-        const char *e = getenv("GBFMM_M2L_TILE");
-        const int v = e ? atoi(e) : 0;
-        return (v >= 0 && v <= 2) ? v : 0;
-    }();
 #define GBFMM_M2L_ARGS L, begin, end, m2l_offs, m2l_ids, m2l_code, ops, M, Lc, zero_block, status, s
-    if (variant == 1) {
-        switch (P) {
-        case 4: launch_m2l_t<4, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 6: launch_m2l_t<6, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 8: launch_m2l_t<8, 64, 8, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 10: launch_m2l_t<10, 64, 8, 8, 3, 1>(GBFMM_M2L_ARGS); break;
-        }
-    } else if (variant == 2) {
-        switch (P) {
-        case 4: launch_m2l_t<4, 32, 4, 8, 4, 2>(GBFMM_M2L_ARGS); break;
-        case 6: launch_m2l_t<6, 32, 4, 8, 4, 2>(GBFMM_M2L_ARGS); break;
-        case 8: launch_m2l_t<8, 32, 4, 8, 3, 2>(GBFMM_M2L_ARGS); break;
-        case 10: launch_m2l_t<10, 32, 4, 8, 2, 2>(GBFMM_M2L_ARGS); break;
-        }
-    } else {
-        switch (P) {
-        case 4: launch_m2l_t<4, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 6: launch_m2l_t<6, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 8: launch_m2l_t<8, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
-        case 10: launch_m2l_t<10, 64, 4, 8, 3, 1>(GBFMM_M2L_ARGS); break;
-        }
+    // 64 targets per CTA, 4 operator rows x 8 targets per thread
+    switch (P) {
+    case 4: launch_m2l_t<4, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+    case 6: launch_m2l_t<6, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+    case 8: launch_m2l_t<8, 64, 4, 8, 4, 1>(GBFMM_M2L_ARGS); break;
+    case 10: launch_m2l_t<10, 64, 4, 8, 3, 1>(GBFMM_M2L_ARGS); break;
     }
 #undef GBFMM_M2L_ARGS
 }

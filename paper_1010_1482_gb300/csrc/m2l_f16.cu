@@ -1,8 +1,9 @@
-// M2L (Eq. 4) on the tcgen05 tensor cores with FP16 operands split in three products
-// ("3xF16"), FP32 accumulation.  Same contraction, tiling and pipeline as the TF32 kernel in
-// m2l_tc.cu (128 targets per CTA as the MMA's M, one offset's operator as B, the gathered
-// source expansions as A in TMEM, per-offset partials drained to FP32 registers); FP16 MMAs
-// run at twice the TF32 rate with K = 16 per instruction.
+// M2L (Eq. 4) over interaction lists on the tcgen05 tensor cores: the adaptive tree's V lists
+// (and the uniform tree's M2L lists with GBFMM_FLAG_M2L_GATHERED).  FP16 operands split in three
+// products ("3xF16"), FP32 accumulation.  A CTA takes 128 target cells of one level and one child
+// position tau (the MMA's M); they share the 189 admissible offsets, walked in stencil-code order:
+// D[128 x p^2] += A[128 x K] (the targets' gathered source expansions, in TMEM) . T_o^T (one
+// offset's operator, in shared memory); each offset's partial is drained to FP32 registers.
 //
 // Range: FP16 has a 5-bit exponent, so both operands are brought to a fixed magnitude by exact
 // power-of-two scales: each offset's operator by 2^g_o (max |T_o| -> 2^12, chosen when the
@@ -105,47 +106,14 @@ void launch_build_m2l_f16(int P, const float *ops, void *table, cudaStream_t s)
     note_launches(1);
 }
 
-// ---- per-cell source scale: s_c = 10 - e with max |M~_c| = f 2^e, f in [0.5, 1) ------------
-__global__ void k_cell_scale(const float *__restrict__ M, int64_t ncells, int PP, int8_t *__restrict__ scale)
-{
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
-    float m = 0.f;
-    for (int k = 0; k < PP; ++k) m = fmaxf(m, fabsf(M[c * PP + k]));
-    int ex = 0;
-    if (m > 0.f && m <= 3.0e38f) frexpf(m, &ex);  // non-finite or zero (empty cells): scale 0
-    int s = (m > 0.f && m <= 3.0e38f) ? 10 - ex : 0;
-    s = s < -100 ? -100 : (s > 100 ? 100 : s);
-    scale[c] = (int8_t)s;
-}
-
-void launch_cell_scale(const float *M, int64_t ncells, int P, int8_t *scale, cudaStream_t s)
-{
-    if (ncells <= 0) return;
-    k_cell_scale<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(M, ncells, P * P, scale);
-    note_launches(1);
-}
-
-// ---- the kernel -----------------------------------------------------------------------------
+// ---- shapes of the list-based kernel --------------------------------------------------------
 template <int P>
 struct F16Cfg {
     static constexpr int PP = P * P;
     static constexpr int KP = (PP + 15) / 16 * 16;   // K, padded to the MMA's K step (16)
     static constexpr int NP = (PP + 15) / 16 * 16;   // N
     static constexpr int KS = KP / 16;
-    static constexpr int NCH = (KS + 3) / 4;          // chunks of <= 4 K steps (64 halves)
-    static constexpr int TM = 128;
-    static constexpr int NSTAGE = 4;
-    static constexpr int TMEM_COLS = 512;
-    static constexpr int A_COL0 = 256;                // A stage: hi 32 columns | lo 32 columns (64 halves each)
-    static constexpr int NH = NP / 2;                 // output columns drained per thread
-    static constexpr int B_HALVES = 2 * NP * 64;      // one stage: B_hi | B_lo
-    static constexpr size_t kStageBytes = (size_t)NSTAGE * B_HALVES * 2;
-    static constexpr size_t kSmemBytes = kStageBytes > 116 * 1024 ? kStageBytes : 116 * 1024;
-    static constexpr int NTHREADS = 288;              // 8 converter warps (2 per TMEM lane quadrant), 1 MMA warp
-    static_assert(NP % 16 == 0 && NP <= 128 && NH % 8 == 0, "MMA N");
-    static_assert(A_COL0 + 64 * NSTAGE <= TMEM_COLS, "TMEM A stages");
-    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+    static_assert(NP % 16 == 0 && NP <= 128, "MMA N");
 };
 
 GB_DEV void chunk16(int c, int KS, int NCH, int &k0, int &kw)
@@ -160,275 +128,6 @@ struct F16Tiles {
     int tile0;  // tile of block 0 (a launch may cover a range of the tiles)
     int ntiles_level[kMaxLevel + 1];
 };
-
-template <int P>
-__global__ void __launch_bounds__(288, 1)
-    k_m2l_f16(F16Tiles tiles, const int4 *__restrict__ tdesc, const int32_t *__restrict__ tlist,
-              const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-              const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
-              const uint16_t *__restrict__ m2l_code, const __half *__restrict__ tab, const int *__restrict__ gexp,
-              const float *__restrict__ M, const int8_t *__restrict__ cscale, float *__restrict__ Lc, int *status)
-{
-    using C = F16Cfg<P>;
-    using T = F16Table<P>;
-    constexpr int PP = C::PP, NP = C::NP, NH = C::NH, TM = C::TM, NSTAGE = C::NSTAGE, NCH = C::NCH;
-    constexpr int S = 189 * NCH;
-    constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);  // F32 += F16 x F16
-    constexpr int kMmaWarp = 8;
-
-    extern __shared__ __align__(1024) unsigned char f16sm[];
-    __half *bstage = reinterpret_cast<__half *>(f16sm);
-    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], drain_full[2], drain_empty[2], done_bar;
-    __shared__ int s_issued[NSTAGE];
-    __shared__ uint32_t s_tmem;
-    __shared__ volatile int s_abort;
-
-    int tau;
-    int64_t q0 = 0, nq = 0, off = 0, tstart = 0;
-    int tcount = 0;
-    if (tdesc) {
-        const int4 d = tdesc[tiles.tile0 + blockIdx.x];
-        tau = d.y;
-        tstart = d.z;
-        tcount = d.w;
-    } else {
-        int rem = tiles.tile0 + blockIdx.x;
-        int l = tiles.L;
-        while (l >= 2 && rem >= tiles.ntiles_level[l]) {
-            rem -= tiles.ntiles_level[l];
-            --l;
-        }
-        if (l < 2) return;
-        nq = int64_t(1) << (3 * (l - 1));
-        const int64_t qtiles = (nq + TM - 1) / TM;
-        tau = (int)(rem / qtiles);
-        q0 = (rem % qtiles) * TM;
-        off = level_offset(l);
-    }
-    auto target = [&](int t) -> int64_t {
-        if (tdesc) return t < tcount ? (int64_t)tlist[tstart + t] : -1;
-        const int64_t q = q0 + t;
-        return q < nq ? off + 8 * q + tau : -1;
-    };
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) {
-        for (int st = 0; st < NSTAGE; ++st) {
-            mbar_init(&full_bar[st], 9);   // 8 converter warps + the operator copies' expect_tx
-            mbar_init(&empty_bar[st], 1);  // one tcgen05.commit
-            s_issued[st] = 0;
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&drain_full[b], 1);
-            mbar_init(&drain_empty[b], 8);
-        }
-        mbar_init(&done_bar, 1);
-        s_abort = 0;
-        fence_mbar_init();
-    }
-    if (warp == kMmaWarp) tmem_alloc(&s_tmem, C::TMEM_COLS);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = s_tmem;
-
-    if (warp < kMmaWarp) {
-        // ===== converters / drainers: target row r; halves [32h, 32h + 32) of each chunk;
-        // output columns [h NH, h NH + NH) =====
-        const int quad = warp & 3, h = warp >> 2;
-        const int r = 32 * quad + lane;
-        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-        const int64_t g = target(r);
-        uint32_t ptr = 0, pend = 0;
-        if (g >= 0 && end[g] > begin[g]) {
-            ptr = m2l_offs[g];
-            pend = m2l_offs[g + 1];
-        }
-        int nxt_code = 0xffff, nxt_id = 0;
-        if (ptr < pend) {
-            nxt_code = m2l_code[ptr];
-            nxt_id = m2l_ids[ptr];
-        }
-        const float *lsrc = nullptr;
-        int lscale = 0;
-        // per offset, in step order: the source's scale exponent (applied when converting)
-        auto load = [&](int s2, float4 (&buf)[8], int &sc) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (s2 >= S) return;
-            const int oc2 = s2 / NCH, c2 = s2 % NCH;
-            int k0, kw;
-            chunk16(c2, C::KS, NCH, k0, kw);
-            if (c2 == 0) {
-                lsrc = nullptr;
-                if (nxt_code == (int)c_f16_codes[tau][oc2]) {
-                    lsrc = M + (size_t)nxt_id * PP;
-                    lscale = cscale[nxt_id];
-                    ++ptr;
-                    nxt_code = 0xffff;
-                    if (ptr < pend) {
-                        nxt_code = m2l_code[ptr];
-                        nxt_id = m2l_ids[ptr];
-                    }
-                }
-            }
-            sc = lscale;
-            if (!lsrc) return;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int kk = 32 * h + 4 * i, k = k0 + kk;
-                if (kk < kw && k < PP) buf[i] = __ldg(reinterpret_cast<const float4 *>(lsrc + k));
-            }
-        };
-        float acc[NH];
-#pragma unroll
-        for (int n = 0; n < NH; ++n) acc[n] = 0.f;
-        auto drain = [&](int oc, float factor) -> bool {
-            const int b = oc & 1;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait_bounded(&drain_full[b], (oc >> 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) return false;
-            tc_fence_after();
-#pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 8) {
-                uint32_t v[8];
-                tmem_ld8(tmem + lane_base + (uint32_t)(b * NP + h * NH + c0), v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[c0 + j] = fmaf(__uint_as_float(v[j]), factor, acc[c0 + j]);
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&drain_empty[b]);
-            return true;
-        };
-        bool alive = true;
-        float pend_factor = 0.f;  // unscaling factor of the offset whose partial is drained next
-        auto step = [&](int s, float4 (&cur)[8], int sc) {
-            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH;
-            if (s >= NSTAGE) {
-                int ok = 1;
-                if (lane == 0)
-                    ok = mbar_wait_bounded(&empty_bar[st], ((s / NSTAGE) - 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) {
-                    alive = false;
-                    return;
-                }
-            }
-            int k0, kw;
-            chunk16(c, C::KS, NCH, k0, kw);
-            const int code = c_f16_codes[tau][oc];
-            if (warp == 0 && lane == 0) {
-                const uint32_t half = (uint32_t)NP * kw * 2u;
-                const __half *tb = tab + (size_t)code * T::CODE_HALVES + (size_t)k0 * NP;
-                __half *B = bstage + (size_t)st * C::B_HALVES;
-                mbar_expect_tx(&full_bar[st], 2u * half);
-                tma_bulk_g2s(B, tb, half, &full_bar[st]);
-                tma_bulk_g2s(B + NP * kw, tb + T::HALF, half, &full_bar[st]);
-                s_issued[st] += 1;
-            }
-            // scale by 2^sc, split into FP16 halves hi = fp16(x), lo = fp16(x - hi), two per column
-            const float up = pow2f(sc);
-            uint32_t hi[16], lo[16];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float x0 = cur[i].x * up, x1 = cur[i].y * up, x2 = cur[i].z * up, x3 = cur[i].w * up;
-                const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
-                const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
-                const __half2 l01 = __floats2half2_rn(x0 - f01.x, x1 - f01.y);
-                const __half2 l23 = __floats2half2_rn(x2 - f23.x, x3 - f23.y);
-                hi[2 * i] = *reinterpret_cast<const uint32_t *>(&h01);
-                hi[2 * i + 1] = *reinterpret_cast<const uint32_t *>(&h23);
-                lo[2 * i] = *reinterpret_cast<const uint32_t *>(&l01);
-                lo[2 * i + 1] = *reinterpret_cast<const uint32_t *>(&l23);
-            }
-            const uint32_t acol = (uint32_t)(C::A_COL0 + 64 * st + 16 * h);
-            tmem_st16(tmem + lane_base + acol, hi);
-            tmem_st16(tmem + lane_base + acol + 32, lo);
-            tmem_wait_st();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full_bar[st]);
-            // the previous offset's partial is complete once this one is queued; its factor
-            // 2^-(g + s) was recorded when its first chunk was converted
-            const float factor_now = pow2f(-(sc + gexp[code]));
-            if (c == NCH - 1 && oc >= 1 && !drain(oc - 1, pend_factor)) alive = false;
-            if (c == NCH - 1) pend_factor = factor_now;
-        };
-        float4 b0[8], b1[8];
-        int sc0 = 0, sc1 = 0;
-        load(0, b0, sc0);
-        load(1, b1, sc1);
-        for (int s = 0; s < S && alive; s += 2) {
-            step(s, b0, sc0);
-            load(s + 2, b0, sc0);
-            if (s + 1 < S && alive) {
-                step(s + 1, b1, sc1);
-                load(s + 3, b1, sc1);
-            }
-        }
-        if (alive && !drain(188, pend_factor)) alive = false;
-        if (!alive && lane == 0) s_abort = 1;
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait_bounded(&done_bar, 0u, kWaitLimitNs, nullptr) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok && lane == 0) s_abort = 1;
-        __syncwarp();
-        if (ok && alive && !s_abort && g >= 0 && end[g] > begin[g]) {
-#pragma unroll
-            for (int n = 0; n < NH; n += 4)
-                if (h * NH + n < PP)
-                    *reinterpret_cast<float4 *>(Lc + g * PP + h * NH + n) =
-                        make_float4(acc[n], acc[n + 1], acc[n + 2], acc[n + 3]);
-        }
-    } else if (lane == 0) {
-        // ================= MMA issuer: offset oc accumulates in TMEM buffer oc & 1 =================
-        for (int s = 0; s < S; ++s) {
-            const int st = s % NSTAGE, oc = s / NCH, c = s % NCH, b = oc & 1;
-            if (c == 0 && oc >= 2 &&
-                !mbar_wait_bounded(&drain_empty[b], ((oc - 2) >> 1) & 1, kWaitLimitNs, &s_abort)) {
-                s_abort = 1;
-                break;
-            }
-            if (!mbar_wait_bounded(&full_bar[st], (s / NSTAGE) & 1, kWaitLimitNs, &s_abort)) {
-                s_abort = 1;
-                break;
-            }
-            tc_fence_after();
-            int k0, kw;
-            chunk16(c, C::KS, NCH, k0, kw);
-            const __half *Bhi = bstage + (size_t)st * C::B_HALVES, *Blo = Bhi + NP * kw;
-            const uint32_t d = tmem + (uint32_t)(b * NP);
-            const uint32_t ahi = tmem + (uint32_t)(C::A_COL0 + 64 * st), alo = ahi + 32;
-            for (int j = 0; j < kw / 16; ++j) {
-                const uint64_t bh = smem_desc(Bhi + j * 2 * NP * 8, NP * 16, 128);
-                const uint64_t bl = smem_desc(Blo + j * 2 * NP * 8, NP * 16, 128);
-                tc_mma_f16_ta(d, alo + 8 * j, bh, kIdesc, (c > 0 || j > 0) ? 1u : 0u);
-                tc_mma_f16_ta(d, ahi + 8 * j, bl, kIdesc, 1u);
-                tc_mma_f16_ta(d, ahi + 8 * j, bh, kIdesc, 1u);
-            }
-            tc_commit(&empty_bar[st]);
-            if (c == NCH - 1) tc_commit(&drain_full[b]);
-        }
-        tc_commit(&done_bar);
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (s_abort) {
-        if (tid == 0) {
-            atomicOr(status, kStatusTimeout);
-            for (int st = 0; st < NSTAGE; ++st)
-                if (s_issued[st] > 0) mbar_wait_bounded(&full_bar[st], (s_issued[st] - 1) & 1, kWaitLimitNs, nullptr);
-        }
-        __syncthreads();
-    }
-    if (warp == kMmaWarp) {
-        __syncwarp();
-        tmem_dealloc(tmem, C::TMEM_COLS);
-    }
-}
 
 // ---- pre-split sources ------------------------------------------------------------------
 // The sources can be converted once per cell instead of once per (target, offset): after the
@@ -456,7 +155,7 @@ __global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, i
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    // the scale of k_cell_scale: max |M~_c| = f 2^e, f in [0.5, 1) -> s_c = 10 - e
+    // the source scale: max |M~_c| = f 2^e, f in [0.5, 1) -> s_c = 10 - e
     const bool fin = m > 0.f && m <= 3.0e38f;
     int ex = 0;
     if (fin) frexpf(m, &ex);
@@ -476,10 +175,6 @@ __global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, i
         }
     }
 }
-
-// FP16 M2L modes (GBFMM_M2L_TC): 2 = pre-split sources staged by the converter warps
-// (k_m2l_f16s, default), 4 = FP32 sources converted in the kernel (k_m2l_f16)
-bool m2l_f16_presplit(int) { return m2l_tc_mode() == 2; }
 
 size_t presplit_bytes(int P, int64_t ncells)
 {
@@ -821,31 +516,21 @@ static void launch_f16_t(const F16Tiles &tiles, int grid, const int4 *tdesc, con
     using T = F16Table<P>;
     const __half *tab = static_cast<const __half *>(table);
     const int *gexp = reinterpret_cast<const int *>(tab + (size_t)kM2LCodes * T::CODE_HALVES);
-    if (ps) {
-        using CS = F16SCfg<P, 8>;
-        cudaFuncSetAttribute(k_m2l_f16s<P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS::kSmemBytes);
-        const int step = max_ctas > 0 ? max_ctas : grid;
-        for (int t0 = 0; t0 < grid; t0 += step) {
-            F16Tiles tt = tiles;
-            tt.tile0 = t0;
-            const int g = grid - t0 < step ? grid - t0 : step;
-            k_m2l_f16s<P, 8><<<g, CS::NTHREADS, CS::kSmemBytes, s>>>(tt, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
-                                                                     m2l_code, tab, gexp,
-                                                                     static_cast<const __half *>(ps), cscale, Lc,
-                                                                     status);
-            note_launches(1);
-        }
-        return;
-    } else {
-        using C = F16Cfg<P>;
-        cudaFuncSetAttribute(k_m2l_f16<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
-        k_m2l_f16<P><<<grid, C::NTHREADS, C::kSmemBytes, s>>>(tiles, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
-                                                              m2l_code, tab, gexp, M, cscale, Lc, status);
+    using CS = F16SCfg<P, 8>;
+    cudaFuncSetAttribute(k_m2l_f16s<P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CS::kSmemBytes);
+    const int step = max_ctas > 0 ? max_ctas : grid;
+    for (int t0 = 0; t0 < grid; t0 += step) {
+        F16Tiles tt = tiles;
+        tt.tile0 = t0;
+        const int g = grid - t0 < step ? grid - t0 : step;
+        k_m2l_f16s<P, 8><<<g, CS::NTHREADS, CS::kSmemBytes, s>>>(tt, tdesc, tlist, begin, end, m2l_offs, m2l_ids,
+                                                                 m2l_code, tab, gexp, static_cast<const __half *>(ps),
+                                                                 cscale, Lc, status);
+        note_launches(1);
     }
-    note_launches(1);
 }
 
-// ps != nullptr: the sources come pre-split (launch_presplit)
+// ps: the pre-split sources (launch_presplit)
 static void dispatch_f16(int P, const F16Tiles &tiles, int grid, const int4 *tdesc, const int32_t *tlist,
                          const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids,
                          const uint16_t *m2l_code, const void *table, const float *M, const int8_t *cscale,
