@@ -413,10 +413,22 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     launch_sort_gather(k0, k1, v0, v1, n, 3 * L, hist, ctx->d_status, x, sx, &skeys, &perm, s);
     mark(2);
     launch_cells(skeys, n, L, begin, end, s);
-    launch_list_count(L, begin, end, p2p_len, m2l_len, s);
-    launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, scan_tmp, s);
-    launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, scan_tmp, s);
-    launch_list_fill(L, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code, s);
+    // the block M2L reads no M2L list: then only the P2P rows are built, on the near field's
+    // stream (the M2L rows are built on demand by gbfmm_export_lists)
+    const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
+    const bool gathered = (prm->flags & GBFMM_FLAG_M2L_GATHERED) != 0;
+    const bool blk = L >= 2 && prm->method == GBFMM_METHOD_FMM && !cores && !gathered;
+    auto p2p_lists = [&](cudaStream_t st) {
+        launch_p2p_list_count(L, begin, end, p2p_len, st);
+        launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, scan_tmp, st);
+        launch_p2p_list_fill(L, begin, end, p2p_offs, p2p_ids, st);
+    };
+    if (!blk) {
+        launch_list_count(L, begin, end, p2p_len, m2l_len, s);
+        launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, scan_tmp, s);
+        launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, scan_tmp, s);
+        launch_list_fill(L, begin, end, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code, s);
+    }
     mark(3);
     // near field beside the far field (FMM): P2P writes its compensated sums, L2P adds the far
     // field to them and writes the output; concurrently on the context's two streams unless the
@@ -431,19 +443,19 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0);
         s = ctx->s_far;
         if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
+        if (blk) p2p_lists(ctx->s_near);
         launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, ctx->s_near);
         if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
         cudaEventRecord(ctx->ev_near, ctx->s_near);
     }
+    if (blk && !fork) p2p_lists(s);  // serial: the P2P rows now, P2P after the far field
     if (L >= 2) launch_p2m(P, L, geo, sx, begin, end, M, s);
     mark(4);
     if (L >= 2)
         for (int l = L - 1; l >= 2; --l) launch_m2m(P, l, begin, end, ops.m2m, M, s);
     mark(5);
     if (L >= 2) {
-        const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
-        const bool gathered = (prm->flags & GBFMM_FLAG_M2L_GATHERED) != 0;
-        if (prm->method == GBFMM_METHOD_FMM && !cores && !gathered) {
+        if (blk) {
             rc = ensure_blk(ctx, P, s);
             if (rc != GBFMM_OK) return rc;
             int8_t *pscale = at<int8_t>(ws, lo.cscale);
@@ -500,6 +512,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     ctx->last_keys = (size_t)(reinterpret_cast<unsigned char *>(skeys) - ctx->last_ws);
     ctx->last_idx = (size_t)(reinterpret_cast<unsigned char *>(perm) - ctx->last_ws);
     ctx->last_method = prm->method;
+    ctx->last_m2l_lists = !blk;
     ctx->timed_last = timing;
     ctx->stage_order_last = fork ? 2 : (split ? 1 : 0);
     ctx->ops_built_last = built_now;
@@ -624,6 +637,23 @@ int gbfmm_export_lists(gbfmm_ctx *ctx, int kind, int32_t *offs, int32_t *ids, in
     }
     if (kind != GBFMM_LIST_P2P && kind != GBFMM_LIST_M2L) return fail(ctx, GBFMM_EINVAL, "unknown list kind");
     const Layout &lo = ctx->last;
+    if (kind == GBFMM_LIST_M2L && !ctx->last_m2l_lists && lo.L >= 2) {
+        // the evaluation's block M2L read no list: build the rows now from its cells
+        unsigned char *w = ctx->last_ws;
+        const int32_t *cb = reinterpret_cast<const int32_t *>(w + lo.cell_begin);
+        const int32_t *ce = reinterpret_cast<const int32_t *>(w + lo.cell_end);
+        uint32_t *p2p_len = reinterpret_cast<uint32_t *>(w + lo.p2p_len), *p2p_offs = reinterpret_cast<uint32_t *>(w + lo.p2p_offs);
+        uint32_t *m2l_len = reinterpret_cast<uint32_t *>(w + lo.m2l_len), *m2l_offs = reinterpret_cast<uint32_t *>(w + lo.m2l_offs);
+        uint32_t *tmp = reinterpret_cast<uint32_t *>(w + lo.scan_tmp);
+        launch_list_count(lo.L, cb, ce, p2p_len, m2l_len, 0);
+        launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, tmp, 0);
+        launch_exclusive_scan(m2l_len, m2l_offs, lo.ncells, tmp, 0);
+        launch_list_fill(lo.L, cb, ce, p2p_offs, reinterpret_cast<int32_t *>(w + lo.p2p_ids), m2l_offs,
+                         reinterpret_cast<int32_t *>(w + lo.m2l_ids), reinterpret_cast<uint16_t *>(w + lo.m2l_code), 0);
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "M2L list build");
+        ctx->last_m2l_lists = true;
+    }
     const int64_t rows = kind == GBFMM_LIST_P2P ? lo.nleaves : lo.ncells;
     std::vector<uint32_t> o(rows + 1);
     cudaMemcpy(o.data(), ctx->last_ws + (kind == GBFMM_LIST_P2P ? lo.p2p_offs : lo.m2l_offs), 4 * (rows + 1),

@@ -230,6 +230,10 @@ void launch_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t
                        cudaStream_t s);
 void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
                       const uint32_t *m2l_offs, int32_t *m2l_ids, uint16_t *m2l_code, cudaStream_t s);
+// the P2P rows alone (the block M2L of the uniform tree reads no M2L list)
+void launch_p2p_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t *p2p_len, cudaStream_t s);
+void launch_p2p_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
+                          cudaStream_t s);
 
 // expansions.cu
 void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_ops, cudaStream_t s);

@@ -68,6 +68,7 @@ struct gbfmm_ctx {
     unsigned char *last_ws = nullptr;
     size_t last_keys = 0, last_idx = 0;
     int last_method = 0;
+    bool last_m2l_lists = true;  // the last uniform evaluation built its M2L rows
     gbfmm::AdaptiveState ad;
     // host-buffer path
     float *h_in = nullptr, *h_out = nullptr;

@@ -636,8 +636,9 @@ GB_DEV void cell_of(int64_t g, int &l, uint32_t &key)
 // -2 - (child bit)), the order the M2L kernels walk.
 constexpr int kListWarps = 8;
 
-template <bool FILL>
-__global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, const int32_t *__restrict__ begin,
+// M2L = false: P2P rows only (the launch covers the leaf level, g0 = level_offset(L))
+template <bool FILL, bool M2L = true>
+__global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t g0, int64_t C, const int32_t *__restrict__ begin,
                                                            const int32_t *__restrict__ end,
                                                            uint32_t *__restrict__ p2p_len, uint32_t *__restrict__ m2l_len,
                                                            const uint32_t *__restrict__ p2p_offs,
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, con
                                                            int32_t *__restrict__ m2l_ids, uint16_t *__restrict__ m2l_code)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x * (int64_t)kListWarps + (threadIdx.x >> 5);
+    const int64_t g = g0 + blockIdx.x * (int64_t)kListWarps + (threadIdx.x >> 5);
     if (g >= C) return;
     int l;
     uint32_t key;
@@ -657,7 +658,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, con
     const int side = 1 << l;
     const int64_t off = level_offset(l);
     const unsigned lt = (1u << lane) - 1u;
-    if (l >= 2) {
+    if (M2L && l >= 2) {
         uint32_t cnt = 0, e = FILL ? m2l_offs[g] : 0u;
         if (ne) {
             // all seven rounds' candidates first, so that their begin/end loads are in flight
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(int L, int64_t C, con
             }
         }
         if (!FILL && lane == 0) m2l_len[g] = cnt;
-    } else if (!FILL && lane == 0) {
+    } else if (M2L && !FILL && lane == 0) {
         m2l_len[g] = 0;
     }
     if (l == L) {
@@ -722,7 +723,24 @@ void launch_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t
 {
     const int64_t C = level_offset(L + 1);
     k_lists<false><<<(unsigned)((C + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
-        L, C, begin, end, p2p_len, m2l_len, nullptr, nullptr, nullptr, nullptr, nullptr);
+        L, 0, C, begin, end, p2p_len, m2l_len, nullptr, nullptr, nullptr, nullptr, nullptr);
+    note_launches(1);
+}
+
+void launch_p2p_list_count(int L, const int32_t *begin, const int32_t *end, uint32_t *p2p_len, cudaStream_t s)
+{
+    const int64_t g0 = level_offset(L), C = level_offset(L + 1);
+    k_lists<false, false><<<(unsigned)((C - g0 + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
+        L, g0, C, begin, end, p2p_len, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    note_launches(1);
+}
+
+void launch_p2p_list_fill(int L, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs, int32_t *p2p_ids,
+                          cudaStream_t s)
+{
+    const int64_t g0 = level_offset(L), C = level_offset(L + 1);
+    k_lists<true, false><<<(unsigned)((C - g0 + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
+        L, g0, C, begin, end, nullptr, nullptr, p2p_offs, p2p_ids, nullptr, nullptr, nullptr);
     note_launches(1);
 }
 
@@ -731,7 +749,7 @@ void launch_list_fill(int L, const int32_t *begin, const int32_t *end, const uin
 {
     const int64_t C = level_offset(L + 1);
     k_lists<true><<<(unsigned)((C + kListWarps - 1) / kListWarps), 32 * kListWarps, 0, s>>>(
-        L, C, begin, end, nullptr, nullptr, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code);
+        L, 0, C, begin, end, nullptr, nullptr, p2p_offs, p2p_ids, m2l_offs, m2l_ids, m2l_code);
     note_launches(1);
 }
 
