@@ -79,6 +79,14 @@ enum {
  * form (one dense GEMM per parent offset over all parents of a level).  Same Eq. 4, same
  * precision scheme; they differ by rounding only. */
 #define GBFMM_FLAG_M2L_GATHERED 8
+/* uniform tree: run the M2L by rotation to the translation axis on the FP32 CUDA cores: per
+ * list entry, rotate the source expansion so that the offset lies on +z, translate along z
+ * (equal orders only), rotate back -- O(p^3) per pair instead of the dense operator's O(p^4)
+ * (the rotation-based M2L of the FMM literature; Section "Overview of Advanced Techniques").
+ * The factors are computed on the host in FP64 and checked against the dense operators at the
+ * first use of an order (synchronous, ECUDA if the check fails).  Ignored by the adaptive tree
+ * and the treecode; GBFMM_FLAG_M2L_CUDA_CORES takes precedence. */
+#define GBFMM_FLAG_M2L_ROTATION 16
 
 /*
  * Parameters of one evaluation (Section "Fast N-body simulation").

@@ -17,6 +17,7 @@ namespace gbfmm {
 void init_expansion_constants();
 void init_m2l_constants();
 void init_m2l_f16_constants();
+void init_m2l_rot_constants();
 }  // namespace gbfmm
 
 using namespace gbfmm;
@@ -208,6 +209,26 @@ int gbfmm::ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now)
     return GBFMM_OK;
 }
 
+// the rotation factors of the M2L operators: computed on the host in FP64 and checked against
+// the dense operators at first use of order P (synchronous)
+static int ensure_rot(gbfmm_ctx *ctx, int P)
+{
+    OpsCache &c = ctx->ops[order_slot(P)];
+    if (c.m2l_rot) return GBFMM_OK;
+    cudaError_t e = cudaMalloc(&c.m2l_rot, m2l_rot_table_bytes(P));
+    if (e != cudaSuccess) {
+        c.m2l_rot = nullptr;
+        return cuda_fail(ctx, e, "cudaMalloc(m2l rotation factors)");
+    }
+    const int rc = build_m2l_rot(P, c.m2l_rot);
+    if (rc != 0) {
+        cudaFree(c.m2l_rot);
+        c.m2l_rot = nullptr;
+        return fail(ctx, GBFMM_ECUDA, "rotation factors of the M2L operators failed their check (" + std::to_string(rc) + ")");
+    }
+    return GBFMM_OK;
+}
+
 // the block operators of the uniform tree's M2L (built on the stream at first use of order P)
 static int ensure_blk(gbfmm_ctx *ctx, int P, cudaStream_t s)
 {
@@ -274,6 +295,7 @@ int gbfmm_create(gbfmm_ctx **out, int device)
         init_expansion_constants();
         init_m2l_constants();
         init_m2l_f16_constants();
+        init_m2l_rot_constants();
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     if (!ok) {
@@ -299,6 +321,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
         cudaFree(c.l2l);
         cudaFree(c.m2l_f16);
         cudaFree(c.m2l_blk);
+        cudaFree(c.m2l_rot);
     }
     cudaFree(ctx->h_in);
     cudaFree(ctx->h_out);
@@ -417,7 +440,8 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     // stream (the M2L rows are built on demand by gbfmm_export_lists)
     const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
     const bool gathered = (prm->flags & GBFMM_FLAG_M2L_GATHERED) != 0;
-    const bool blk = L >= 2 && prm->method == GBFMM_METHOD_FMM && !cores && !gathered;
+    const bool rot = (prm->flags & GBFMM_FLAG_M2L_ROTATION) != 0;
+    const bool blk = L >= 2 && prm->method == GBFMM_METHOD_FMM && !cores && !gathered && !rot;
     auto p2p_lists = [&](cudaStream_t st) {
         launch_p2p_list_count(L, begin, end, p2p_len, st);
         launch_exclusive_scan(p2p_len, p2p_offs, lo.nleaves, scan_tmp, st);
@@ -464,6 +488,10 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
             if (launch_m2l_blk(P, L, begin, end, ps, pscale, ops.m2l_blk, Lc, at<float>(ws, lo.lpart), ctx->d_status,
                                s, fork ? sm_count() : 0) != 0)
                 return fail(ctx, GBFMM_ECUDA, "TMA tensor map encoding failed");
+        } else if (prm->method == GBFMM_METHOD_FMM && rot && !cores) {
+            rc = ensure_rot(ctx, P);
+            if (rc != GBFMM_OK) return rc;
+            launch_m2l_rot(P, L, begin, end, m2l_offs, m2l_ids, m2l_code, ops.m2l_rot, M, Lc, s);
         } else if (prm->method == GBFMM_METHOD_FMM && !cores) {
             int8_t *cscale = at<int8_t>(ws, lo.cscale);
             void *ps = at<void>(ws, lo.presplit);

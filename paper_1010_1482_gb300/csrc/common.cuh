@@ -322,6 +322,14 @@ size_t m2l_blk_part_bytes(int P, int L);
 int launch_m2l_blk(int P, int L, const int32_t *begin, const int32_t *end, const void *presplit, const int8_t *pscale,
                    const void *table, float *Lc, float *Lpart, int *status, cudaStream_t s, int max_ctas);
 
+// m2l_rot.cu: the M2L by rotation to the translation axis (O(p^3) per pair, FP32 CUDA cores)
+void init_m2l_rot_constants();
+size_t m2l_rot_table_bytes(int P);
+int build_m2l_rot(int P, void *table);  // host FP64 factors, checked, copied to the device; 0 = OK
+void launch_m2l_rot(int P, int L, const int32_t *begin, const int32_t *end, const uint32_t *m2l_offs,
+                    const int32_t *m2l_ids, const uint16_t *m2l_code, const void *table, const float *M, float *Lc,
+                    cudaStream_t s);
+
 // p2p.cu
 // P2P without the far field: the compensated near-field sums of every particle in sorted order,
 // near[2 i] = sums (phi, dphi/dx, dphi/dy, dphi/dz), near[2 i + 1] = their compensations (the

@@ -19,7 +19,8 @@ struct OpsCache {
     int P = 0;
     float *m2l = nullptr, *m2m = nullptr, *l2l = nullptr;
     void *m2l_f16 = nullptr;  // FP16 tensor-core operator blocks (hi | lo) + per-code scales (list-based M2L)
-    void *m2l_blk = nullptr;  // uniform tree: per parent offset, the 8p^2 x 8p^2 FP16 blocks (hi | lo) + scale
+    void *m2l_blk = nullptr;
+    void *m2l_rot = nullptr;  // rotation factors of the M2L operators (GBFMM_FLAG_M2L_ROTATION)  // uniform tree: per parent offset, the 8p^2 x 8p^2 FP16 blocks (hi | lo) + scale
     bool built = false;
 };
 

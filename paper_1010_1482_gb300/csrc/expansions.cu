@@ -20,6 +20,10 @@
 #include "common.cuh"
 
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 namespace gbfmm {
 
@@ -73,10 +77,10 @@ GB_HD constexpr int im_idx(int n, int m) { return n * n + 2 * m; }
 struct C64 {
     double re, im;
 };
-GB_DEV C64 cmul(C64 a, C64 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-GB_DEV C64 conj64(C64 a) { return {a.re, -a.im}; }
+GB_HD C64 cmul(C64 a, C64 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+GB_HD C64 conj64(C64 a) { return {a.re, -a.im}; }
 
-GB_DEV void dof_decode(int i, int &n, int &m, int &im)
+GB_HD void dof_decode(int i, int &n, int &m, int &im)
 {
     n = 0;
     while ((n + 1) * (n + 1) <= i) ++n;
@@ -90,17 +94,17 @@ GB_DEV void dof_decode(int i, int &n, int &m, int &im)
     }
 }
 
-GB_DEV double fact64(int k)
+GB_HD double fact64(int k)
 {
     double f = 1.0;
     for (int i = 2; i <= k; ++i) f *= i;
     return f;
 }
-GB_DEV double Anm64(int n, int m) { return 1.0 / sqrt(fact64(n - m) * fact64(n + m)); }
-GB_DEV double ipow_even(int e) { return ((e / 2) % 2 == 0) ? 1.0 : -1.0; }
+GB_HD double Anm64(int n, int m) { return 1.0 / sqrt(fact64(n - m) * fact64(n + m)); }
+GB_HD double ipow_even(int e) { return ((e / 2) % 2 == 0) ? 1.0 : -1.0; }
 
 // regular (irreg = 0) or irregular (irreg = 1) solid harmonics H[n(n+1)/2 + m], m >= 0, n < nmax
-GB_DEV void harmonics64(int nmax, double x, double y, double z, int irreg, C64 *H)
+GB_HD void harmonics64(int nmax, double x, double y, double z, int irreg, C64 *H)
 {
     double r2 = x * x + y * y + z * z;
     double ir2 = 1.0 / r2;
@@ -128,13 +132,13 @@ GB_DEV void harmonics64(int nmax, double x, double y, double z, int irreg, C64 *
     }
 }
 
-GB_DEV C64 hfull(const C64 *H, int n, int m)
+GB_HD C64 hfull(const C64 *H, int n, int m)
 {
     return m >= 0 ? H[n * (n + 1) / 2 + m] : conj64(H[n * (n + 1) / 2 - m]);
 }
 
 // complex coefficient of input C_n^m in output D_j^k for the three operators
-GB_DEV C64 k_m2l(const C64 *I, int j, int k, int n, int m)
+GB_HD C64 k_m2l(const C64 *I, int j, int k, int n, int m)
 {
     double f = ipow_even(abs(k - m) - abs(k) - abs(m)) * Anm64(n, m) * Anm64(j, k) / Anm64(j + n, m - k) *
                ((j & 1) ? -1.0 : 1.0);
@@ -226,6 +230,208 @@ void launch_build_operators(int P, float *m2l_ops, float *m2m_ops, float *l2l_op
 {
     k_build_ops<<<kM2LCodes + 16, 256, 0, s>>>(P, m2l_ops, m2m_ops, l2l_ops);
     note_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Rotation factors of the M2L operators (host, FP64).  For an offset code with translation
+// v = target centre - source centre and a rotation Q taking v / |v| to +z,
+//   T_v = F^-1 C_|v| F,
+// F: block-diagonal in the degree, the map of a degree-n coefficient block under the change
+//    of frame x -> Q x (multipole and local blocks alike: both are sums of q f(rho) R_n^-m);
+//    found by least squares from the blocks of point charges at sample directions and at their
+//    rotated images (the map is exactly linear, so the fit is exact up to rounding);
+// F^-1: the same for Q^T;
+// C: the M2L operator of the coaxial translation (0, 0, |v|), which couples equal orders only,
+//    with one real coefficient for the real and the imaginary parts.
+// The factorisation is checked against the dense operator before it is used.
+// Layout per code (kM2LCodes slots of m2l_rot_code_floats): F blocks (n = 0..P-1, (2n+1)^2 each,
+// [row][col]), F^-1 blocks, then C blocks (m = 0..P-1, (P-m)^2 each, [j-m][n-m]), zero padding.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+void packed_block_regular(int n, const double x[3], double *out)
+{
+    C64 H[(kMaxDeg + 1) * (kMaxDeg + 2) / 2];
+    harmonics64(n + 1, x[0], x[1], x[2], 0, H);
+    for (int m = 0; m <= n; ++m) {
+        const C64 r = H[n * (n + 1) / 2 + m];  // the block holds conj(R_n^m)
+        if (m == 0) {
+            out[0] = r.re;
+        } else {
+            out[2 * m - 1] = r.re;
+            out[2 * m] = -r.im;
+        }
+    }
+}
+
+// solve G X = B for X (s x s, G symmetric positive definite), partial pivoting
+bool solve_dense(int s, std::vector<double> G, std::vector<double> &B)
+{
+    for (int c = 0; c < s; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < s; ++r)
+            if (fabs(G[r * s + c]) > fabs(G[piv * s + c])) piv = r;
+        if (fabs(G[piv * s + c]) < 1e-300) return false;
+        if (piv != c)
+            for (int k = 0; k < s; ++k) {
+                std::swap(G[c * s + k], G[piv * s + k]);
+                std::swap(B[c * s + k], B[piv * s + k]);
+            }
+        for (int r = 0; r < s; ++r) {
+            if (r == c) continue;
+            const double f = G[r * s + c] / G[c * s + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < s; ++k) {
+                G[r * s + k] -= f * G[c * s + k];
+                B[r * s + k] -= f * B[c * s + k];
+            }
+        }
+    }
+    for (int r = 0; r < s; ++r)
+        for (int k = 0; k < s; ++k) B[r * s + k] /= G[r * s + r];
+    return true;
+}
+
+// F_n for the frame change x -> Q x, row-major (2n+1)^2
+bool rotation_block(int n, const double Q[9], double *F)
+{
+    const int s = 2 * n + 1, K = 2 * s + 3;
+    std::vector<double> G(s * s, 0.0), Hm(s * s, 0.0), p(s), q(s);
+    for (int i = 0; i < K; ++i) {
+        double x[3] = {sin(1.31 * i + 0.7), cos(2.17 * i + 0.23), sin(0.93 * i + 1.1) + 0.3 * cos(3.7 * i)};
+        const double nx = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (double &c : x) c /= nx;
+        const double y[3] = {Q[0] * x[0] + Q[1] * x[1] + Q[2] * x[2], Q[3] * x[0] + Q[4] * x[1] + Q[5] * x[2],
+                             Q[6] * x[0] + Q[7] * x[1] + Q[8] * x[2]};
+        packed_block_regular(n, x, p.data());
+        packed_block_regular(n, y, q.data());
+        for (int a = 0; a < s; ++a)
+            for (int b = 0; b < s; ++b) {
+                G[a * s + b] += p[a] * p[b];
+                Hm[a * s + b] += p[a] * q[b];  // (sum p q^T): F^T = G^-1 (sum p q^T)
+            }
+    }
+    if (!solve_dense(s, G, Hm)) return false;
+    for (int a = 0; a < s; ++a)
+        for (int b = 0; b < s; ++b) F[a * s + b] = Hm[b * s + a];
+    return true;
+}
+
+// the dense M2L operator (real-packed, [row][col]) of translation v, as k_build_ops builds it
+void dense_m2l(int P, const double v[3], std::vector<double> &T)
+{
+    const int PP = P * P;
+    std::vector<C64> H((2 * kMaxP) * (2 * kMaxP + 1) / 2);
+    harmonics64(2 * P - 1, v[0], v[1], v[2], 1, H.data());
+    T.assign((size_t)PP * PP, 0.0);
+    for (int row = 0; row < PP; ++row)
+        for (int col = 0; col < PP; ++col) {
+            int j, k, rim, n, m, cim;
+            dof_decode(row, j, k, rim);
+            dof_decode(col, n, m, cim);
+            const C64 u = cim ? C64{0.0, 1.0} : C64{1.0, 0.0};
+            const C64 a = k_m2l(H.data(), j, k, n, m);
+            const C64 b = m > 0 ? k_m2l(H.data(), j, k, n, -m) : C64{0.0, 0.0};
+            C64 val = cmul(a, u);
+            const C64 w = cmul(b, conj64(u));
+            val.re += w.re;
+            val.im += w.im;
+            T[(size_t)row * PP + col] = rim ? val.im : val.re;
+        }
+}
+
+}  // namespace
+
+// floats per code: F, F^-1 and C, padded to a multiple of 4 (16-byte aligned codes)
+size_t m2l_rot_code_floats(int P)
+{
+    size_t f = 0, c = 0;
+    for (int n = 0; n < P; ++n) f += (size_t)(2 * n + 1) * (2 * n + 1);
+    for (int m = 0; m < P; ++m) c += (size_t)(P - m) * (P - m);
+    return (2 * f + c + 3) / 4 * 4;
+}
+
+int build_m2l_rot_table(int P, std::vector<float> &out)
+{
+    const int PP = P * P;
+    const size_t RS = m2l_rot_code_floats(P);
+    out.assign(RS * kM2LCodes, 0.f);
+    std::vector<double> T, Cz, Fd((size_t)PP * PP), Fi((size_t)PP * PP);
+    for (int code = 0; code < kM2LCodes; ++code) {
+        const int dx = code % 7 - 3, dy = (code / 7) % 7 - 3, dz = code / 49 - 3;
+        if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+        const double v[3] = {-(double)dx, -(double)dy, -(double)dz};  // target centre - source centre
+        const double d = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double u[3] = {v[0] / d, v[1] / d, v[2] / d};
+        double Q[9];  // rotation taking u to +z (Rodrigues about u x z)
+        const double ax = u[1], ay = -u[0], s2 = ax * ax + ay * ay, c = u[2];
+        if (s2 < 1e-30) {
+            const double sg = c > 0 ? 1.0 : -1.0;  // u = +-z: identity or a half turn about x
+            const double Qi[9] = {1, 0, 0, 0, sg, 0, 0, 0, sg};
+            memcpy(Q, Qi, sizeof(Q));
+        } else {
+            const double sn = sqrt(s2), kx = ax / sn, ky = ay / sn, t = 1.0 - c;
+            const double Qi[9] = {c + kx * kx * t, kx * ky * t, ky * sn, kx * ky * t, c + ky * ky * t, -kx * sn,
+                                  -ky * sn, kx * sn, c};
+            memcpy(Q, Qi, sizeof(Q));
+        }
+        const double Qt[9] = {Q[0], Q[3], Q[6], Q[1], Q[4], Q[7], Q[2], Q[5], Q[8]};
+        const double z[3] = {0.0, 0.0, d};
+        dense_m2l(P, v, T);
+        dense_m2l(P, z, Cz);
+        std::fill(Fd.begin(), Fd.end(), 0.0);
+        std::fill(Fi.begin(), Fi.end(), 0.0);
+        float *o = out.data() + RS * code;
+        size_t at = 0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int n = 0; n < P; ++n) {
+                const int s = 2 * n + 1;
+                std::vector<double> B(s * s);
+                if (!rotation_block(n, pass == 0 ? Q : Qt, B.data())) return -1;
+                for (int a = 0; a < s; ++a)
+                    for (int b = 0; b < s; ++b) {
+                        (pass == 0 ? Fd : Fi)[(size_t)(n * n + a) * PP + n * n + b] = B[a * s + b];
+                        o[at++] = (float)B[a * s + b];
+                    }
+            }
+        // C: equal orders only, one coefficient for real and imaginary parts
+        double cmax = 0.0, off = 0.0, imdiff = 0.0;
+        for (int r = 0; r < PP; ++r)
+            for (int cc = 0; cc < PP; ++cc) cmax = fmax(cmax, fabs(Cz[(size_t)r * PP + cc]));
+        for (int r = 0; r < PP; ++r)
+            for (int cc = 0; cc < PP; ++cc) {
+                int j, k, rim, n, m, cim;
+                dof_decode(r, j, k, rim);
+                dof_decode(cc, n, m, cim);
+                if (k != m || rim != cim) off = fmax(off, fabs(Cz[(size_t)r * PP + cc]));
+            }
+        for (int m = 0; m < P; ++m)
+            for (int j = m; j < P; ++j)
+                for (int n = m; n < P; ++n) {
+                    const double cre = Cz[(size_t)(m == 0 ? j * j : j * j + 2 * m - 1) * PP + (m == 0 ? n * n : n * n + 2 * m - 1)];
+                    if (m > 0) imdiff = fmax(imdiff, fabs(cre - Cz[(size_t)(j * j + 2 * m) * PP + n * n + 2 * m]));
+                    o[at++] = (float)cre;
+                }
+        if (off > 1e-12 * cmax || imdiff > 1e-12 * cmax) return -2;
+        // F^-1 C F against the dense operator
+        std::vector<double> CF((size_t)PP * PP, 0.0);
+        for (int r = 0; r < PP; ++r)
+            for (int k2 = 0; k2 < PP; ++k2) {
+                const double cv = Cz[(size_t)r * PP + k2];
+                if (cv == 0.0) continue;
+                for (int cc = 0; cc < PP; ++cc) CF[(size_t)r * PP + cc] += cv * Fd[(size_t)k2 * PP + cc];
+            }
+        double err = 0.0, tmax = 0.0;
+        for (int r = 0; r < PP; ++r)
+            for (int cc = 0; cc < PP; ++cc) {
+                double acc = 0.0;
+                for (int k2 = 0; k2 < PP; ++k2) acc += Fi[(size_t)r * PP + k2] * CF[(size_t)k2 * PP + cc];
+                err = fmax(err, fabs(acc - T[(size_t)r * PP + cc]));
+                tmax = fmax(tmax, fabs(T[(size_t)r * PP + cc]));
+            }
+        if (err > 1e-9 * tmax) return -3;
+    }
+    return 0;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -26,6 +26,7 @@ FLAG_STAGE_TIMING = 1
 FLAG_M2L_CUDA_CORES = 2
 FLAG_SERIAL = 4
 FLAG_M2L_GATHERED = 8
+FLAG_M2L_ROTATION = 16
 STAGES = ["box+keys", "sort", "cells+lists", "P2M", "M2M", "M2L/M2P", "L2L", "L2P", "P2P", "operators"]
 
 

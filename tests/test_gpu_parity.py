@@ -180,6 +180,31 @@ def test_m2l_tensor_cores_and_cuda_cores_agree(G, ctx, p):
     assert O.rel_l2(gat, cc) <= 5e-6
 
 
+@pytest.mark.parametrize("p", [4, 6, 8, 10])
+def test_m2l_rotation_matches(G, ctx, p):
+    """The M2L by rotation to the translation axis (FLAG_M2L_ROTATION: rotate, coaxial
+    translation, rotate back; O(p^3) per pair) computes the same Eq. 4 as the dense operators:
+    outputs match the oracle and the FP32 CUDA-core M2L, local expansions per level match the
+    CUDA-core ones (scaled coefficients)."""
+    n, leaf = 30000, 16
+    x = inputs.uniform_cube(n, 321 + p)
+    rot, L = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_ROTATION)
+    C = O.level_offset(L + 1)
+    Lr = G.gbfmm_export_expansions(ctx, 1, C, p)
+    cc, _ = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_CUDA_CORES)
+    Lcc = G.gbfmm_export_expansions(ctx, 1, C, p)
+    ref = O.fmm(x, p, leaf)["out"]
+    assert O.rel_l2(rot[:, 0], ref[:, 0]) <= TOL_FMM
+    assert O.rel_l2(rot[:, 1:], ref[:, 1:]) <= TOL_FMM
+    assert O.rel_l2(rot, cc) <= 5e-6
+    side = float(np.max(x[:, :3].max(0).astype(np.float64) - x[:, :3].min(0)))
+    deg = np.concatenate([np.full(k + 1, k) for k in range(p)])
+    for l in range(2, L + 1):
+        sl = slice(O.level_offset(l), O.level_offset(l + 1))
+        sc = (side / 2**l) ** (deg + 1.0)
+        assert np.linalg.norm((Lr[sl] - Lcc[sl]) * sc) <= 1e-5 * np.linalg.norm(Lcc[sl] * sc), l
+
+
 @pytest.mark.parametrize("p,n,leaf", [(8, 40000, 8), (10, 30000, 16), (4, 5000, 64), (6, 300000, 64)])
 def test_m2l_block_local_expansions(G, ctx, p, n, leaf):
     """Local expansions after the M2L and L2L of the block form against the FP32 CUDA-core M2L,
