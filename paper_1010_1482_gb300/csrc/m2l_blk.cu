@@ -15,8 +15,8 @@
 //
 // Tiles: one CTA takes 128 target parents (a box of 8 x 4 x 4 in the parent grid; smaller on
 // levels 2 and 3) as the MMA's M and one N-tile of the 8 p^2 outputs, and walks the 26 offsets
-// D in chunks of 64 K values.  Operands stream through shared memory by TMA tiled loads (the
-// source box shifted by D, out-of-range parents zero-filled; B_D's N-tile), 128-byte swizzled,
+// D in chunks of 32 or 64 K values.  Operands stream through shared memory by TMA tiled loads
+// (the source box shifted by D, out-of-range parents zero-filled; B_D's N-tile), swizzled,
 // and both are read by the MMA from shared memory.  Precision is the 3xF16 scheme of the
 // gathered kernel: x = hi + lo in FP16, D += A_lo B_hi + A_hi B_lo + A_hi B_hi with FP32
 // accumulation in TMEM.  Scales: every source parent's coefficients by 2^s_S (max -> 2^10), the
@@ -39,7 +39,6 @@ namespace gbfmm {
 namespace {
 
 constexpr int kBlkRows = 128;  // target parents per CTA (MMA M)
-constexpr int kBlkChunk = 64;  // K values per pipeline stage (one 128-byte swizzled row)
 constexpr int kBlkDrainWarps = 8;
 // drains per offset: each offset's K range (8 p^2) is accumulated in TMEM in two pieces, so no
 // truncating accumulation chain is longer than about half an offset (75 MMAs at p = 10)
@@ -57,18 +56,21 @@ GB_HD void blk_delta(int d, int &dx, int &dy, int &dz)
 
 }  // namespace
 
-template <int P>
+// CH: K values per pipeline stage, one swizzled shared-memory row (64: 128-byte swizzle, 32:
+// 64-byte swizzle)
+template <int P, int CH>
 struct BlkCfg {
     static constexpr int PP = P * P, KD = 8 * PP;
     // N-tile: rows of B_D per CTA (the MMA's N, a multiple of 16) and the stride between tiles
     static constexpr int NT = P == 4 ? 128 : P == 6 ? 144 : P == 8 ? 256 : 208;
     static constexpr int NSTRIDE = P == 10 ? 200 : NT;
     static constexpr int NTILES = (KD + NSTRIDE - 1) / NSTRIDE;
-    static constexpr int NKC = (KD + kBlkChunk - 1) / kBlkChunk;
-    static constexpr int A_BYTES = kBlkRows * kBlkChunk * 2;  // one of hi / lo
-    static constexpr int B_BYTES = NT * kBlkChunk * 2;
+    static constexpr int NKC = (KD + CH - 1) / CH;
+    static constexpr int A_BYTES = kBlkRows * CH * 2;  // one of hi / lo
+    static constexpr int B_BYTES = NT * CH * 2;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int NSTAGE = (3 * STAGE_BYTES <= 210 * 1024) ? 3 : 2;
+    static constexpr int NSTAGE_FIT = (210 * 1024) / STAGE_BYTES;
+    static constexpr int NSTAGE = NSTAGE_FIT > 4 ? 4 : NSTAGE_FIT;
     static constexpr size_t kSmemBytes = (size_t)NSTAGE * STAGE_BYTES + 1024;  // + alignment slack
     static constexpr int NH = NT / 2;  // accumulator columns per drain thread
     static constexpr int TMEM_COLS = 2 * NT <= 256 ? 256 : 512;
@@ -76,6 +78,8 @@ struct BlkCfg {
     static_assert(NH % 8 == 0 && NSTRIDE % 4 == 0 && PP % 4 == 0, "drain / store granularity");
     static_assert(NSTRIDE <= NT && NTILES * NSTRIDE >= KD, "N tiling");
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms");
+    static_assert(CH == 64 || CH == 32, "swizzled row of 128 or 64 bytes");
+    static_assert(NSTAGE >= 2, "pipeline stages");
     static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 
@@ -90,16 +94,17 @@ struct BlkParams {
     int64_t part_stride;             // ksplit > 1: floats between the partial sums of two ranges
 };
 
-// ---- shared-memory matrix descriptor, K-major with 128-byte swizzle ---------------------------
-// rows of 128 bytes, 8-row atoms of 1024 bytes (SBO); a K step of 16 halves advances the start
-// address by 32 bytes inside the atom
-GB_DEV uint64_t blk_desc_sw128(uint32_t saddr)
+// ---- shared-memory matrix descriptor, K-major, swizzled -----------------------------------------
+// rows of 2 CH bytes, 8-row atoms of 16 CH bytes (SBO); a K step of 16 halves advances the start
+// address by 32 bytes inside the atom.  Swizzle mode: 2 = 128-byte, 4 = 64-byte.
+template <int CH>
+GB_DEV uint64_t blk_desc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major operands)
-    d |= (uint64_t)(1024 >> 4) << 32;   // SBO: 8-row atoms
-    d |= (uint64_t)1 << 46;             // descriptor version of the 5th-generation tensor cores
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    d |= (uint64_t)1 << 16;                   // LBO (unused for swizzled K-major operands)
+    d |= (uint64_t)((16 * CH) >> 4) << 32;    // SBO: 8-row atoms
+    d |= (uint64_t)1 << 46;                   // descriptor version of the 5th-generation tensor cores
+    d |= (uint64_t)(CH == 64 ? 2 : 4) << 61;  // swizzle mode
     return d;
 }
 
@@ -249,13 +254,13 @@ __global__ void __launch_bounds__(256) k_blk_build(const float *__restrict__ ops
 }
 
 // ---- the kernel -------------------------------------------------------------------------------
-template <int P, int DS>
+template <int P, int DS, int CH>
 __global__ void __launch_bounds__(kBlkThreads, 1)
     k_m2l_blk(const __grid_constant__ BlkParams prm, const int32_t *__restrict__ begin,
               const int32_t *__restrict__ end, const int8_t *__restrict__ pscale, const int *__restrict__ gexp,
               float *__restrict__ Lc, float *__restrict__ Lpart, int *status)
 {
-    using C = BlkCfg<P>;
+    using C = BlkCfg<P, CH>;
     constexpr int PP = C::PP, KD = C::KD, NT = C::NT, NH = C::NH, NKC = C::NKC, NSTAGE = C::NSTAGE;
     constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(kBlkRows >> 4) << 24);
     constexpr int kProdWarp = kBlkDrainWarps, kMmaWarp = kBlkDrainWarps + 1;
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(kBlkThreads, 1)
     t /= C::NTILES;
     const int tx = t % (pg / bx), ty = (t / (pg / bx)) % (pg / by), tz = t / ((pg / bx) * (pg / by));
     const int x0 = tx * bx, y0 = ty * by, z0 = tz * bz;
-    const uint32_t a_bytes = (uint32_t)rows * kBlkChunk * 2;
+    const uint32_t a_bytes = (uint32_t)rows * CH * 2;
 
     unsigned char *smem =
         blk_smem_raw + ((1024u - (smem_u32(blk_smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned stages
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(kBlkThreads, 1)
                 int dx, dy, dz;
                 blk_delta(d, dx, dy, dz);
                 mbar_expect_tx(&full_bar[st], 2u * a_bytes + 2u * (uint32_t)C::B_BYTES);
-                const int k0 = c * kBlkChunk;
+                const int k0 = c * CH;
                 blk_tma5(a_hi(st), &prm.tmA[l], k0, 0, x0 + dx, y0 + dy, z0 + dz, &full_bar[st]);
                 blk_tma5(a_lo(st), &prm.tmA[l], k0, 1, x0 + dx, y0 + dy, z0 + dz, &full_bar[st]);
                 blk_tma4(b_hi(st), &prm.tmB, k0, nt * C::NSTRIDE, 0, d, &full_bar[st]);
@@ -354,15 +359,15 @@ __global__ void __launch_bounds__(kBlkThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const int kw = KD - c * kBlkChunk < kBlkChunk ? KD - c * kBlkChunk : kBlkChunk;
+                const int kw = KD - c * CH < CH ? KD - c * CH : CH;
                 const uint32_t ah = smem_u32(a_hi(st)), al = smem_u32(a_lo(st));
                 const uint32_t bh = smem_u32(b_hi(st)), bl = smem_u32(b_lo(st));
                 const uint32_t dt = tmem + (uint32_t)(b * NT);
                 for (int j = 0; j < (kw + 15) / 16; ++j) {
                     const uint32_t o = 32u * j;
-                    blk_mma_ss(dt, blk_desc_sw128(al + o), blk_desc_sw128(bh + o), kIdesc, (first && j == 0) ? 0u : 1u);
-                    blk_mma_ss(dt, blk_desc_sw128(ah + o), blk_desc_sw128(bl + o), kIdesc, 1u);
-                    blk_mma_ss(dt, blk_desc_sw128(ah + o), blk_desc_sw128(bh + o), kIdesc, 1u);
+                    blk_mma_ss(dt, blk_desc<CH>(al + o), blk_desc<CH>(bh + o), kIdesc, (first && j == 0) ? 0u : 1u);
+                    blk_mma_ss(dt, blk_desc<CH>(ah + o), blk_desc<CH>(bl + o), kIdesc, 1u);
+                    blk_mma_ss(dt, blk_desc<CH>(ah + o), blk_desc<CH>(bh + o), kIdesc, 1u);
                 }
                 tc_commit(&empty_bar[st]);
                 if (last) tc_commit(&dfull[b]);
@@ -513,7 +518,7 @@ static int blk_tiles(int L)
     for (int l = 2; l <= L; ++l) {
         const int pg = 1 << (l - 1);
         const int bx = pg < 8 ? pg : 8, by = pg < 4 ? pg : 4;
-        n += (pg / bx) * (pg / by) * (pg / by) * BlkCfg<P>::NTILES;
+        n += (pg / bx) * (pg / by) * (pg / by) * BlkCfg<P, 64>::NTILES;
     }
     return n;
 }
@@ -603,12 +608,13 @@ void launch_blk_presplit(int P, int L, const int32_t *begin, const int32_t *end,
     }
 }
 
-template <int P>
+template <int P, int CH>
 static int launch_blk_t(int L, const int32_t *begin, const int32_t *end, const void *presplit,
                         const int8_t *pscale, const void *table, float *Lc, float *Lpart, int *status, cudaStream_t s,
                         int max_ctas)
 {
-    using C = BlkCfg<P>;
+    using C = BlkCfg<P, CH>;
+    constexpr CUtensorMapSwizzle kSw = CH == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return -1;
     BlkParams prm;  // the kernel parameter (copied at launch)
@@ -625,10 +631,10 @@ static int launch_blk_t(int L, const int32_t *begin, const int32_t *end, const v
         void *A = const_cast<__half *>(static_cast<const __half *>(presplit) + (size_t)blk_parents_before(l - 1) * 2 * KD);
         const cuuint64_t dims[5] = {KD, 2, (cuuint64_t)pg, (cuuint64_t)pg, (cuuint64_t)pg};
         const cuuint64_t strides[4] = {KD * 2, KD * 4, KD * 4 * pg, KD * 4 * pg * pg};
-        const cuuint32_t box[5] = {(cuuint32_t)kBlkChunk, 1, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+        const cuuint32_t box[5] = {(cuuint32_t)CH, 1, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
         const cuuint32_t es[5] = {1, 1, 1, 1, 1};
         if (enc(&prm.tmA[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, A, dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, kSw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return -1;
     }
@@ -639,14 +645,14 @@ static int launch_blk_t(int L, const int32_t *begin, const int32_t *end, const v
     {
         const cuuint64_t dims[4] = {KD, KD, 2, 26};
         const cuuint64_t strides[3] = {KD * 2, KD * KD * 2, KD * KD * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)kBlkChunk, (cuuint32_t)C::NT, 1, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)CH, (cuuint32_t)C::NT, 1, 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
         if (enc(&prm.tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(table), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, kSw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return -1;
     }
-    auto kern = k_m2l_blk<P, kBlkDrainsPerOffset>;
+    auto kern = k_m2l_blk<P, kBlkDrainsPerOffset, CH>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
     const int nctas = ntiles * prm.ksplit;
     const int step = max_ctas > 0 ? max_ctas : nctas;
@@ -674,11 +680,13 @@ int launch_m2l_blk(int P, int L, const int32_t *begin, const int32_t *end, const
                    int max_ctas)
 {
     if (L < 2) return 0;
+    // p = 8, 10: four stages of 32-wide K chunks (64-byte swizzle) cover the TMA latency better
+    // than two of 64 (1M, p = 10: 0.343 against 0.372 ms); p = 4, 6 fit three 64-wide stages
     switch (P) {
-    case 4: return launch_blk_t<4>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
-    case 6: return launch_blk_t<6>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
-    case 8: return launch_blk_t<8>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
-    case 10: return launch_blk_t<10>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
+    case 4: return launch_blk_t<4, 64>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
+    case 6: return launch_blk_t<6, 64>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
+    case 8: return launch_blk_t<8, 32>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
+    case 10: return launch_blk_t<10, 32>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
     }
     return -1;
 }
