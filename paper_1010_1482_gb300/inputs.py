@@ -136,10 +136,10 @@ def served_requests(rate: float = 200.0, duration: float = 60.0, seed: int = SEE
                     n_hi: float = 1e6, orders=(4, 6, 10)) -> list[dict]:
     """A request stream: Poisson arrivals at `rate` per second over `duration` seconds
     (exponential gaps), N log-uniform in [n_lo, n_hi], uniform cube or Plummer with equal
-    probability, p drawn uniformly from `orders`.  Each request names a contiguous slice
-    [offset, offset + n) of a particle pool of its distribution (see `request_pool`)."""
+    probability, p drawn uniformly from `orders`.  Request i is an independent particle set:
+    make_particles(n, dist, seed * 1000 + i)."""
     est = int(rate * duration * 1.5 + 64)
-    u = uniform01(seed, 5 * est).reshape(est, 5)
+    u = uniform01(seed, 4 * est).reshape(est, 4)
     t, out = 0.0, []
     for i in range(est):
         t += -np.log(1.0 - u[i, 0]) / rate
@@ -147,12 +147,5 @@ def served_requests(rate: float = 200.0, duration: float = 60.0, seed: int = SEE
             break
         n = int(round(float(np.exp(np.log(n_lo) + u[i, 1] * (np.log(n_hi) - np.log(n_lo))))))
         out.append(dict(t=t, n=n, dist="uniform" if u[i, 2] < 0.5 else "plummer",
-                        p=int(orders[min(int(u[i, 3] * len(orders)), len(orders) - 1)]), slot=float(u[i, 4])))
+                        p=int(orders[min(int(u[i, 3] * len(orders)), len(orders) - 1)]), seed=seed * 1000 + i))
     return out
-
-
-def request_pool(dist: str, size: int, seed: int = SEED_BASE + 5) -> np.ndarray:
-    """The particle pool requests of one distribution take their slices from (iid particles, so
-    every contiguous slice is a sample of the distribution; q of a uniform-cube pool is
-    U[0,1)/size, masses of a Plummer pool 1/size)."""
-    return make_particles(size, dist, seed + (0 if dist == "uniform" else 1))

@@ -64,15 +64,12 @@ def test_batch_matches_single_instances(G, S):
 def test_served_results_identical_alone_and_in_mix(G, S):
     reqs = inputs.served_requests(rate=2000.0, duration=0.03, n_lo=1e3, n_hi=6e4, seed=77)
     assert len(reqs) >= 20
-    pools = {d: inputs.request_pool(d, 1 << 17) for d in ("uniform", "plummer")}
     e = G.gbfmm_engine_create(0, 4, 8 << 30)
     try:
         G.gbfmm_engine_prepare(e, [4, 6, 10])
         bufs, tickets = [], []
         for r in reqs:  # a burst: everything is queued at once and overlaps on the device
-            pool = pools[r["dist"]]
-            off = int(r["slot"] * (len(pool) - r["n"]))
-            hin = pool[off: off + r["n"]]
+            hin = inputs.make_particles(r["n"], r["dist"], r["seed"])
             hout = np.empty_like(hin)
             bufs.append((hin, hout, r))
             tickets.append(G.gbfmm_engine_submit(e, S.params_for(r["dist"], r["p"]), hin, hout))
