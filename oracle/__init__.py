@@ -344,7 +344,7 @@ def _adaptive_sigs():
         ("orc_adaptive_tree", i64, [i64, P, ci, ci, i64, P, P, P, P, P, P, P, P]),
         ("orc_adaptive_colleagues", None, [i64, P, P, P, P, P, P]),
         ("orc_adaptive_list", i64, [ci, i64, P, P, P, P, P, P, P, P, i64]),
-        ("orc_adaptive_passes", ci, [ci, d, P, d, i64, P, P, P, P, P, P, P, P, ci, P, P, P, P, P, P, P, P, P, P,
+        ("orc_adaptive_passes", ci, [ci, ci, d, P, d, i64, P, P, P, P, P, P, P, P, ci, P, P, P, P, P, P, P, P, P, P,
                                      P, P, P]),
         ("orc_p2l_ri", None, [ci, P, i64, P, P]),
     ):
@@ -415,9 +415,11 @@ def build_adaptive_lists(tree: dict) -> dict:
 
 
 def fmm_adaptive(xyzq, p: int, leaf_size: int, eps2: float = 0.0, targets=None, keep: bool = False,
-                 max_level: int = ADAPTIVE_MAX_LEVEL) -> dict:
-    """FP64 adaptive FMM: U (P2P), V (M2L), W (M2P), X (P2L) lists.  Returns 'out' (n, 4) in
-    original order; with `targets`, only the leaves holding them are evaluated."""
+                 max_level: int = ADAPTIVE_MAX_LEVEL, method: int = FMM) -> dict:
+    """FP64 adaptive FMM (method=FMM): U (P2P), V (M2L), W (M2P), X (P2L) lists; or the
+    adaptive treecode (method=TREECODE): M2P over W and over V of the leaf and its ancestors,
+    P2P over U and over X of the leaf and its ancestors.  Returns 'out' (n, 4) in original
+    order; with `targets`, only the leaves holding them are evaluated."""
     L = _adaptive_sigs()
     xyzq32 = _c(xyzq, np.float32).reshape(-1, 4)
     n = len(xyzq32)
@@ -437,7 +439,7 @@ def fmm_adaptive(xyzq, p: int, leaf_size: int, eps2: float = 0.0, targets=None, 
         inv[t["perm"]] = np.arange(n)
         need[leaf_of[inv[np.asarray(targets)]]] = 1
     rc = L.orc_adaptive_passes(
-        p, float(eps2), _p(t["origin"]), float(t["side"]), nc, _p(t["level"]), _p(t["key"]), _p(t["begin"]),
+        p, int(method), float(eps2), _p(t["origin"]), float(t["side"]), nc, _p(t["level"]), _p(t["key"]), _p(t["begin"]),
         _p(t["count"]), _p(t["parent"]), _p(t["child_begin"]), _p(t["nchild"]), _p(t["level_start"]),
         max_level, _p(sx), _p(ls["u_offs"]), _p(ls["u_ids"]), _p(ls["v_offs"]), _p(ls["v_ids"]),
         _p(ls["w_offs"]), _p(ls["w_ids"]), _p(ls["x_offs"]), _p(ls["x_ids"]),

@@ -1008,13 +1008,20 @@ void orc_adaptive_colleagues(int64_t ncells, const int32_t *level, const uint64_
 }
 
 /*
- * Adaptive FMM passes (FP64): P2M at the leaves, M2M up the tree, M2L over V, P2L over X,
- * L2L down the tree, L2P at the leaves, M2P over W and P2P over U.  Particles sorted by key
- * (sxyzq); M, Lc zero on entry (ncells * p(p+1)/2 complex, interleaved); out accumulates
- * (phi, grad) in sorted order.  need: optional mask over cells; when given, only leaves with
- * need set are evaluated (and only the local expansions they use are formed).
+ * Adaptive passes (FP64).  method 0, the FMM: P2M at the leaves, M2M up the tree, M2L over
+ * V, P2L over X, L2L down the tree, L2P at the leaves, M2P over W and P2P over U.
+ * method 1, the treecode (Section "Fast N-body simulation": the treecode evaluates the
+ * multipole expansions at the particles, no local expansions): P2M and M2M as above, then
+ * at each leaf B, M2P over W(B) and over V(A) of B and of every ancestor A, and P2P over U(B)
+ * and over X(A) of B and of every ancestor A.  X(A) holds leaves adjacent to A's parent and
+ * larger than A, whose multipoles do not converge at A's particles: the FMM reaches them
+ * through P2L, the treecode through direct sums.  The sources reached are the FMM's, each once.
+ * Particles sorted by key (sxyzq); M, Lc zero on entry (ncells * p(p+1)/2 complex,
+ * interleaved; Lc unused by the treecode); out accumulates (phi, grad) in sorted order.
+ * need: optional mask over cells; when given, only leaves with need set are evaluated (and
+ * only the local expansions they use are formed).
  */
-int orc_adaptive_passes(int p, double eps2, const double *origin3, double side, int64_t ncells, const int32_t *level,
+int orc_adaptive_passes(int p, int method, double eps2, const double *origin3, double side, int64_t ncells, const int32_t *level,
                         const uint64_t *key, const int32_t *begin, const int32_t *count, const int32_t *parent,
                         const int32_t *child_begin, const int32_t *nchild, const int32_t *level_start, int max_level,
                         const double *sxyzq, const int32_t *u_offs, const int32_t *u_ids, const int32_t *v_offs,
@@ -1052,6 +1059,42 @@ int orc_adaptive_passes(int p, double eps2, const double *origin3, double side, 
                 orc_m2m(p, cc, pc, M + ch * nt, M + c * nt);
             }
         }
+    }
+    if (method == 1) {
+        /* treecode: every needed leaf's particles take the multipoles of W(B) and of V along
+         * its ancestor chain, and the particles of U(B) and of X along that chain */
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t b = 0; b < ncells; ++b) {
+            if (nchild[b] != 0 || !needc[b]) continue;
+            for (int32_t i = begin[b]; i < begin[b] + count[b]; ++i) {
+                const double *xi = sxyzq + 4 * (int64_t)i;
+                double *oi = out + 4 * (int64_t)i;
+                for (int32_t e = w_offs[b]; e < w_offs[b + 1]; ++e) {
+                    const int32_t s = w_ids[e];
+                    double sc[3];
+                    orc_cell_centre(origin3, side, level[s], key[s], sc);
+                    orc_m2p(p, sc, M + (int64_t)s * nt, xi, oi);
+                }
+                for (int32_t e = u_offs[b]; e < u_offs[b + 1]; ++e) {
+                    const int32_t s = u_ids[e];
+                    p2p_one(xi, count[s], sxyzq + 4 * (int64_t)begin[s], eps2, oi);
+                }
+                for (int32_t a = (int32_t)b; a >= 0; a = parent[a]) {
+                    for (int32_t e = v_offs[a]; e < v_offs[a + 1]; ++e) {
+                        const int32_t s = v_ids[e];
+                        double sc[3];
+                        orc_cell_centre(origin3, side, level[s], key[s], sc);
+                        orc_m2p(p, sc, M + (int64_t)s * nt, xi, oi);
+                    }
+                    for (int32_t e = x_offs[a]; e < x_offs[a + 1]; ++e) {
+                        const int32_t s = x_ids[e];
+                        p2p_one(xi, count[s], sxyzq + 4 * (int64_t)begin[s], eps2, oi);
+                    }
+                }
+            }
+        }
+        free(needc);
+        return 0;
     }
     /* M2L over V and P2L over X, into every needed cell */
 #pragma omp parallel for schedule(dynamic, 4)

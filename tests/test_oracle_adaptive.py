@@ -137,3 +137,54 @@ def test_duplicates_beyond_leaf_size_stop_at_max_level():
     e4 = O.rel_l2(O.fmm_adaptive(x, 4, 8, max_level=6)["out"], ref)
     e10 = O.rel_l2(O.fmm_adaptive(x, 10, 8, max_level=6)["out"], ref)
     assert e10 < e4 < 1e-2 and e10 < 1e-5
+
+
+def test_adaptive_treecode_reduces_to_uniform_treecode_on_a_lattice():
+    # with every leaf at level 3, W and X are empty and V along the ancestor chain is the
+    # uniform treecode's M2L list of the leaf and its ancestors
+    x = _lattice(3, 6, 9)
+    ta = O.fmm_adaptive(x, 6, 7, method=O.TREECODE)
+    assert np.all(ta["tree"]["level"][ta["tree"]["nchild"] == 0] == 3)
+    fu = O.fmm(x, 6, 7, level=3, method=O.TREECODE)["out"]
+    assert np.allclose(ta["out"], fu, rtol=1e-12, atol=1e-12 * np.abs(fu).max())
+    # and differs from the FMM on the same tree (local expansions are not formed)
+    ff = O.fmm_adaptive(x, 6, 7)["out"]
+    assert not np.allclose(ta["out"], ff, rtol=1e-12, atol=1e-12 * np.abs(fu).max())
+
+
+@pytest.mark.parametrize("dist", ["plummer", "uniform"])
+def test_adaptive_treecode_error_falls_with_p(dist):
+    x = inputs.make_particles(2500, dist, 37)
+    ref = O.direct(x)
+    errs = [O.rel_l2(O.fmm_adaptive(x, p, 12, method=O.TREECODE)["out"][:, 1:], ref[:, 1:])
+            for p in (2, 4, 6, 8, 10)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-5
+
+
+def test_adaptive_treecode_single_leaf_is_the_direct_sum():
+    x = inputs.plummer(300, 4)
+    ref = O.direct(x, eps2=1e-4)
+    tc = O.fmm_adaptive(x, 4, 300, eps2=1e-4, method=O.TREECODE)["out"]
+    assert np.allclose(tc, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_adaptive_treecode_x_sources_are_direct():
+    # a heavy cluster next to a sparse region: leaves with X lists exist, and the treecode's
+    # error stays at the multipole truncation of the V and W cells alone
+    x = np.vstack([inputs.plummer(1500, 3) * np.array([0.05, 0.05, 0.05, 1.0], dtype=np.float32),
+                   inputs.uniform_cube(400, 5)]).astype(np.float32)
+    t = O.build_adaptive_tree(x, 10)
+    ls = O.build_adaptive_lists(t)
+    assert len(ls["x_ids"]) > 0
+    ref = O.direct(x)
+    e = O.rel_l2(O.fmm_adaptive(x, 10, 10, method=O.TREECODE)["out"][:, 1:], ref[:, 1:])
+    assert e < 1e-5
+
+
+def test_adaptive_treecode_target_subset_matches_full():
+    x = inputs.plummer(3000, 17)
+    tg = inputs.sample_indices(3000, 60, 3)
+    full = O.fmm_adaptive(x, 6, 16, method=O.TREECODE)["out"]
+    part = O.fmm_adaptive(x, 6, 16, targets=tg, method=O.TREECODE)["out"]
+    assert np.array_equal(full[tg], part[tg])
