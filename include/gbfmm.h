@@ -101,9 +101,13 @@ enum {
  *              "Fast N-body simulation"; the paper's own experiments);
  *              GBFMM_TREE_ADAPTIVE: the adaptive octree of the FMM of Cheng,
  *              Greengard & Rokhlin (1999), which the paper cites for its
- *              translation operators, with its U, V, W, X lists.  FMM only.
- *   method     GBFMM_METHOD_FMM or GBFMM_METHOD_TREECODE (same lists, M2P;
- *              uniform tree only).
+ *              translation operators, with its U, V, W, X lists.
+ *   method     GBFMM_METHOD_FMM or GBFMM_METHOD_TREECODE: the multipoles of the
+ *              interaction list of a leaf and of its ancestors act on its
+ *              particles by M2P; no local expansions.  On the adaptive tree the
+ *              treecode takes M2P over W and over V of the leaf and its
+ *              ancestors, and P2P over U and over X of the leaf and its
+ *              ancestors (X cells are larger than the target and close to it).
  *   eps2       softening added to r^2 in P2P only (Listing 1's eps); pairs at
  *              exactly zero distance contribute nothing whatever eps2 is.
  *   has_box    0: root cube from the data (centre of the bounding box, side =

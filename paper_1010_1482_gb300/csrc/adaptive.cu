@@ -622,6 +622,45 @@ __global__ void k_leaf_list(int64_t nc, const int32_t *__restrict__ nchild, uint
     leaves[atomicAdd(cursor, 1u)] = (int32_t)c;
 }
 
+// Treecode lists of a leaf B: its own row of list A followed by the rows of list B of B and of
+// each ancestor up to the root (W then V for M2P; U then X for P2P).  Cells with children
+// get empty rows.  The ancestor walk stops after kAdaptMaxLevel + 1 cells whatever the links.
+__global__ void k_chain_count(int64_t nc, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
+                              const uint32_t *__restrict__ offs_a, const uint32_t *__restrict__ offs_b,
+                              uint32_t *__restrict__ cnt)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    uint32_t k = 0;
+    if (nchild[c] == 0) {
+        k = offs_a[c + 1] - offs_a[c];
+        int32_t a = (int32_t)c;
+        for (int d = 0; d <= kAdaptMaxLevel && a >= 0; ++d, a = parent[a]) k += offs_b[a + 1] - offs_b[a];
+    }
+    cnt[c] = k;
+}
+
+// a warp per leaf copies the rows counted by k_chain_count into its slice of ids
+__global__ void k_chain_fill(int64_t nc, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
+                             const uint32_t *__restrict__ offs_a, const int32_t *__restrict__ ids_a,
+                             const uint32_t *__restrict__ offs_b, const int32_t *__restrict__ ids_b,
+                             const uint32_t *__restrict__ offs, int32_t *__restrict__ ids)
+{
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nc || nchild[c] != 0) return;
+    uint32_t o = offs[c];
+    const uint32_t o_end = offs[c + 1];
+    auto copy = [&](const int32_t *src, uint32_t e0, uint32_t e1) {
+        for (uint32_t e = e0 + lane; e < e1; e += 32)
+            if (o + (e - e0) < o_end) ids[o + (e - e0)] = src[e];
+        o += e1 - e0;
+    };
+    copy(ids_a, offs_a[c], offs_a[c + 1]);
+    int32_t a = (int32_t)c;
+    for (int d = 0; d <= kAdaptMaxLevel && a >= 0; ++d, a = parent[a]) copy(ids_b, offs_b[a], offs_b[a + 1]);
+}
+
 // ---- host orchestration ---------------------------------------------------------------------
 namespace {
 
@@ -659,7 +698,8 @@ void free_adaptive(AdaptiveState &a)
     DevBuf *all[] = {&a.keys0, &a.keys1, &a.idx0, &a.idx1, &a.sx, &a.far, &a.hist, &a.scan_tmp, &a.flags, &a.scan,
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
-                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit, &a.near};
+                     &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit, &a.near,
+                     &a.tc_cnt, &a.tc_offs[0], &a.tc_offs[1], &a.tc_ids[0], &a.tc_ids[1]};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -673,6 +713,83 @@ void free_adaptive(AdaptiveState &a)
         }
     }
 }
+
+namespace {
+
+// The treecode on the adaptive tree, once the tree and its U, V, W, X lists are built: P2M at
+// the leaves and M2M up to level 2, then per leaf M2P over W and the ancestors' V rows and P2P
+// over U and the ancestors' X rows, the M2P sums added in P2P's epilogue.  No local expansions.
+template <class Mark>
+int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float *d_out, cudaStream_t s,
+                      Mark &mark)
+{
+    AdaptiveState &A = ctx->ad;
+    const int P = prm->p, PP = P * P;
+    const int64_t ncells = A.ncells;
+    const int maxl = A.max_level;
+    const std::vector<int> &ls = A.level_start;
+    const OpsCache &ops = ctx->ops[order_slot(P)];
+    ctx->stage_order_last = 0;
+    // chain lists: [0] U + ancestors' X (P2P), [1] W + ancestors' V (M2P)
+    if (grow(A.tc_cnt, 4 * (ncells + 1), false, 0, s) || grow(A.tc_offs[0], 4 * (ncells + 1), false, 0, s) ||
+        grow(A.tc_offs[1], 4 * (ncells + 1), false, 0, s))
+        return fail(ctx, GBFMM_ENOMEM, "treecode lists");
+    const int ka[2] = {kListU, kListW}, kb[2] = {kListX, kListV};
+    for (int j = 0; j < 2; ++j) {
+        k_chain_count<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.nchild.as<int32_t>(), A.parent.as<int32_t>(),
+                                                         A.loffs[ka[j]].as<uint32_t>(), A.loffs[kb[j]].as<uint32_t>(),
+                                                         A.tc_cnt.as<uint32_t>());
+        note_launches(1);
+        launch_exclusive_scan(A.tc_cnt.as<uint32_t>(), A.tc_offs[j].as<uint32_t>(), ncells, A.scan_tmp.as<uint32_t>(),
+                              s);
+    }
+    int32_t *info = A.info.as<int32_t>();
+    k_list_totals<<<1, 32, 0, s>>>(ncells, A.tc_offs[0].as<uint32_t>(), A.tc_offs[1].as<uint32_t>(),
+                                   A.tc_offs[0].as<uint32_t>(), A.tc_offs[1].as<uint32_t>(), info + 40);
+    note_launches(1);
+    int32_t tot[4];
+    cudaMemcpyAsync(tot, info + 40, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int j = 0; j < 2; ++j) {
+        if (grow(A.tc_ids[j], 4 * (size_t)(uint32_t)tot[j] + 4, false, 0, s))
+            return fail(ctx, GBFMM_ENOMEM, "treecode lists");
+        k_chain_fill<<<blocks_for(ncells, 8), 256, 0, s>>>(
+            ncells, A.nchild.as<int32_t>(), A.parent.as<int32_t>(), A.loffs[ka[j]].as<uint32_t>(),
+            A.lids[ka[j]].as<int32_t>(), A.loffs[kb[j]].as<uint32_t>(), A.lids[kb[j]].as<int32_t>(),
+            A.tc_offs[j].as<uint32_t>(), A.tc_ids[j].as<int32_t>());
+        note_launches(1);
+    }
+
+    if (grow(A.M, 4 * (size_t)ncells * PP, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive expansions");
+    float *M = A.M.as<float>();
+    float4 *far = A.far.as<float4>();
+    const float4 *geom = A.geom.as<float4>();
+    const bool deep = maxl >= 2;
+    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), geom,
+                               A.begin.as<int32_t>(), A.count.as<int32_t>(), A.sx.as<float4>(), M, s);
+    mark(4);
+    for (int l = maxl - 1; l >= 2; --l)
+        launch_translate_cells(P, true, ls[l], ls[l + 1] - ls[l], A.child_of.as<int32_t>(), A.nchild.as<int32_t>(),
+                               ops.m2m, M, s);
+    mark(5);
+    cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
+    if (deep)
+        launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                         A.tc_offs[1].as<uint32_t>(), A.tc_ids[1].as<int32_t>(), A.sx.as<float4>(), M, far, s);
+    mark(6);  // M2P is reported with M2L; no L2L, no L2P
+    mark(7);
+    mark(8);
+    launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+                     A.end.as<int32_t>(), A.tc_offs[0].as<uint32_t>(), A.tc_ids[0].as<int32_t>(), far, A.perm,
+                     (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
+    mark(9);
+    A.P = P;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adaptive treecode launch");
+    return GBFMM_OK;
+}
+
+}  // namespace
 
 int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
                       cudaStream_t s)
@@ -906,6 +1023,10 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             launch_alist(k, true, nullptr, offs, ids);
     }
     mark(3);
+    A.n = n;
+    A.skeys = skeys;
+    A.perm = perm;
+    if (prm->method == GBFMM_METHOD_TREECODE) return treecode_adaptive(ctx, prm, n, d_out, s, mark);
 
     // near field beside the far field: P2P (U lists) writes its compensated sums on the
     // context's low-priority stream while the expansions run on its high-priority one (unless
@@ -1049,10 +1170,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                          (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
         mark(9);
     }
-    A.n = n;
     A.P = P;
-    A.skeys = skeys;
-    A.perm = perm;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adaptive launch");
     return GBFMM_OK;
@@ -1089,12 +1207,14 @@ int export_adaptive_expansions(gbfmm_ctx *ctx, int which, double *coef)
     std::vector<int32_t> lev(nc);
     Box box;
     cudaMemcpy(&box, A.box.p, sizeof(Box), cudaMemcpyDeviceToHost);
-    if (A.max_level >= 2) cudaMemcpy(v.data(), which == 0 ? A.M.p : A.Lc.p, 4 * v.size(), cudaMemcpyDeviceToHost);
+    // the treecode forms no local expansions: those export as zeros
+    const bool any = A.max_level >= 2 && (which == 0 || ctx->last_method == GBFMM_METHOD_FMM);
+    if (any) cudaMemcpy(v.data(), which == 0 ? A.M.p : A.Lc.p, 4 * v.size(), cudaMemcpyDeviceToHost);
     cudaMemcpy(lev.data(), A.level.p, 4 * nc, cudaMemcpyDeviceToHost);
     for (size_t c = 0; c < nc; ++c) {
         const int l = lev[c];
         const double h = box.side / (double)(int64_t(1) << l);
-        const bool formed = A.max_level >= 2 && l >= 2;
+        const bool formed = any && l >= 2;
         double *out = coef + c * 2 * NT;
         for (int n = 0; n < P; ++n) {
             const double sc = which == 0 ? pow(h, n) : pow(h, -(n + 1));

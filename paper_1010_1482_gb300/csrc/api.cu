@@ -99,10 +99,6 @@ int check_params(const gbfmm_params *prm, int64_t n, int *L_out, std::string *ms
         *msg = "unknown method";
         return GBFMM_EINVAL;
     }
-    if (prm->tree == GBFMM_TREE_ADAPTIVE && prm->method != GBFMM_METHOD_FMM) {
-        *msg = "the adaptive tree runs the FMM only";
-        return GBFMM_EUNSUPPORTED;
-    }
     if (!(prm->eps2 >= 0.0) || !isfinite(prm->eps2)) {
         *msg = "eps2 must be finite and >= 0";
         return GBFMM_EINVAL;

@@ -45,6 +45,7 @@ struct AdaptiveState {
     DevBuf anchor;                                                 // int4 integer box per cell (depth 21)
     DevBuf presplit;                                               // FP16 pre-split source rows (gathered M2L)
     DevBuf near;                                                   // P2P's compensated sums, 2 float4 per particle
+    DevBuf tc_cnt, tc_offs[2], tc_ids[2];  // treecode rows: [0] U + ancestors' X, [1] W + ancestors' V
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
     int P = 0, max_level = 0;
     std::vector<int> level_start;

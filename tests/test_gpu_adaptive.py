@@ -3,7 +3,8 @@ the FMM the paper cites for its translation operators) against the FP64 adaptive
 
 Tolerances as for the uniform tree:
   * cells (level, key, particle range, parent), sort permutation and the four lists: bit-exact;
-  * potentials and gradients vs the oracle adaptive FMM (same tree, same p): relative L2 <= 1e-5;
+  * potentials and gradients vs the oracle adaptive FMM or treecode (same tree, same p):
+    relative L2 <= 1e-5;
   * expansions: per-degree relative L2 of the scaled coefficients <= 1e-4.
 """
 import numpy as np
@@ -184,7 +185,7 @@ def test_adaptive_concurrent_near_field_equals_serial(G, ctx, n, leaf):
     assert O.rel_l2(a, ref) <= TOL_FMM
 
 
-def test_adaptive_host_path_timing_and_treecode_rejected(G, ctx):
+def test_adaptive_host_path_and_timing(G, ctx):
     x = inputs.plummer(10000, 31)
     prm = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, p=4, leaf_size=32, flags=G.FLAG_STAGE_TIMING)
     xh = torch.from_numpy(x).pin_memory()
@@ -195,10 +196,6 @@ def test_adaptive_host_path_timing_and_treecode_rejected(G, ctx):
     st = G.gbfmm_stage_times(ctx)
     assert st["P2P"] > 0 and st["M2L/M2P"] > 0
     assert G.gbfmm_last_launch_count(ctx) > 0
-    bad = G.gbfmm_default_params(tree=G.TREE_ADAPTIVE, method=G.METHOD_TREECODE)
-    with pytest.raises(G.GbfmmError) as ei:
-        G.gbfmm_plan(bad, 100)
-    assert ei.value.code == G.GBFMM_EUNSUPPORTED
     with pytest.raises(G.GbfmmError):  # the uniform-tree export refuses an adaptive evaluation
         G.gbfmm_export_tree(ctx, len(x), 1)
 
@@ -219,3 +216,55 @@ def test_large_plummer_p8_sampled(G, ctx):
     sub = tg[:256]
     f = O.fmm_adaptive(x, w["p"], w["leaf_size"], targets=sub)["out"]
     assert O.rel_l2(out[sub], f[sub]) <= TOL_FMM
+
+
+# the treecode on the adaptive tree: the level-by-level tree (leaf 20000), one leaf (no
+# expansions), a shell (leaves at many levels), softening
+TC_CASES = [("plummer", 30000, 32, 8, 0.0), ("uniform", 20000, 16, 6, 0.0), ("plummer", 60000, 20000, 4, 0.0),
+            ("plummer", 40, 64, 6, 0.0), ("shell", 8000, 16, 10, 0.0), ("plummer", 20000, 24, 4, 1e-4)]
+
+
+def _shell(n, seed):
+    u = inputs.uniform_cube(n, seed).astype(np.float64)
+    v = u[:, :3] - 0.5
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return np.concatenate([v * 0.5 + 0.5, u[:, 3:]], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("dist,n,leaf,p,eps2", TC_CASES)
+def test_adaptive_treecode_matches_oracle(G, ctx, dist, n, leaf, p, eps2):
+    x = _shell(n, 41) if dist == "shell" else inputs.make_particles(n, dist, 4100 + n)
+    out = run(G, ctx, x, p=p, leaf_size=leaf, method=G.METHOD_TREECODE, eps2=eps2)
+    ref = O.fmm_adaptive(x, p, leaf, eps2=eps2, method=O.TREECODE)["out"]
+    assert O.rel_l2(out[:, 0], ref[:, 0]) <= TOL_FMM
+    assert O.rel_l2(out[:, 1:], ref[:, 1:]) <= TOL_FMM
+    if n >= 20000 and leaf < 1000:
+        # the treecode's error against the direct sum is the oracle treecode's, not the FMM's
+        d = O.direct(x, targets=np.arange(0, n, 97), eps2=eps2)
+        e_or = O.rel_l2(ref[::97, 1:], d[:, 1:])
+        assert O.rel_l2(out[::97, 1:], d[:, 1:]) <= e_or + TOL_FMM
+
+
+def test_adaptive_treecode_expansions_and_stages(G, ctx):
+    n, leaf, p = 20000, 32, 6
+    x = inputs.plummer(n, 616)
+    prm = dict(p=p, leaf_size=leaf, method=G.METHOD_TREECODE)
+    a = run(G, ctx, x, **prm)
+    r = O.fmm_adaptive(x, p, leaf, keep=True, method=O.TREECODE)
+    t = r["tree"]
+    nc = t["ncells"]
+    Mg = G.gbfmm_export_expansions(ctx, 0, nc, p)
+    Lg = G.gbfmm_export_expansions(ctx, 1, nc, p)
+    assert np.all(Lg == 0)  # no local expansions are formed
+    h = t["side"] / 2.0 ** t["level"]
+    deep = t["level"] >= 2
+    for n_ in range(p):
+        cols = slice(n_ * (n_ + 1) // 2, (n_ + 1) * (n_ + 2) // 2)
+        sc = h ** (-n_)
+        a_ = Mg[deep, cols] * sc[deep, None]
+        b_ = r["M"][deep, cols] * sc[deep, None]
+        assert np.linalg.norm(a_ - b_) <= 1e-4 * np.linalg.norm(b_), n_
+    b = run(G, ctx, x, flags=G.FLAG_STAGE_TIMING, **prm)
+    assert np.array_equal(a, b)
+    st = G.gbfmm_stage_times(ctx)
+    assert st["P2P"] > 0 and st["M2L/M2P"] > 0
