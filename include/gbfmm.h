@@ -376,6 +376,43 @@ int gbfmm_graph_destroy(gbfmm_graph *g);
 int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
                     int32_t ncand, int32_t *best_leaf, float *best_ms);
 
+/*
+ * Batched evaluation: nb independent instances (uneven N, orders, trees) in one CUDA graph.
+ * Instance i is d_xyzq + 4*offsets[i] .. 4*offsets[i+1] (floats, DEVICE; offsets is a HOST array
+ * of nb + 1 ascending entries from >= 0), its result at the same offsets of d_out (which must not
+ * overlap d_xyzq), prm[i] (host array) its parameters; GBFMM_FLAG_SERIAL is forced and
+ * GBFMM_FLAG_STAGE_TIMING ignored.  The instances share no state but the context's operator
+ * tables and status word.
+ *
+ * gbfmm_batch_create: evaluates every instance once with counts read back (synchronous; the
+ *   outputs are then valid), lays each adaptive instance out for capacities a margin (1/4 plus a
+ *   constant) above its tree's and lists' counts, evaluates it once more that way, and captures
+ *   all of them into one graph whose `lanes` concurrent branches (1..64) take the instances by
+ *   particle count, largest first, each lane running its instances one after another.  In the
+ *   graph every adaptive stage reads its counts on the device: no host synchronisation, no
+ *   allocation.  The batch owns the instances' trees, lists, expansions and uniform workspaces
+ *   (device memory of the order of the sum of the instances' own).  Adaptive leaf sizes above
+ *   16384 are EUNSUPPORTED.  EINVAL / ENOMEM / ECUDA / EUNSUPPORTED.
+ * gbfmm_batch_launch: one replay on `stream`, asynchronous: it evaluates the particles the
+ *   arrays hold at that time (same pointers, counts and parameters).  An adaptive instance whose
+ *   tree or lists outgrow its capacities (the caller moved its particles far) leaves its output
+ *   unwritten and the next gbfmm_sync_status returns ENOMEM: re-create the batch.
+ * gbfmm_batch_info: *lanes and the number of kernel nodes of the graph (either may be NULL).
+ * gbfmm_batch_destroy: waits for the device and frees the batch.  NULL-safe.  Destroy it before
+ *   its context.
+ * gbfmm_evaluate_batch: the same through a batch the context keeps: the first call with a given
+ *   (nb, offsets, prm, d_xyzq, d_out) creates it with 16 lanes (that call is synchronous),
+ *   later calls with the same arguments only launch its graph on `stream`.
+ */
+typedef struct gbfmm_batch gbfmm_batch;
+int gbfmm_batch_create(gbfmm_batch **out, gbfmm_ctx *ctx, int32_t nb, const int64_t *offsets, const gbfmm_params *prm,
+                       const float *d_xyzq, float *d_out, int32_t lanes);
+int gbfmm_batch_launch(gbfmm_batch *b, void *stream);
+int gbfmm_batch_info(const gbfmm_batch *b, int32_t *lanes, int64_t *kernel_nodes);
+int gbfmm_batch_destroy(gbfmm_batch *b);
+int gbfmm_evaluate_batch(gbfmm_ctx *ctx, int32_t nb, const int64_t *offsets, const gbfmm_params *prm,
+                         const float *d_xyzq, float *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -237,9 +237,11 @@ __global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t
                                                        uint64_t *__restrict__ key, int32_t *__restrict__ begin,
                                                        int32_t *__restrict__ parent, int32_t *__restrict__ child_begin,
                                                        int32_t *__restrict__ nchild, int32_t *__restrict__ child_of,
-                                                       int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_ord)
+                                                       int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_ord,
+                                                       const int32_t *__restrict__ abort)
 {
     __shared__ uint32_t wc[kTreeB / 32][kTreeBins];
+    if (abort && *abort) return;  // the tree outgrew the capacities: nothing is written
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i = blockIdx.x * (int64_t)kTreeB + tid;
     int a = kAdaptMaxLevel + 1, lam = -1;
@@ -286,14 +288,15 @@ __global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t
 // per cell: particle count (end of its key prefix in the sorted keys), the parent of a cell
 // whose parent starts at an earlier particle (key search within the parent level), and the
 // parent's child links
-__global__ void k_tree_links(int64_t nc, int64_t n, const uint64_t *__restrict__ sk, const int32_t *__restrict__ info,
+__global__ void k_tree_links(Span cells, int64_t n, const uint64_t *__restrict__ sk, const int32_t *__restrict__ info,
                              const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
                              const int32_t *__restrict__ begin, int32_t *__restrict__ count, int32_t *__restrict__ end,
                              int32_t *__restrict__ parent, int32_t *__restrict__ child_begin,
                              int32_t *__restrict__ nchild, int32_t *__restrict__ child_of)
 {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     const int l = level[c];
     const uint64_t kk = key[c];
     const int64_t b = begin[c];
@@ -333,10 +336,11 @@ __global__ void k_tree_links(int64_t nc, int64_t n, const uint64_t *__restrict__
     }
 }
 
-__global__ void k_tree_leaf_of(int64_t n, const int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_of)
+__global__ void k_tree_leaf_of(int64_t n, const int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_of,
+                               const int32_t *__restrict__ abort)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) leaf_of[i] = leaves[leaf_of[i]];
+    if (i < n && !(abort && *abort)) leaf_of[i] = leaves[leaf_of[i]];
 }
 
 // list sizes of the four kinds into info[0..3]
@@ -361,12 +365,12 @@ __global__ void k_cell_end(int64_t nc, const int32_t *__restrict__ begin, const 
 // ---- colleagues (positional: slot (dx+1) + 3(dy+1) + 9(dz+1)) -----------------------------
 GB_DEV int slot27(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
 
-__global__ void k_colleagues(int64_t lo, int64_t hi, int l, const uint64_t *__restrict__ key,
-                             const int32_t *__restrict__ parent, const int32_t *__restrict__ child_of,
-                             int32_t *__restrict__ coll)
+__global__ void k_colleagues(Span lv, int l, const uint64_t *__restrict__ key, const int32_t *__restrict__ parent,
+                             const int32_t *__restrict__ child_of, int32_t *__restrict__ coll)
 {
-    int64_t b = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= hi) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(lv)) return;
+    const int64_t b = span_first(lv) + i;
     int32_t *out = coll + b * 27;
     if (l == 0) {
         for (int s = 0; s < 27; ++s) out[s] = -1;
@@ -398,11 +402,12 @@ struct TreeView {
 };
 
 // integer box of every cell at depth 21 (the adjacency tests read it instead of decoding keys)
-__global__ void k_cell_anchor(int64_t nc, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+__global__ void k_cell_anchor(Span cells, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
                               int4 *__restrict__ anc)
 {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     int x, y, z;
     demorton63(key[c], x, y, z);
     const int sh = kAdaptMaxLevel - level[c];
@@ -475,12 +480,13 @@ GB_DEV uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t &total)
 // descent below it, then (U, X) ancestors from the parent up, colleague slot within each.  The
 // count pass (FILL = false) writes the row lengths; the fill pass writes the rows at `offs`.
 template <int KIND, bool FILL>
-__global__ void k_alist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+__global__ void k_alist_warp(Span cells, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
                              int32_t *__restrict__ ids, int *status)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t bb = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (bb >= nc) return;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= span_count(cells)) return;
+    const int64_t bb = span_first(cells) + w;
     const int32_t b = (int32_t)bb;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t e = FILL ? offs[b] : 0u;
@@ -519,11 +525,12 @@ __global__ void k_alist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt,
 // The same U, W and X rows, one thread per cell (slots in sequence): on large trees the warp
 // form leaves most lanes idle while one descends, and its fill repeats the descents.
 template <int KIND, bool FILL>
-__global__ void k_alist_thread(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+__global__ void k_alist_thread(Span cells, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
                                int32_t *__restrict__ ids, int *status)
 {
-    const int64_t bb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (bb >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t bb = span_first(cells) + i;
     const int32_t b = (int32_t)bb;
     uint32_t e = FILL ? offs[b] : 0u;
     auto emit = [&](int32_t d) {
@@ -558,12 +565,13 @@ __global__ void k_alist_thread(int64_t nc, TreeView t, uint32_t *__restrict__ cn
 // (ox + 2 + cx): oz slowest, ox fastest), and a ballot compacts the hits so that a row is
 // written in that order with coalesced stores.
 template <bool FILL>
-__global__ void k_vlist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
+__global__ void k_vlist_warp(Span cells, TreeView t, uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
                              int32_t *__restrict__ ids, uint16_t *__restrict__ codes)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= nc) return;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= span_count(cells)) return;
+    const int64_t b = span_first(cells) + w;
     const int l = t.level[b];
     if (l < 2) {
         if (!FILL && lane == 0) cnt[b] = 0;
@@ -596,20 +604,21 @@ __global__ void k_vlist_warp(int64_t nc, TreeView t, uint32_t *__restrict__ cnt,
 }
 
 // ---- M2L targets grouped by (level, child position) ----------------------------------------
-__global__ void k_group_count(int64_t lo, int64_t nc, const int32_t *__restrict__ level,
-                              const uint64_t *__restrict__ key, uint32_t *__restrict__ gcnt)
+__global__ void k_group_count(Span cells, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                              uint32_t *__restrict__ gcnt)
 {
-    int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     atomicAdd(&gcnt[level[c] * 8 + (int)(key[c] & 7)], 1u);
 }
 
-__global__ void k_group_fill(int64_t lo, int64_t nc, const int32_t *__restrict__ level,
-                             const uint64_t *__restrict__ key, uint32_t *__restrict__ gcur,
-                             int32_t *__restrict__ tlist)
+__global__ void k_group_fill(Span cells, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+                             uint32_t *__restrict__ gcur, int32_t *__restrict__ tlist)
 {
-    int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     const uint32_t pos = atomicAdd(&gcur[level[c] * 8 + (int)(key[c] & 7)], 1u);
     tlist[pos] = (int32_t)c;
 }
@@ -625,12 +634,13 @@ __global__ void k_leaf_list(int64_t nc, const int32_t *__restrict__ nchild, uint
 // Treecode lists of a leaf B: its own row of list A followed by the rows of list B of B and of
 // each ancestor up to the root (W then V for M2P; U then X for P2P).  Cells with children
 // get empty rows.  The ancestor walk stops after kAdaptMaxLevel + 1 cells whatever the links.
-__global__ void k_chain_count(int64_t nc, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
+__global__ void k_chain_count(Span cells, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
                               const uint32_t *__restrict__ offs_a, const uint32_t *__restrict__ offs_b,
                               uint32_t *__restrict__ cnt)
 {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     uint32_t k = 0;
     if (nchild[c] == 0) {
         k = offs_a[c + 1] - offs_a[c];
@@ -641,14 +651,16 @@ __global__ void k_chain_count(int64_t nc, const int32_t *__restrict__ nchild, co
 }
 
 // a warp per leaf copies the rows counted by k_chain_count into its slice of ids
-__global__ void k_chain_fill(int64_t nc, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
+__global__ void k_chain_fill(Span cells, const int32_t *__restrict__ nchild, const int32_t *__restrict__ parent,
                              const uint32_t *__restrict__ offs_a, const int32_t *__restrict__ ids_a,
                              const uint32_t *__restrict__ offs_b, const int32_t *__restrict__ ids_b,
                              const uint32_t *__restrict__ offs, int32_t *__restrict__ ids)
 {
-    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (c >= nc || nchild[c] != 0) return;
+    if (w >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + w;
+    if (nchild[c] != 0) return;
     uint32_t o = offs[c];
     const uint32_t o_end = offs[c + 1];
     auto copy = [&](const int32_t *src, uint32_t e0, uint32_t e1) {
@@ -659,6 +671,87 @@ __global__ void k_chain_fill(int64_t nc, const int32_t *__restrict__ nchild, con
     copy(ids_a, offs_a[c], offs_a[c + 1]);
     int32_t a = (int32_t)c;
     for (int d = 0; d <= kAdaptMaxLevel && a >= 0; ++d, a = parent[a]) copy(ids_b, offs_b[a], offs_b[a + 1]);
+}
+
+// ---- capacities of captured evaluations --------------------------------------------------------
+// info words: [0, kTreeBins] level starts, cells and cells + leaves (k_tree_starts); [32, 36) the
+// list totals; [40, 42) the treecode chain totals; kInfoAbort: set when a count exceeds its
+// capacity, after which every remaining launch of the evaluation does nothing
+constexpr int kInfoLists = 32, kInfoChain = 40, kInfoAbort = 48;
+
+struct GuardCaps {
+    int64_t v[kTreeBins + 1];
+};
+
+// stage 0: the tree (cells, leaves, the cells of every level); stage 1: the four lists;
+// stage 2: the chain lists.  A count above its capacity sets the abort word and kStatusCapacity.
+__global__ void k_guard(const int32_t *__restrict__ info, GuardCaps g, int stage, int32_t *__restrict__ abort,
+                        int *__restrict__ status)
+{
+    if (threadIdx.x != 0) return;
+    bool over = false;
+    if (stage == 0) {
+        over = info[kTreeBins - 1] > g.v[0] || info[kTreeBins] - info[kTreeBins - 1] > g.v[1];
+        for (int l = 0; l <= kAdaptMaxLevel; ++l) over = over || (info[l + 1] - info[l] > g.v[2 + l]);
+    } else {
+        const int base = stage == 1 ? kInfoLists : kInfoChain, k = stage == 1 ? 4 : 2;
+        for (int j = 0; j < k; ++j) over = over || info[base + j] > g.v[j];
+    }
+    if (over) {
+        *abort = 1;
+        atomicOr(status, kStatusCapacity);
+    }
+}
+
+// M2L tiles from the per-(level, child position) target counts, in the order levels 21 .. 2,
+// child positions 0 .. 7, TN targets per tile: gcur[g] = the first tlist slot of group g, and
+// tdesc[t] = (level, position, first slot, count) for t < tcap, count 0 past the last tile (or
+// for every tile once the evaluation is aborted).  One CTA.
+__global__ void k_tile_plan(const uint32_t *__restrict__ gcnt, uint32_t *__restrict__ gcur, int4 *__restrict__ tdesc,
+                            int64_t tcap, int TN, const int32_t *__restrict__ abort)
+{
+    constexpr int NG = 8 * (kAdaptMaxLevel + 1);
+    __shared__ uint32_t s_t0[NG + 1], s_slot[NG];
+    __shared__ int s_g[NG];
+    if (threadIdx.x == 0) {
+        const bool ab = abort && *abort;
+        uint32_t slot = 0, t = 0;
+        int k = 0;
+        for (int l = kAdaptMaxLevel; l >= 2; --l)
+            for (int tau = 0; tau < 8; ++tau) {
+                const int g = l * 8 + tau;
+                const uint32_t c = ab ? 0u : gcnt[g];
+                gcur[g] = slot;
+                s_g[k] = g;
+                s_slot[k] = slot;
+                s_t0[k] = t;
+                ++k;
+                slot += c;
+                t += (c + TN - 1) / TN;
+            }
+        s_t0[k] = t;
+        s_g[k] = -1;
+    }
+    __syncthreads();
+    const int ng = 8 * (kAdaptMaxLevel - 1);
+    for (int64_t t = threadIdx.x; t < tcap; t += blockDim.x) {
+        int4 d = make_int4(0, 0, 0, 0);
+        if (t < s_t0[ng]) {
+            int lo = 0, hi = ng - 1;  // the group k with s_t0[k] <= t < s_t0[k + 1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_t0[mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int g = s_g[lo];
+            const uint32_t j = (uint32_t)(t - s_t0[lo]) * TN;
+            const uint32_t c = gcnt[g];
+            d = make_int4(g / 8, g % 8, (int)(s_slot[lo] + j), (int)min((uint32_t)TN, c - j));
+        }
+        tdesc[t] = d;
+    }
 }
 
 // ---- host orchestration ---------------------------------------------------------------------
@@ -699,7 +792,7 @@ void free_adaptive(AdaptiveState &a)
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
                      &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit, &a.near,
-                     &a.tc_cnt, &a.tc_offs[0], &a.tc_offs[1], &a.tc_ids[0], &a.tc_ids[1]};
+                     &a.tc_cnt, &a.tc_offs[0], &a.tc_offs[1], &a.tc_ids[0], &a.tc_ids[1], &a.partials};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -716,18 +809,42 @@ void free_adaptive(AdaptiveState &a)
 
 namespace {
 
+// Launch ranges of one evaluation: from counts the host read back (exact sizes), or, under
+// capacities, read on the device (cells: ncells capacity; levels: the per-level capacities).
+struct Ranges {
+    bool dev = false;
+    const int32_t *info = nullptr, *abort = nullptr;
+    int64_t ncells = 0, nleaves = 0;
+    const std::vector<int> *ls = nullptr;
+    const AdaptCaps *caps = nullptr;
+    Span cells() const { return dev ? Span{0, ncells, nullptr, info + kTreeBins - 1, abort} : host_span(0, ncells); }
+    // leaf ordinals (a span over the leaf list)
+    Span leaves() const
+    {
+        return dev ? Span{0, nleaves, info + kTreeBins - 1, info + kTreeBins, abort} : host_span(0, nleaves);
+    }
+    Span level(int l) const
+    {
+        return dev ? Span{0, caps->level[l], info + l, info + l + 1, abort}
+                   : host_span((*ls)[l], (*ls)[l + 1] - (*ls)[l]);
+    }
+    // the cells of levels >= 2
+    Span deep() const
+    {
+        return dev ? Span{0, ncells, info + 2, info + kTreeBins - 1, abort} : host_span((*ls)[2], ncells - (*ls)[2]);
+    }
+};
+
 // The treecode on the adaptive tree, once the tree and its U, V, W, X lists are built: P2M at
 // the leaves and M2M up to level 2, then per leaf M2P over W and the ancestors' V rows and P2P
 // over U and the ancestors' X rows, the M2P sums added in P2P's epilogue.  No local expansions.
 template <class Mark>
-int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float *d_out, cudaStream_t s,
-                      Mark &mark)
+int treecode_adaptive(gbfmm_ctx *ctx, AdaptiveState &A, const Ranges &R, const gbfmm_params *prm, int64_t n,
+                      float *d_out, cudaStream_t s, Mark &mark)
 {
-    AdaptiveState &A = ctx->ad;
     const int P = prm->p, PP = P * P;
-    const int64_t ncells = A.ncells;
+    const int64_t ncells = R.ncells;
     const int maxl = A.max_level;
-    const std::vector<int> &ls = A.level_start;
     const OpsCache &ops = ctx->ops[order_slot(P)];
     ctx->stage_order_last = 0;
     // chain lists: [0] U + ancestors' X (P2P), [1] W + ancestors' V (M2P)
@@ -736,7 +853,8 @@ int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float 
         return fail(ctx, GBFMM_ENOMEM, "treecode lists");
     const int ka[2] = {kListU, kListW}, kb[2] = {kListX, kListV};
     for (int j = 0; j < 2; ++j) {
-        k_chain_count<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.nchild.as<int32_t>(), A.parent.as<int32_t>(),
+        if (R.dev) cudaMemsetAsync(A.tc_cnt.p, 0, 4 * (ncells + 1), s);
+        k_chain_count<<<blocks_for(ncells), 256, 0, s>>>(R.cells(), A.nchild.as<int32_t>(), A.parent.as<int32_t>(),
                                                          A.loffs[ka[j]].as<uint32_t>(), A.loffs[kb[j]].as<uint32_t>(),
                                                          A.tc_cnt.as<uint32_t>());
         note_launches(1);
@@ -745,16 +863,24 @@ int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float 
     }
     int32_t *info = A.info.as<int32_t>();
     k_list_totals<<<1, 32, 0, s>>>(ncells, A.tc_offs[0].as<uint32_t>(), A.tc_offs[1].as<uint32_t>(),
-                                   A.tc_offs[0].as<uint32_t>(), A.tc_offs[1].as<uint32_t>(), info + 40);
+                                   A.tc_offs[0].as<uint32_t>(), A.tc_offs[1].as<uint32_t>(), info + kInfoChain);
     note_launches(1);
-    int32_t tot[4];
-    cudaMemcpyAsync(tot, info + 40, sizeof(tot), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    int64_t tot[2];
+    if (!R.dev) {
+        int32_t h[4];
+        cudaMemcpyAsync(h, info + kInfoChain, sizeof(h), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        for (int j = 0; j < 2; ++j) A.counts.chain[j] = tot[j] = (uint32_t)h[j];
+    } else {
+        GuardCaps g{};
+        for (int j = 0; j < 2; ++j) g.v[j] = tot[j] = R.caps->chain[j];
+        k_guard<<<1, 32, 0, s>>>(info, g, 2, info + kInfoAbort, ctx->d_status);
+        note_launches(1);
+    }
     for (int j = 0; j < 2; ++j) {
-        if (grow(A.tc_ids[j], 4 * (size_t)(uint32_t)tot[j] + 4, false, 0, s))
-            return fail(ctx, GBFMM_ENOMEM, "treecode lists");
+        if (grow(A.tc_ids[j], 4 * (size_t)tot[j] + 4, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "treecode lists");
         k_chain_fill<<<blocks_for(ncells, 8), 256, 0, s>>>(
-            ncells, A.nchild.as<int32_t>(), A.parent.as<int32_t>(), A.loffs[ka[j]].as<uint32_t>(),
+            R.cells(), A.nchild.as<int32_t>(), A.parent.as<int32_t>(), A.loffs[ka[j]].as<uint32_t>(),
             A.lids[ka[j]].as<int32_t>(), A.loffs[kb[j]].as<uint32_t>(), A.lids[kb[j]].as<int32_t>(),
             A.tc_offs[j].as<uint32_t>(), A.tc_ids[j].as<int32_t>());
         note_launches(1);
@@ -765,21 +891,20 @@ int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float 
     float4 *far = A.far.as<float4>();
     const float4 *geom = A.geom.as<float4>();
     const bool deep = maxl >= 2;
-    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), geom,
+    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), R.leaves(), A.level.as<int32_t>(), geom,
                                A.begin.as<int32_t>(), A.count.as<int32_t>(), A.sx.as<float4>(), M, s);
     mark(4);
     for (int l = maxl - 1; l >= 2; --l)
-        launch_translate_cells(P, true, ls[l], ls[l + 1] - ls[l], A.child_of.as<int32_t>(), A.nchild.as<int32_t>(),
-                               ops.m2m, M, s);
+        launch_translate_cells(P, true, R.level(l), A.child_of.as<int32_t>(), A.nchild.as<int32_t>(), ops.m2m, M, s);
     mark(5);
     cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
     if (deep)
-        launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+        launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
                          A.tc_offs[1].as<uint32_t>(), A.tc_ids[1].as<int32_t>(), A.sx.as<float4>(), M, far, s);
     mark(6);  // M2P is reported with M2L; no L2L, no L2P
     mark(7);
     mark(8);
-    launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+    launch_p2p_cells(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                      A.end.as<int32_t>(), A.tc_offs[0].as<uint32_t>(), A.tc_ids[0].as<int32_t>(), far, A.perm,
                      (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
     mark(9);
@@ -794,14 +919,24 @@ int treecode_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, float 
 int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
                       cudaStream_t s)
 {
-    AdaptiveState &A = ctx->ad;
+    return evaluate_adaptive_in(ctx, ctx->ad, nullptr, prm, n, d_xyzq, d_out, s, ctx->d_partials, ctx->d_counter);
+}
+
+int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps, const gbfmm_params *prm,
+                         int64_t n, const float *d_xyzq, float *d_out, cudaStream_t s, float *partials,
+                         unsigned *counter)
+{
+    const bool dev = caps != nullptr;
     const int P = prm->p, PP = P * P;
     const int leaf_size = prm->leaf_size;
-    const bool timing = (prm->flags & GBFMM_FLAG_STAGE_TIMING) != 0;
+    const bool timing = !dev && (prm->flags & GBFMM_FLAG_STAGE_TIMING) != 0;
     auto mark = [&](int k) {
         if (timing) cudaEventRecord(ctx->ev[k], s);
     };
-    const int64_t nblk = (n + 4095) / 4096;
+    const int64_t window = std::min<int64_t>(leaf_size, n);
+    if (dev && !caps->valid) return fail(ctx, GBFMM_EINVAL, "adaptive capacities not set");
+    if (dev && !(n > 0 && window <= kTreeMaxWindow))
+        return fail(ctx, GBFMM_EUNSUPPORTED, "device-counted adaptive evaluations take leaf sizes up to 16384");
     bool ok = true;
     auto need = [&](DevBuf &b, size_t bytes) {
         if (grow(b, bytes, false, 0, s) != 0) ok = false;
@@ -830,13 +965,15 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     if (rc != GBFMM_OK) return rc;
     const OpsCache &ops = ctx->ops[order_slot(P)];
     ctx->ops_built_last = built_now;
+    int32_t *info = A.info.as<int32_t>();
+    const int32_t *abort = dev ? info + kInfoAbort : nullptr;
+    if (dev) cudaMemsetAsync(info + kInfoAbort, 0, 4, s);
 
     // ---- box, keys, sort ----
     mark(0);
     const float4 *x = reinterpret_cast<const float4 *>(d_xyzq);
     Box *box = A.box.as<Box>();
-    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, ctx->d_partials, ctx->d_counter,
-                ctx->d_status, s);
+    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, partials, counter, ctx->d_status, s);
     k_keys64<<<blocks_for(n), 256, 0, s>>>(x, n, box, A.keys0.as<uint64_t>(), A.idx0.as<uint32_t>());
     note_launches(1);
     mark(1);
@@ -862,10 +999,9 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     std::vector<int> ls;
     int64_t ncells = 0;
     int maxl = 0;
-    const int64_t window = std::min<int64_t>(leaf_size, n);
-    int32_t *info = A.info.as<int32_t>();
     if (n > 0 && window <= kTreeMaxWindow) {
         // one pass: per-particle level ranges, per-level ranks, one host read of the level sizes
+        // (or, under capacities, a device check of them)
         uint16_t *range = A.flags.as<uint16_t>();
         uint32_t *hist = A.scan.as<uint32_t>(), *hbase = reinterpret_cast<uint32_t *>(A.pcell.p);
         k_tree_ranges<<<(unsigned)tb, kTreeB, 2 * (kTreeB + (int)window), s>>>(n, skeys, (int)window, tb, range,
@@ -873,14 +1009,26 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         launch_exclusive_scan(hist, hbase, kTreeBins * tb, A.scan_tmp.as<uint32_t>(), s);
         k_tree_starts<<<1, 32, 0, s>>>(tb, hbase, info);
         note_launches(2);
-        int32_t hinfo[kTreeBins + 1];
-        cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        ncells = hinfo[kTreeBins - 1];
-        A.nleaves = (uint32_t)(hinfo[kTreeBins] - hinfo[kTreeBins - 1]);
-        for (int l = 0; l <= kAdaptMaxLevel; ++l)
-            if (hinfo[l + 1] > hinfo[l]) maxl = l;
-        for (int l = 0; l <= maxl + 1; ++l) ls.push_back(hinfo[l]);
+        if (!dev) {
+            int32_t hinfo[kTreeBins + 1];
+            cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            ncells = hinfo[kTreeBins - 1];
+            A.nleaves = (uint32_t)(hinfo[kTreeBins] - hinfo[kTreeBins - 1]);
+            for (int l = 0; l <= kAdaptMaxLevel; ++l)
+                if (hinfo[l + 1] > hinfo[l]) maxl = l;
+            for (int l = 0; l <= maxl + 1; ++l) ls.push_back(hinfo[l]);
+        } else {
+            ncells = caps->cells;
+            A.nleaves = caps->leaves;
+            maxl = caps->maxl;
+            GuardCaps g{};
+            g.v[0] = caps->cells;
+            g.v[1] = caps->leaves;
+            for (int l = 0; l <= kAdaptMaxLevel; ++l) g.v[2 + l] = l <= maxl ? caps->level[l] : 0;
+            k_guard<<<1, 32, 0, s>>>(info, g, 0, info + kInfoAbort, ctx->d_status);
+            note_launches(1);
+        }
         if (!cell_bufs(ncells, false, 0) || grow(A.end, 4 * ncells, false, 0, s) ||
             grow(A.leaves, 4 * ncells + 4, false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
@@ -888,13 +1036,15 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
                                                      A.key.as<uint64_t>(), A.begin.as<int32_t>(),
                                                      A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
                                                      A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
-                                                     A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>());
-        k_tree_links<<<blocks_for(ncells), 256, 0, s>>>(ncells, n, skeys, info, A.level.as<int32_t>(),
-                                                       A.key.as<uint64_t>(), A.begin.as<int32_t>(),
-                                                       A.count.as<int32_t>(), A.end.as<int32_t>(),
-                                                       A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
-                                                       A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
-        k_tree_leaf_of<<<blocks_for(n), 256, 0, s>>>(n, A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>());
+                                                     A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>(), abort);
+        const Span cs = dev ? Span{0, ncells, nullptr, info + kTreeBins - 1, abort} : host_span(0, ncells);
+        if (ncells > 0)
+            k_tree_links<<<blocks_for(ncells), 256, 0, s>>>(cs, n, skeys, info, A.level.as<int32_t>(),
+                                                           A.key.as<uint64_t>(), A.begin.as<int32_t>(),
+                                                           A.count.as<int32_t>(), A.end.as<int32_t>(),
+                                                           A.parent.as<int32_t>(), A.child_begin.as<int32_t>(),
+                                                           A.nchild.as<int32_t>(), A.child_of.as<int32_t>());
+        k_tree_leaf_of<<<blocks_for(n), 256, 0, s>>>(n, A.leaves.as<int32_t>(), A.leaf_of.as<int32_t>(), abort);
         note_launches(3);
     } else {
         // level by level (leaf sizes beyond the one-pass window, or no particles): one flag /
@@ -953,35 +1103,41 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     A.ncells = ncells;
     A.max_level = maxl;
     A.level_start = ls;
+    const Ranges R{dev, info, abort, ncells, A.nleaves, &A.level_start, caps};
     if (grow(A.coll, 4 * 27 * ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
     if (grow(A.geom, 16 * (size_t)ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive cells");
     const float4 *geom = A.geom.as<float4>();
-    launch_cell_geom(ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(), box, A.geom.as<float4>(), s);
+    launch_cell_geom(R.cells(), A.level.as<int32_t>(), A.key.as<uint64_t>(), box, A.geom.as<float4>(), s);
     for (int l = 0; l <= maxl; ++l) {
-        const int64_t lo = ls[l], hi = ls[l + 1];
-        k_colleagues<<<blocks_for(hi - lo), 256, 0, s>>>(lo, hi, l, A.key.as<uint64_t>(), A.parent.as<int32_t>(),
-                                                        A.child_of.as<int32_t>(), A.coll.as<int32_t>());
+        const Span lv = R.level(l);
+        if (lv.cap <= 0) continue;
+        k_colleagues<<<blocks_for(lv.cap), 256, 0, s>>>(lv, l, A.key.as<uint64_t>(), A.parent.as<int32_t>(),
+                                                       A.child_of.as<int32_t>(), A.coll.as<int32_t>());
         note_launches(1);
     }
 
-    // ---- lists: counts and offsets of the four kinds, one host read of their sizes, fills ----
+    // ---- lists: counts and offsets of the four kinds, one host read of their sizes (or a device
+    // check against the capacities), fills ----
     if (grow(A.scan_tmp, 4 * (exclusive_scan_tmp_words(ncells + 1) + 64), false, 0, s))
         return fail(ctx, GBFMM_ENOMEM, "adaptive scan");
     if (grow(A.anchor, 16 * (size_t)ncells, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
-    k_cell_anchor<<<blocks_for(ncells), 256, 0, s>>>(ncells, A.level.as<int32_t>(), A.key.as<uint64_t>(),
-                                                    A.anchor.as<int4>());
-    note_launches(1);
+    if (ncells > 0) {
+        k_cell_anchor<<<blocks_for(ncells), 256, 0, s>>>(R.cells(), A.level.as<int32_t>(), A.key.as<uint64_t>(),
+                                                        A.anchor.as<int4>());
+        note_launches(1);
+    }
     TreeView tv{A.level.as<int32_t>(), A.parent.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
                 A.coll.as<int32_t>(), A.key.as<uint64_t>(), A.anchor.as<int4>()};
     const unsigned g8 = blocks_for(ncells, 8);
     // U, W, X rows: a warp per cell while the tree is small (latency: the 27 colleague slots in
     // parallel), a thread per cell on large trees (throughput)
     const bool warp_rows = ncells < kListWarpCells;
+    const Span cs = R.cells();
     auto launch_alist = [&](int k, bool fill, uint32_t *cnt, const uint32_t *offs, int32_t *ids) {
         const unsigned gt = blocks_for(ncells, 128);
 #define GB_ALIST(KIND, FILL)                                                                               \
-    (warp_rows ? k_alist_warp<KIND, FILL><<<g8, 256, 0, s>>>(ncells, tv, cnt, offs, ids, ctx->d_status)    \
-               : k_alist_thread<KIND, FILL><<<gt, 128, 0, s>>>(ncells, tv, cnt, offs, ids, ctx->d_status))
+    (warp_rows ? k_alist_warp<KIND, FILL><<<g8, 256, 0, s>>>(cs, tv, cnt, offs, ids, ctx->d_status)        \
+               : k_alist_thread<KIND, FILL><<<gt, 128, 0, s>>>(cs, tv, cnt, offs, ids, ctx->d_status))
         if (k == kListU) {
             if (fill) GB_ALIST(kListU, true); else GB_ALIST(kListU, false);
         } else if (k == kListW) {
@@ -996,29 +1152,40 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         if (grow(A.lcnt[k], 4 * (ncells + 1), false, 0, s) || grow(A.loffs[k], 4 * (ncells + 1), false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
         uint32_t *cnt = A.lcnt[k].as<uint32_t>();
-        if (k == kListV)
-            k_vlist_warp<false><<<g8, 256, 0, s>>>(ncells, tv, cnt, nullptr, nullptr, nullptr);
-        else
-            launch_alist(k, false, cnt, nullptr, nullptr);
+        if (dev) cudaMemsetAsync(cnt, 0, 4 * (ncells + 1), s);  // rows past the cells stay empty
+        if (ncells > 0) {
+            if (k == kListV)
+                k_vlist_warp<false><<<g8, 256, 0, s>>>(cs, tv, cnt, nullptr, nullptr, nullptr);
+            else
+                launch_alist(k, false, cnt, nullptr, nullptr);
+        }
         launch_exclusive_scan(A.lcnt[k].as<uint32_t>(), A.loffs[k].as<uint32_t>(), ncells,
                               A.scan_tmp.as<uint32_t>(), s);
     }
     k_list_totals<<<1, 32, 0, s>>>(ncells, A.loffs[0].as<uint32_t>(), A.loffs[1].as<uint32_t>(),
-                                   A.loffs[2].as<uint32_t>(), A.loffs[3].as<uint32_t>(), info + 32);
+                                   A.loffs[2].as<uint32_t>(), A.loffs[3].as<uint32_t>(), info + kInfoLists);
     note_launches(1);
-    int32_t ltot[4];
-    cudaMemcpyAsync(ltot, info + 32, sizeof(ltot), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    if (!dev) {
+        int32_t ltot[4];
+        cudaMemcpyAsync(ltot, info + kInfoLists, sizeof(ltot), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        for (int k = 0; k < 4; ++k) A.entries[k] = (uint32_t)ltot[k];
+    } else {
+        GuardCaps g{};
+        for (int k = 0; k < 4; ++k) g.v[k] = A.entries[k] = caps->list[k];
+        k_guard<<<1, 32, 0, s>>>(info, g, 1, info + kInfoAbort, ctx->d_status);
+        note_launches(1);
+    }
     for (int k = 0; k < 4; ++k) {
-        const uint32_t ne = (uint32_t)ltot[k];
-        A.entries[k] = ne;
+        const int64_t ne = A.entries[k];
         if (grow(A.lids[k], 4 * (size_t)ne + 4, false, 0, s)) return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
         if (k == kListV && grow(A.vcode, 2 * (size_t)ne + 4, false, 0, s))
             return fail(ctx, GBFMM_ENOMEM, "adaptive lists");
+        if (ncells == 0) continue;
         const uint32_t *offs = A.loffs[k].as<uint32_t>();
         int32_t *ids = A.lids[k].as<int32_t>();
         if (k == kListV)
-            k_vlist_warp<true><<<g8, 256, 0, s>>>(ncells, tv, nullptr, offs, ids, A.vcode.as<uint16_t>());
+            k_vlist_warp<true><<<g8, 256, 0, s>>>(cs, tv, nullptr, offs, ids, A.vcode.as<uint16_t>());
         else
             launch_alist(k, true, nullptr, offs, ids);
     }
@@ -1026,13 +1193,24 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     A.n = n;
     A.skeys = skeys;
     A.perm = perm;
-    if (prm->method == GBFMM_METHOD_TREECODE) return treecode_adaptive(ctx, prm, n, d_out, s, mark);
+    if (!dev) {
+        AdaptCaps &c = A.counts;
+        c = AdaptCaps{};
+        c.cells = ncells;
+        c.leaves = A.nleaves;
+        c.maxl = maxl;
+        for (int l = 0; l <= maxl && l + 1 < (int)ls.size(); ++l) c.level[l] = ls[l + 1] - ls[l];
+        for (int k = 0; k < 4; ++k) c.list[k] = A.entries[k];
+        c.valid = n > 0 && window <= kTreeMaxWindow;
+    }
+    if (prm->method == GBFMM_METHOD_TREECODE) return treecode_adaptive(ctx, A, R, prm, n, d_out, s, mark);
 
     // near field beside the far field: P2P (U lists) writes its compensated sums on the
     // context's low-priority stream while the expansions run on its high-priority one (unless
-    // the evaluation is timed or serial); L2P adds the far field to them and writes the output
+    // the evaluation is timed, serial or device-counted); L2P adds the far field to them and
+    // writes the output
     const bool split = p2p_near_supported();
-    const bool fork = split && (prm->flags & GBFMM_FLAG_SERIAL) == 0;
+    const bool fork = split && (prm->flags & GBFMM_FLAG_SERIAL) == 0 && !dev;
     ctx->stage_order_last = fork ? 2 : (split ? 1 : 0);
     float4 *near = nullptr;
     if (split) {
@@ -1055,7 +1233,7 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
         cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0);
         s = ctx->s_far;
         if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
-        launch_p2p_cells_near(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+        launch_p2p_cells_near(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                               A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
                               (float)prm->eps2, near, ctx->s_near);
         if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
@@ -1068,90 +1246,80 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
     float *M = A.M.as<float>(), *Lc = A.Lc.as<float>();
     float4 *far = A.far.as<float4>();
     const bool deep = maxl >= 2;
-    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), A.nleaves, A.level.as<int32_t>(), geom,
+    if (deep) launch_p2m_cells(P, A.leaves.as<int32_t>(), R.leaves(), A.level.as<int32_t>(), geom,
                                A.begin.as<int32_t>(), A.count.as<int32_t>(), A.sx.as<float4>(), M, s);
     mark(4);
     for (int l = maxl - 1; l >= 2; --l)
-        launch_translate_cells(P, true, ls[l], ls[l + 1] - ls[l], A.child_of.as<int32_t>(), A.nchild.as<int32_t>(),
-                               ops.m2m, M, s);
+        launch_translate_cells(P, true, R.level(l), A.child_of.as<int32_t>(), A.nchild.as<int32_t>(), ops.m2m, M, s);
     mark(5);
     if (deep) {
-        // M2L targets: every cell at levels >= 2, grouped by (level, child position)
-        const int64_t lo2 = ls[2];
+        // M2L targets: every cell at levels >= 2, grouped by (level, child position) into tiles
+        // planned on the device (no host read); launched over a bound on the tile count, tiles
+        // past the last one empty
+        const Span dp = R.deep();
         uint32_t *gcnt = A.group_cnt.as<uint32_t>();
+        uint32_t *gcur = gcnt + 8 * (kAdaptMaxLevel + 2);
         cudaMemsetAsync(gcnt, 0, 4 * 8 * (kAdaptMaxLevel + 2), s);
-        k_group_count<<<blocks_for(ncells - lo2), 256, 0, s>>>(lo2, ncells, A.level.as<int32_t>(),
-                                                               A.key.as<uint64_t>(), gcnt);
-        note_launches(1);
-        std::vector<uint32_t> hcnt(8 * (kAdaptMaxLevel + 2));
-        cudaMemcpyAsync(hcnt.data(), gcnt, 4 * hcnt.size(), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        std::vector<uint32_t> hcur(hcnt.size());
-        std::vector<int4> tiles;
+        if (dp.cap > 0) {
+            k_group_count<<<blocks_for(dp.cap), 256, 0, s>>>(dp, A.level.as<int32_t>(), A.key.as<uint64_t>(), gcnt);
+            note_launches(1);
+        }
         const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
         const bool f16 = !cores;
         const int TN = f16 ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
-        uint32_t acc = 0;
-        for (int l = maxl; l >= 2; --l)
-            for (int tau = 0; tau < 8; ++tau) {
-                const int gi = l * 8 + tau;
-                hcur[gi] = acc;
-                for (uint32_t st = 0; st < hcnt[gi]; st += TN)
-                    tiles.push_back(make_int4(l, tau, (int)(acc + st), (int)std::min<uint32_t>(TN, hcnt[gi] - st)));
-                acc += hcnt[gi];
-            }
-        if (grow(A.tlist, 4 * (size_t)acc + 4, false, 0, s) || grow(A.tdesc, sizeof(int4) * tiles.size() + 16, false, 0, s))
+        const int64_t tcap = dp.cap / TN + 8 * (int64_t)(maxl - 1) + 1;
+        if (grow(A.tlist, 4 * (size_t)dp.cap + 4, false, 0, s) || grow(A.tdesc, sizeof(int4) * tcap + 16, false, 0, s))
             return fail_joined(GBFMM_ENOMEM, "adaptive tiles");
-        uint32_t *gcur = gcnt + 8 * (kAdaptMaxLevel + 2);
-        cudaMemcpyAsync(gcur, hcur.data(), 4 * hcur.size(), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(A.tdesc.p, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s);
-        k_group_fill<<<blocks_for(ncells - lo2), 256, 0, s>>>(lo2, ncells, A.level.as<int32_t>(),
-                                                              A.key.as<uint64_t>(), gcur, A.tlist.as<int32_t>());
+        k_tile_plan<<<1, 256, 0, s>>>(gcnt, gcur, A.tdesc.as<int4>(), tcap, TN, abort);
         note_launches(1);
-        cudaStreamSynchronize(s);  // the host tile vectors go out of scope
+        if (dp.cap > 0) {
+            k_group_fill<<<blocks_for(dp.cap), 256, 0, s>>>(dp, A.level.as<int32_t>(), A.key.as<uint64_t>(), gcur,
+                                                           A.tlist.as<int32_t>());
+            note_launches(1);
+        }
         if (f16) {
             if (grow(A.cscale, (size_t)ncells + 16, false, 0, s)) return fail_joined(GBFMM_ENOMEM, "adaptive scales");
             if (grow(A.presplit, presplit_bytes(P, ncells), false, 0, s))
                 return fail_joined(GBFMM_ENOMEM, "adaptive pre-split sources");
             void *ps = A.presplit.p;
-            launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s);  // sources split once per cell
-            launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
+            launch_presplit(P, M, ncells, A.cscale.as<int8_t>(), ps, s, R.cells());  // sources split once per cell
+            launch_m2l_f16_tiles(P, A.tdesc.as<int4>(), (int)tcap, A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                                  A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                                  A.vcode.as<uint16_t>(), ops.m2l_f16, M, A.cscale.as<int8_t>(), ps, Lc,
                                  ctx->d_status, s, fork ? sm_count() : 0);
         } else
-            launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tiles.size(), A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
+            launch_m2l_tiles(P, A.tdesc.as<int4>(), (int)tcap, A.tlist.as<int32_t>(), A.begin.as<int32_t>(),
                              A.end.as<int32_t>(), A.loffs[kListV].as<uint32_t>(), A.lids[kListV].as<int32_t>(),
                              A.vcode.as<uint16_t>(), ops.m2l, M, Lc, ctx->d_zero, ctx->d_status, s);
-        launch_p2l_cells(P, ncells, A.level.as<int32_t>(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+        launch_p2l_cells(P, R.cells(), A.level.as<int32_t>(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
                          A.loffs[kListX].as<uint32_t>(), A.lids[kListX].as<int32_t>(), A.sx.as<float4>(), Lc, s);
     }
     mark(6);
     for (int l = 3; l <= maxl; ++l)
-        launch_translate_cells(P, false, ls[l - 1], ls[l] - ls[l - 1], A.child_of.as<int32_t>(),
-                               A.nchild.as<int32_t>(), ops.l2l, Lc, s);
+        launch_translate_cells(P, false, R.level(l - 1), A.child_of.as<int32_t>(), A.nchild.as<int32_t>(), ops.l2l,
+                               Lc, s);
     mark(7);
     if (split) {
         // M2P into the zeroed far field, then L2P adds the local expansion's value and the
         // near-field sums (the same rounding as L2P then M2P: one addition each)
         if (!fork) {
-            launch_p2p_cells_near(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+            launch_p2p_cells_near(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                                   A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
                                   (float)prm->eps2, near, s);
             mark(8);
         }
         cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
         if (deep)
-            launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
-                             A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far,
-                             s);
+            launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(),
+                             A.count.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
+                             A.sx.as<float4>(), M, far, s);
         if (fork) {
             mark(8);
             cudaStreamWaitEvent(s, ctx->ev_near, 0);
             if (timing) cudaEventRecord(ctx->ev_aux[2], s);
         }
         launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s,
-                         near, perm, reinterpret_cast<float4 *>(d_out));
+                         near, perm, reinterpret_cast<float4 *>(d_out), abort);
         mark(9);
         if (fork) {
             cudaEventRecord(ctx->ev_join, s);
@@ -1159,13 +1327,14 @@ int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const 
             s = s_main;
         }
     } else {
-        launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s);
+        launch_l2p_cells(P, n, A.leaf_of.as<int32_t>(), A.level.as<int32_t>(), geom, A.sx.as<float4>(), Lc, far, s,
+                         nullptr, nullptr, nullptr, abort);
         if (deep)
-            launch_m2p_cells(P, A.leaves.as<int32_t>(), A.nleaves, geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
-                             A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(), A.sx.as<float4>(), M, far,
-                             s);
+            launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(),
+                             A.count.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
+                             A.sx.as<float4>(), M, far, s);
         mark(8);
-        launch_p2p_cells(A.leaves.as<int32_t>(), A.nleaves, n, A.sx.as<float4>(), A.begin.as<int32_t>(),
+        launch_p2p_cells(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                          A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(), far, perm,
                          (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
         mark(9);

@@ -307,6 +307,7 @@ int gbfmm_destroy(gbfmm_ctx *ctx)
     if (!ctx) return GBFMM_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    gbfmm_batch_destroy(ctx->batch);
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->d_partials);
@@ -379,6 +380,23 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
         ctx->timed_last = (prm->flags & GBFMM_FLAG_STAGE_TIMING) != 0;
         return GBFMM_OK;
     }
+    return evaluate_uniform_in(ctx, prm, n, d_xyzq, d_out, d_workspace, workspace_bytes,
+                               static_cast<cudaStream_t>(stream), ctx->d_partials, ctx->d_counter);
+}
+
+}  // extern "C"
+
+namespace gbfmm {
+
+int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
+                        void *d_workspace, size_t workspace_bytes, cudaStream_t stream, float *partials,
+                        unsigned *counter)
+{
+    std::string msg;
+    int L = 0;
+    int rc = check_params(prm, n, &L, &msg);
+    if (rc != GBFMM_OK) return fail(ctx, rc, msg);
+    if (n == 0) return GBFMM_OK;
     if (!d_xyzq || !d_out || !d_workspace) return fail(ctx, GBFMM_EINVAL, "null device pointer");
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return fail(ctx, GBFMM_EINVAL, "workspace not 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(d_xyzq) % 16 != 0 || reinterpret_cast<uintptr_t>(d_out) % 16 != 0)
@@ -423,8 +441,7 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
 
     const int64_t launches0 = tl_launches;
     mark(0);
-    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, ctx->d_partials, ctx->d_counter,
-                ctx->d_status, s);
+    launch_bbox(x, n, prm->has_box, prm->box_origin, prm->box_side, box, partials, counter, ctx->d_status, s);
     launch_keys(x, n, box, L, k0, v0, s);
     if (L >= 2) launch_geo_levels(box, L, geo, s);
     mark(1);
@@ -543,6 +560,10 @@ int gbfmm_evaluate(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const flo
     return GBFMM_OK;
 }
 
+}  // namespace gbfmm
+
+extern "C" {
+
 int gbfmm_sync_status(gbfmm_ctx *ctx, void *stream)
 {
     if (!ctx) return GBFMM_EINVAL;
@@ -555,6 +576,8 @@ int gbfmm_sync_status(gbfmm_ctx *ctx, void *stream)
     cudaMemset(ctx->d_status, 0, sizeof(int));
     if (st & kStatusTimeout) return fail(ctx, GBFMM_ETIMEOUT, "a bounded device wait gave up");
     if (st & kStatusNonFinite) return fail(ctx, GBFMM_EINVAL, "non-finite particle coordinate");
+    if (st & kStatusCapacity)
+        return fail(ctx, GBFMM_ENOMEM, "an adaptive tree outgrew the capacities of a captured batch (re-create it)");
     return GBFMM_OK;
 }
 

@@ -137,6 +137,25 @@ struct Frag {
 // Device status bits (OR-ed into the context's status word).
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusCapacity = 4;  // a captured adaptive evaluation outgrew its capacities
+
+// The items one launch covers.  The grid spans `cap` items; the kernel takes count() of them,
+// starting at first().  With no device pointers this is [lo, lo + cap) as launched (counts the
+// host knows); with them, the range [*dlo, *dhi) is read on the device and clamped to cap, and
+// it is empty once *abort is nonzero (counts only the device knows: captured evaluations).
+struct Span {
+    int64_t lo = 0, cap = 0;
+    const int32_t *dlo = nullptr, *dhi = nullptr, *abort = nullptr;
+};
+inline Span host_span(int64_t lo, int64_t n) { return Span{lo, n < 0 ? 0 : n, nullptr, nullptr, nullptr}; }
+GB_DEV int64_t span_first(const Span &s) { return s.dlo ? (int64_t)*s.dlo : s.lo; }
+GB_DEV int64_t span_count(const Span &s)
+{
+    if (s.abort && *s.abort) return 0;
+    if (!s.dhi) return s.cap;
+    const int64_t n = (int64_t)*s.dhi - span_first(s);
+    return n < 0 ? 0 : (n < s.cap ? n : s.cap);
+}
 
 // compensated (Kahan) summation: s the running sum, c the lost low-order part
 struct Kahan {
@@ -262,12 +281,17 @@ void launch_wait_selftest(uint64_t limit_ns, int *status, cudaStream_t s);
 void launch_sort_gather64(uint64_t *k0, uint64_t *k1, uint32_t *v0, uint32_t *v1, int64_t n, int bits,
                           void *scratch, int *err, const float4 *x, float4 *sx, uint64_t **keys_out,
                           uint32_t **idx_out, cudaStream_t s);
-void launch_cell_geom(int64_t nc, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
+// Cell launches over the adaptive tree take their cells as a Span (cells c = first() + i), leaf
+// launches their leaves as a Span over the leaf list (leaf ordinals i < count()).
+void launch_cell_geom(Span cells, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
                       cudaStream_t s);
-void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,
+void launch_p2m_cells(int P, const int32_t *leaves, Span lv, const int32_t *level, const float4 *geom,
                       const int32_t *begin, const int32_t *count, const float4 *sx, float *M, cudaStream_t s);
-void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,
-                            const int32_t *nchild, const float *ops, float *X, cudaStream_t s);
+// parents: the cells whose children are translated (M2M up into them, L2L down from them)
+void launch_translate_cells(int P, bool up, Span parents, const int32_t *child_of, const int32_t *nchild,
+                            const float *ops, float *X, cudaStream_t s);
+// tile lists (tdesc: level, child position, first target in tlist, target count): tiles with a
+// count of 0 are empty and return at once
 void launch_m2l_tiles(int P, const int4 *tdesc, int ntiles, const int32_t *tlist, const int32_t *begin,
                       const int32_t *end, const uint32_t *m2l_offs, const int32_t *m2l_ids, const uint16_t *m2l_code,
                       const float *ops, const float *M, float *Lc, const float *zero_block, int *status,
@@ -291,19 +315,20 @@ int sm_count();
 // per cell: the FP16 scale s_c and the pre-split halves of M~_c 2^s_c (KP / 8 pieces of 8 hi
 // then 8 lo halves), the sources of the list-based FP16 M2L
 size_t presplit_bytes(int P, int64_t ncells);
-void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s);
-void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
+void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s,
+                     Span cells = Span{});
+void launch_p2l_cells(int P, Span cells, const int32_t *level, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
                       cudaStream_t s);
 // near != nullptr: far holds the M2P sums; the local expansion's value, those and the near-field
-// sums are added and written to out[perm[i]]
+// sums are added and written to out[perm[i]].  Nothing runs once *abort is nonzero.
 void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
                       const float4 *sx, const float *Lc, float4 *far, cudaStream_t s, const float4 *near = nullptr,
-                      const uint32_t *perm = nullptr, float4 *out = nullptr);
-void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float4 *geom, const int32_t *begin,
+                      const uint32_t *perm = nullptr, float4 *out = nullptr, const int32_t *abort = nullptr);
+void launch_m2p_cells(int P, const int32_t *leaves, Span lv, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
                       const float *M, float4 *far, cudaStream_t s);
-void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+void launch_p2p_cells(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);
 
@@ -337,7 +362,7 @@ void launch_m2l_rot(int P, int L, const int32_t *begin, const int32_t *end, cons
 bool p2p_near_supported();
 void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
                      const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, cudaStream_t s);
-void launch_p2p_cells_near(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+void launch_p2p_cells_near(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                            const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
                            cudaStream_t s);
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,

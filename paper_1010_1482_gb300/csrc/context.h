@@ -35,6 +35,17 @@ struct DevBuf {
     }
 };
 
+// Sizes of an adaptive evaluation: the counts an evaluation read back (exact), or the
+// capacities a captured evaluation is laid out for.  level[l]: cells of level l; list: U, V,
+// W, X entries; chain: the treecode's two chain-list totals; maxl: deepest level.
+struct AdaptCaps {
+    int64_t cells = 0, leaves = 0;
+    int64_t level[kAdaptiveMaxLevel + 1] = {};
+    int64_t list[4] = {}, chain[2] = {};
+    int32_t maxl = 0;
+    bool valid = false;
+};
+
 // device state of the last adaptive evaluation (all buffers owned by the context)
 struct AdaptiveState {
     DevBuf keys0, keys1, idx0, idx1, sx, far, hist, scan_tmp, flags, scan, pcell, leaf_of, box;
@@ -46,6 +57,8 @@ struct AdaptiveState {
     DevBuf presplit;                                               // FP16 pre-split source rows (gathered M2L)
     DevBuf near;                                                   // P2P's compensated sums, 2 float4 per particle
     DevBuf tc_cnt, tc_offs[2], tc_ids[2];  // treecode rows: [0] U + ancestors' X, [1] W + ancestors' V
+    DevBuf partials;  // root-box reduction scratch of evaluations that do not use the context's
+    AdaptCaps counts;  // the sizes the last host-counted evaluation read back
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
     int P = 0, max_level = 0;
     std::vector<int> level_start;
@@ -91,6 +104,12 @@ struct gbfmm_ctx {
     cudaEvent_t ev_aux[3] = {};
     bool ops_built_last = false;
     int64_t launches_last = 0;
+    // gbfmm_evaluate_batch: the captured batch of the last call and the arguments it was made for
+    gbfmm_batch *batch = nullptr;
+    std::vector<int64_t> batch_offsets;
+    std::vector<gbfmm_params> batch_prm;
+    const float *batch_x = nullptr;
+    float *batch_out = nullptr;
 };
 
 namespace gbfmm {
@@ -102,6 +121,19 @@ int64_t launch_count();
 // adaptive tree (adaptive.cu)
 int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
                       cudaStream_t s);
+// The same evaluation into the state A.  caps == nullptr: sized from counts read back (A.counts
+// receives them).  caps given: no host read, no synchronisation and (after a first call with the
+// same caps) no allocation, so the call can be captured into a CUDA graph; every launch covers
+// the capacities and reads the counts on the device, and a tree or list that outgrows them
+// raises kStatusCapacity and skips the rest of the evaluation.  partials / counter: the root-box
+// reduction scratch (kBoxPartials floats, one zeroed unsigned) of this evaluation.
+int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps, const gbfmm_params *prm,
+                         int64_t n, const float *d_xyzq, float *d_out, cudaStream_t s, float *partials,
+                         unsigned *counter);
+// the uniform-tree evaluation (api.cu) with its root-box reduction scratch given
+int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,
+                        void *d_workspace, size_t workspace_bytes, cudaStream_t s, float *partials,
+                        unsigned *counter);
 int export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *ncells, int32_t *level, uint64_t *key,
                          int32_t *begin, int32_t *count, int32_t *parent, uint32_t *perm);
 int export_adaptive_expansions(gbfmm_ctx *ctx, int which, double *coef);

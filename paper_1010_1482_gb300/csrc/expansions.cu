@@ -1115,26 +1115,27 @@ GB_DEV CellGeom cell_geom63(const Box &b, int l, uint64_t key)
     return g;
 }
 
-__global__ void k_cell_geom(int64_t nc, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
+__global__ void k_cell_geom(Span cells, const int32_t *__restrict__ level, const uint64_t *__restrict__ key,
                             const Box *__restrict__ box, float4 *__restrict__ geom)
 {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
     const CellGeom g = cell_geom63(*box, level[c], key[c]);
     geom[c] = make_float4(g.cx, g.cy, g.cz, g.inv_h);
 }
 
-void launch_cell_geom(int64_t nc, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
+void launch_cell_geom(Span cells, const int32_t *level, const uint64_t *key, const Box *box, float4 *geom,
                       cudaStream_t s)
 {
-    if (nc <= 0) return;
-    k_cell_geom<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, level, key, box, geom);
+    if (cells.cap <= 0) return;
+    k_cell_geom<<<(unsigned)((cells.cap + 255) / 256), 256, 0, s>>>(cells, level, key, box, geom);
     note_launches(1);
 }
 
 // P2M at the listed leaves (levels >= 2), one warp per leaf
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ leaves, int64_t nleaves,
+__global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ leaves, Span lv,
                                                    const int32_t *__restrict__ level, const float4 *__restrict__ geom,
                                                    const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                                                    const float4 *__restrict__ sx, float *__restrict__ M)
@@ -1142,7 +1143,7 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
     __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
     const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= nleaves) return;
+    if (w >= span_count(lv)) return;
     const int32_t c = leaves[w];
     if (level[c] < 2) return;
     const CellGeom cg = geo_cell(geom, c);
@@ -1156,7 +1157,7 @@ __global__ void __launch_bounds__(128) k_p2m_cells(const int32_t *__restrict__ l
 // P2L over the X list (Eq. 3's L from the particles of each X leaf), one warp per cell; adds
 // into the cell's local expansion
 template <int P>
-__global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t *__restrict__ level,
+__global__ void __launch_bounds__(128) k_p2l_cells(Span cells, const int32_t *__restrict__ level,
                                                    const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
                                                    const int32_t *__restrict__ count,
                                                    const uint32_t *__restrict__ x_offs,
@@ -1165,8 +1166,9 @@ __global__ void __launch_bounds__(128) k_p2l_cells(int64_t ncells, const int32_t
 {
     __shared__ float scr[4][32 * WarpSum<P>::LD];
     const int lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= ncells) return;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= span_count(cells)) return;
+    const int64_t b = span_first(cells) + w;
     const uint32_t e0 = x_offs[b], e1 = x_offs[b + 1];
     if (e0 == e1 || level[b] < 2) return;
     const CellGeom cg = geo_cell(geom, b);
@@ -1186,10 +1188,11 @@ __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__r
                                                    const int32_t *__restrict__ level, const float4 *__restrict__ geom,
                                                    const float4 *__restrict__ sx, const float *__restrict__ Lc,
                                                    float4 *__restrict__ far, const float4 *__restrict__ near,
-                                                   const uint32_t *__restrict__ perm, float4 *__restrict__ out)
+                                                   const uint32_t *__restrict__ perm, float4 *__restrict__ out,
+                                                   const int32_t *__restrict__ abort)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (abort && *abort)) return;
     const int32_t c = leaf_of[i];
     float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
     if (level[c] >= 2) {
@@ -1212,7 +1215,7 @@ __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__r
 
 // M2P over the W list, one CTA per listed leaf; adds into the far-field accumulator
 template <int P>
-__global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ leaves,
+__global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ leaves, Span lv,
                                                   const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
                                                   const int32_t *__restrict__ count,
                                                   const uint32_t *__restrict__ w_offs,
@@ -1222,6 +1225,7 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
     __shared__ float4 sF[2 * M2PFold<P>::NM];
     __shared__ float sM[P * P];
     __shared__ M2PFoldTab<P> sT[M2PFold<P>::NM];
+    if (blockIdx.x >= span_count(lv)) return;
     const int32_t b = leaves[blockIdx.x];
     const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
     if (e0 == e1) return;
@@ -1258,7 +1262,7 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
 // shared memory with cp.async (zero-filled for missing children), the next child position's
 // copies in flight while the current one is applied.
 template <int P, bool UP, int TN, int CN>
-__global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells(int64_t lo, int64_t np,
+__global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells(Span par,
                                                                          const int32_t *__restrict__ child_of,
                                                                          const int32_t *__restrict__ nchild,
                                                                          const float *__restrict__ ops,
@@ -1268,6 +1272,8 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
     constexpr int PP = Cfg::PP, PR = Cfg::PR, SB = Cfg::SB, NCG = Cfg::NCG, NRG = Cfg::NRG;
     extern __shared__ __align__(16) float tsm[];
     const int64_t q0 = blockIdx.x * (int64_t)TN;
+    const int64_t lo = span_first(par), np = span_count(par);
+    if (q0 >= np) return;  // the whole CTA: beyond the parents
     const int tid = threadIdx.x;
     const bool work = tid < NRG * NCG;
     const int cg = tid % NCG, rg = tid / NCG;
@@ -1362,78 +1368,80 @@ __global__ void __launch_bounds__(TransCfg<P, UP, TN, CN>::NT) k_translate_cells
     }
 }
 
-void launch_p2m_cells(int P, const int32_t *leaves, int64_t nleaves, const int32_t *level, const float4 *geom,
+void launch_p2m_cells(int P, const int32_t *leaves, Span lv, const int32_t *level, const float4 *geom,
                       const int32_t *begin, const int32_t *count, const float4 *sx, float *M, cudaStream_t s)
 {
-    if (nleaves <= 0) return;
-    const unsigned grid = (unsigned)((nleaves + 3) / 4);
-    GBFMM_DISPATCH_P(P, (k_p2m_cells<PQ><<<grid, 128, 0, s>>>(leaves, nleaves, level, geom, begin, count, sx, M)));
+    if (lv.cap <= 0) return;
+    const unsigned grid = (unsigned)((lv.cap + 3) / 4);
+    GBFMM_DISPATCH_P(P, (k_p2m_cells<PQ><<<grid, 128, 0, s>>>(leaves, lv, level, geom, begin, count, sx, M)));
     note_launches(1);
 }
 
-void launch_p2l_cells(int P, int64_t ncells, const int32_t *level, const float4 *geom, const int32_t *begin,
+void launch_p2l_cells(int P, Span cells, const int32_t *level, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *x_offs, const int32_t *x_ids, const float4 *sx, float *Lc,
                       cudaStream_t s)
 {
-    if (ncells <= 0) return;
-    const unsigned grid = (unsigned)((ncells + 3) / 4);
-    GBFMM_DISPATCH_P(P, (k_p2l_cells<PQ><<<grid, 128, 0, s>>>(ncells, level, geom, begin, count, x_offs, x_ids, sx,
+    if (cells.cap <= 0) return;
+    const unsigned grid = (unsigned)((cells.cap + 3) / 4);
+    GBFMM_DISPATCH_P(P, (k_p2l_cells<PQ><<<grid, 128, 0, s>>>(cells, level, geom, begin, count, x_offs, x_ids, sx,
                                                               Lc)));
     note_launches(1);
 }
 
 void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
                       const float4 *sx, const float *Lc, float4 *far, cudaStream_t s, const float4 *near,
-                      const uint32_t *perm, float4 *out)
+                      const uint32_t *perm, float4 *out, const int32_t *abort)
 {
     if (n <= 0) return;
     const unsigned grid = (unsigned)((n + 127) / 128);
-    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, geom, sx, Lc, far, near, perm, out)));
+    GBFMM_DISPATCH_P(P, (k_l2p_cells<PQ><<<grid, 128, 0, s>>>(n, leaf_of, level, geom, sx, Lc, far, near, perm, out,
+                                                              abort)));
     note_launches(1);
 }
 
-void launch_m2p_cells(int P, const int32_t *leaves, int64_t nleaves, const float4 *geom, const int32_t *begin,
+void launch_m2p_cells(int P, const int32_t *leaves, Span lv, const float4 *geom, const int32_t *begin,
                       const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
                       const float *M, float4 *far, cudaStream_t s)
 {
-    if (nleaves <= 0) return;
-    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)nleaves, 64, 0, s>>>(leaves, geom, begin, count, w_offs, w_ids,
-                                                                          sx, M, far)));
+    if (lv.cap <= 0) return;
+    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)lv.cap, 64, 0, s>>>(leaves, lv, geom, begin, count, w_offs,
+                                                                         w_ids, sx, M, far)));
     note_launches(1);
 }
 
 template <int P, bool UP, int TN, int CN>
-static void translate_cells_tn(int64_t lo, int64_t np, const int32_t *child_of, const int32_t *nchild,
-                               const float *ops, float *X, cudaStream_t s)
+static void translate_cells_tn(Span par, const int32_t *child_of, const int32_t *nchild, const float *ops, float *X,
+                               cudaStream_t s)
 {
     using Cfg = TransCfg<P, UP, TN, CN>;
     const int smem = (int)Cfg::kSmem;  // operator + column block, double-buffered for M2M
     cudaFuncSetAttribute(k_translate_cells<P, UP, TN, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    dim3 grid((unsigned)((np + TN - 1) / TN), UP ? 1 : 8);
-    k_translate_cells<P, UP, TN, CN><<<grid, Cfg::NT, smem, s>>>(lo, np, child_of, nchild, ops, X);
+    dim3 grid((unsigned)((par.cap + TN - 1) / TN), UP ? 1 : 8);
+    k_translate_cells<P, UP, TN, CN><<<grid, Cfg::NT, smem, s>>>(par, child_of, nchild, ops, X);
     note_launches(1);
 }
 
-// the cells-per-CTA choice of the uniform tree's translations (launch_translate_t)
+// the cells-per-CTA choice of the uniform tree's translations (launch_translate_t), on the
+// launch's capacity
 template <int P, bool UP>
-static void translate_cells_t(int64_t lo, int64_t np, const int32_t *child_of, const int32_t *nchild, const float *ops,
-                              float *X, cudaStream_t s)
+static void translate_cells_t(Span par, const int32_t *child_of, const int32_t *nchild, const float *ops, float *X,
+                              cudaStream_t s)
 {
-    const int64_t ctas32 = (np + 31) / 32 * (UP ? 1 : 8);
+    const int64_t ctas32 = (par.cap + 31) / 32 * (UP ? 1 : 8);
     if (ctas32 >= 2 * 152)
-        translate_cells_tn<P, UP, 32, 8>(lo, np, child_of, nchild, ops, X, s);
+        translate_cells_tn<P, UP, 32, 8>(par, child_of, nchild, ops, X, s);
     else
-        translate_cells_tn<P, UP, 16, 2>(lo, np, child_of, nchild, ops, X, s);
+        translate_cells_tn<P, UP, 16, 2>(par, child_of, nchild, ops, X, s);
 }
 
-void launch_translate_cells(int P, bool up, int64_t lo, int64_t nparents, const int32_t *child_of,
-                            const int32_t *nchild, const float *ops, float *X, cudaStream_t s)
+void launch_translate_cells(int P, bool up, Span parents, const int32_t *child_of, const int32_t *nchild,
+                            const float *ops, float *X, cudaStream_t s)
 {
-    if (nparents <= 0) return;
+    if (parents.cap <= 0) return;
     if (up) {
-        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, true>(lo, nparents, child_of, nchild, ops, X, s)));
+        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, true>(parents, child_of, nchild, ops, X, s)));
     } else {
-        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, false>(lo, nparents, child_of, nchild, ops, X, s)));
+        GBFMM_DISPATCH_P(P, (translate_cells_t<PQ, false>(parents, child_of, nchild, ops, X, s)));
     }
 }
 #undef GBFMM_DISPATCH_P

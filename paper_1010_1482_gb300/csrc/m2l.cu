@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(M2LConfig<P, TN, RM, CN, NSTAGE, MINB>::NTHREA
     int tcount = 0;
     if (tdesc) {
         const int4 d = tdesc[blockIdx.x];
+        if (d.w <= 0) return;  // an empty tile (the whole CTA, before any barrier)
         l = d.x;
         tau = d.y;
         tstart = d.z;

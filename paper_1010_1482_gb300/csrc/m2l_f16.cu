@@ -138,13 +138,14 @@ struct F16Tiles {
 // the conversion produces, so the result is identical).
 // one warp per cell
 template <int P>
-__global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, int64_t ncells,
+__global__ void __launch_bounds__(256) k_presplit(const float *__restrict__ M, Span cells,
                                                   int8_t *__restrict__ scale, __half *__restrict__ ps)
 {
     constexpr int PP = P * P, KP = F16Cfg<P>::KP, PER = (KP + 31) / 32;
     const int lane = threadIdx.x & 31;
-    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= ncells) return;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + w;
     float v[PER];
     float m = 0.f;
 #pragma unroll
@@ -182,16 +183,18 @@ size_t presplit_bytes(int P, int64_t ncells)
     return (size_t)ncells * 4 * KP;
 }
 
-void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s)
+// cells: the cells to split (default: all ncells of them, counted on the host)
+void launch_presplit(int P, const float *M, int64_t ncells, int8_t *scale, void *ps, cudaStream_t s, Span cells)
 {
-    if (ncells <= 0) return;
-    const unsigned grid = (unsigned)((ncells + 7) / 8);
+    if (cells.cap == 0 && !cells.dhi) cells = host_span(0, ncells);
+    if (cells.cap <= 0) return;
+    const unsigned grid = (unsigned)((cells.cap + 7) / 8);
     __half *h = static_cast<__half *>(ps);
     switch (P) {
-    case 4: k_presplit<4><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
-    case 6: k_presplit<6><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
-    case 8: k_presplit<8><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
-    case 10: k_presplit<10><<<grid, 256, 0, s>>>(M, ncells, scale, h); break;
+    case 4: k_presplit<4><<<grid, 256, 0, s>>>(M, cells, scale, h); break;
+    case 6: k_presplit<6><<<grid, 256, 0, s>>>(M, cells, scale, h); break;
+    case 8: k_presplit<8><<<grid, 256, 0, s>>>(M, cells, scale, h); break;
+    case 10: k_presplit<10><<<grid, 256, 0, s>>>(M, cells, scale, h); break;
     }
     note_launches(1);
 }
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(F16SCfg<P, CW_>::NTHREADS, 1)
     int tcount = 0;
     if (tdesc) {
         const int4 d = tdesc[tiles.tile0 + blockIdx.x];
+        if (d.w <= 0) return;  // an empty tile (the whole CTA, before any barrier or TMEM)
         tau = d.y;
         tstart = d.z;
         tcount = d.w;

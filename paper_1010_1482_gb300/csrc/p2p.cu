@@ -115,9 +115,10 @@ __global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ 
                                                       const int32_t *__restrict__ p2p_ids,
                                                       const float4 *__restrict__ far,
                                                       const uint32_t *__restrict__ perm, float eps2,
-                                                      float4 *__restrict__ out, float4 *__restrict__ near)
+                                                      float4 *__restrict__ out, float4 *__restrict__ near, Span lv)
 {
     constexpr int NPK = TPT / 2;
+    if (leaves && blockIdx.x >= span_count(lv)) return;  // beyond the listed leaves
     __shared__ ulonglong2 sA[kSrcCap2], sB[kSrcCap2];  // (x, x | y, y), (z, z | q, q)
     __shared__ float4 red[TPT][NT];
     __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1], s_self;
@@ -255,7 +256,8 @@ __global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ 
 // M2L's when both run at once
 static void launch_leaf(unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
                         const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
-                        const uint32_t *perm, float eps2, float4 *out, float4 *near, cudaStream_t s)
+                        const uint32_t *perm, float eps2, float4 *out, float4 *near, cudaStream_t s,
+                        Span lv = Span{})
 {
     static const bool carve = [] {
         cudaFuncSetAttribute(k_p2p2<true, 2, kP2PThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -267,10 +269,10 @@ static void launch_leaf(unsigned grid, int L, const int32_t *leaves, const float
     (void)carve;
     if (eps2 > 0.f)
         k_p2p2<true, 2, kP2PThreads><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm,
-                                                                  eps2, out, near);
+                                                                  eps2, out, near, lv);
     else
         k_p2p2<false, 2, kP2PThreads><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm,
-                                                                   eps2, out, near);
+                                                                   eps2, out, near, lv);
     note_launches(1);
 }
 
@@ -283,12 +285,12 @@ void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const 
                 out, nullptr, s);
 }
 
-void launch_p2p_cells(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+void launch_p2p_cells(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
 {
-    if (n <= 0 || nleaves <= 0) return;
-    launch_leaf((unsigned)nleaves, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, nullptr, s);
+    if (n <= 0 || lv.cap <= 0) return;
+    launch_leaf((unsigned)lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, nullptr, s, lv);
 }
 
 bool p2p_near_supported() { return true; }
@@ -301,12 +303,13 @@ void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, c
                 eps2, nullptr, near, s);
 }
 
-void launch_p2p_cells_near(const int32_t *leaves, int64_t nleaves, int64_t n, const float4 *sx, const int32_t *begin,
+void launch_p2p_cells_near(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                            const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
                            cudaStream_t s)
 {
-    if (n <= 0 || nleaves <= 0) return;
-    launch_leaf((unsigned)nleaves, 0, leaves, sx, begin, end, u_offs, u_ids, nullptr, nullptr, eps2, nullptr, near, s);
+    if (n <= 0 || lv.cap <= 0) return;
+    launch_leaf((unsigned)lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, nullptr, nullptr, eps2, nullptr, near, s,
+                lv);
 }
 
 // Direct all-pairs sum: one thread per target, sources streamed through shared memory in

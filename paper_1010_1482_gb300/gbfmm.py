@@ -104,6 +104,11 @@ def lib():
         "gbfmm_graph_destroy": (i, [P]),
         "gbfmm_tune_leaf": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, ctypes.c_int32,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "gbfmm_batch_create": (i, [ctypes.POINTER(P), P, ctypes.c_int32, P, P, P, P, ctypes.c_int32]),
+        "gbfmm_batch_launch": (i, [P, P]),
+        "gbfmm_batch_info": (i, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64)]),
+        "gbfmm_batch_destroy": (i, [P]),
+        "gbfmm_evaluate_batch": (i, [P, ctypes.c_int32, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -359,6 +364,54 @@ def gbfmm_graph_launch(g, stream=None) -> None:
 
 def gbfmm_graph_destroy(g) -> None:
     lib().gbfmm_graph_destroy(g)
+
+
+def _batch_args(offsets, params):
+    import numpy as np
+
+    nb = len(params)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    assert len(off) == nb + 1
+    arr = (gbfmm_params * max(nb, 1))(*params)
+    return nb, off, arr
+
+
+def gbfmm_batch_create(ctx, offsets, params, xyzq: torch.Tensor, out: torch.Tensor, lanes: int = 16):
+    """Captures the batch (instance i: rows offsets[i]:offsets[i+1] of the device (total, 4)
+    tensors, parameters params[i]) into one CUDA graph; returns its handle."""
+    assert xyzq.is_cuda and out.is_cuda and xyzq.shape == out.shape
+    nb, off, arr = _batch_args(offsets, params)
+    b = ctypes.c_void_p()
+    _check(ctx, lib().gbfmm_batch_create(ctypes.byref(b), ctx, nb, _np_ptr(off), ctypes.cast(arr, ctypes.c_void_p),
+                                         _ptr(xyzq), _ptr(out), lanes))
+    return b
+
+
+def gbfmm_batch_launch(ctx, b, stream=None) -> None:
+    _check(ctx, lib().gbfmm_batch_launch(b, _stream(stream)))
+
+
+def gbfmm_batch_info(b) -> tuple:
+    """(lanes, kernel nodes of the graph)."""
+    lanes = ctypes.c_int32()
+    nodes = ctypes.c_int64()
+    rc = lib().gbfmm_batch_info(b, ctypes.byref(lanes), ctypes.byref(nodes))
+    if rc != GBFMM_OK:
+        raise GbfmmError(rc, "batch info")
+    return int(lanes.value), int(nodes.value)
+
+
+def gbfmm_batch_destroy(b) -> None:
+    lib().gbfmm_batch_destroy(b)
+
+
+def gbfmm_evaluate_batch(ctx, offsets, params, xyzq: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+    """The batch through the graph the context keeps (captured at the first call with these
+    arguments, replayed after)."""
+    assert xyzq.is_cuda and out.is_cuda and xyzq.shape == out.shape
+    nb, off, arr = _batch_args(offsets, params)
+    _check(ctx, lib().gbfmm_evaluate_batch(ctx, nb, _np_ptr(off), ctypes.cast(arr, ctypes.c_void_p), _ptr(xyzq),
+                                           _ptr(out), _stream(stream)))
 
 
 def gbfmm_tune_leaf(ctx, prm: gbfmm_params, xyzq: torch.Tensor, candidates) -> tuple:
