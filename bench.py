@@ -502,9 +502,10 @@ def run_gpu(args, w):
 
 def run_next_rows(args, G, dev, local) -> dict:
     """Batched uneven instances (512 sets, N log-uniform in [1e3, 2e5], half uniform cube on the
-    uniform octree and half Plummer on the adaptive one, p in {4, 8}) through the engine against
-    the plain one-at-a-time evaluation, and a served Poisson request stream (200 req/s, N
-    log-uniform in [1e3, 1e6], p in {4, 6, 10}) with latency percentiles."""
+    uniform octree and half Plummer on the adaptive one, p in {4, 8}) as one captured CUDA graph
+    (gbfmm_batch_*) against the plain one-at-a-time evaluation and the engine's host workers, and
+    a served Poisson request stream (200 req/s, N log-uniform in [1e3, 1e6], p in {4, 6, 10})
+    with latency percentiles."""
     import torch
 
     from paper_1010_1482_gb300 import serving
@@ -512,41 +513,78 @@ def run_next_rows(args, G, dev, local) -> dict:
     res = {}
     inst = inputs.batch_instances()
     x, offsets, params = serving.make_batch(inst, dev)
+    total = int(offsets[-1])
     ctx = G.gbfmm_create(local)
     serving.run_plain(ctx, x, offsets, params)  # warm-up (operator tables, workspace)
     t_plain, out_plain = serving.run_plain(ctx, x, offsets, params)
-    G.gbfmm_destroy(ctx)
+
+    def graph_batch(prms, ref, lanes=64, reps=10):
+        """Create the batch's graph (timed on the host), replay it `reps` times (CUDA events per
+        replay, median), compare with the plain outputs, then refill the arrays with another
+        sample of the same counts and compare one replay with that sample's plain outputs."""
+        out = torch.empty_like(x)
+        t0 = time.perf_counter()
+        b = G.gbfmm_batch_create(ctx, offsets, prms, x, out, lanes=lanes)
+        create_s = time.perf_counter() - t0
+        nl, nodes = G.gbfmm_batch_info(b)
+        for _ in range(3):
+            G.gbfmm_batch_launch(ctx, b)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.gbfmm_batch_launch(ctx, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        G.gbfmm_sync_status(ctx)
+        same = bool(torch.equal(out, ref))
+        x_keep = x.clone()
+        x2, off2, _ = serving.make_batch([dict(r, seed=r["seed"] + 10 ** 6) for r in inst], dev)
+        assert np.array_equal(off2, offsets)
+        x.copy_(x2)
+        G.gbfmm_batch_launch(ctx, b)
+        G.gbfmm_sync_status(ctx)
+        _, ref2 = serving.run_plain(ctx, x, offsets, prms)
+        same2 = bool(torch.equal(out, ref2))
+        x.copy_(x_keep)
+        G.gbfmm_batch_destroy(b)
+        ms = float(np.median(ts))
+        return {"lanes": nl, "kernel_nodes": nodes, "create_s": create_s, "replay_ms": ms,
+                "batched_particles_per_s": total / (ms / 1e3), "identical_to_plain": same,
+                "new_sample_identical_to_plain": same2}, out
+
+    g64, out_g = graph_batch(params, out_plain)
+    # the engine: independent gbfmm_evaluate calls on host worker threads (contexts, streams)
     e = G.gbfmm_engine_create(local, args.workers, 40 << 30)
     G.gbfmm_engine_prepare(e, [4, 6, 8, 10])
     out = torch.empty_like(x)
-
-    def batched(prms):
-        G.gbfmm_engine_run_batch(e, offsets, prms, x, out)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = G.gbfmm_engine_run_batch(e, offsets, prms, x, out)
-        torch.cuda.synchronize()
-        return time.perf_counter() - t0, st
-
-    t_batch, st = batched(params)
-    total = int(offsets[-1])
-    res["batched"] = {
-        "instances": len(inst), "particles": total, "workers": args.workers,
-        "plain_particles_per_s": total / t_plain, "batched_particles_per_s": total / t_batch,
-        "speedup": t_plain / t_batch, "failed": int(sum(1 for v in st if v != 0)),
-        "identical_to_plain": bool(torch.equal(out, out_plain)),
-        "note": "plain = gbfmm_evaluate one instance at a time on one stream; batched = "
-                "gbfmm_engine_run_batch over the workers (their own streams and contexts), wall clock",
-    }
+    G.gbfmm_engine_run_batch(e, offsets, params, x, out)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = G.gbfmm_engine_run_batch(e, offsets, params, x, out)
+    torch.cuda.synchronize()
+    t_engine = time.perf_counter() - t0
+    res["batched"] = dict(g64, **{
+        "instances": len(inst), "particles": total,
+        "plain_particles_per_s": total / t_plain,
+        "speedup_vs_plain": t_plain / (g64["replay_ms"] / 1e3),
+        "engine_particles_per_s": total / t_engine, "engine_workers": args.workers,
+        "engine_failed": int(sum(1 for v in st if v != 0)),
+        "engine_identical_to_plain": bool(torch.equal(out, out_plain)),
+        "note": "batched = one replay of the captured graph of all 512 instances (gbfmm_batch_launch), device time; "
+                "plain = gbfmm_evaluate one instance at a time on one stream, wall clock; engine = "
+                "gbfmm_engine_run_batch over host worker threads, wall clock; new_sample = the arrays refilled "
+                "with another seeded sample of the same counts and replayed",
+    })
     # the same batch with leaf sizes from the autotuner (gbfmm_tune_leaf per (distribution, p,
-    # log2 N) bucket, candidates 32 / 64 / 128 / 256), plain and batched
-    ctx = G.gbfmm_create(local)
+    # log2 N) bucket, candidates 32 / 64 / 128 / 256)
     leaves = serving.tune_leaves(ctx, x, offsets, inst)
     tparams = serving.tuned_params(inst, leaves)
     serving.run_plain(ctx, x, offsets, tparams)
     t_plain_t, out_plain_t = serving.run_plain(ctx, x, offsets, tparams)
-    G.gbfmm_destroy(ctx)
-    t_batch_t, st_t = batched(tparams)
+    gt, _ = graph_batch(tparams, out_plain_t)
     # accuracy of both leaf choices on 8 instances, 256 seeded targets each, vs FP64 direct
     import oracle
 
@@ -559,14 +597,13 @@ def run_next_rows(args, G, dev, local) -> dict:
         for name, o in (("leaf_64", out_plain), ("tuned", out_plain_t)):
             got = o[a:b].cpu().numpy().astype(np.float64)[tg]
             errs[name].append(oracle.rel_l2(got[:, 1:], ref[:, 1:]))
-    res["batched_tuned"] = {
+    res["batched_tuned"] = dict(gt, **{
         "leaf_sizes": {f"{d}/p{p}/2^{k}": v for (d, p, k), v in sorted(leaves.items())},
-        "plain_particles_per_s": total / t_plain_t, "batched_particles_per_s": total / t_batch_t,
-        "speedup_vs_leaf64_batched": t_batch / t_batch_t, "failed": int(sum(1 for v in st_t if v != 0)),
-        "identical_to_plain": bool(torch.equal(out, out_plain_t)),
+        "plain_particles_per_s": total / t_plain_t,
         "grad_err_max": {k: float(max(v)) for k, v in errs.items()},
-    }
-    del x, out, out_plain, out_plain_t
+    })
+    G.gbfmm_destroy(ctx)
+    del x, out, out_plain, out_plain_t, out_g
     res["graph"] = run_graph(G, dev, local)
     reqs = inputs.served_requests(duration=args.serve_seconds)
     warm = inputs.served_requests(duration=0.5, seed=inputs.SEED_BASE + 6)

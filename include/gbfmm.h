@@ -385,8 +385,10 @@ int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const fl
  * tables and status word.
  *
  * gbfmm_batch_create: evaluates every instance once with counts read back (synchronous; the
- *   outputs are then valid), lays each adaptive instance out for capacities a margin (1/4 plus a
- *   constant) above its tree's and lists' counts, evaluates it once more that way, and captures
+ *   outputs are then valid), lays each adaptive instance out for capacities above its tree's
+ *   and lists' counts (twice the cells and leaves, levels down to three below the deepest, lists
+ *   in proportion to the cells with half again as margin, V rows up to 189 per cell),
+ *   evaluates it once more that way, and captures
  *   all of them into one graph whose `lanes` concurrent branches (1..64) take the instances by
  *   particle count, largest first, each lane running its instances one after another.  In the
  *   graph every adaptive stage reads its counts on the device: no host synchronisation, no
@@ -401,7 +403,7 @@ int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const fl
  * gbfmm_batch_destroy: waits for the device and frees the batch.  NULL-safe.  Destroy it before
  *   its context.
  * gbfmm_evaluate_batch: the same through a batch the context keeps: the first call with a given
- *   (nb, offsets, prm, d_xyzq, d_out) creates it with 16 lanes (that call is synchronous),
+ *   (nb, offsets, prm, d_xyzq, d_out) creates it with 64 lanes (that call is synchronous),
  *   later calls with the same arguments only launch its graph on `stream`.
  */
 typedef struct gbfmm_batch gbfmm_batch;

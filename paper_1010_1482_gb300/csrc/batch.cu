@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -31,25 +32,33 @@ using gbfmm::fail;
 namespace {
 
 constexpr int kMaxLanes = 64;
-constexpr int kEvaluateBatchLanes = 16;  // gbfmm_evaluate_batch's concurrent branches
+constexpr int kEvaluateBatchLanes = 64;  // gbfmm_evaluate_batch's concurrent branches
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Capacities a margin above the counts of an evaluation (a quarter, plus a constant: list totals
-// of two samples of 5000 Plummer particles differ by up to 14%).  Another sample of the same
-// distribution moves cells between levels and may reach a few levels deeper (a close pair), so
-// every level up to three below the deepest one may hold as many cells as the whole tree; the
-// per-level launches then cover the whole capacity, their CTAs past the level's cells idle.
+// Capacities above the counts of an evaluation.  Another sample of the same distribution and
+// count can have twice the cells on a small tree (a cell near the split threshold splits or not:
+// 119 against 237 cells for two samples of 3981 Plummer particles at leaf size 256), moves cells
+// between levels and may reach a few levels deeper; so the cells and leaves get twice the count
+// plus a constant, and every level down to three below the deepest may hold as many cells as
+// the whole tree (the per-level launches cover the whole capacity, their CTAs past the level's
+// cells idle).  The lists grow with the cells, and by more than the cells on small trees (their
+// rows fill as the tree deepens): the V rows are bounded by 189 per cell, the others take their
+// entries per cell times the cell capacity, with half again as margin.
 AdaptCaps with_margin(const AdaptCaps &c)
 {
     auto up = [](int64_t v, int64_t slack) { return v + v / 4 + slack; };
+    auto per_cell = [&](int64_t v, int64_t cap_cells) {
+        const int64_t prop = c.cells > 0 ? (int64_t)std::ceil(1.5 * (double)v * (double)cap_cells / (double)c.cells) : 0;
+        return std::max(up(v, 256), prop) + 256;
+    };
     AdaptCaps r = c;
-    r.cells = up(c.cells, 64);
-    r.leaves = up(c.leaves, 64);
+    r.cells = 2 * c.cells + 64;
+    r.leaves = 2 * c.leaves + 64;
     r.maxl = std::min(gbfmm::kAdaptiveMaxLevel, c.maxl + 3);
     for (int l = 0; l <= gbfmm::kAdaptiveMaxLevel; ++l) r.level[l] = l <= r.maxl ? r.cells : 0;
-    for (int k = 0; k < 4; ++k) r.list[k] = up(c.list[k], 256);
-    for (int j = 0; j < 2; ++j) r.chain[j] = up(c.chain[j], 256);
+    for (int k = 0; k < 4; ++k) r.list[k] = k == 1 ? 189 * r.cells : per_cell(c.list[k], r.cells);
+    for (int j = 0; j < 2; ++j) r.chain[j] = per_cell(c.chain[j], r.cells);
     return r;
 }
 
