@@ -252,13 +252,6 @@ int gbfmm_export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *nce
  */
 int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
 
-/* Measured arithmetic throughput of the current device, for roofline denominators (no
- * counterpart in the paper): kind 0 = FP32 FFMA on the CUDA cores, 1 = warp-level TF32 tensor
- * MMA (m16n8k8), 2 = warp-level BF16 tensor MMA (m16n8k16), FP32 accumulation.  Runs a
- * register-only kernel on 4 CTAs per SM (allocates and frees a small buffer, synchronises
- * the device).  *tflops receives TFLOP/s.  EINVAL / ENOMEM / ECUDA. */
-int gbfmm_probe_peak(int kind, double *tflops);
-
 /* Test of the bounded device waits (no counterpart in the paper): enqueues one CTA that waits
  * on an mbarrier no thread arrives on, with the same bounded-wait routine the M2L pipeline
  * uses, limited to limit_ms (0 < limit_ms <= 2000).  When it gives up it raises the context's

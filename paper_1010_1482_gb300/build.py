@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", CSRC, "-I", INCLUDE]
 PER_TU = {"tree.cu": ["-fmad=false"]}
-SOURCES = ["api.cu", "tree.cu", "expansions.cu", "m2l.cu", "m2l_f16.cu", "p2p.cu", "adaptive.cu", "engine.cu", "graph.cu", "static_sort.cu", "peak.cu", "m2l_blk.cu", "m2l_rot.cu", "batch.cu"]
+SOURCES = ["api.cu", "tree.cu", "expansions.cu", "m2l.cu", "m2l_f16.cu", "p2p.cu", "adaptive.cu", "engine.cu", "graph.cu", "static_sort.cu", "m2l_blk.cu", "m2l_rot.cu", "batch.cu"]
 
 
 def nvcc() -> str:

@@ -89,7 +89,6 @@ def lib():
         "gbfmm_stage_times": (i, [P, P, i, ctypes.POINTER(i)]),
         "gbfmm_last_launch_count": (i, [P, ctypes.POINTER(i64)]),
         "gbfmm_sort_static": (i, [ctypes.POINTER(gbfmm_params), i64, P, P, P, P, P, P]),
-        "gbfmm_probe_peak": (i, [i, ctypes.POINTER(ctypes.c_double)]),
         "gbfmm_selftest_wait": (i, [P, ctypes.c_double, P]),
         "gbfmm_engine_create": (i, [ctypes.POINTER(P), i, ctypes.c_int32, ctypes.c_size_t]),
         "gbfmm_engine_destroy": (i, [P]),
@@ -272,13 +271,6 @@ def gbfmm_last_launch_count(ctx) -> int:
 
 def gbfmm_selftest_wait(ctx, limit_ms: float, stream=None) -> None:
     _check(ctx, lib().gbfmm_selftest_wait(ctx, float(limit_ms), _stream(stream)))
-
-
-def gbfmm_probe_peak(kind: int) -> float:
-    """Measured TFLOP/s of the current device: 0 FP32 FFMA, 1 TF32 warp MMA, 2 BF16 warp MMA."""
-    t = ctypes.c_double()
-    _check(None, lib().gbfmm_probe_peak(int(kind), ctypes.byref(t)))
-    return t.value
 
 
 def gbfmm_sort_static(prm: gbfmm_params, xyzq: torch.Tensor, sorted_xyzq: torch.Tensor, perm: torch.Tensor,
