@@ -899,8 +899,9 @@ int treecode_adaptive(gbfmm_ctx *ctx, AdaptiveState &A, const Ranges &R, const g
     mark(5);
     cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
     if (deep)
-        launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
-                         A.tc_offs[1].as<uint32_t>(), A.tc_ids[1].as<int32_t>(), A.sx.as<float4>(), M, far, s);
+        launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(), A.end.as<int32_t>(),
+                         A.tc_offs[1].as<uint32_t>(), A.tc_ids[1].as<int32_t>(), A.sx.as<float4>(), M, far, s,
+                         true);
     mark(6);  // M2P is reported with M2L; no L2L, no L2P
     mark(7);
     mark(8);
@@ -1311,7 +1312,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
         cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
         if (deep)
             launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(),
-                             A.count.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
+                             A.end.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
                              A.sx.as<float4>(), M, far, s);
         if (fork) {
             mark(8);
@@ -1331,7 +1332,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
                          nullptr, nullptr, nullptr, abort);
         if (deep)
             launch_m2p_cells(P, A.leaves.as<int32_t>(), R.leaves(), geom, A.begin.as<int32_t>(),
-                             A.count.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
+                             A.end.as<int32_t>(), A.loffs[kListW].as<uint32_t>(), A.lids[kListW].as<int32_t>(),
                              A.sx.as<float4>(), M, far, s);
         mark(8);
         launch_p2p_cells(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),

@@ -325,9 +325,11 @@ void launch_p2l_cells(int P, Span cells, const int32_t *level, const float4 *geo
 void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *level, const float4 *geom,
                       const float4 *sx, const float *Lc, float4 *far, cudaStream_t s, const float4 *near = nullptr,
                       const uint32_t *perm = nullptr, float4 *out = nullptr, const int32_t *abort = nullptr);
+// long_rows: the treecode's chain rows (the warp kernel, k_m2p_warp); else the FMM's short W
+// rows (one CTA of 64 per leaf, k_m2p_cells)
 void launch_m2p_cells(int P, const int32_t *leaves, Span lv, const float4 *geom, const int32_t *begin,
-                      const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
-                      const float *M, float4 *far, cudaStream_t s);
+                      const int32_t *end, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
+                      const float *M, float4 *far, cudaStream_t s, bool long_rows = false);
 void launch_p2p_cells(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
                       const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);

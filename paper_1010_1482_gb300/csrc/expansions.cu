@@ -916,8 +916,8 @@ void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, con
 }
 
 // ------------------------------------------------------------------------------------------
-// M2P (treecode far field): one CTA per target leaf, one thread per target particle; for
-// every level 2..L the sources are the M2L list of the leaf's ancestor.  With x^ = (x - c)/h:
+// M2P (treecode far field; the adaptive FMM's W lists): the multipole of a source cell evaluated
+// at a target particle.  With x^ = (x - c)/h:
 //   phi = (1/h) sum M~_n^m I_n^m(x^)
 //   dphi/dz             = -(1/h^2) sum sqrt((n+1-m)(n+1+m)) M~_n^m I_{n+1}^m
 //   dphi/dx + i dphi/dy =  (1/h^2) sum s(m) sqrt((n+m+2)(n+m+1)) M~_n^m I_{n+1}^{m+1},
@@ -1050,52 +1050,210 @@ GB_DEV void m2p_accumulate_folded(const float4 *__restrict__ F, float x, float y
     o[3] += gz * ih2;
 }
 
-template <int P>
-__global__ void __launch_bounds__(128) k_m2p(int L, const float *__restrict__ geo, const float4 *__restrict__ sx,
-                                             const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                                             const uint32_t *__restrict__ m2l_offs, const int32_t *__restrict__ m2l_ids,
-                                             const float *__restrict__ M, float4 *__restrict__ far)
+// The M2P sums of m2p_accumulate_folded for NT targets at once against one source cell's folded
+// coefficients (Fa[q] = {phi, dz} pair, Fb[q] = {A - B, A + B} pair of (N, m) = q), so that every
+// coefficient load serves NT targets.  x, y, z: target minus cell centre over h; ih = 1/h.  The
+// degree recurrence takes z/r^2 and the constants' products with it once per term:
+// I_N = (a z/r^2) I_{N-1} - (b / r^2) I_{N-2}.
+template <int P, int NT>
+GB_DEV void m2p_acc_n(const float4 *__restrict__ Fa, const float4 *__restrict__ Fb, const float (&x)[NT],
+                      const float (&y)[NT], const float (&z)[NT], float ih, float (&o)[NT][4])
 {
-    __shared__ float4 sF[2 * M2PFold<P>::NM];
-    __shared__ float sM[P * P];
-    __shared__ M2PFoldTab<P> sT[M2PFold<P>::NM];
-    m2p_fold_table<P>(sT, threadIdx.x, blockDim.x);  // read after the first fold's barrier
-    const int64_t leaf = blockIdx.x;
-    const int64_t g = level_offset(L) + leaf;
-    const int b0 = begin[g], e0 = end[g];
-    if (e0 <= b0) return;
-    for (int t0 = b0; t0 < e0; t0 += blockDim.x) {
-        const int t = t0 + threadIdx.x;
-        const bool act = t < e0;
-        float4 p = act ? __ldg(&sx[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float o[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int l = 2; l <= L; ++l) {
-            const int64_t a = level_offset(l) + (leaf >> (3 * (L - l)));
-            for (uint32_t e = m2l_offs[a]; e < m2l_offs[a + 1]; ++e) {
-                const int64_t s = m2l_ids[e];
-                __syncthreads();
-                m2p_fold<P>(M + s * (P * P), sM, sT, sF, threadIdx.x, blockDim.x);
-                __syncthreads();
-                const CellGeom cg = geo_level_cell(geo, l, (uint32_t)(s - level_offset(l)));
-                if (act)
-                    m2p_accumulate_folded<P>(sF, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
-                                             (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
+    float ir2[NT], zi[NT], mre[NT], mim[NT], phi[NT], gz[NT], gpr[NT], gpi[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+        const float r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+        const float ir = rsqrt_ftz(r2);
+        ir2[k] = ir * ir;
+        zi[k] = z[k] * ir2[k];
+        mre[k] = ir;  // I_0^0 = 1/r
+        mim[k] = 0.f;
+        phi[k] = gz[k] = gpr[k] = gpi[k] = 0.f;
+    }
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+                const float f = -c_rmm[m] * ir2[k];
+                const float tr = f * (x[k] * mre[k] - y[k] * mim[k]), ti = f * (x[k] * mim[k] + y[k] * mre[k]);
+                mre[k] = tr;
+                mim[k] = ti;
             }
         }
-        if (act) far[t] = make_float4(o[0], o[1], o[2], o[3]);
+        float are[NT], aim[NT], bre[NT], bim[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            are[k] = mre[k];
+            aim[k] = mim[k];
+            bre[k] = bim[k] = 0.f;
+        }
+#pragma unroll
+        for (int N = m; N <= P; ++N) {
+            if (N > m) {
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    const float A = c_ra[N - 1][m] * zi[k], B = c_rb[N - 1][m] * ir2[k];
+                    const float nre = fmaf(A, are[k], -B * bre[k]), nim = fmaf(A, aim[k], -B * bim[k]);
+                    bre[k] = are[k];
+                    bim[k] = aim[k];
+                    are[k] = nre;
+                    aim[k] = nim;
+                }
+            }
+            const int q = nm_idx(N, m);
+            if (N <= P - 1 || (N >= 1 && m <= N - 1)) {
+                const float4 a = Fa[q];
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    if (N <= P - 1) phi[k] = fmaf(a.x, are[k], fmaf(-a.y, aim[k], phi[k]));
+                    if (N >= 1 && m <= N - 1) gz[k] = fmaf(a.z, are[k], fmaf(-a.w, aim[k], gz[k]));
+                }
+            }
+            if (N >= 1 && (m >= 1 || m + 1 <= N - 1)) {
+                const float4 bb = Fb[q];
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    gpr[k] = fmaf(bb.x, are[k], fmaf(-bb.y, aim[k], gpr[k]));
+                    gpi[k] = fmaf(bb.z, aim[k], fmaf(bb.w, are[k], gpi[k]));
+                }
+            }
+        }
+    }
+    const float ih2 = ih * ih;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+        o[k][0] += phi[k] * ih;
+        o[k][1] += gpr[k] * ih2;
+        o[k][2] += gpi[k] * ih2;
+        o[k][3] += gz[k] * ih2;
+    }
+}
+
+// M2P by warps (the treecode on both trees): two warps per target leaf and no block barrier.
+// The leaf's targets go in chunks of up to 32, warp h of the leaf taking chunks h, h + 2, ...;
+// a chunk of T targets takes G = min(4, 32 / T) source cells per step (lane l: target l % T,
+// source group l / T), so small leaves and the remainder chunk still fill the warp.  Per step the warp stages the cells' coefficients and folds them into its own
+// shared memory (the M2P constants of m2p_fold), then every active lane evaluates its target
+// against its group's cell (m2p_acc_n).  At the end of a chunk the groups' partial sums are
+// added in group order (deterministic).  Sources: the M2L rows of the leaf's ancestors at levels
+// 2..L (uniform tree, UNI) or one cell-list row (adaptive tree).  ADD: add into far (else write).
+template <int P>
+struct M2PW {
+    static constexpr int NM = M2PFold<P>::NM;
+    static constexpr int GMAX = 4;
+    static constexpr int NMP = NM % 8 == 0 ? NM + 1 : NM;  // float4 stride of the two halves (bank spread)
+    static constexpr int WARPS = 4;                         // per CTA; two per leaf
+};
+
+template <int P, bool UNI, bool ADD>
+__global__ void __launch_bounds__(128) k_m2p_warp(int L, const float *__restrict__ geo,
+                                                  const int32_t *__restrict__ leaves, Span lv,
+                                                  const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
+                                                  const int32_t *__restrict__ end, const uint32_t *__restrict__ offs,
+                                                  const int32_t *__restrict__ ids, const float4 *__restrict__ sx,
+                                                  const float *__restrict__ M, float4 *__restrict__ far)
+{
+    using W = M2PW<P>;
+    constexpr int PP = P * P, NM = W::NM, G4 = W::GMAX, NMP = W::NMP;
+    __shared__ M2PFoldTab<P> sT[NM];
+    __shared__ float4 sF[W::WARPS][G4 * 2 * NMP];
+    __shared__ float sM[W::WARPS][G4 * PP];
+    __shared__ float4 sR[W::WARPS][32];
+    m2p_fold_table<P>(sT, threadIdx.x, blockDim.x);
+    __syncthreads();  // the only block barrier: the table
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)W::WARPS + warp) >> 1;
+    const int half = warp & 1;
+    if (w >= span_count(lv)) return;
+    const int64_t b = UNI ? level_offset(L) + w : (int64_t)leaves[w];
+    const int b0 = begin[b], nt = end[b] - b0;
+    if (nt <= 32 * half || (!UNI && offs[b] == offs[b + 1])) return;  // no chunk, or no sources (far untouched)
+    float4 *F = sF[warp];
+    float *Ms = sM[warp];
+    for (int c0 = 32 * half; c0 < nt; c0 += 64) {
+        const int T = min(32, nt - c0);
+        const int G = min(G4, 32 / T);
+        const int t = lane % T, g = lane / T;
+        const bool act = g < G;
+        const float4 p = __ldg(&sx[b0 + c0 + (act ? t : 0)]);
+        float o[1][4] = {{0.f, 0.f, 0.f, 0.f}};
+        auto row = [&](uint32_t e0, uint32_t e1, int l) {
+            for (uint32_t e = e0; e < e1; e += G) {
+                const int ng = (int)(e1 - e < (uint32_t)G ? e1 - e : (uint32_t)G);
+                __syncwarp();
+                for (int k = lane; k < ng * PP; k += 32) {
+                    const int gg = k / PP, kk = k - gg * PP;
+                    Ms[k] = M[(int64_t)ids[e + gg] * PP + kk];
+                }
+                __syncwarp();
+                for (int q = lane; q < ng * NM; q += 32) {
+                    const int gg = q / NM, qq = q - gg * NM;
+                    const M2PFoldTab<P> en = sT[qq];
+                    const float *m = Ms + gg * PP;
+                    auto at = [&](int k) { return k >= 0 ? m[k] : 0.f; };
+                    const float pr = en.c.x * at(en.re.x), pi = en.c.x * at(en.im.x);
+                    const float zr = en.c.y * at(en.re.y), zi = en.c.y * at(en.im.y);
+                    const float ar = en.c.z * at(en.re.z), ai = en.c.z * at(en.im.z);
+                    const float br = en.c.w * at(en.re.w), bi = en.c.w * at(en.im.w);
+                    F[gg * 2 * NMP + qq] = make_float4(pr, pi, zr, zi);
+                    F[gg * 2 * NMP + NMP + qq] = make_float4(ar - br, ai - bi, ar + br, ai + bi);
+                }
+                __syncwarp();
+                if (act && g < ng) {
+                    const int64_t sc = ids[e + g];
+                    const CellGeom cg = UNI ? geo_level_cell(geo, l, (uint32_t)(sc - level_offset(l))) : geo_cell(geom, sc);
+                    const float4 *Fa = F + g * 2 * NMP;
+                    float xs[1] = {(p.x - cg.cx) * cg.inv_h}, ys[1] = {(p.y - cg.cy) * cg.inv_h};
+                    float zs[1] = {(p.z - cg.cz) * cg.inv_h};
+                    m2p_acc_n<P, 1>(Fa, Fa + NMP, xs, ys, zs, cg.inv_h, o);
+                }
+            }
+        };
+        if (UNI) {
+            for (int l = 2; l <= L; ++l) {
+                const int64_t a = level_offset(l) + (w >> (3 * (L - l)));
+                row(offs[a], offs[a + 1], l);
+            }
+        } else {
+            row(offs[b], offs[b + 1], 0);
+        }
+        // the groups' partial sums, added in group order
+        __syncwarp();
+        sR[warp][lane] = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
+        __syncwarp();
+        if (act && g == 0) {
+            float4 r = sR[warp][t];
+            for (int gg = 1; gg < G; ++gg) {
+                const float4 v = sR[warp][t + gg * T];
+                r.x += v.x;
+                r.y += v.y;
+                r.z += v.z;
+                r.w += v.w;
+            }
+            const int64_t i = b0 + c0 + t;
+            if (ADD) {
+                float4 f = far[i];
+                f.x += r.x;
+                f.y += r.y;
+                f.z += r.z;
+                f.w += r.w;
+                far[i] = f;
+            } else {
+                far[i] = r;
+            }
+        }
     }
 }
 
 void launch_m2p(int P, int L, const float *geo, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *m2l_offs, const int32_t *m2l_ids, const float *M, float4 *far, cudaStream_t s)
 {
-    unsigned grid = (unsigned)(int64_t(1) << (3 * L));
-    switch (P) {
-    case 4: k_m2p<4><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 6: k_m2p<6><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 8: k_m2p<8><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    case 10: k_m2p<10><<<grid, 64, 0, s>>>(L, geo, sx, begin, end, m2l_offs, m2l_ids, M, far); break;
-    }
+    const int64_t nl = int64_t(1) << (3 * L);
+    const unsigned grid = (unsigned)((nl + 1) / 2);  // two warps per leaf, four per CTA
+    const Span lv = host_span(0, nl);
+    GBFMM_DISPATCH_P(P, (k_m2p_warp<PQ, true, false><<<grid, 128, 0, s>>>(L, geo, nullptr, lv, nullptr, begin, end,
+                                                                          m2l_offs, m2l_ids, sx, M, far)));
     note_launches(1);
 }
 
@@ -1217,7 +1375,7 @@ __global__ void __launch_bounds__(128) k_l2p_cells(int64_t n, const int32_t *__r
 template <int P>
 __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ leaves, Span lv,
                                                   const float4 *__restrict__ geom, const int32_t *__restrict__ begin,
-                                                  const int32_t *__restrict__ count,
+                                                  const int32_t *__restrict__ end,
                                                   const uint32_t *__restrict__ w_offs,
                                                   const int32_t *__restrict__ w_ids, const float4 *__restrict__ sx,
                                                   const float *__restrict__ M, float4 *__restrict__ far)
@@ -1230,7 +1388,7 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
     const uint32_t e0 = w_offs[b], e1 = w_offs[b + 1];
     if (e0 == e1) return;
     m2p_fold_table<P>(sT, threadIdx.x, blockDim.x);  // read after the first fold's barrier
-    const int b0 = begin[b], bend = begin[b] + count[b];
+    const int b0 = begin[b], bend = end[b];
     for (int t0 = b0; t0 < bend; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
         const bool act = t < bend;
@@ -1400,12 +1558,18 @@ void launch_l2p_cells(int P, int64_t n, const int32_t *leaf_of, const int32_t *l
 }
 
 void launch_m2p_cells(int P, const int32_t *leaves, Span lv, const float4 *geom, const int32_t *begin,
-                      const int32_t *count, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
-                      const float *M, float4 *far, cudaStream_t s)
+                      const int32_t *end, const uint32_t *w_offs, const int32_t *w_ids, const float4 *sx,
+                      const float *M, float4 *far, cudaStream_t s, bool long_rows)
 {
     if (lv.cap <= 0) return;
-    GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)lv.cap, 64, 0, s>>>(leaves, lv, geom, begin, count, w_offs,
-                                                                         w_ids, sx, M, far)));
+    if (long_rows) {
+        const unsigned grid = (unsigned)((lv.cap + 1) / 2);  // two warps per leaf, four per CTA
+        GBFMM_DISPATCH_P(P, (k_m2p_warp<PQ, false, true><<<grid, 128, 0, s>>>(0, nullptr, leaves, lv, geom, begin,
+                                                                              end, w_offs, w_ids, sx, M, far)));
+    } else {
+        GBFMM_DISPATCH_P(P, (k_m2p_cells<PQ><<<(unsigned)lv.cap, 64, 0, s>>>(leaves, lv, geom, begin, end, w_offs,
+                                                                             w_ids, sx, M, far)));
+    }
     note_launches(1);
 }
 
