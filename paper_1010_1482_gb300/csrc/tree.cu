@@ -355,9 +355,11 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 constexpr int kRsThreads = 512, kRsItems = 8, kRsTile = kRsThreads * kRsItems;  // tile of 4096 keys
 constexpr int kRsWarps = kRsThreads / 32, kRsWarpKeys = kRsTile / kRsWarps;
 constexpr int kRsHistThreads = 256;  // one per digit
+constexpr int64_t kRsScanMinN = int64_t(1) << 22;  // from here on the passes take the reduce-then-scan form
 constexpr uint64_t kRsAgg = 1ull << 62, kRsInc = 2ull << 62, kRsFlags = 3ull << 62;
 
 static_assert(kRsWarpKeys == 32 * kRsItems, "blocked layout: a warp owns kRsItems rounds of 32 keys");
+static_assert(kRsTile <= 65535, "16-bit per-warp digit counts and offsets");
 
 GB_DEV void st_release_u64(uint64_t *p, uint64_t v)
 {
@@ -413,42 +415,54 @@ __global__ void __launch_bounds__(kRsHistThreads) k_rs_ghist(const KeyT *__restr
         if (h[d][threadIdx.x]) atomicAdd(&ghist[d * 256 + threadIdx.x], h[d][threadIdx.x]);
 }
 
-template <class KeyT>
-__global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin,
+// LB: the tile's digit starts by decoupled look-back over the earlier tiles (tiles taken in
+// launch order from a counter); else read from `starts` (tile_starts of the reduce-then-scan
+// form: starts[d * nblk + tile]), tile = blockIdx.x
+template <class KeyT, bool LB>
+__global__ void __launch_bounds__(kRsThreads, 3) k_rs_pass(const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                         KeyT *__restrict__ kout, uint32_t *__restrict__ vout,
                                                         int64_t n, int pass, int64_t nblk,
                                                         const uint32_t *__restrict__ ghist, uint64_t *status,
                                                         uint32_t *counter, const float4 *__restrict__ gx,
-                                                        float4 *__restrict__ gsx, int *err)
+                                                        float4 *__restrict__ gsx, int *err,
+                                                        const uint32_t *__restrict__ starts)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     KeyT *skey = reinterpret_cast<KeyT *>(rs_smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kRsTile);
-    __shared__ uint32_t wcnt[kRsWarps][256];
+    __shared__ uint16_t wcnt[kRsWarps][256];  // per-warp digit counts, then offsets (< kRsTile)
     __shared__ uint32_t dstart[256], gbase[256], wsum[kRsWarps];
     __shared__ uint32_t tile_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int shift = 8 * pass;
     const bool dig = tid < 256;  // the per-digit work: thread tid, digit tid
-    if (tid == 0) tile_sh = atomicAdd(&counter[pass], 1u);
+    if (tid == 0) tile_sh = LB ? atomicAdd(&counter[pass], 1u) : blockIdx.x;
     for (int e = tid; e < kRsWarps * 256; e += kRsThreads) (&wcnt[0][0])[e] = 0;
     __syncthreads();
     const int64_t tile = tile_sh;
     const int64_t base = tile * kRsTile + (int64_t)warp * kRsWarpKeys;
-    KeyT k[kRsItems];
-    uint32_t v[kRsItems], rk[kRsItems];
+    // only the ranks stay in registers across the scans: the keys and indices are read again
+    // (from L1 / L2) when they are staged, which leaves room for three CTAs per SM
+    uint32_t rk[kRsItems];
 #pragma unroll
     for (int r = 0; r < kRsItems; ++r) {
         const int64_t i = base + 32 * r + lane;
         const bool valid = i < n;
-        k[r] = valid ? kin[i] : KeyT(0);
-        v[r] = valid ? vin[i] : 0u;
-        const uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & 0xffu) : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const KeyT key = valid ? kin[i] : KeyT(0);
+        const uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 256u;
+        // the lanes holding the same digit (invalid lanes: digit 256, a class of their own),
+        // from one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
         const uint32_t before = valid ? wcnt[warp][d] : 0u;
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = (uint16_t)(before + __popc(peers));
         __syncwarp();
         rk[r] = before + __popc(peers & lt);
     }
@@ -459,12 +473,15 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
 #pragma unroll
         for (int w = 0; w < kRsWarps; ++w) {
             const uint32_t t = wcnt[w][tid];
-            wcnt[w][tid] = cnt;
+            wcnt[w][tid] = (uint16_t)cnt;
             cnt += t;
         }
     }
     const uint32_t ds = block_excl_scan(cnt, wsum);  // threads >= 256 add zeros after the digits
     if (dig) dstart[tid] = ds;
+    if (!LB) {
+        if (dig) gbase[tid] = starts[(int64_t)tid * nblk + tile];
+    } else {
     // look back over the earlier tiles' counts of digit tid
     uint64_t *st = status + (size_t)pass * nblk * 256;
     uint32_t excl = 0;
@@ -492,16 +509,18 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
     }
     const uint32_t gb = block_excl_scan(dig ? ghist[pass * 256 + tid] : 0u, wsum);
     if (dig) gbase[tid] = gb + excl;
+    }
     __syncthreads();
     // stage in tile-sorted order, then write the runs of each digit
 #pragma unroll
     for (int r = 0; r < kRsItems; ++r) {
         const int64_t i = base + 32 * r + lane;
         if (i < n) {
-            const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+            const KeyT key = kin[i];
+            const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
             const uint32_t pos = dstart[d] + wcnt[warp][d] + rk[r];
-            skey[pos] = k[r];
-            sval[pos] = v[r];
+            skey[pos] = key;
+            sval[pos] = vin[i];
         }
     }
     __syncthreads();
@@ -515,6 +534,78 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_pass(const KeyT *__restrict__
         kout[gp] = key;
         vout[gp] = val;
         if (gsx) gsx[gp] = __ldg(&gx[val]);
+    }
+}
+
+// Reduce-then-scan form of a pass (large inputs): every tile's digit counts (k_rs_upsweep),
+// their exclusive scan in digit-major order started at each digit's global start
+// (k_rs_tile_starts), then k_rs_pass<KeyT, false> ranks and scatters with those starts.  The
+// passes then carry no chain from tile to tile (the look-back's latency bound the one-sweep
+// passes on large inputs), for one more read of the keys per pass.
+template <class KeyT>
+__global__ void __launch_bounds__(256) k_rs_upsweep(const KeyT *__restrict__ kin, int64_t n, int pass, int64_t nblk,
+                                                    uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    h[tid] = 0;
+    __syncthreads();
+    const int64_t t0 = blockIdx.x * (int64_t)kRsTile;
+    const int shift = 8 * pass;
+    for (int j = tid; j < kRsTile; j += 256) {  // every lane of a warp takes the same rounds
+        const int64_t i = t0 + j;
+        const bool valid = i < n;
+        const uint32_t d = valid ? ((uint32_t)(kin[i] >> shift) & 0xffu) : 256u;
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)tid * nblk + blockIdx.x] = h[tid];
+}
+
+// CTA d: starts[d * nblk + t] = (keys of digits < d) + (keys of digit d in tiles < t)
+__global__ void __launch_bounds__(1024) k_rs_tile_starts(const uint32_t *__restrict__ counts,
+                                                         uint32_t *__restrict__ starts, int64_t nblk,
+                                                         const uint32_t *__restrict__ ghist, int pass)
+{
+    __shared__ uint32_t wsum[32], s_carry;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        uint32_t b = 0;
+        for (int e = lane; e < d; e += 32) b += ghist[pass * 256 + e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (lane == 0) s_carry = b;
+    }
+    __syncthreads();
+    const uint32_t *c = counts + (int64_t)d * nblk;
+    uint32_t *o = starts + (int64_t)d * nblk;
+    for (int64_t c0 = 0; c0 < nblk; c0 += 4 * 1024) {
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t t = c0 + 4 * tid + k;
+            v[k] = t < nblk ? c[t] : 0u;
+            sum += v[k];
+        }
+        const uint32_t carry = s_carry;
+        const uint32_t ex = block_excl_scan(sum, wsum);
+        uint32_t run = carry + ex;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t t = c0 + 4 * tid + k;
+            if (t < nblk) o[t] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = run;  // the chunk's end
+        __syncthreads();
     }
 }
 
@@ -546,15 +637,29 @@ static void sort_gather_t(KeyT *k0, KeyT *k1, uint32_t *v0, uint32_t *v1, int64_
     uint32_t *counter = reinterpret_cast<uint32_t *>(sc);
     uint32_t *ghist = reinterpret_cast<uint32_t *>(sc + kRsCounterBytes);
     uint64_t *status = reinterpret_cast<uint64_t *>(sc + kRsCounterBytes + kRsHistBytes);
-    cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s);
+    // large inputs of several passes take the reduce-then-scan form; its tile counts and starts
+    // (4 bytes each per tile and digit) use the look-back words' space of the first two passes
+    const bool rts = passes >= 2 && n >= kRsScanMinN;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(status);
+    uint32_t *starts = counts + 256 * nblk;
+    cudaMemsetAsync(scratch, 0, rts ? kRsCounterBytes + kRsHistBytes : sort_scratch_bytes(n, bits), s);
     const unsigned hgrid = (unsigned)std::min<int64_t>(nblk * (kRsTile / kRsHistThreads) / 4 + 1, 1216);
     k_rs_ghist<KeyT><<<hgrid, kRsHistThreads, 0, s>>>(kin, n, passes, ghist);
     const int smem = kRsTile * (int)(sizeof(KeyT) + sizeof(uint32_t));
-    cudaFuncSetAttribute(k_rs_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rs_pass<KeyT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rs_pass<KeyT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     for (int pass = 0; pass < passes; ++pass) {
         const bool last = pass + 1 == passes;
-        k_rs_pass<KeyT><<<(unsigned)nblk, kRsThreads, smem, s>>>(kin, vin, kout, vout, n, pass, nblk, ghist, status,
-                                                                 counter, x, last ? sx : nullptr, err);
+        if (rts) {
+            k_rs_upsweep<KeyT><<<(unsigned)nblk, 256, 0, s>>>(kin, n, pass, nblk, counts);
+            k_rs_tile_starts<<<256, 1024, 0, s>>>(counts, starts, nblk, ghist, pass);
+            k_rs_pass<KeyT, false><<<(unsigned)nblk, kRsThreads, smem, s>>>(
+                kin, vin, kout, vout, n, pass, nblk, ghist, status, counter, x, last ? sx : nullptr, err, starts);
+            note_launches(2);
+        } else {
+            k_rs_pass<KeyT, true><<<(unsigned)nblk, kRsThreads, smem, s>>>(
+                kin, vin, kout, vout, n, pass, nblk, ghist, status, counter, x, last ? sx : nullptr, err, nullptr);
+        }
         KeyT *t = kin;
         kin = kout;
         kout = t;

@@ -50,10 +50,11 @@ def sorted_rows(offs, ids):
     return ids[np.lexsort((ids, row))]
 
 
-# ("plummer", 1000000, 8) has more than 2^17 cells (list rows a thread per cell); the last case
-# has a leaf size beyond the one-pass construction's window (level-by-level rounds)
+# ("plummer", 1000000, 8) has more than 2^17 cells (list rows a thread per cell); ("plummer",
+# 60000, 20000) has a leaf size beyond the one-pass construction's window (level-by-level
+# rounds); the 5,000,000-particle case sorts in the reduce-then-scan form (2^22 and more)
 TREE_CASES = [("plummer", 30000, 32), ("plummer", 100000, 64), ("uniform", 20000, 16), ("plummer", 1000000, 8),
-              ("plummer", 60000, 20000)]
+              ("plummer", 60000, 20000), ("plummer", 5000000, 64)]
 
 
 @pytest.mark.parametrize("dist,n,leaf", TREE_CASES)

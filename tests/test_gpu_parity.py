@@ -87,6 +87,21 @@ def test_tree_and_lists_bit_exact(G, ctx, dist, n, leaf):
     assert np.array_equal(offs, ls["m2l_offs"]) and np.array_equal(ids, ls["m2l_ids"])
 
 
+def test_sort_of_large_inputs_bit_exact(G, ctx):
+    # 5,000,000 particles at leaf 8: depth 7, 21-bit keys in 3 radix passes of the
+    # reduce-then-scan form (inputs of 2^22 particles and more)
+    n, leaf = 5_000_000, 8
+    x = inputs.uniform_cube(n, 4242)
+    _, L = run(G, ctx, x, p=4, leaf_size=leaf)
+    assert L == 7
+    origin, side, _ = O.root_box(x)
+    keys = O.morton_keys(x, origin, side) >> np.uint64(3 * (O.ADAPTIVE_MAX_LEVEL - L))
+    perm = np.lexsort((np.arange(n), keys))
+    g = G.gbfmm_export_tree(ctx, n, O.level_offset(L + 1))
+    assert np.array_equal(g["perm"].astype(np.int64), perm)
+    assert np.array_equal(g["sorted_leaf_keys"].astype(np.uint64), keys[perm])
+
+
 def test_keys_on_leaf_cell_faces(G, ctx):
     """Coordinates exactly on leaf-cell faces (j / 32 in the unit box, depth 5) and one float step
     to either side: the key kernel's FP32 estimate cannot decide these and takes the FP64 steps;
