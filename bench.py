@@ -621,7 +621,44 @@ def run_next_rows(args, G, dev, local) -> dict:
                                  "4 requests of each (distribution, p) class"})
     res["served"] = stats
     res["crossover"] = run_crossover(G, dev, local)
+    res["sort_16m"] = run_sort_16m(G, dev, local)
     return res
+
+
+def run_sort_16m(G, dev, local) -> dict:
+    """Keys and sort of 16,777,216 particles: the uniform tree (leaf 64: depth 8, 24-bit keys, 3
+    radix passes) and the adaptive tree of the Plummer set (63-bit keys, 8 passes), from the
+    stage timing of serial evaluations (median of 3 after one warm-up)."""
+    import torch
+
+    out_rows = {}
+    ctx = G.gbfmm_create(local)
+    hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    for name, dist, tree, kbytes, passes in (("uniform_16m", "uniform", G.TREE_UNIFORM, 4, 3),
+                                             ("plummer_16m_adaptive", "plummer", G.TREE_ADAPTIVE, 8, 8)):
+        n = 1 << 24
+        xd = torch.from_numpy(inputs.make_particles(n, dist, inputs.SEED_BASE + 10)).to(dev)
+        out = torch.empty_like(xd)
+        prm = G.gbfmm_default_params(p=4, leaf_size=64, tree=tree, flags=G.FLAG_STAGE_TIMING)
+        _, wsb = G.gbfmm_plan(prm, n)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+        sts = []
+        for _ in range(4):
+            G.gbfmm_evaluate(ctx, prm, xd, out, ws)
+            torch.cuda.synchronize()
+            sts.append(G.gbfmm_stage_times(ctx))
+        G.gbfmm_sync_status(ctx)
+        med = {k: float(np.median([st[k] for st in sts[1:]])) for k in ("box+keys", "sort", "cells+lists")}
+        sort_bytes = kbytes + passes * 2 * (kbytes + 4) + 32
+        out_rows[name] = {"n": n, "radix_passes": passes, "sort_ms": med["sort"], "sort_bytes_per_particle": sort_bytes,
+                          "sort_achieved_gbs": sort_bytes * n / (med["sort"] / 1e3) / 1e9,
+                          "sort_frac": sort_bytes * n / (med["sort"] / 1e3) / 1e9 / hbm,
+                          "box_keys_ms": med["box+keys"], "cells_lists_ms": med["cells+lists"]}
+        del xd, out, ws
+    G.gbfmm_destroy(ctx)
+    out_rows["note"] = ("algorithmic bytes: one histogram read of the keys, every pass reads and writes key + index, "
+                        "the gather reads and writes 16 B; frac of the measured HBM copy rate")
+    return out_rows
 
 
 def run_graph(G, dev, local) -> dict:

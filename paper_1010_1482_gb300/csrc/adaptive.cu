@@ -43,14 +43,7 @@ __global__ void k_keys64(const float4 *__restrict__ x, int64_t n, const Box *__r
     float c[3] = {p.x, p.y, p.z};
     uint64_t k[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double t = __dsub_rn((double)c[d], b.origin[d]);
-        double v = __dmul_rn(t, b.key_scale);
-        double f = floor(v);
-        if (!(f >= 0.0)) f = 0.0;
-        if (f > 2097151.0) f = 2097151.0;
-        k[d] = (uint64_t)f;
-    }
+    for (int d = 0; d < 3; ++d) k[d] = grid_coord21(c[d], b, d);  // the FP64 steps' result
     keys[i] = morton63(k[0], k[1], k[2]);
     idx[i] = (uint32_t)i;
 }

@@ -189,7 +189,62 @@ struct Box {
     float origin_f[3];
     float key_scale_f;
     float key_slack;
+    // the FP32 roundings of origin - origin_f and key_scale - key_scale_f: with them the origin and
+    // the scale as float-float pairs (the 63-bit keys' estimate, grid_coord21)
+    float origin_lo[3];
+    float key_scale_lo;
 };
+
+// k = clamp(floor((c - origin) * scale), 0, 2^21 - 1) with every step one IEEE FP64 rounding
+// (NaN maps to 0): the key coordinate at depth 21.  Not inlined: the key kernels call it for the
+// rare coordinates their FP32 estimates cannot decide, and a real branch keeps the FP64
+// instructions (slow on this part) off the path of every other lane.
+static __device__ __noinline__ uint32_t grid_coord_fp64(float c, double origin, double scale)
+{
+    double t = __dsub_rn((double)c, origin);
+    double v = __dmul_rn(t, scale);
+    double f = floor(v);
+    if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
+    if (f > 2097151.0) f = 2097151.0;
+    return (uint32_t)f;
+}
+
+// The same coordinate from a float-float estimate of the real w = (c - o) s (o = origin_f +
+// origin_lo, s = key_scale_f + key_scale_lo): p + e with p = RN(th sh), e its product error plus
+// the low parts, th + tl = c - origin_f exactly (two-sum).  The estimate is within 2^-45 (|o| s +
+// |w|) of w and the FP64 value within 2^-52 |w| of w; with f = floor(RN(p + e)), moved by one
+// when that rounding crossed an integer, and r = (p - f) + e (p - f exact, at most two roundings
+// of 2^-24 after it), both floors are f when r lies at least E = 2^-44 (|o| s + |p|) + 2^-22
+// inside (0, 1).  Otherwise, and for |p| >= 2^22 or a non-finite
+// coordinate, the FP64 steps decide.
+GB_DEV uint32_t grid_coord21(float c, const Box &b, int d)
+{
+    const float oh = b.origin_f[d], ol = b.origin_lo[d], sh = b.key_scale_f, sl = b.key_scale_lo;
+    const float th = __fsub_rn(c, oh);
+    const float bv = __fsub_rn(th, c);
+    const float tl = __fadd_rn(__fsub_rn(c, __fsub_rn(th, bv)), __fsub_rn(-oh, bv));
+    const float tl2 = __fsub_rn(tl, ol);
+    const float p = __fmul_rn(th, sh);
+    const float e1 = __fmaf_rn(th, sh, -p);
+    const float e2 = __fadd_rn(__fmul_rn(th, sl), __fmul_rn(tl2, sh));
+    const float e = __fadd_rn(e1, e2);
+    if (fabsf(p) < 4194304.f) {
+        // RN(p + e) can round across an integer (its unit in the last place is up to 1/4):
+        // one step back or forward puts r in [0, 1)
+        float f = floorf(__fadd_rn(p, e));
+        float r = __fadd_rn(__fsub_rn(p, f), e);
+        if (r < 0.f) {
+            f = __fsub_rn(f, 1.f);
+            r = __fadd_rn(r, 1.f);
+        } else if (r >= 1.f) {
+            f = __fadd_rn(f, 1.f);
+            r = __fsub_rn(r, 1.f);
+        }
+        const float E = __fadd_ru(__fmul_ru(__fadd_ru(__fmul_ru(fabsf(oh), sh), fabsf(p)), 0x1p-44f), 0x1p-22f);
+        if (r >= E && r <= __fsub_rd(1.f, E)) return f < 0.f ? 0u : (f > 2097151.f ? 2097151u : (uint32_t)f);
+    }
+    return grid_coord_fp64(c, b.origin[d], b.key_scale);
+}
 
 // Cell geometry table of the uniform tree (expansions.cu, k_geo_levels): 1/h_l for
 // l < kGeoLevels, then the 2^l cell-centre coordinates of every level l = 0..L along x, y, z.

@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_bbox(const float4 *__restrict__
             m = fmax(m, fabs(b.origin[d]));
         }
         b.key_scale_f = __double2float_rn(b.key_scale);
+        b.key_scale_lo = __double2float_rn(__dsub_rn(b.key_scale, (double)b.key_scale_f));
+        for (int d = 0; d < 3; ++d) b.origin_lo[d] = __double2float_rn(__dsub_rn(b.origin[d], (double)b.origin_f[d]));
         // twice the bound 2^-22 (|o| s + |v|) + 2^-40 of the FP32 estimate's error (see k_keys)
         b.key_slack = __double2float_ru(__dmul_ru(__dmul_ru(m, b.key_scale), 0x1p-21) + 0x1p-20);
         *box_out = b;
@@ -179,15 +181,6 @@ GB_DEV uint32_t leaf_coord_f(float v, int sh)
     return (uint32_t)f >> sh;
 }
 
-GB_DEV uint32_t grid_coord_fp64(float c, double origin, double scale)
-{
-    double t = __dsub_rn((double)c, origin);
-    double v = __dmul_rn(t, scale);
-    double f = floor(v);
-    if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
-    if (f > 2097151.0) f = 2097151.0;
-    return (uint32_t)f;
-}
 
 __global__ void k_keys(const float4 *__restrict__ x, int64_t n, const Box *__restrict__ box, int L,
                        uint32_t *__restrict__ leafkey, uint32_t *__restrict__ idx)

@@ -80,6 +80,35 @@ def test_adaptive_tree_and_lists_bit_exact(G, ctx, dist, n, leaf):
         assert len(ls["w_ids"]) > 0 and len(ls["x_ids"]) > 0
 
 
+def test_adaptive_keys_on_depth21_faces(G, ctx):
+    # coordinates on faces of the depth-21 grid of the unit box (the 8 corners pin the root box
+    # to [0, 1]^3, so the key scale is 2^21) and one float step to either side, each with a
+    # partner one grid unit away; leaf size 1 resolves every pair down to the level where it
+    # parts, so a key coordinate off by one changes the tree.  The keys' float-float estimate
+    # cannot decide these coordinates and takes the FP64 steps.
+    m = 1500
+    u = inputs.uniform01(77, 7 * m).reshape(m, 7)
+    j = np.floor(u[:, :3] * (2 ** 21 - 2)).astype(np.int64) + 1
+    c = (j / 2.0 ** 21).astype(np.float32)
+    step = np.floor(u[:, 3:6] * 3).astype(np.int64) - 1  # -1, 0, +1 float steps
+    c = np.where(step < 0, np.nextafter(c, np.float32(0)), np.where(step > 0, np.nextafter(c, np.float32(1)), c))
+    partner = (c + np.float32(2.0 ** -21) * np.where(u[:, 6:7] < 0.5, -1, 1)).astype(np.float32)
+    pts = np.vstack([c, np.clip(partner, 0, 1)])
+    corners = np.array([[a, b, d] for a in (0, 1) for b in (0, 1) for d in (0, 1)], dtype=np.float32)
+    pts = np.vstack([corners, pts])
+    x = np.concatenate([pts, np.ones((len(pts), 1), np.float32)], axis=1).astype(np.float32)
+    run(G, ctx, x, p=4, leaf_size=1)
+    t = O.build_adaptive_tree(x, 1)
+    assert t["side"] == 1.0 and np.all(t["origin"] == 0.0)
+    g = G.gbfmm_export_adaptive_tree(ctx, len(x))
+    assert g["ncells"] == t["ncells"]
+    for k in ("level", "begin", "count", "parent"):
+        assert np.array_equal(g[k], t[k]), k
+    assert np.array_equal(g["key"], t["key"])
+    assert np.array_equal(g["perm"].astype(np.int64), t["perm"])
+    assert t["level"].max() == O.ADAPTIVE_MAX_LEVEL
+
+
 @pytest.mark.parametrize("p", [4, 6, 8, 10])
 def test_adaptive_fmm_matches_oracle(G, ctx, p):
     n, leaf = 20000, 32

@@ -260,6 +260,19 @@ def test_treecode_matches_oracle(G, ctx, p):
     assert O.rel_l2(out[:, 1:], ref[:, 1:]) <= TOL_FMM
 
 
+def test_treecode_1m_sampled(G, ctx):
+    # the treecode at full size (1,048,576 uniform particles, p = 8, leaf 64): 256 seeded targets
+    # against the oracle treecode on the same tree
+    n, p, leaf = 1 << 20, 8, 64
+    x = inputs.uniform_cube(n, 5150)
+    out, L = run(G, ctx, x, p=p, leaf_size=leaf, method=G.METHOD_TREECODE)
+    assert L == 5 and np.all(np.isfinite(out))
+    tg = inputs.sample_indices(n, 256, 5151)
+    ref = O.fmm(x, p, leaf, method=O.TREECODE, targets=tg)["out"]
+    assert O.rel_l2(out[tg, 0], ref[tg, 0]) <= TOL_FMM
+    assert O.rel_l2(out[tg, 1:], ref[tg, 1:]) <= TOL_FMM
+
+
 def test_small_config_p4(G, ctx):
     w = inputs.workload("uniform_4k_p4")
     x = inputs.make_particles(w["n"], w["dist"], w["seed"])
