@@ -439,11 +439,14 @@ __global__ void __launch_bounds__(kRsThreads, 3) k_rs_pass(const KeyT *__restric
     // (from L1 / L2) when they are staged, which leaves room for three CTAs per SM
     uint32_t rk[kRsItems];
 #pragma unroll
-    for (int r = 0; r < kRsItems; ++r) {
+    for (int r = 0; r < kRsItems; ++r) {  // the digits first: all the warp's loads in flight at once
         const int64_t i = base + 32 * r + lane;
-        const bool valid = i < n;
-        const KeyT key = valid ? kin[i] : KeyT(0);
-        const uint32_t d = valid ? ((uint32_t)(key >> shift) & 0xffu) : 256u;
+        rk[r] = i < n ? ((uint32_t)(kin[i] >> shift) & 0xffu) : 256u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRsItems; ++r) {
+        const uint32_t d = rk[r];
+        const bool valid = d < 256u;
         // the lanes holding the same digit (invalid lanes: digit 256, a class of their own),
         // from one ballot per digit bit
         unsigned peers = __ballot_sync(0xffffffffu, valid);
@@ -545,10 +548,17 @@ __global__ void __launch_bounds__(256) k_rs_upsweep(const KeyT *__restrict__ kin
     __syncthreads();
     const int64_t t0 = blockIdx.x * (int64_t)kRsTile;
     const int shift = 8 * pass;
-    for (int j = tid; j < kRsTile; j += 256) {  // every lane of a warp takes the same rounds
-        const int64_t i = t0 + j;
-        const bool valid = i < n;
-        const uint32_t d = valid ? ((uint32_t)(kin[i] >> shift) & 0xffu) : 256u;
+    constexpr int R = kRsTile / 256;
+    uint32_t dd[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {  // all the tile's loads in flight at once
+        const int64_t i = t0 + r * 256 + tid;
+        dd[r] = i < n ? ((uint32_t)(kin[i] >> shift) & 0xffu) : 256u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {  // every lane of a warp takes the same rounds
+        const uint32_t d = dd[r];
+        const bool valid = d < 256u;
         unsigned peers = __ballot_sync(0xffffffffu, valid);
         if (!valid) peers = ~peers;
 #pragma unroll
