@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t
                                                        const int32_t *__restrict__ abort)
 {
     __shared__ uint32_t wc[kTreeB / 32][kTreeBins];
+    __shared__ uint32_t sb0[kTreeBins], sbl;
     if (abort && *abort) return;  // the tree outgrew the capacities: nothing is written
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i = blockIdx.x * (int64_t)kTreeB + tid;
@@ -250,14 +251,27 @@ __global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t
         if (lane == 0) wc[warp][b] = __popc(bal);
     }
     __syncthreads();
+    // per bin: the warps' counts become their exclusive offsets; the block's first index and
+    // (leaves) the first leaf index, from the scanned histogram
+    if (tid < kTreeBins) {
+        uint32_t acc = 0;
+        for (int w = 0; w < kTreeB / 32; ++w) {
+            const uint32_t t = wc[w][tid];
+            wc[w][tid] = acc;
+            acc += t;
+        }
+        sb0[tid] = base[(int64_t)tid * nblk + blockIdx.x];
+        if (tid == kTreeBins - 1) sbl = base[(int64_t)tid * nblk];
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     int32_t prev = -1;
+#pragma unroll
     for (int b = 0; b < kTreeBins; ++b) {
         const bool p = tree_bin(b, a, lam);
         const unsigned bal = __ballot_sync(0xffffffffu, p);
-        uint32_t off = __popc(bal & lt);
-        for (int w = 0; w < warp; ++w) off += wc[w][b];
-        const uint32_t b0 = base[(int64_t)b * nblk + blockIdx.x];
+        const uint32_t off = __popc(bal & lt) + wc[warp][b];
+        const uint32_t b0 = sb0[b];
         if (b < kTreeBins - 1) {
             if (!p) continue;
             const int32_t id = (int32_t)(b0 + off);
@@ -271,7 +285,7 @@ __global__ void __launch_bounds__(kTreeB) k_tree_cells(int64_t n, const uint64_t
             for (int q = 0; q < 8; ++q) child_of[(int64_t)id * 8 + q] = -1;
             prev = id;
         } else if (i < n) {
-            const int64_t ord = (int64_t)b0 - (int64_t)base[(int64_t)b * nblk] + off + (p ? 1 : 0) - 1;
+            const int64_t ord = (int64_t)b0 - (int64_t)sbl + off + (p ? 1 : 0) - 1;
             leaf_ord[i] = (int32_t)ord;
             if (p) leaves[ord] = prev;  // the cell of level lambda_i
         }
