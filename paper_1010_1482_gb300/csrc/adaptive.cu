@@ -587,18 +587,19 @@ __global__ void k_vlist_warp(Span cells, TreeView t, uint32_t *__restrict__ cnt,
     int x, y, z;
     demorton63(t.key[b], x, y, z);
     const int side = 1 << l, cx = x & 1, cy = y & 1, cz = z & 1;
-    const int32_t *pc = t.coll + (int64_t)t.parent[b] * 27;
+    // the parent's 27 colleagues, one per lane, read once per cell and shuffled to the candidates
+    const int32_t pcv = lane < 27 ? t.coll[(int64_t)t.parent[b] * 27 + lane] : -1;
     uint32_t e = FILL ? offs[b] : 0u;
     for (int t0 = 0; t0 < 216; t0 += 32) {
         const int u = t0 + lane;
         const int ox = u % 6 - 2 - cx, oy = (u / 6) % 6 - 2 - cy, oz = u / 36 - 2 - cz;
         const int nx = x + ox, ny = y + oy, nz = z + oz;
+        const bool cand = u < 216 && !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) &&
+                          nx >= 0 && ny >= 0 && nz >= 0 && nx < side && ny < side && nz < side;
+        const int sl = cand ? slot27((nx >> 1) - (x >> 1), (ny >> 1) - (y >> 1), (nz >> 1) - (z >> 1)) : 13;
+        const int32_t a = __shfl_sync(0xffffffffu, pcv, sl);
         int32_t src = -1;
-        if (u < 216 && !(ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) && nx >= 0 && ny >= 0 &&
-            nz >= 0 && nx < side && ny < side && nz < side) {
-            const int32_t a = pc[slot27((nx >> 1) - (x >> 1), (ny >> 1) - (y >> 1), (nz >> 1) - (z >> 1))];
-            if (a >= 0) src = t.child_of[(int64_t)a * 8 + ((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2))];
-        }
+        if (cand && a >= 0) src = t.child_of[(int64_t)a * 8 + ((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2))];
         const unsigned hit = __ballot_sync(0xffffffffu, src >= 0);
         if (FILL && src >= 0) {
             const uint32_t at = e + __popc(hit & ((1u << lane) - 1u));
