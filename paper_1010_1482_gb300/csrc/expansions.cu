@@ -925,7 +925,7 @@ void launch_l2p(int P, int L, const float *geo, int64_t n, const float4 *sx, con
 // ------------------------------------------------------------------------------------------
 // The constants of these sums are folded into the source cell's coefficients once per cell
 // (staged in shared memory), so that each (particle, cell) evaluation spends two FMAs per real
-// term: per (N, m), 0 <= m <= N <= P, two float4
+// term: per (N, m), 0 <= m <= N <= P, two float4 (in two halves of the fold, F[q] and F[NM + q])
 //   {w M_N^m (re, im), -w sqrt((N-m)(N+m)) M_{N-1}^m (re, im)},
 //   {A - B (re, im), A + B (re, im)},  A = sqrt((N+m)(N+m-1)) M_{N-1}^{m-1},
 //                                      B = sqrt((N-m)(N-m-1)) M_{N-1}^{m+1},
@@ -998,59 +998,12 @@ GB_DEV void m2p_fold(const float *__restrict__ M, float *__restrict__ sM, const 
         const float zr = e.c.y * at(e.re.y), zi = e.c.y * at(e.im.y);
         const float ar = e.c.z * at(e.re.z), ai = e.c.z * at(e.im.z);
         const float br = e.c.w * at(e.re.w), bi = e.c.w * at(e.im.w);
-        F[2 * q] = make_float4(pr, pi, zr, zi);
-        F[2 * q + 1] = make_float4(ar - br, ai - bi, ar + br, ai + bi);
+        F[q] = make_float4(pr, pi, zr, zi);
+        F[M2PFold<P>::NM + q] = make_float4(ar - br, ai - bi, ar + br, ai + bi);
     }
 }
 
-template <int P>
-GB_DEV void m2p_accumulate_folded(const float4 *__restrict__ F, float x, float y, float z, float ih, float *o)
-{
-    const float r2 = x * x + y * y + z * z;
-    const float ir = rsqrt_ftz(r2);
-    const float ir2 = ir * ir;
-    float phi = 0.f, gz = 0.f, gpr = 0.f, gpi = 0.f;
-    float mre = ir, mim = 0.f;  // I_0^0 = 1/r
-#pragma unroll
-    for (int m = 0; m <= P; ++m) {
-        if (m > 0) {
-            const float f = -c_rmm[m] * ir2;
-            const float tr = f * (x * mre - y * mim), ti = f * (x * mim + y * mre);
-            mre = tr;
-            mim = ti;
-        }
-        float are = mre, aim = mim, bre = 0.f, bim = 0.f;
-#pragma unroll
-        for (int N = m; N <= P; ++N) {
-            if (N > m) {
-                const float ca = c_ra[N - 1][m] * z, cb = c_rb[N - 1][m];
-                const float nre = (ca * are - cb * bre) * ir2, nim = (ca * aim - cb * bim) * ir2;
-                bre = are;
-                bim = aim;
-                are = nre;
-                aim = nim;
-            }
-            const int q = nm_idx(N, m);
-            if (N <= P - 1 || (N >= 1 && m <= N - 1)) {
-                const float4 a = F[2 * q];
-                if (N <= P - 1) phi = fmaf(a.x, are, fmaf(-a.y, aim, phi));
-                if (N >= 1 && m <= N - 1) gz = fmaf(a.z, are, fmaf(-a.w, aim, gz));
-            }
-            if (N >= 1 && (m >= 1 || m + 1 <= N - 1)) {
-                const float4 b = F[2 * q + 1];
-                gpr = fmaf(b.x, are, fmaf(-b.y, aim, gpr));
-                gpi = fmaf(b.z, aim, fmaf(b.w, are, gpi));
-            }
-        }
-    }
-    o[0] += phi * ih;
-    const float ih2 = ih * ih;
-    o[1] += gpr * ih2;
-    o[2] += gpi * ih2;
-    o[3] += gz * ih2;
-}
-
-// The M2P sums of m2p_accumulate_folded for NT targets at once against one source cell's folded
+// The M2P sums for NT targets at once against one source cell's folded
 // coefficients (Fa[q] = {phi, dz} pair, Fb[q] = {A - B, A + B} pair of (N, m) = q), so that every
 // coefficient load serves NT targets.  x, y, z: target minus cell centre over h; ih = 1/h.  The
 // degree recurrence takes z/r^2 and the constants' products with it once per term:
@@ -1400,9 +1353,14 @@ __global__ void __launch_bounds__(64) k_m2p_cells(const int32_t *__restrict__ le
             m2p_fold<P>(M + (int64_t)sc * (P * P), sM, sT, sF, threadIdx.x, blockDim.x);
             __syncthreads();
             const CellGeom cg = geo_cell(geom, sc);
-            if (act)
-                m2p_accumulate_folded<P>(sF, (p.x - cg.cx) * cg.inv_h, (p.y - cg.cy) * cg.inv_h,
-                                         (p.z - cg.cz) * cg.inv_h, cg.inv_h, o);
+            if (act) {
+                float xs[1] = {(p.x - cg.cx) * cg.inv_h}, ys[1] = {(p.y - cg.cy) * cg.inv_h};
+                float zs[1] = {(p.z - cg.cz) * cg.inv_h};
+                float o1[1][4] = {{o[0], o[1], o[2], o[3]}};
+                m2p_acc_n<P, 1>(sF, sF + M2PFold<P>::NM, xs, ys, zs, cg.inv_h, o1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = o1[0][k];
+            }
         }
         if (act) {
             float4 f = far[t];
