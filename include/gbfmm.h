@@ -74,10 +74,11 @@ enum {
  * caller's stream (event waits only, so stream capture sees one graph); the output is the same
  * bit for bit. */
 #define GBFMM_FLAG_SERIAL 4
-/* uniform tree: run the M2L as the list-based tensor-core kernel of the adaptive tree (128
- * target cells per CTA, sources gathered through the M2L list) instead of the default block
- * form (one dense GEMM per parent offset over all parents of a level).  Same Eq. 4, same
- * precision scheme; they differ by rounding only. */
+/* run the M2L as the list-based tensor-core kernel (128 target cells per CTA, sources gathered
+ * through the M2L / V list) instead of the default block form (one GEMM per parent offset:
+ * over all parents of a level on the uniform tree, over the cells with children on the adaptive
+ * tree, whose colleagues' children are gathered).  Same Eq. 4, same precision scheme; they
+ * differ by rounding only. */
 #define GBFMM_FLAG_M2L_GATHERED 8
 /* uniform tree: run the M2L by rotation to the translation axis on the FP32 CUDA cores: per
  * list entry, rotate the source expansion so that the offset lies on +z, translate along z

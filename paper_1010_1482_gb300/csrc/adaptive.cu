@@ -800,7 +800,9 @@ void free_adaptive(AdaptiveState &a)
                      &a.pcell, &a.leaf_of, &a.box, &a.level, &a.key, &a.begin, &a.count, &a.end, &a.parent,
                      &a.child_begin, &a.nchild, &a.child_of, &a.coll, &a.vcode, &a.M, &a.Lc, &a.tlist, &a.tdesc,
                      &a.leaves, &a.group_cnt, &a.cscale, &a.geom, &a.info, &a.anchor, &a.presplit, &a.near,
-                     &a.tc_cnt, &a.tc_offs[0], &a.tc_offs[1], &a.tc_ids[0], &a.tc_ids[1], &a.partials};
+                     &a.tc_cnt, &a.tc_offs[0], &a.tc_offs[1], &a.tc_ids[0], &a.tc_ids[1], &a.partials,
+                     &a.ab_flag, &a.ab_scan, &a.ab_unit_of, &a.ab_units, &a.ab_nu, &a.ab_pre, &a.ab_scale,
+                     &a.ab_src, &a.lpart};
     for (DevBuf *b : all) {
         cudaFree(b->p);
         b->p = nullptr;
@@ -1261,7 +1263,37 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
     for (int l = maxl - 1; l >= 2; --l)
         launch_translate_cells(P, true, R.level(l), A.child_of.as<int32_t>(), A.nchild.as<int32_t>(), ops.m2m, M, s);
     mark(5);
-    if (deep) {
+    const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
+    const bool gathered = (prm->flags & GBFMM_FLAG_M2L_GATHERED) != 0;
+    if (deep && !cores && !gathered) {
+        // M2L in block form: one GEMM per parent offset over the units (cells with children),
+        // their colleagues' children gathered per tile; no V list is read
+        rc = ensure_blk(ctx, P, s);
+        if (rc != GBFMM_OK) return fail_joined(rc, "block operators");
+        const int64_t ucap = dev ? ncells : std::max<int64_t>(1, ncells - A.nleaves);
+        const int64_t up = m2l_ablk_tiles_units(ucap);
+        if (grow(A.ab_flag, 4 * (size_t)(ncells + 1), false, 0, s) || grow(A.ab_scan, 4 * (size_t)(ncells + 1), false, 0, s) ||
+            grow(A.ab_unit_of, 4 * (size_t)ncells + 4, false, 0, s) || grow(A.ab_units, 4 * (size_t)up + 4, false, 0, s) ||
+            grow(A.ab_nu, 16, false, 0, s) || grow(A.ab_pre, m2l_ablk_presplit_bytes(P, ucap), false, 0, s) ||
+            grow(A.ab_scale, (size_t)ucap + 16, false, 0, s) || grow(A.ab_src, m2l_ablk_src_bytes(ucap), false, 0, s))
+            return fail_joined(GBFMM_ENOMEM, "block M2L buffers");
+        const int ksplit = m2l_ablk_ksplit(P, n, prm->leaf_size);
+        const int64_t part_stride = ncells * PP;
+        if (ksplit > 1 && grow(A.lpart, 4 * (size_t)ksplit * part_stride, false, 0, s))
+            return fail_joined(GBFMM_ENOMEM, "block M2L partial sums");
+        launch_ablk_prep(P, R.cells(), ucap, A.level.as<int32_t>(), A.nchild.as<int32_t>(), A.child_of.as<int32_t>(),
+                         A.coll.as<int32_t>(), M, A.ab_flag.as<uint32_t>(), A.ab_scan.as<uint32_t>(),
+                         A.scan_tmp.as<uint32_t>(), A.ab_unit_of.as<int32_t>(), A.ab_units.as<int32_t>(),
+                         A.ab_nu.as<int32_t>(), A.ab_pre.p, A.ab_scale.as<int8_t>(), A.ab_src.as<int32_t>(), s);
+        if (launch_m2l_ablk(P, ucap, A.ab_nu.as<int32_t>(), A.ab_units.as<int32_t>(), A.child_of.as<int32_t>(),
+                            A.ab_src.as<int32_t>(), A.ab_pre.p, A.ab_scale.as<int8_t>(), ops.m2l_blk, Lc,
+                            ksplit > 1 ? A.lpart.as<float>() : nullptr, ksplit, part_stride, ctx->d_status, s,
+                            fork ? sm_count() : 0) != 0)
+            return fail_joined(GBFMM_ECUDA, "TMA tensor map encoding failed");
+        if (ksplit > 1) launch_ablk_reduce(P, R.deep(), ksplit, part_stride, A.lpart.as<float>(), Lc, s);
+        launch_p2l_cells(P, R.cells(), A.level.as<int32_t>(), geom, A.begin.as<int32_t>(), A.count.as<int32_t>(),
+                         A.loffs[kListX].as<uint32_t>(), A.lids[kListX].as<int32_t>(), A.sx.as<float4>(), Lc, s);
+    } else if (deep) {
         // M2L targets: every cell at levels >= 2, grouped by (level, child position) into tiles
         // planned on the device (no host read); launched over a bound on the tile count, tiles
         // past the last one empty
@@ -1273,7 +1305,6 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
             k_group_count<<<blocks_for(dp.cap), 256, 0, s>>>(dp, A.level.as<int32_t>(), A.key.as<uint64_t>(), gcnt);
             note_launches(1);
         }
-        const bool cores = (prm->flags & GBFMM_FLAG_M2L_CUDA_CORES) != 0;
         const bool f16 = !cores;
         const int TN = f16 ? kM2LTcTargetsPerTile : kM2LTargetsPerTile;
         const int64_t tcap = dp.cap / TN + 8 * (int64_t)(maxl - 1) + 1;

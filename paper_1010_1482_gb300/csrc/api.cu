@@ -226,7 +226,7 @@ static int ensure_rot(gbfmm_ctx *ctx, int P)
 }
 
 // the block operators of the uniform tree's M2L (built on the stream at first use of order P)
-static int ensure_blk(gbfmm_ctx *ctx, int P, cudaStream_t s)
+int gbfmm::ensure_blk(gbfmm_ctx *ctx, int P, cudaStream_t s)
 {
     OpsCache &c = ctx->ops[order_slot(P)];
     if (c.m2l_blk) return GBFMM_OK;

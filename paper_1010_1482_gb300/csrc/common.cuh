@@ -404,6 +404,23 @@ size_t m2l_blk_part_bytes(int P, int L);
 int launch_m2l_blk(int P, int L, const int32_t *begin, const int32_t *end, const void *presplit, const int8_t *pscale,
                    const void *table, float *Lc, float *Lpart, int *status, cudaStream_t s, int max_ctas);
 
+// m2l_blk.cu, adaptive tree: the block form over units (cells of levels >= 1 with children;
+// ucap >= their count, zrow = ucap the zero row)
+size_t m2l_ablk_presplit_bytes(int P, int64_t ucap);
+size_t m2l_ablk_src_bytes(int64_t ucap);
+int64_t m2l_ablk_tiles_units(int64_t ucap);
+int m2l_ablk_ksplit(int P, int64_t n, int leaf_size);
+void launch_ablk_prep(int P, Span cells, int64_t ucap, const int32_t *level, const int32_t *nchild,
+                      const int32_t *child_of, const int32_t *coll, const float *M, uint32_t *flag, uint32_t *scan,
+                      uint32_t *scan_tmp, int32_t *unit_of, int32_t *units, int32_t *n_units, void *Apre,
+                      int8_t *uscale, int32_t *src, cudaStream_t s);
+// -1 if the operators' tensor map cannot be encoded (nothing launched)
+int launch_m2l_ablk(int P, int64_t ucap, const int32_t *n_units, const int32_t *units, const int32_t *child_of,
+                    const int32_t *src, const void *Apre, const int8_t *uscale, const void *table, float *Lc,
+                    float *Lpart, int ksplit, int64_t part_stride, int *status, cudaStream_t s, int max_ctas);
+void launch_ablk_reduce(int P, Span deep, int ksplit, int64_t part_stride, const float *Lpart, float *Lc,
+                        cudaStream_t s);
+
 // m2l_rot.cu: the M2L by rotation to the translation axis (O(p^3) per pair, FP32 CUDA cores)
 void init_m2l_rot_constants();
 size_t m2l_rot_table_bytes(int P);

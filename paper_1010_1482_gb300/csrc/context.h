@@ -57,6 +57,9 @@ struct AdaptiveState {
     DevBuf presplit;                                               // FP16 pre-split source rows (gathered M2L)
     DevBuf near;                                                   // P2P's compensated sums, 2 float4 per particle
     DevBuf tc_cnt, tc_offs[2], tc_ids[2];  // treecode rows: [0] U + ancestors' X, [1] W + ancestors' V
+    // block-form M2L: unit flags and their scan, unit of every cell, the units, their count, the
+    // pre-split rows and scales, the colleague rows per (tile, offset), the offset ranges' partial sums
+    DevBuf ab_flag, ab_scan, ab_unit_of, ab_units, ab_nu, ab_pre, ab_scale, ab_src, lpart;
     DevBuf partials;  // root-box reduction scratch of evaluations that do not use the context's
     AdaptCaps counts;  // the sizes the last host-counted evaluation read back
     int64_t n = 0, ncells = 0, nleaves = 0, entries[4] = {0, 0, 0, 0};
@@ -117,6 +120,8 @@ int order_slot(int p);
 int fail(gbfmm_ctx *ctx, int code, const std::string &msg);
 int cuda_fail(gbfmm_ctx *ctx, cudaError_t e, const char *what);
 int ensure_ops(gbfmm_ctx *ctx, int P, cudaStream_t s, bool *built_now);
+// the block operators of the M2L's block form (both trees), built on the stream at first use
+int ensure_blk(gbfmm_ctx *ctx, int P, cudaStream_t s);
 int64_t launch_count();
 // adaptive tree (adaptive.cu)
 int evaluate_adaptive(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, float *d_out,

@@ -457,6 +457,359 @@ __global__ void __launch_bounds__(kBlkThreads, 1)
     }
 }
 
+// ---- the same block M2L on the adaptive tree ---------------------------------------------------
+// On the adaptive tree the V list of a cell t (child tau of parent Q) is the children sigma of
+// Q's colleagues S = Q + D (the positional colleagues of the level, D != 0) with |2D + sigma -
+// tau|_inf >= 2: the block form above with S taken from the colleague table instead of the
+// dense grid.  A colleague that is absent or a leaf, and a child that is absent, contribute zero
+// coefficients; a colleague that is a leaf reaches t through its U or X list instead.  Target
+// units are the cells of levels >= 1 with children (their children are the targets of levels
+// >= 2), numbered in cell order; unit u has a row of the 8 p^2 coefficients of its children in
+// the pre-split array (k_ablk_presplit), and row Z (the unit capacity) is zero.  A tile is 128
+// consecutive units; its A operand for offset D gathers the rows of the units' colleagues
+// (k_ablk_src: the row of every (unit, D), Z where the colleague has no children) by two loader
+// warps (16-byte loads, stored in the swizzled layout the TMA writes for the dense form, then a
+// proxy fence and one arrival each); B_D comes by TMA as before.
+
+// unit numbering: flag of every cell (levels >= 1 with children)
+__global__ void k_ablk_flags(Span cells, const int32_t *__restrict__ level, const int32_t *__restrict__ nchild,
+                             uint32_t *__restrict__ flag)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= cells.cap) return;
+    uint32_t f = 0;
+    if (i < span_count(cells)) {
+        const int64_t c = span_first(cells) + i;
+        f = (level[c] >= 1 && nchild[c] > 0) ? 1u : 0u;
+    }
+    flag[i] = f;
+}
+
+// unit_of[c] = its unit or -1; units[u] = its cell; n_units (one word) = the count
+__global__ void k_ablk_units(Span cells, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ scan,
+                             int32_t *__restrict__ unit_of, int32_t *__restrict__ units, int32_t *__restrict__ n_units)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) *n_units = (int32_t)scan[cells.cap];
+    if (i >= span_count(cells)) return;
+    const int64_t c = span_first(cells) + i;
+    if (flag[i]) {
+        unit_of[c] = (int32_t)scan[i];
+        units[scan[i]] = (int32_t)c;
+    } else {
+        unit_of[c] = -1;
+    }
+}
+
+// pre-split rows: unit u (one warp): its children's scaled coefficients 2^s_u M~ in FP16 hi | lo,
+// s_u = 10 - e with max |M~| = f 2^e over its children (0 and zeros for none); row Z and its scale
+// are zero
+template <int P>
+__global__ void __launch_bounds__(256) k_ablk_presplit(const int32_t *__restrict__ n_units, int64_t zrow,
+                                                       const int32_t *__restrict__ units,
+                                                       const int32_t *__restrict__ child_of,
+                                                       const float *__restrict__ M, __half *__restrict__ A,
+                                                       int8_t *__restrict__ scale)
+{
+    constexpr int PP = P * P, KD = 8 * PP, PER = (KD + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nu = *n_units;
+    if (u > zrow || (u >= nu && u != zrow)) return;
+    __half *row = A + u * (2 * KD);
+    if (u == zrow || u >= nu) {
+        for (int k = lane; k < 2 * KD; k += 32) row[k] = __float2half_rn(0.f);
+        if (lane == 0) scale[u] = 0;
+        return;
+    }
+    const int64_t q = units[u];
+    float v[PER];
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int k = lane + 32 * j;
+        float a = 0.f;
+        if (k < KD) {
+            const int32_t c = child_of[q * 8 + k / PP];
+            if (c >= 0) a = M[(int64_t)c * PP + k % PP];
+        }
+        v[j] = a;
+        m = fmaxf(m, fabsf(a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const bool fin = m > 0.f && m <= 3.0e38f;
+    int ex = 0;
+    if (fin) frexpf(m, &ex);
+    int sc = fin ? 10 - ex : 0;
+    sc = sc < -100 ? -100 : (sc > 100 ? 100 : sc);
+    if (lane == 0) scale[u] = (int8_t)sc;
+    const float up = blk_pow2(sc);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int k = lane + 32 * j;
+        if (k < KD) {
+            const float xs = v[j] * up;
+            const __half hi = __float2half_rn(xs);
+            row[k] = hi;
+            row[KD + k] = __float2half_rn(xs - __half2float(hi));
+        }
+    }
+}
+
+// src[(tile 26 + d) 128 + r] = the row of unit tile 128 + r's colleague at offset d (Z if none);
+// ucap: the units covered, a multiple of 128
+__global__ void k_ablk_src(const int32_t *__restrict__ n_units, int64_t ucap, int64_t zrow,
+                           const int32_t *__restrict__ units, const int32_t *__restrict__ coll,
+                           const int32_t *__restrict__ unit_of, int32_t *__restrict__ src)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // over units (padded to tiles) x 26
+    if (i >= ucap * 26) return;
+    const int64_t u = i / 26;
+    const int d = (int)(i % 26);
+    int32_t row = (int32_t)zrow;
+    if (u < *n_units) {
+        int dx, dy, dz;
+        blk_delta(d, dx, dy, dz);
+        const int32_t s = coll[(int64_t)units[u] * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+        if (s >= 0 && unit_of[s] >= 0) row = unit_of[s];
+    }
+    src[((u / kBlkRows) * 26 + d) * kBlkRows + u % kBlkRows] = row;
+}
+
+constexpr int kAblkLoadWarps = 2;  // each loads 64 rows (more would leave the drains too few registers)
+constexpr int kAblkThreads = 32 * (kBlkDrainWarps + kAblkLoadWarps + 2);  // drains, loaders, B producer, MMA
+
+struct AblkParams {
+    CUtensorMap tmB;  // B_D, FP16 hi | lo
+    int tile0;        // tile of block 0 (launch in waves)
+    int ksplit;
+    int64_t part_stride;  // floats between the partial sums of two offset ranges
+    int64_t zrow;
+};
+
+template <int P, int DS, int CH>
+__global__ void __launch_bounds__(kAblkThreads, 1)
+    k_m2l_ablk(const __grid_constant__ AblkParams prm, const int32_t *__restrict__ n_units,
+               const int32_t *__restrict__ units, const int32_t *__restrict__ child_of,
+               const int32_t *__restrict__ src, const __half *__restrict__ Apre, const int8_t *__restrict__ uscale,
+               const int *__restrict__ gexp, float *__restrict__ Lc, float *__restrict__ Lpart, int *status)
+{
+    using C = BlkCfg<P, CH>;
+    constexpr int PP = C::PP, KD = C::KD, NT = C::NT, NH = C::NH, NKC = C::NKC, NSTAGE = C::NSTAGE;
+    constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(kBlkRows >> 4) << 24);
+    constexpr int kLoad0 = kBlkDrainWarps, kProdWarp = kLoad0 + kAblkLoadWarps, kMmaWarp = kProdWarp + 1;
+
+    extern __shared__ unsigned char blk_smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], dfull[2], dempty[2], done_bar;
+    __shared__ int s_issued[NSTAGE];
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    // ---- tile: unit tile, N-tile, offset range [d_lo, d_hi)
+    const int ks = (prm.tile0 + (int)blockIdx.x) % prm.ksplit;
+    const int tt = (prm.tile0 + (int)blockIdx.x) / prm.ksplit;
+    const int nt = tt % C::NTILES;
+    const int64_t ut = tt / C::NTILES;
+    const int64_t nu = *n_units;
+    if (ut * kBlkRows >= nu) return;  // the whole CTA: past the units (before any barrier or TMEM)
+    const int d_lo = (26 * ks) / prm.ksplit, d_hi = (26 * (ks + 1)) / prm.ksplit;
+    const int S = (d_hi - d_lo) * NKC, NU = (d_hi - d_lo) * DS;
+    const int32_t *tsrc = src + ut * 26 * kBlkRows;
+
+    unsigned char *smem =
+        blk_smem_raw + ((1024u - (smem_u32(blk_smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned stages
+    auto a_pl = [&](int st, int pl) { return smem + (size_t)st * C::STAGE_BYTES + pl * C::A_BYTES; };
+    auto b_hi = [&](int st) { return smem + (size_t)st * C::STAGE_BYTES + 2 * C::A_BYTES; };
+    auto b_lo = [&](int st) { return smem + (size_t)st * C::STAGE_BYTES + 2 * C::A_BYTES + C::B_BYTES; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < NSTAGE; ++st) {
+            mbar_init(&full_bar[st], kAblkLoadWarps + 1);  // the loader warps + the B copies' expect_tx
+            mbar_init(&empty_bar[st], 1);                  // one tcgen05.commit
+            s_issued[st] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&dfull[b], 1);
+            mbar_init(&dempty[b], kBlkDrainWarps);
+        }
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == kProdWarp && lane == 0) blk_prefetch_tmap(&prm.tmB);
+    if (warp == kMmaWarp) tmem_alloc(&s_tmem, C::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp >= kLoad0 && warp < kProdWarp) {
+        // ===== loader warps: rows 64 w + lane and 64 w + 32 + lane of A (hi and lo planes) =====
+        constexpr int RPW = kBlkRows / kAblkLoadWarps / 32;  // rows per lane
+        constexpr int CPR = CH / 8;                          // 16-byte chunks per row
+        for (int s = 0; s < S; ++s) {
+            const int st = s % NSTAGE, d = d_lo + s / NKC, c = s % NKC;
+            int ok = 1;
+            if (s >= NSTAGE && lane == 0)
+                ok = mbar_wait_bounded(&empty_bar[st], ((s / NSTAGE) - 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok || s_abort) {
+                if (lane == 0) s_abort = 1;
+                break;
+            }
+            const int kw = KD - c * CH < CH ? KD - c * CH : CH;
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int r = (kBlkRows / kAblkLoadWarps) * (warp - kLoad0) + 32 * rr + lane;
+                const int64_t row = tsrc[d * kBlkRows + r];
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl) {
+                    const int4 *g = reinterpret_cast<const int4 *>(Apre + (row * 2 + pl) * KD + (int64_t)c * CH);
+                    unsigned char *dst = a_pl(st, pl) + (size_t)r * (2 * CH);
+#pragma unroll
+                    for (int q = 0; q < CPR; ++q) {
+                        if (8 * q >= kw) break;
+                        const int4 v = __ldg(g + q);
+                        // the TMA's swizzle of this row: 16-byte chunk q at q ^ (row bits)
+                        const int qs = CH == 64 ? (q ^ (r & 7)) : (q ^ ((r >> 1) & 3));
+                        *reinterpret_cast<int4 *>(dst + 16 * qs) = v;
+                    }
+                }
+            }
+            fence_proxy_async();  // the generic-proxy stores, before the MMA's async-proxy reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[st]);
+        }
+    } else if (warp == kProdWarp) {
+        if (lane == 0) {
+            for (int s = 0; s < S; ++s) {
+                const int st = s % NSTAGE, d = d_lo + s / NKC, c = s % NKC;
+                if (s >= NSTAGE &&
+                    !mbar_wait_bounded(&empty_bar[st], ((s / NSTAGE) - 1) & 1, kWaitLimitNs, &s_abort)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                mbar_expect_tx(&full_bar[st], 2u * (uint32_t)C::B_BYTES);
+                const int k0 = c * CH;
+                blk_tma4(b_hi(st), &prm.tmB, k0, nt * C::NSTRIDE, 0, d, &full_bar[st]);
+                blk_tma4(b_lo(st), &prm.tmB, k0, nt * C::NSTRIDE, 1, d, &full_bar[st]);
+                s_issued[st] += 1;
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            for (int s = 0; s < S; ++s) {
+                const int st = s % NSTAGE, c = s % NKC;
+                const int uc = (c * DS) / NKC, u = (s / NKC) * DS + uc, b = u & 1;
+                const bool first = c == 0 || ((c - 1) * DS) / NKC != uc;
+                const bool last = c == NKC - 1 || ((c + 1) * DS) / NKC != uc;
+                if (first && u >= 2 &&
+                    !mbar_wait_bounded(&dempty[b], ((u - 2) >> 1) & 1, kWaitLimitNs, &s_abort)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (!mbar_wait_bounded(&full_bar[st], (s / NSTAGE) & 1, kWaitLimitNs, &s_abort)) {
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const int kw = KD - c * CH < CH ? KD - c * CH : CH;
+                const uint32_t ah = smem_u32(a_pl(st, 0)), al = smem_u32(a_pl(st, 1));
+                const uint32_t bh = smem_u32(b_hi(st)), bl = smem_u32(b_lo(st));
+                const uint32_t dt = tmem + (uint32_t)(b * NT);
+                for (int j = 0; j < (kw + 15) / 16; ++j) {
+                    const uint32_t o = 32u * j;
+                    blk_mma_ss(dt, blk_desc<CH>(al + o), blk_desc<CH>(bh + o), kIdesc, (first && j == 0) ? 0u : 1u);
+                    blk_mma_ss(dt, blk_desc<CH>(ah + o), blk_desc<CH>(bl + o), kIdesc, 1u);
+                    blk_mma_ss(dt, blk_desc<CH>(ah + o), blk_desc<CH>(bh + o), kIdesc, 1u);
+                }
+                tc_commit(&empty_bar[st]);
+                if (last) tc_commit(&dfull[b]);
+            }
+            tc_commit(&done_bar);
+        }
+    } else {
+        // ===== drain warps: row r (target unit), columns [h NH, h NH + NH) of the N-tile =====
+        const int quad = warp & 3, h = warp >> 2;
+        const int r = 32 * quad + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        const int64_t unit = ut * kBlkRows + r;
+        const bool rok = unit < nu;
+        const int g = *gexp;
+        float acc[NH];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) acc[i] = 0.f;
+        bool alive = true;
+        for (int u = 0; u < NU && alive; ++u) {
+            const int d = d_lo + u / DS, b = u & 1;
+            const int64_t row = tsrc[d * kBlkRows + r];
+            const float f = row == prm.zrow ? 0.f : blk_pow2(-((int)uscale[row] + g));
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_bounded(&dfull[b], (u >> 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                alive = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t col0 = tmem + lane_base + (uint32_t)(b * NT + h * NH);
+#pragma unroll
+            for (int c0 = 0; c0 < NH; c0 += 32) {
+                constexpr int W = 32;
+                uint32_t v[W];
+#pragma unroll
+                for (int q = 0; q < W; q += 8)
+                    if (c0 + q < NH) blk_ld8(col0 + (uint32_t)(c0 + q), v + q);
+                tmem_wait_ld_regs(v);
+#pragma unroll
+                for (int q = 0; q < W; ++q)
+                    if (c0 + q < NH) acc[c0 + q] = fmaf(__uint_as_float(v[q]), f, acc[c0 + q]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dempty[b]);
+        }
+        if (!alive && lane == 0) s_abort = 1;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&done_bar, 0u, kWaitLimitNs, nullptr) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok && lane == 0) s_abort = 1;
+        __syncwarp();
+        if (ok && alive && !s_abort && rok) {
+            float *dst = prm.ksplit > 1 ? Lpart + (int64_t)ks * prm.part_stride : Lc;
+            const int64_t q = units[unit];
+#pragma unroll
+            for (int i = 0; i < NH; i += 4) {
+                const int col = h * NH + i;
+                const int gc = nt * C::NSTRIDE + col;
+                if (col >= C::NSTRIDE || gc >= KD) continue;
+                const int tau = gc / PP, n = gc % PP;
+                const int32_t cell = child_of[q * 8 + tau];
+                if (cell < 0) continue;
+                *reinterpret_cast<float4 *>(dst + (int64_t)cell * PP + n) =
+                    make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            atomicOr(status, kStatusTimeout);
+            for (int st = 0; st < NSTAGE; ++st)
+                if (s_issued[st] > 0) mbar_wait_bounded(&full_bar[st], (s_issued[st] - 1) & 1, kWaitLimitNs, nullptr);
+        }
+        __syncthreads();
+    }
+    if (warp == kMmaWarp) {
+        __syncwarp();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
 // ---- sum of the offset ranges' partial sums (fixed order, so the result does not depend on
 // which CTA finished first): Lc = sum_k Lpart[k] over the nonempty cells of levels 2..L
 __global__ void __launch_bounds__(256) k_blk_reduce(int64_t c0, int64_t c1, int PP4, int ksplit, int64_t stride4,
@@ -689,6 +1042,137 @@ int launch_m2l_blk(int P, int L, const int32_t *begin, const int32_t *end, const
     case 10: return launch_blk_t<10, 32>(L, begin, end, presplit, pscale, table, Lc, Lpart, status, s, max_ctas);
     }
     return -1;
+}
+
+// ---- adaptive tree ----------------------------------------------------------------------------
+size_t m2l_ablk_presplit_bytes(int P, int64_t ucap) { return (size_t)(ucap + 1) * 2 * 8 * P * P * sizeof(__half); }
+
+int64_t m2l_ablk_tiles_units(int64_t ucap) { return (ucap + kBlkRows - 1) / kBlkRows * kBlkRows; }
+
+size_t m2l_ablk_src_bytes(int64_t ucap) { return (size_t)m2l_ablk_tiles_units(ucap) * 26 * sizeof(int32_t); }
+
+// offset ranges per tile from the particle count and leaf size alone (an estimate of the units:
+// a quarter of n / leaf_size), so that evaluations of the same count split alike whatever their
+// trees (a captured batch and the same instance alone sum in the same order)
+int m2l_ablk_ksplit(int P, int64_t n, int leaf_size)
+{
+    const int nt = P == 4 ? BlkCfg<4, 64>::NTILES : P == 6 ? BlkCfg<6, 64>::NTILES : P == 8 ? BlkCfg<8, 32>::NTILES
+                                                                                            : BlkCfg<10, 32>::NTILES;
+    const int64_t units = n / (4 * (int64_t)(leaf_size > 0 ? leaf_size : 1)) + 1;
+    const int64_t t = (units + kBlkRows - 1) / kBlkRows * nt;
+    if (t <= 0 || t >= kBlkFillCtas) return 1;
+    const int64_t k = (2 * kBlkFillCtas + t - 1) / t;
+    return k < 26 ? (int)k : 26;
+}
+
+void launch_ablk_prep(int P, Span cells, int64_t ucap, const int32_t *level, const int32_t *nchild,
+                      const int32_t *child_of, const int32_t *coll, const float *M, uint32_t *flag, uint32_t *scan,
+                      uint32_t *scan_tmp, int32_t *unit_of, int32_t *units, int32_t *n_units, void *Apre,
+                      int8_t *uscale, int32_t *src, cudaStream_t s)
+{
+    const unsigned gc = (unsigned)((cells.cap + 255) / 256);
+    k_ablk_flags<<<gc, 256, 0, s>>>(cells, level, nchild, flag);
+    launch_exclusive_scan(flag, scan, cells.cap, scan_tmp, s);
+    k_ablk_units<<<gc, 256, 0, s>>>(cells, flag, scan, unit_of, units, n_units);
+    const int64_t zrow = ucap;
+    const unsigned gp = (unsigned)((ucap + 1 + 7) / 8);
+    __half *A = static_cast<__half *>(Apre);
+    switch (P) {
+    case 4: k_ablk_presplit<4><<<gp, 256, 0, s>>>(n_units, zrow, units, child_of, M, A, uscale); break;
+    case 6: k_ablk_presplit<6><<<gp, 256, 0, s>>>(n_units, zrow, units, child_of, M, A, uscale); break;
+    case 8: k_ablk_presplit<8><<<gp, 256, 0, s>>>(n_units, zrow, units, child_of, M, A, uscale); break;
+    case 10: k_ablk_presplit<10><<<gp, 256, 0, s>>>(n_units, zrow, units, child_of, M, A, uscale); break;
+    }
+    const int64_t up = m2l_ablk_tiles_units(ucap);
+    k_ablk_src<<<(unsigned)((up * 26 + 255) / 256), 256, 0, s>>>(n_units, up, zrow, units, coll, unit_of, src);
+    note_launches(4);
+}
+
+template <int P, int CH>
+static int launch_ablk_t(int64_t ucap, const int32_t *n_units, const int32_t *units, const int32_t *child_of,
+                         const int32_t *src, const void *Apre, const int8_t *uscale, const void *table, float *Lc,
+                         float *Lpart, int ksplit, int64_t part_stride, int *status, cudaStream_t s, int max_ctas)
+{
+    using C = BlkCfg<P, CH>;
+    constexpr CUtensorMapSwizzle kSw = CH == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return -1;
+    AblkParams prm;
+    memset(&prm, 0, sizeof(prm));
+    const cuuint64_t KD = C::KD;
+    const int *gexp = reinterpret_cast<const int *>(static_cast<const __half *>(table) + 26 * 2 * KD * KD);
+    {
+        const cuuint64_t dims[4] = {KD, KD, 2, 26};
+        const cuuint64_t strides[3] = {KD * 2, KD * KD * 2, KD * KD * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)CH, (cuuint32_t)C::NT, 1, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&prm.tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(table), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, kSw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+    }
+    prm.ksplit = ksplit;
+    prm.part_stride = part_stride;
+    prm.zrow = ucap;
+    if (ksplit > 1 && !Lpart) return -1;
+    auto kern = k_m2l_ablk<P, kBlkDrainsPerOffset, CH>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmemBytes);
+    const int64_t nctas64 = (ucap + kBlkRows - 1) / kBlkRows * C::NTILES * ksplit;
+    const int nctas = (int)nctas64;
+    const int step = max_ctas > 0 ? max_ctas : nctas;
+    for (int t0 = 0; t0 < nctas; t0 += step) {
+        prm.tile0 = t0;
+        const int gsz = nctas - t0 < step ? nctas - t0 : step;
+        kern<<<gsz, kAblkThreads, C::kSmemBytes, s>>>(prm, n_units, units, child_of, src,
+                                                      static_cast<const __half *>(Apre), uscale, gexp, Lc, Lpart,
+                                                      status);
+        note_launches(1);
+    }
+    return 0;
+}
+
+int launch_m2l_ablk(int P, int64_t ucap, const int32_t *n_units, const int32_t *units, const int32_t *child_of,
+                    const int32_t *src, const void *Apre, const int8_t *uscale, const void *table, float *Lc,
+                    float *Lpart, int ksplit, int64_t part_stride, int *status, cudaStream_t s, int max_ctas)
+{
+    if (ucap <= 0) return 0;
+    switch (P) {
+    case 4: return launch_ablk_t<4, 64>(ucap, n_units, units, child_of, src, Apre, uscale, table, Lc, Lpart, ksplit, part_stride, status, s, max_ctas);
+    case 6: return launch_ablk_t<6, 64>(ucap, n_units, units, child_of, src, Apre, uscale, table, Lc, Lpart, ksplit, part_stride, status, s, max_ctas);
+    case 8: return launch_ablk_t<8, 32>(ucap, n_units, units, child_of, src, Apre, uscale, table, Lc, Lpart, ksplit, part_stride, status, s, max_ctas);
+    case 10: return launch_ablk_t<10, 32>(ucap, n_units, units, child_of, src, Apre, uscale, table, Lc, Lpart, ksplit, part_stride, status, s, max_ctas);
+    }
+    return -1;
+}
+
+// Lc = the sum of the offset ranges' partial sums, in range order, over the cells of `deep`
+__global__ void __launch_bounds__(256) k_ablk_reduce(Span deep, int PP4, int ksplit, int64_t stride4,
+                                                     const float4 *__restrict__ part, float4 *__restrict__ Lc)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= span_count(deep) * PP4) return;
+    const int64_t i = span_first(deep) * PP4 + j;
+    float4 a = part[i];
+    for (int k = 1; k < ksplit; ++k) {
+        const float4 b = part[i + k * stride4];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+    }
+    Lc[i] = a;
+}
+
+void launch_ablk_reduce(int P, Span deep, int ksplit, int64_t part_stride, const float *Lpart, float *Lc,
+                        cudaStream_t s)
+{
+    const int64_t PP4 = (int64_t)P * P / 4;
+    const int64_t nthr = deep.cap * PP4;
+    if (nthr <= 0) return;
+    k_ablk_reduce<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(deep, (int)PP4, ksplit, part_stride / 4,
+                                                                 reinterpret_cast<const float4 *>(Lpart),
+                                                                 reinterpret_cast<float4 *>(Lc));
+    note_launches(1);
 }
 
 }  // namespace gbfmm

@@ -122,13 +122,18 @@ def test_adaptive_fmm_matches_oracle(G, ctx, p):
     assert O.rel_l2(out[:, 1:], d[:, 1:]) <= e_or + TOL_FMM
 
 
-def test_adaptive_m2l_tensor_cores_and_cuda_cores_agree(G, ctx):
-    x = inputs.plummer(30000, 77)
-    tc = run(G, ctx, x, p=8, leaf_size=32)
-    cc = run(G, ctx, x, p=8, leaf_size=32, flags=G.FLAG_M2L_CUDA_CORES)
-    ref = O.fmm_adaptive(x, 8, 32)["out"]
-    assert O.rel_l2(tc, ref) <= TOL_FMM and O.rel_l2(cc, ref) <= TOL_FMM
-    assert O.rel_l2(tc, cc) <= 5e-6
+@pytest.mark.parametrize("p,n,leaf", [(8, 30000, 32), (4, 200000, 64), (10, 20000, 16), (6, 3000, 8)])
+def test_adaptive_m2l_forms_agree(G, ctx, p, n, leaf):
+    # the block form (default: one GEMM per parent offset over the cells with children), the
+    # list form over the V lists (gathered) and the FP32 CUDA-core form
+    x = inputs.plummer(n, 77 + p)
+    blk = run(G, ctx, x, p=p, leaf_size=leaf)
+    gat = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_GATHERED)
+    cc = run(G, ctx, x, p=p, leaf_size=leaf, flags=G.FLAG_M2L_CUDA_CORES)
+    ref = O.fmm_adaptive(x, p, leaf)["out"]
+    for out in (blk, gat, cc):
+        assert O.rel_l2(out, ref) <= TOL_FMM
+    assert O.rel_l2(blk, cc) <= 5e-6 and O.rel_l2(gat, cc) <= 5e-6
 
 
 @pytest.mark.parametrize("p", [4, 10])
