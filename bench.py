@@ -262,17 +262,16 @@ def run_gpu(args, w):
         m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_V, C)
         p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_U, C)
         cnt_leaf = tree["count"].astype(np.int64)  # U rows of non-leaves are empty
-        # M2L tiles: targets grouped by (level, child position), 128 per tile
+        # block-form M2L units: the cells of levels >= 1 with children (the parents of the cells of
+        # levels >= 2), 128 per tile
         deep = tree["level"] >= 2
-        grp = tree["level"][deep].astype(np.int64) * 8 + (tree["key"][deep] & np.uint64(7)).astype(np.int64)
-        tiles = int(np.sum(-(-np.bincount(grp) // 128)))
+        units = int(np.unique(tree["parent"][deep]).size)
     else:
         C = G.level_offset(L + 1)
         m2l_offs, _ = G.gbfmm_export_lists(fmm.ctx, G.LIST_M2L, C)
         tree = G.gbfmm_export_tree(fmm.ctx, n, C)
         p2p_offs, p2p_ids = G.gbfmm_export_lists(fmm.ctx, G.LIST_P2P, 8 ** L)
         cnt_leaf = tree["count"][G.level_offset(L): G.level_offset(L) + 8 ** L].astype(np.int64)
-        tiles = sum(8 * -(-(8 ** (l - 1)) // 128) for l in range(2, L + 1))
     m2l_pairs = int(m2l_offs[-1])
     cs = np.concatenate([[0], np.cumsum(tree["count"][p2p_ids[:p2p_offs[-1]]].astype(np.int64))])
     src_per_leaf = cs[p2p_offs[1:]] - cs[p2p_offs[:-1]]
@@ -379,21 +378,26 @@ def run_gpu(args, w):
     except Exception:
         tpeak, tbasis = 1900.0, "fallback 1900 TFLOP/s dense FP16/BF16 (of fallback)"
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nt = {4: 128, 6: 144, 8: 256, 10: 208}[P]
+    nstride = 200 if P == 10 else nt
+    kd = 8 * P * P
+    ntiles_n = -(-kd // nstride)
     if adaptive:
-        # list-based kernel: 128 targets per tile (MMA M), N = K = p^2 padded to 16, 189 offsets
-        # per tile, 3 MMAs per product (hi*hi + lo*hi + hi*lo)
-        npad = -(-P * P // 16) * 16
-        kname, ksrc, kprof = "k_m2l_f16s", "m2l_f16.cu", f"m2l_f16s_{w['name']}.md"
-        tensor_flops = tiles * 189 * 3 * 2 * 128 * npad * npad
-        m2l_launches = -(-tiles // sms)
-        kshape = "128 target cells x p^2 (padded to 16) per MMA, 189 offsets per tile"
+        # block kernel over units: per tile 128 units (MMA M) x NT outputs over the 26 parent
+        # offsets, K = 8 p^2 per offset (colleagues' children gathered); 3 MMAs per product;
+        # offset ranges per tile from the particle count (m2l_ablk_ksplit)
+        ablk_tiles = -(-units // 128) * ntiles_n
+        est = -(-(n // (4 * w["leaf_size"]) + 1) // 128) * ntiles_n
+        ksplit = 1 if est >= 152 else min(26, -(-304 // est))
+        kname, ksrc, kprof = "k_m2l_ablk", "m2l_blk.cu", f"m2l_ablk_{w['name']}.md"
+        tensor_flops = ablk_tiles * 26 * kd * 3 * 2 * 128 * nt
+        m2l_launches = -(-(ablk_tiles * ksplit) // sms)
+        kshape = (f"{ablk_tiles} tiles of 128 units (cells with children) x {nt} outputs (of 8p^2 = {kd}), K = {kd} "
+                  f"per parent offset, 26 offsets, offsets split over {ksplit} CTA(s) per tile; the M2L stage "
+                  "also holds P2L over the X lists")
     else:
         # block kernel: per tile 128 target parents (MMA M) x NT outputs (MMA N) over the 26 parent
         # offsets, K = 8 p^2 per offset; 3 MMAs per product
-        nt = {4: 128, 6: 144, 8: 256, 10: 208}[P]
-        nstride = 200 if P == 10 else nt
-        kd = 8 * P * P
-        ntiles_n = -(-kd // nstride)
         blk_tiles = sum(max(1, 8 ** (l - 1) // 128) * ntiles_n for l in range(2, L + 1))
         ksplit = 1 if blk_tiles >= 152 else min(26, -(-304 // blk_tiles))
         kname, ksrc, kprof = "k_m2l_blk", "m2l_blk.cu", f"m2l_blk_{w['name']}.md"
