@@ -647,40 +647,72 @@ __global__ void __launch_bounds__(kAblkThreads, 1)
 
     if (warp >= kLoad0 && warp < kProdWarp) {
         // ===== loader warps: rows 64 w + lane and 64 w + 32 + lane of A (hi and lo planes) =====
+        // a stage's 16-byte chunks go through registers; where they fit twice (p = 8, 10), the
+        // next stage's loads are issued before this stage is stored, so their latency overlaps
         constexpr int RPW = kBlkRows / kAblkLoadWarps / 32;  // rows per lane
         constexpr int CPR = CH / 8;                          // 16-byte chunks per row
-        for (int s = 0; s < S; ++s) {
-            const int st = s % NSTAGE, d = d_lo + s / NKC, c = s % NKC;
+        constexpr int NB = RPW * 2 * CPR;                    // chunks per lane and stage
+        const int r0 = (kBlkRows / kAblkLoadWarps) * (warp - kLoad0) + lane;
+        auto fetch = [&](int s, int4(&v)[NB]) {
+            const int d = d_lo + s / NKC, c = s % NKC;
+            const int kw = KD - c * CH < CH ? KD - c * CH : CH;
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int64_t row = tsrc[d * kBlkRows + r0 + 32 * rr];
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl) {
+                    const int4 *g = reinterpret_cast<const int4 *>(Apre + (row * 2 + pl) * KD + (int64_t)c * CH);
+#pragma unroll
+                    for (int q = 0; q < CPR; ++q) v[(rr * 2 + pl) * CPR + q] = 8 * q < kw ? __ldg(g + q) : int4{0, 0, 0, 0};
+                }
+            }
+        };
+        auto put = [&](int s, const int4(&v)[NB]) {
+            const int st = s % NSTAGE, c = s % NKC;
             int ok = 1;
             if (s >= NSTAGE && lane == 0)
                 ok = mbar_wait_bounded(&empty_bar[st], ((s / NSTAGE) - 1) & 1, kWaitLimitNs, &s_abort) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok || s_abort) {
                 if (lane == 0) s_abort = 1;
-                break;
+                return false;
             }
             const int kw = KD - c * CH < CH ? KD - c * CH : CH;
 #pragma unroll
             for (int rr = 0; rr < RPW; ++rr) {
-                const int r = (kBlkRows / kAblkLoadWarps) * (warp - kLoad0) + 32 * rr + lane;
-                const int64_t row = tsrc[d * kBlkRows + r];
+                const int r = r0 + 32 * rr;
 #pragma unroll
                 for (int pl = 0; pl < 2; ++pl) {
-                    const int4 *g = reinterpret_cast<const int4 *>(Apre + (row * 2 + pl) * KD + (int64_t)c * CH);
                     unsigned char *dst = a_pl(st, pl) + (size_t)r * (2 * CH);
 #pragma unroll
                     for (int q = 0; q < CPR; ++q) {
                         if (8 * q >= kw) break;
-                        const int4 v = __ldg(g + q);
                         // the TMA's swizzle of this row: 16-byte chunk q at q ^ (row bits)
                         const int qs = CH == 64 ? (q ^ (r & 7)) : (q ^ ((r >> 1) & 3));
-                        *reinterpret_cast<int4 *>(dst + 16 * qs) = v;
+                        *reinterpret_cast<int4 *>(dst + 16 * qs) = v[(rr * 2 + pl) * CPR + q];
                     }
                 }
             }
             fence_proxy_async();  // the generic-proxy stores, before the MMA's async-proxy reads
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_bar[st]);
+            return true;
+        };
+        if constexpr (NB <= 16) {
+            int4 va[NB], vb[NB];
+            if (S > 0) fetch(0, va);
+            for (int s = 0; s < S; s += 2) {
+                if (s + 1 < S) fetch(s + 1, vb);
+                if (!put(s, va) || s + 1 >= S) break;
+                if (s + 2 < S) fetch(s + 2, va);
+                if (!put(s + 1, vb)) break;
+            }
+        } else {
+            int4 va[NB];
+            for (int s = 0; s < S; ++s) {
+                fetch(s, va);
+                if (!put(s, va)) break;
+            }
         }
     } else if (warp == kProdWarp) {
         if (lane == 0) {
