@@ -131,14 +131,35 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_from_profile(kernel_file: str, summary: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel source is unchanged."""
+def kernel_source_text(src_text: str, kname: str) -> str:
+    """The source of one __global__ kernel: from the template (or __global__) line that opens its
+    definition to the next section comment ("// ----") or the end of the file."""
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(kname) + r"\s*\(", src_text)
+    if not m:
+        return ""
+    start = src_text.rfind("\ntemplate", 0, m.start())
+    gl = src_text.rfind("\n__global__", 0, m.start() + 1)
+    if start < 0 or (gl > start and src_text[start:gl].count("\n") > 2):
+        start = gl
+    end = src_text.find("\n// ----", m.end())
+    return src_text[start:end if end >= 0 else len(src_text)]
+
+
+def kernel_sha16(kernel_file: str, kname: str) -> str:
+    src = os.path.join(ROOT, "paper_1010_1482_gb300", "csrc", kernel_file)
+    text = kernel_source_text(open(src, encoding="utf-8").read(), kname)
+    return hashlib.sha256(text.encode()).hexdigest()[:16] if text else ""
+
+
+def traffic_from_profile(kernel_file: str, summary: str, kname: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel's own source is unchanged
+    (the recorded hash is kernel_sha16 of the kernel's text)."""
     path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_1010_1482_gb300", "csrc", kernel_file)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
     text = open(path).read()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_sha16(kernel_file, kname)
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not (m_sha and m_tr) or m_sha.group(1) != sha:
@@ -405,7 +426,7 @@ def run_gpu(args, w):
         m2l_launches = -(-(blk_tiles * ksplit) // sms)
         kshape = (f"{blk_tiles} tiles of 128 target parents x {nt} outputs (of 8p^2 = {kd}), K = {kd} per parent "
                   f"offset, 26 offsets, offsets split over {ksplit} CTA(s) per tile")
-    traffic = traffic_from_profile(ksrc, kprof)
+    traffic = traffic_from_profile(ksrc, kprof, kname)
     roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": m2l_tf / tpeak,
                 "traffic": traffic,
