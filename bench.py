@@ -456,7 +456,7 @@ def run_gpu(args, w):
                    "l2": "flushed between steps (256 MiB write outside the per-step events)"},
         "roofline": roofline,
         "kernels": {
-            "p2p": {"kernel": "k_p2p2", "achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
+            "p2p": {"kernel": "k_p2p_ws", "achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
                     "flop_per_pair": 20, "peak": peak, "bound": "alu",
                     "achieved_tflops_alone": p2p_flops / (ser_stages["P2P"] / 1e3) / 1e12,
                     "frac_alone": p2p_flops / (ser_stages["P2P"] / 1e3) / 1e12 / peak,

@@ -917,7 +917,7 @@ int treecode_adaptive(gbfmm_ctx *ctx, AdaptiveState &A, const Ranges &R, const g
     mark(8);
     launch_p2p_cells(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                      A.end.as<int32_t>(), A.tc_offs[0].as<uint32_t>(), A.tc_ids[0].as<int32_t>(), far, A.perm,
-                     (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
+                     (float)prm->eps2, reinterpret_cast<float4 *>(d_out), ctx->d_status, s);
     mark(9);
     A.P = P;
     cudaError_t e = cudaGetLastError();
@@ -1246,7 +1246,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
         if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
         launch_p2p_cells_near(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                               A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
-                              (float)prm->eps2, near, ctx->s_near);
+                              (float)prm->eps2, near, ctx->d_status, ctx->s_near);
         if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
         cudaEventRecord(ctx->ev_near, ctx->s_near);
     }
@@ -1345,7 +1345,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
         if (!fork) {
             launch_p2p_cells_near(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                                   A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(),
-                                  (float)prm->eps2, near, s);
+                                  (float)prm->eps2, near, ctx->d_status, s);
             mark(8);
         }
         cudaMemsetAsync(far, 0, 16 * (size_t)n, s);
@@ -1376,7 +1376,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
         mark(8);
         launch_p2p_cells(A.leaves.as<int32_t>(), R.leaves(), n, A.sx.as<float4>(), A.begin.as<int32_t>(),
                          A.end.as<int32_t>(), A.loffs[kListU].as<uint32_t>(), A.lids[kListU].as<int32_t>(), far, perm,
-                         (float)prm->eps2, reinterpret_cast<float4 *>(d_out), s);
+                         (float)prm->eps2, reinterpret_cast<float4 *>(d_out), ctx->d_status, s);
         mark(9);
     }
     A.P = P;

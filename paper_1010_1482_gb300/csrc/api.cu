@@ -481,7 +481,7 @@ int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, cons
         s = ctx->s_far;
         if (timing) cudaEventRecord(ctx->ev_aux[0], ctx->s_near);
         if (blk) p2p_lists(ctx->s_near);
-        launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, ctx->s_near);
+        launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, ctx->d_status, ctx->s_near);
         if (timing) cudaEventRecord(ctx->ev_aux[1], ctx->s_near);
         cudaEventRecord(ctx->ev_near, ctx->s_near);
     }
@@ -526,7 +526,7 @@ int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, cons
             cudaStreamWaitEvent(s, ctx->ev_near, 0);
             if (timing) cudaEventRecord(ctx->ev_aux[2], s);
         } else {
-            launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, s);
+            launch_p2p_near(L, n, sx, begin, end, p2p_offs, p2p_ids, (float)prm->eps2, near, ctx->d_status, s);
             mark(8);
         }
         launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s, near, perm, out);
@@ -539,7 +539,8 @@ int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, cons
     } else {
         if (L >= 2 && prm->method == GBFMM_METHOD_FMM) launch_l2p(P, L, geo, n, sx, skeys, Lc, far, s);
         mark(8);
-        launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out, s);
+        launch_p2p(L, n, sx, begin, end, p2p_offs, p2p_ids, L >= 2 ? far : nullptr, perm, (float)prm->eps2, out,
+                   ctx->d_status, s);
         mark(9);
     }
     e = cudaGetLastError();

@@ -387,7 +387,7 @@ void launch_m2p_cells(int P, const int32_t *leaves, Span lv, const float4 *geom,
                       const float *M, float4 *far, cudaStream_t s, bool long_rows = false);
 void launch_p2p_cells(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
-                      const uint32_t *perm, float eps2, float4 *out, cudaStream_t s);
+                      const uint32_t *perm, float eps2, float4 *out, int *status, cudaStream_t s);
 
 // m2l_blk.cu: the uniform tree's M2L as one dense GEMM per parent offset on the tensor cores
 size_t m2l_blk_table_bytes(int P);
@@ -432,16 +432,18 @@ void launch_m2l_rot(int P, int L, const int32_t *begin, const int32_t *end, cons
 // p2p.cu
 // P2P without the far field: the compensated near-field sums of every particle in sorted order,
 // near[2 i] = sums (phi, dphi/dx, dphi/dy, dphi/dz), near[2 i + 1] = their compensations (the
-// packed-pair kernels only: p2p_near_supported())
+// warp-specialised kernel: p2p_near_supported()).  The P2P launchers take the context's status
+// word: a bounded wait that expires raises kStatusTimeout there.
 bool p2p_near_supported();
 void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
-                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, cudaStream_t s);
+                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, int *status,
+                     cudaStream_t s);
 void launch_p2p_cells_near(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                            const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
-                           cudaStream_t s);
+                           int *status, cudaStream_t s);
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
                 const uint32_t *p2p_offs, const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2,
-                float4 *out, cudaStream_t s);
+                float4 *out, int *status, cudaStream_t s);
 void launch_direct(int64_t n_src, const float4 *src, int64_t n_tgt, const float4 *tgt, float eps2, float4 *out,
                    cudaStream_t s);
 

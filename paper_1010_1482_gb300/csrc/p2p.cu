@@ -5,23 +5,23 @@
 //   phi_i  += q_j / sqrt(d2 + eps2),   grad_i -= q_j d / (d2 + eps2)^(3/2),
 // and pairs with d2 == 0 (the particle itself, exact duplicates) contribute nothing.
 //
-// Decomposition: one CTA (128 threads) per target leaf.  The leaf's neighbour cells (the
-// uniform tree's <= 27, or an adaptive leaf's U list) are gathered into shared memory in chunks,
-// as packed pairs (x, x | y, y), (z, z | q, q).  Each thread holds two targets in one 64-bit
-// register per coordinate and applies the pair rule with packed FP32x2 instructions, so one
-// staged source feeds two pair interactions; when the leaf has fewer target slots than the CTA
-// has threads, the threads form G groups that split the sources round-robin, so the lanes stay
-// busy for leaves of any occupancy (the paper instead pads targets to the block size).  Each
+// Decomposition (k_p2p_ws): one producer warp and four consumer warps per CTA; a CTA takes
+// every gridDim.x-th target leaf.  The producer reads a leaf's neighbour rows (the uniform tree's
+// <= 27 cells, or an adaptive leaf's U list), puts the leaf's own cell first, and copies the rows'
+// particles with 1D bulk copies into one of two shared-memory stages while the consumers work on
+// the other.  Each consumer thread holds two targets; when the leaf has fewer target slots than
+// there are consumers the threads form G groups that split the sources round-robin, so the lanes
+// stay busy for leaves of any occupancy (the paper instead pads targets to the block size).  Each
 // thread sums its share in FP32; the group partials are combined per target with compensated
 // (Kahan) summation.  Then either the far-field value is added the same way and the result
 // written to the caller's original particle order, or (FMM) the compensated sums are stored for
 // L2P, which adds the far field and writes the output.
 #include "common.cuh"
+#include "ptx.cuh"
+
+#include <algorithm>
 
 namespace gbfmm {
-
-constexpr int kP2PThreads = 128;
-constexpr int kRowCap = 32;
 
 template <bool SOFT>
 GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi, float &gx, float &gy, float &gz)
@@ -38,278 +38,369 @@ GB_DEV void pair(float xi, float yi, float zi, float4 s, float eps2, float &phi,
     gz = fmaf(-dz, qi3, gz);
 }
 
-// ---- packed FP32x2 arithmetic (two lanes of one 64-bit register: targets a and b) -------------
-GB_DEV uint64_t f2_pack(float a, float b)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-GB_DEV void f2_unpack(uint64_t r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-GB_DEV uint64_t f2_sub(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-GB_DEV uint64_t f2_add(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-GB_DEV uint64_t f2_mul(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-GB_DEV uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// The pair rule for two targets at once (packed X, Y, Z) and one source whose coordinates and
-// charge are staged duplicated: xy = (x, x, y, y), zq = (z, z, q, q).  Same operation order as
-// pair(); the gradient accumulates +d q / r^3 and is negated once at the end.  MASK drops pairs
-// at zero distance (only the target's own cell can hold them).
+// Scalar pair rule of pair(), with the zero-distance test only where MASK (the target's own
+// cell); the gradient accumulates +d q / r^3 and is negated once at the end.
 template <bool SOFT, bool MASK>
-GB_DEV void pair2(uint64_t X, uint64_t Y, uint64_t Z, ulonglong2 xy, ulonglong2 zq, uint64_t E2, uint64_t &P,
-                  uint64_t &GX, uint64_t &GY, uint64_t &GZ)
+GB_DEV void pairm(float xi, float yi, float zi, float4 s, float eps2, float &phi, float &gx, float &gy, float &gz)
 {
-    const uint64_t dx = f2_sub(X, xy.x);
-    const uint64_t dy = f2_sub(Y, xy.y);
-    const uint64_t dz = f2_sub(Z, zq.x);
-    uint64_t d2 = f2_mul(dz, dz);
-    d2 = f2_fma(dy, dy, d2);
-    d2 = f2_fma(dx, dx, d2);
-    float r0, r1;
-    f2_unpack(SOFT ? f2_add(d2, E2) : d2, r0, r1);
-    float i0 = rsqrt_ftz(r0), i1 = rsqrt_ftz(r1);
-    if (MASK) {
-        float a0, a1;
-        f2_unpack(d2, a0, a1);
-        i0 = a0 > 0.f ? i0 : 0.f;
-        i1 = a1 > 0.f ? i1 : 0.f;
-    }
-    const uint64_t inv = f2_pack(i0, i1);
-    const uint64_t w = f2_mul(zq.y, inv);
-    P = f2_add(P, w);
-    const uint64_t w3 = f2_mul(f2_mul(w, inv), inv);
-    GX = f2_fma(dx, w3, GX);
-    GY = f2_fma(dy, w3, GY);
-    GZ = f2_fma(dz, w3, GZ);
+    const float dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float inv = rsqrt_ftz(SOFT ? d2 + eps2 : d2);
+    if (MASK) inv = d2 > 0.f ? inv : 0.f;
+    const float w = s.w * inv;
+    phi += w;
+    const float w3 = w * inv * inv;
+    gx = fmaf(dx, w3, gx);
+    gy = fmaf(dy, w3, gy);
+    gz = fmaf(dz, w3, gz);
 }
 
-constexpr int kSrcCap2 = 512;
+// ---- warp-specialised P2P: one producer warp stages, four consumer warps apply the pair rule ---
+//
+// A CTA takes the leaves blockIdx.x, blockIdx.x + gridDim.x, ...  The producer warp reads a
+// leaf's neighbour rows (lane e holds row e of a block of up to 32: its first particle and count),
+// moves the target's own cell to the front of its block (only its sources pay for the
+// zero-distance test), scans the counts across the warp, and copies the rows' particles
+// (contiguous float4 runs of the sorted array) with 1D bulk copies into one of two stage buffers
+// of kP2PCap sources; the stage's full barrier completes when the bytes have landed.  The
+// consumers apply the pair rule to a stage while the producer fills the other, so a leaf's list
+// reads, row copies and the previous leaf's reduction overlap the pair loop.  Targets: 2 per
+// consumer thread; when a leaf has fewer target slots than there are consumers the threads form G
+// groups that take the staged sources round-robin; group partials are combined per target with
+// compensated sums as before.  Every wait is bounded: on expiry the kernel raises kStatusTimeout,
+// stops, and returns once its own copies have landed (bounded again).
+constexpr int kP2PCap = 512;
+constexpr int kP2PConsumers = 128;
+constexpr int kP2PWsThreads = kP2PConsumers + 32;
+constexpr int kP2PTargets = 2 * kP2PConsumers;  // targets per pass over the sources
 
-// CTA per target leaf, TPT targets per thread in packed pairs; the leaf's own cell is staged
-// first so that only its sources pay for the zero-distance test
-template <bool SOFT, int TPT, int NT = kP2PThreads>
-__global__ void __launch_bounds__(NT) k_p2p2(int L, const int32_t *__restrict__ leaves,
-                                                      const float4 *__restrict__ sx,
-                                                      const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-                                                      const uint32_t *__restrict__ p2p_offs,
-                                                      const int32_t *__restrict__ p2p_ids,
-                                                      const float4 *__restrict__ far,
-                                                      const uint32_t *__restrict__ perm, float eps2,
-                                                      float4 *__restrict__ out, float4 *__restrict__ near, Span lv)
+struct P2PItem {
+    int b0;     // the leaf's first particle (sorted order); -1 ends the stream
+    int T;      // the leaf's particle count
+    int tc;     // first target of this pass
+    int chunk;  // sources staged (0: none, the pass only ends)
+    int mend;   // leading staged sources of the target's own cell (zero-distance test)
+    int flags;  // 1: first stage of the pass, 2: last stage of the pass, 4: targets are staged at tc
+};
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kP2PWsThreads, 8) k_p2p_ws(int L, const int32_t *__restrict__ leaves, Span lv,
+                                                           int64_t nleaf, const float4 *__restrict__ sx,
+                                                           const int32_t *__restrict__ begin,
+                                                           const int32_t *__restrict__ end,
+                                                           const uint32_t *__restrict__ p2p_offs,
+                                                           const int32_t *__restrict__ p2p_ids,
+                                                           const float4 *__restrict__ far,
+                                                           const uint32_t *__restrict__ perm, float eps2,
+                                                           float4 *__restrict__ out, float4 *__restrict__ near,
+                                                           int *status)
 {
-    constexpr int NPK = TPT / 2;
-    if (leaves && blockIdx.x >= span_count(lv)) return;  // beyond the listed leaves
-    __shared__ ulonglong2 sA[kSrcCap2], sB[kSrcCap2];  // (x, x | y, y), (z, z | q, q)
-    __shared__ float4 red[TPT][NT];
-    __shared__ int s_cb[kRowCap], s_pref[kRowCap + 1], s_self;
-    const int64_t leaf = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
-    const int64_t g = leaves ? leaf : level_offset(L) + leaf;
-    const int b0 = begin[g], e0 = end[g];
-    if (e0 <= b0) return;
-    const int tid = threadIdx.x;
-    const uint32_t r0 = p2p_offs[leaf];
-    const int nrow = (int)(p2p_offs[leaf + 1] - r0);
-    const int T = e0 - b0;
-    const uint64_t E2 = f2_pack(eps2, eps2);
-    for (int tc = 0; tc < T; tc += TPT * NT) {
-        const int Tc = min(T - tc, TPT * NT);
-        const int slots = (Tc + TPT - 1) / TPT;
-        const int G = NT / slots;
-        const int slot = tid % slots, grp = tid / slots;
-        const bool active = grp < G;
-        uint64_t X[NPK], Y[NPK], Z[NPK], P[NPK], GX[NPK], GY[NPK], GZ[NPK];
-#pragma unroll
-        for (int k = 0; k < NPK; ++k) {
-            // a missing target repeats the slot's first one; its result is discarded
-            const int ta = TPT * slot + 2 * k, tb = ta + 1;
-            const float4 pa = __ldg(&sx[b0 + tc + (ta < Tc ? ta : TPT * slot)]);
-            const float4 pb = __ldg(&sx[b0 + tc + (tb < Tc ? tb : TPT * slot)]);
-            X[k] = f2_pack(pa.x, pb.x);
-            Y[k] = f2_pack(pa.y, pb.y);
-            Z[k] = f2_pack(pa.z, pb.z);
-            P[k] = GX[k] = GY[k] = GZ[k] = 0ull;
+    // two stages: the consumers read one while the producer's copies fill the other
+    __shared__ __align__(128) float4 buf[2][kP2PCap];
+    __shared__ float4 red[2][2][kP2PConsumers];
+    __shared__ P2PItem item[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2], redbar[2];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kP2PConsumers / 32);
+            mbar_init(&redbar[k], kP2PConsumers);
         }
-        for (int rb = 0; rb < nrow; rb += kRowCap) {
-            const int nr = min(kRowCap, nrow - rb);
-            __syncthreads();
-            if (tid < nr) {
-                const int c = p2p_ids[r0 + rb + tid];
-                s_cb[tid] = begin[c];
-                s_pref[tid + 1] = end[c] - begin[c];
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int64_t count = leaves ? span_count(lv) : nleaf;
+
+    if (tid >= kP2PConsumers) {  // ---------------- producer warp
+        int stage = 0;
+        uint32_t used = 0u, par = 0u;  // per stage: filled before; parity of its last fill
+        bool ok = true;
+        // claim the stage: wait until the consumers have released its previous fill
+        auto claim = [&]() -> bool {
+            if (((used >> stage) & 1u) &&
+                !mbar_wait_bounded(&empty[stage], (par >> stage) & 1u, kWaitLimitNs, &abort_flag)) {
+                abort_flag = 1;
+                if (status) atomicOr(status, kStatusTimeout);
             }
-            __syncthreads();
-            if (tid == 0) {
-                // the target's own cell first
-                int self = 0;
-                for (int k = 0; k < nr; ++k)
-                    if (s_cb[k] == b0 && s_pref[k + 1] == T) {
-                        const int cb = s_cb[k], cn = s_pref[k + 1];
-                        s_cb[k] = s_cb[0];
-                        s_pref[k + 1] = s_pref[1];
-                        s_cb[0] = cb;
-                        s_pref[1] = cn;
-                        self = T;
+            return !abort_flag;
+        };
+        auto advance = [&] {
+            par = ((used >> stage) & 1u) ? par ^ (1u << stage) : par;
+            used |= 1u << stage;
+            stage ^= 1;
+        };
+        // publish one stage (lane 0); a stage with no sources completes on the arrival alone
+        auto publish = [&](const P2PItem &v) {
+            if (lane == 0) {
+                item[stage] = v;
+                if (v.chunk > 0)
+                    mbar_expect_tx(&full[stage], (uint32_t)v.chunk * 16u);
+                else
+                    mbar_arrive(&full[stage]);
+            }
+            __syncwarp();
+        };
+        for (int64_t li = blockIdx.x; ok && li < count; li += gridDim.x) {
+            const int64_t leaf = leaves ? (int64_t)leaves[li] : li;
+            const int64_t g = leaves ? leaf : level_offset(L) + leaf;
+            const int b0 = begin[g], T = end[g] - b0;
+            if (T <= 0) continue;
+            const uint32_t r0 = p2p_offs[leaf];
+            const int nrow = (int)(p2p_offs[leaf + 1] - r0);
+            for (int tc = 0; ok && tc < T; tc += kP2PTargets) {
+                const int Tc = min(T - tc, kP2PTargets);
+                bool emitted = false;
+                for (int rb = 0; ok && rb < nrow; rb += 32) {
+                    const int nr = min(32, nrow - rb);
+                    const bool last_rb = rb + 32 >= nrow;
+                    int cb = 0, cn = 0;
+                    if (lane < nr) {
+                        const int c = p2p_ids[r0 + rb + lane];
+                        cb = begin[c];
+                        cn = end[c] - cb;
+                    }
+                    // the target's own cell first
+                    const unsigned self = __ballot_sync(~0u, lane < nr && cb == b0 && cn == T);
+                    const int k = self ? __ffs(self) - 1 : 0;
+                    const int cb0 = __shfl_sync(~0u, cb, 0), cn0 = __shfl_sync(~0u, cn, 0);
+                    const int cbk = __shfl_sync(~0u, cb, k), cnk = __shfl_sync(~0u, cn, k);
+                    if (self && k > 0) {
+                        if (lane == 0) cb = cbk, cn = cnk;
+                        else if (lane == k) cb = cb0, cn = cn0;
+                    }
+                    int incl = cn;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int v = __shfl_up_sync(~0u, incl, d);
+                        if (lane >= d) incl += v;
+                    }
+                    const int pref = incl - cn, S = __shfl_sync(~0u, incl, 31);
+                    const int nself = self ? T : 0;
+                    for (int sc = 0; sc < S; sc += kP2PCap) {
+                        const int chunk = min(kP2PCap, S - sc);
+                        if (!claim()) {
+                            ok = false;
+                            break;
+                        }
+                        const bool last = last_rb && sc + kP2PCap >= S;
+                        const bool staged = rb == 0 && sc == 0 && nself > 0 && tc + Tc <= chunk;
+                        publish(P2PItem{b0, T, tc, chunk, max(0, min(chunk, nself - sc)),
+                                        (emitted ? 0 : 1) | (last ? 2 : 0) | (staged ? 4 : 0)});
+                        const int lo = max(pref, sc), hi = min(pref + cn, sc + chunk);
+                        if (hi > lo)
+                            tma_bulk_g2s(&buf[stage][lo - sc], &sx[cb + (lo - pref)], (uint32_t)(hi - lo) * 16u,
+                                         &full[stage]);
+                        emitted = true;
+                        advance();
+                    }
+                    if (ok && last_rb && S == 0) {  // the pass ends on an empty block
+                        if (!claim()) {
+                            ok = false;
+                            break;
+                        }
+                        publish(P2PItem{b0, T, tc, 0, 0, (emitted ? 0 : 1) | 2});
+                        emitted = true;
+                        advance();
+                    }
+                }
+                if (ok && !emitted) {  // no neighbour rows at all
+                    if (!claim()) {
+                        ok = false;
                         break;
                     }
-                s_self = self;
-                s_pref[0] = 0;
-                for (int k = 0; k < nr; ++k) s_pref[k + 1] += s_pref[k];
-            }
-            __syncthreads();
-            const int S = s_pref[nr], nself = s_self;
-            for (int sc = 0; sc < S; sc += kSrcCap2) {
-                const int chunk = min(kSrcCap2, S - sc);
-                if (sc > 0) __syncthreads();
-                // warp w stages rows w, w + 4, ... (its lanes stride the row's particles)
-                for (int e = tid >> 5; e < nr; e += NT / 32) {
-                    const int lo = max(s_pref[e], sc), hi = min(s_pref[e + 1], sc + chunk);
-                    for (int q = lo + (tid & 31); q < hi; q += 32) {
-                        const float4 p = __ldg(&sx[s_cb[e] + (q - s_pref[e])]);
-                        sA[q - sc] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
-                        sB[q - sc] = make_ulonglong2(f2_pack(p.z, p.z), f2_pack(p.w, p.w));
-                    }
+                    publish(P2PItem{b0, T, tc, 0, 0, 3});
+                    advance();
                 }
-                __syncthreads();
-                if (active) {
-                    const int mend = max(0, min(chunk, nself - sc));
-                    int j = grp;
-                    for (; j < mend; j += G) {
-                        const ulonglong2 a = sA[j], b = sB[j];
-#pragma unroll
-                        for (int k = 0; k < NPK; ++k) pair2<SOFT, true>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
-                    }
+            }
+        }
+        if (ok && claim()) {  // end of stream
+            publish(P2PItem{-1, 0, 0, 0, 0, 0});
+            advance();
+        }
+        if (abort_flag) {
+            // stopped early: return only once this warp's copies have landed
+            for (int k = 0; k < 2; ++k)
+                if ((used >> k) & 1u) mbar_wait_bounded(&full[k], ((par >> k) & 1u), kWaitLimitNs, nullptr);
+        }
+        return;
+    }
+
+    // -------------------------------------------------- consumer warps
+    int stage = 0, rpar = 0;
+    uint32_t fpar = 0u, rphase = 0u;  // per stage / per reduction buffer: parity of the next phase
+    int slots = 1, G = 1, slot = 0, grp = 0, Tc = 0;
+    float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    float pa = 0.f, gax = 0.f, gay = 0.f, gaz = 0.f, pb = 0.f, gbx = 0.f, gby = 0.f, gbz = 0.f;
+    while (true) {
+        if (!mbar_wait_bounded(&full[stage], (fpar >> stage) & 1u, kWaitLimitNs, &abort_flag) || abort_flag) {
+            if (!abort_flag) {
+                abort_flag = 1;
+                if (status) atomicOr(status, kStatusTimeout);
+            }
+            return;
+        }
+        const P2PItem it = item[stage];
+        if (it.b0 < 0) return;
+        const float4 *src = buf[stage];
+        if (it.flags & 1) {  // a new pass: its targets
+            Tc = min(it.T - it.tc, kP2PTargets);
+            slots = (Tc + 1) / 2;
+            G = kP2PConsumers / slots;
+            slot = tid % slots;
+            grp = tid / slots;
+            // a missing target repeats the slot's first one; its result is discarded
+            const int ta = 2 * slot, tb = ta + 1 < Tc ? ta + 1 : ta;
+            const float4 A = (it.flags & 4) ? src[it.tc + ta] : __ldg(&sx[it.b0 + it.tc + ta]);
+            const float4 B = (it.flags & 4) ? src[it.tc + tb] : __ldg(&sx[it.b0 + it.tc + tb]);
+            ax = A.x, ay = A.y, az = A.z, bx = B.x, by = B.y, bz = B.z;
+            pa = gax = gay = gaz = pb = gbx = gby = gbz = 0.f;
+        }
+        if (grp < G) {
+            int j = grp;
+            for (; j < it.mend; j += G) {
+                const float4 s4 = src[j];
+                pairm<SOFT, true>(ax, ay, az, s4, eps2, pa, gax, gay, gaz);
+                pairm<SOFT, true>(bx, by, bz, s4, eps2, pb, gbx, gby, gbz);
+            }
 #pragma unroll 4
-                    for (; j < chunk; j += G) {
-                        const ulonglong2 a = sA[j], b = sB[j];
-#pragma unroll
-                        for (int k = 0; k < NPK; ++k) pair2<SOFT, false>(X[k], Y[k], Z[k], a, b, E2, P[k], GX[k], GY[k], GZ[k]);
-                    }
-                }
+            for (; j < it.chunk; j += G) {
+                const float4 s4 = src[j];
+                pairm<SOFT, false>(ax, ay, az, s4, eps2, pa, gax, gay, gaz);
+                pairm<SOFT, false>(bx, by, bz, s4, eps2, pb, gbx, gby, gbz);
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < NPK; ++k) {
-            float p0, p1, x0, x1, y0, y1, z0, z1;
-            f2_unpack(P[k], p0, p1);
-            f2_unpack(GX[k], x0, x1);
-            f2_unpack(GY[k], y0, y1);
-            f2_unpack(GZ[k], z0, z1);
-            red[2 * k][tid] = make_float4(p0, -x0, -y0, -z0);
-            red[2 * k + 1][tid] = make_float4(p1, -x1, -y1, -z1);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[stage]);
+        fpar ^= 1u << stage;
+        stage ^= 1;
+        if (!(it.flags & 2)) continue;
+        // end of the pass: combine the groups' partials per target.  red alternates between two
+        // buffers, and every consumer waits for the pass's arrivals, so a pass's writes never
+        // meet the previous pass's reads.
+        red[rpar][0][tid] = make_float4(pa, -gax, -gay, -gaz);
+        red[rpar][1][tid] = make_float4(pb, -gbx, -gby, -gbz);
+        mbar_arrive(&redbar[rpar]);
+        if (!mbar_wait_bounded(&redbar[rpar], (rphase >> rpar) & 1u, kWaitLimitNs, &abort_flag)) {
+            if (!abort_flag) {
+                abort_flag = 1;
+                if (status) atomicOr(status, kStatusTimeout);
+            }
+            return;
         }
-        __syncthreads();
+        rphase ^= 1u << rpar;
         if (grp == 0) {
 #pragma unroll
-            for (int h = 0; h < TPT; ++h) {
-                const int t = TPT * slot + h;
+            for (int h = 0; h < 2; ++h) {
+                const int t = 2 * slot + h;
                 if (t >= Tc) break;
-                const int i = b0 + tc + t;
-                Kahan a{0.f, 0.f}, bx{0.f, 0.f}, by{0.f, 0.f}, bz{0.f, 0.f};
+                const int i = it.b0 + it.tc + t;
+                Kahan a{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, kz{0.f, 0.f};
                 for (int k = 0; k < G; ++k) {
-                    const float4 v = red[h][k * slots + slot];
+                    const float4 v = red[rpar][h][k * slots + slot];
                     a.add(v.x);
-                    bx.add(v.y);
-                    by.add(v.z);
-                    bz.add(v.w);
+                    kx.add(v.y);
+                    ky.add(v.z);
+                    kz.add(v.w);
                 }
                 if (near) {  // the compensated sums so far; the far field is added by L2P
-                    near[2 * (int64_t)i] = make_float4(a.s, bx.s, by.s, bz.s);
-                    near[2 * (int64_t)i + 1] = make_float4(a.c, bx.c, by.c, bz.c);
+                    near[2 * (int64_t)i] = make_float4(a.s, kx.s, ky.s, kz.s);
+                    near[2 * (int64_t)i + 1] = make_float4(a.c, kx.c, ky.c, kz.c);
                     continue;
                 }
                 if (far) {
                     const float4 f = far[i];
                     a.add(f.x);
-                    bx.add(f.y);
-                    by.add(f.z);
-                    bz.add(f.w);
+                    kx.add(f.y);
+                    ky.add(f.z);
+                    kz.add(f.w);
                 }
-                out[perm[i]] = make_float4(a.s, bx.s, by.s, bz.s);
+                out[perm[i]] = make_float4(a.s, kx.s, ky.s, kz.s);
             }
         }
+        rpar ^= 1;
     }
 }
 
 // ---- launchers --------------------------------------------------------------------------------
-// the largest shared-memory carveout, so that the kernel's CTAs can share an SM with a tensor-core
-// M2L's when both run at once
-static void launch_leaf(unsigned grid, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
+// CTAs resident per SM, and the largest shared-memory carveout so that the kernel's CTAs can
+// share an SM with the far field's when both run at once
+static int p2p_blocks_per_sm()
+{
+    static const int b = [] {
+        cudaFuncSetAttribute(k_p2p_ws<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_p2p_ws<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_p2p_ws<false>, kP2PWsThreads, 0);
+        return v > 0 ? v : 1;
+    }();
+    return b;
+}
+
+// nleaf: the leaves (uniform tree) or the capacity of the listed leaves (lv.cap).  Each CTA takes
+// about kP2PLeavesPerCta of them (never fewer CTAs than fit on the GPU at once): enough leaves
+// that the producer's staging of one hides behind the pair loop of another, few enough that CTAs
+// retire often and the far field's kernels, beside P2P on the other stream, get SMs.  Measured on
+// the 1M uniform step (p = 10): 1, 2, 4, 8 leaves and one persistent wave gave P2P 0.528, 0.520,
+// 0.525, 0.541, 0.596 ms alone and 1.158, 1.152, 1.163, 1.189, 1.248 ms for the forked step; on
+// 16M Plummer (p = 8) P2P took 8.91, 7.97, 9.29 ms with 1, 4 and one wave.
+constexpr int kP2PLeavesPerCta = 4;
+
+static void launch_leaf(int64_t nleaf, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
                         const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
-                        const uint32_t *perm, float eps2, float4 *out, float4 *near, cudaStream_t s,
+                        const uint32_t *perm, float eps2, float4 *out, float4 *near, int *status, cudaStream_t s,
                         Span lv = Span{})
 {
-    static const bool carve = [] {
-        cudaFuncSetAttribute(k_p2p2<true, 2, kP2PThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_p2p2<false, 2, kP2PThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-        return true;
-    }();
-    (void)carve;
+    const int64_t resident = (int64_t)sm_count() * p2p_blocks_per_sm();
+    int64_t grid = (nleaf + kP2PLeavesPerCta - 1) / kP2PLeavesPerCta;
+    grid = std::min<int64_t>(nleaf, std::max<int64_t>(grid, resident));
     if (eps2 > 0.f)
-        k_p2p2<true, 2, kP2PThreads><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm,
-                                                                  eps2, out, near, lv);
+        k_p2p_ws<true><<<(unsigned)grid, kP2PWsThreads, 0, s>>>(L, leaves, lv, nleaf, sx, begin, end, offs, ids, far,
+                                                                 perm, eps2, out, near, status);
     else
-        k_p2p2<false, 2, kP2PThreads><<<grid, kP2PThreads, 0, s>>>(L, leaves, sx, begin, end, offs, ids, far, perm,
-                                                                   eps2, out, near, lv);
+        k_p2p_ws<false><<<(unsigned)grid, kP2PWsThreads, 0, s>>>(L, leaves, lv, nleaf, sx, begin, end, offs, ids, far,
+                                                                  perm, eps2, out, near, status);
     note_launches(1);
 }
 
 void launch_p2p(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end, const uint32_t *p2p_offs,
-                const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2, float4 *out,
+                const int32_t *p2p_ids, const float4 *far, const uint32_t *perm, float eps2, float4 *out, int *status,
                 cudaStream_t s)
 {
     if (n <= 0) return;
-    launch_leaf((unsigned)(int64_t(1) << (3 * L)), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2,
-                out, nullptr, s);
+    launch_leaf(int64_t(1) << (3 * L), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, far, perm, eps2, out, nullptr,
+                status, s);
 }
 
 void launch_p2p_cells(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                       const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, const float4 *far,
-                      const uint32_t *perm, float eps2, float4 *out, cudaStream_t s)
+                      const uint32_t *perm, float eps2, float4 *out, int *status, cudaStream_t s)
 {
     if (n <= 0 || lv.cap <= 0) return;
-    launch_leaf((unsigned)lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, nullptr, s, lv);
+    launch_leaf(lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, far, perm, eps2, out, nullptr, status, s, lv);
 }
 
 bool p2p_near_supported() { return true; }
 
 void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
-                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, cudaStream_t s)
+                     const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, int *status,
+                     cudaStream_t s)
 {
     if (n <= 0) return;
-    launch_leaf((unsigned)(int64_t(1) << (3 * L)), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, nullptr, nullptr,
-                eps2, nullptr, near, s);
+    launch_leaf(int64_t(1) << (3 * L), L, nullptr, sx, begin, end, p2p_offs, p2p_ids, nullptr, nullptr, eps2, nullptr,
+                near, status, s);
 }
 
 void launch_p2p_cells_near(const int32_t *leaves, Span lv, int64_t n, const float4 *sx, const int32_t *begin,
                            const int32_t *end, const uint32_t *u_offs, const int32_t *u_ids, float eps2, float4 *near,
-                           cudaStream_t s)
+                           int *status, cudaStream_t s)
 {
     if (n <= 0 || lv.cap <= 0) return;
-    launch_leaf((unsigned)lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, nullptr, nullptr, eps2, nullptr, near, s,
-                lv);
+    launch_leaf(lv.cap, 0, leaves, sx, begin, end, u_offs, u_ids, nullptr, nullptr, eps2, nullptr, near, status, s, lv);
 }
 
 // Direct all-pairs sum: one thread per target, sources streamed through shared memory in
