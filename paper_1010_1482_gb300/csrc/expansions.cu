@@ -1550,7 +1550,10 @@ static void translate_cells_t(Span par, const int32_t *child_of, const int32_t *
                               cudaStream_t s)
 {
     const int64_t ctas32 = (par.cap + 31) / 32 * (UP ? 1 : 8), ctas64 = (par.cap + 63) / 64 * (UP ? 1 : 8);
-    if (ctas64 >= 4 * 152)  // large levels: 64 cells per CTA share each staged operator
+    if constexpr (UP) {  // large levels: 128 (upward) or 64 cells per CTA share each staged operator
+        if ((par.cap + 127) / 128 >= 4 * 152) return translate_cells_tn<P, UP, 128, 8>(par, child_of, nchild, ops, X, s);
+    }
+    if (ctas64 >= 4 * 152)
         translate_cells_tn<P, UP, 64, 8>(par, child_of, nchild, ops, X, s);
     else if (ctas32 >= 2 * 152)
         translate_cells_tn<P, UP, 32, 8>(par, child_of, nchild, ops, X, s);
