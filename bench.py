@@ -427,7 +427,7 @@ def run_gpu(args, w):
         kshape = (f"{blk_tiles} tiles of 128 target parents x {nt} outputs (of 8p^2 = {kd}), K = {kd} per parent "
                   f"offset, 26 offsets, offsets split over {ksplit} CTA(s) per tile")
     traffic = traffic_from_profile(ksrc, kprof, kname)
-    roofline = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
+    m2l_roof = {"kernel": kname, "bound": "tensor", "achieved": m2l_tf, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": m2l_tf / tpeak,
                 "traffic": traffic,
                 "launches_per_evaluation": m2l_launches,
@@ -447,6 +447,27 @@ def run_gpu(args, w):
                                  "launch from a cold L2); null if the kernel source changed since",
                 "note": "FP32-accurate products as 3 FP16 MMAs (hi*hi + lo*hi + hi*lo): frac <= 1/3 by "
                         "construction; tensor_pipe_frac counts every issued MMA flop"}
+    p2p_alone = p2p_flops / (ser_stages["P2P"] / 1e3) / 1e12
+    p2p_roof = {"kernel": "k_p2p_ws", "bound": "alu", "achieved": p2p_tf, "peak": peak, "unit": "TFLOP/s",
+                "frac": p2p_tf / peak,
+                "traffic": traffic_from_profile("p2p.cu", f"p2p_{w['name']}.md", "k_p2p_ws"),
+                "launches_per_evaluation": 1,
+                "work": f"{p2p_pairs} pairs x 20 flop (the paper's 19 + 1 for phi) = {p2p_flops:.4g} flop per "
+                        "evaluation, one launch",
+                "pairs": p2p_pairs, "flop_per_pair": 20,
+                "achieved_alone": p2p_alone, "frac_alone": p2p_alone / peak,
+                "measured": "achieved: CUDA events around the P2P launch on its stream (the low-priority "
+                            "stream, beside P2M .. L2L) in the timed steps; alone: the serial evaluation",
+                "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz",
+                "traffic_basis": "DRAM bytes per launch from the ncu capture in profiles/ (ncu starts each "
+                                 "launch from a cold L2); null if the kernel source changed since",
+                "note": "13 FP32-pipe operations + 1 reciprocal square root per pair: at 100% of the FP32 "
+                        "pipe the 20-flop rate is 20/26 = 0.77 of the peak"}
+    # the roofline follows the step's dominant kernel: the larger serial stage time
+    p2p_dominant = ser_stages["P2P"] >= ser_stages["M2L/M2P"]
+    roofline = dict(p2p_roof if p2p_dominant else m2l_roof)
+    roofline["dominant_basis"] = (f"largest serial stage time: P2P {ser_stages['P2P']:.3f} ms, M2L/M2P "
+                                  f"{ser_stages['M2L/M2P']:.3f} ms of the {float(np.median(ser_ms)):.3f} ms serial step")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -456,13 +477,7 @@ def run_gpu(args, w):
                    "l2": "flushed between steps (256 MiB write outside the per-step events)"},
         "roofline": roofline,
         "kernels": {
-            "p2p": {"kernel": "k_p2p_ws", "achieved_tflops": p2p_tf, "frac": p2p_tf / peak, "pairs": p2p_pairs,
-                    "flop_per_pair": 20, "peak": peak, "bound": "alu",
-                    "achieved_tflops_alone": p2p_flops / (ser_stages["P2P"] / 1e3) / 1e12,
-                    "frac_alone": p2p_flops / (ser_stages["P2P"] / 1e3) / 1e12 / peak,
-                    "note": "achieved: the kernel's duration in the timed steps, on the low-priority "
-                            "stream beside the expansions; alone: the serial evaluation",
-                    "peak_basis": f"derived FP32 CUDA-core peak: SMs x 128 x 2 x {peak_mhz:.0f} MHz"},
+            ("m2l" if p2p_dominant else "p2p"): (m2l_roof if p2p_dominant else p2p_roof),
             "m2l_fp32_cores": {"kernel": "k_m2l", "ms": float(np.median(cc_ms)),
                                "achieved_tflops": m2l_flops / (float(np.median(cc_ms)) / 1e3) / 1e12,
                                "frac": m2l_flops / (float(np.median(cc_ms)) / 1e3) / 1e12 / peak, "peak": peak,
