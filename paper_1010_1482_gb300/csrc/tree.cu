@@ -542,9 +542,12 @@ template <class KeyT>
 __global__ void __launch_bounds__(256) k_rs_upsweep(const KeyT *__restrict__ kin, int64_t n, int pass, int64_t nblk,
                                                     uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t h[256];
-    const int tid = threadIdx.x, lane = tid & 31;
-    h[tid] = 0;
+    // one digit histogram per warp; a key is one shared-memory add (the whole warp's 32 in one
+    // add when its lanes agree), not a ballot match per key: counting needs no ranks
+    __shared__ uint32_t h[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k][tid] = 0;
     __syncthreads();
     const int64_t t0 = blockIdx.x * (int64_t)kRsTile;
     const int shift = 8 * pass;
@@ -556,20 +559,19 @@ __global__ void __launch_bounds__(256) k_rs_upsweep(const KeyT *__restrict__ kin
         dd[r] = i < n ? ((uint32_t)(kin[i] >> shift) & 0xffu) : 256u;
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {  // every lane of a warp takes the same rounds
-        const uint32_t d = dd[r];
-        const bool valid = d < 256u;
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
-        if (!valid) peers = ~peers;
-#pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+    for (int r = 0; r < R; ++r) {
+        const uint32_t d = dd[r], d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0)) {
+            if (lane == 0 && d0 < 256u) atomicAdd(&h[warp][d0], 32u);
+        } else if (d < 256u) {
+            atomicAdd(&h[warp][d], 1u);
         }
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    counts[(int64_t)tid * nblk + blockIdx.x] = h[tid];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c += h[k][tid];
+    counts[(int64_t)tid * nblk + blockIdx.x] = c;
 }
 
 // CTA d: starts[d * nblk + t] = (keys of digits < d) + (keys of digit d in tiles < t)
