@@ -254,8 +254,8 @@ int gbfmm_export_adaptive_tree(gbfmm_ctx *ctx, double *origin_side, int64_t *nce
 int gbfmm_stage_times(gbfmm_ctx *ctx, float *ms, int max, int *count);
 
 /* Test of the bounded device waits (no counterpart in the paper): enqueues one CTA that waits
- * on an mbarrier no thread arrives on, with the same bounded-wait routine the M2L pipeline
- * uses, limited to limit_ms (0 < limit_ms <= 2000).  When it gives up it raises the context's
+ * on an mbarrier no thread arrives on, with the same bounded-wait routine the M2L and P2P pipelines
+ * use, limited to limit_ms (0 < limit_ms <= 2000).  When it gives up it raises the context's
  * status word, so the next gbfmm_sync_status returns ETIMEOUT; the context stays usable.
  * Asynchronous on `stream`.  EINVAL / ECUDA. */
 int gbfmm_selftest_wait(gbfmm_ctx *ctx, double limit_ms, void *stream);
