@@ -361,6 +361,14 @@ int gbfmm_engine_run_batch(gbfmm_engine *e, int32_t nb, const int64_t *offsets, 
  *   only) after one warm-up, with prm's other fields, into the context's own device buffers;
  *   *best_leaf receives the fastest candidate and *best_ms (may be NULL) its time.
  *   Synchronous.  Candidates that gbfmm_plan rejects are skipped; EINVAL if none is valid.
+ * gbfmm_tune: the same over every pair of a leaf size (leaf_candidates) and a P2P launch shape
+ *   (lpc_candidates: target leaves per CTA of the P2P kernel, 0 .. 64, 0 = the library's
+ *   choice; n_lpc = 0 keeps the context's setting).  *best_leaf and *best_lpc (may be NULL)
+ *   receive the fastest pair and *best_ms its time; the context keeps best_lpc for its later
+ *   evaluations (as gbfmm_set_p2p_leaves_per_cta).  The leaf size is the caller's to apply.
+ * gbfmm_set_p2p_leaves_per_cta: this context's P2P launch shape, 0 .. 64 target leaves per CTA
+ *   (0 = the library's choice, 4).  Every leaf's sums are formed the same way whichever CTA
+ *   takes it, so results are bit-identical for every setting; only the time changes.  EINVAL.
  */
 typedef struct gbfmm_graph gbfmm_graph;
 int gbfmm_graph_create(gbfmm_graph **out, gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq,
@@ -369,6 +377,10 @@ int gbfmm_graph_launch(gbfmm_graph *g, void *stream);
 int gbfmm_graph_destroy(gbfmm_graph *g);
 int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
                     int32_t ncand, int32_t *best_leaf, float *best_ms);
+int gbfmm_tune(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *leaf_candidates,
+               int32_t n_leaf, const int32_t *lpc_candidates, int32_t n_lpc, int32_t *best_leaf, int32_t *best_lpc,
+               float *best_ms);
+int gbfmm_set_p2p_leaves_per_cta(gbfmm_ctx *ctx, int32_t leaves);
 
 /*
  * Batched evaluation: nb independent instances (uneven N, orders, trees) in one CUDA graph.

@@ -937,6 +937,7 @@ int evaluate_adaptive_in(gbfmm_ctx *ctx, AdaptiveState &A, const AdaptCaps *caps
                          int64_t n, const float *d_xyzq, float *d_out, cudaStream_t s, float *partials,
                          unsigned *counter)
 {
+    set_p2p_leaves_per_cta(ctx->p2p_leaves_per_cta);
     const bool dev = caps != nullptr;
     const int P = prm->p, PP = P * P;
     const int leaf_size = prm->leaf_size;

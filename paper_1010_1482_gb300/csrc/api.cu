@@ -392,6 +392,7 @@ int evaluate_uniform_in(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, cons
                         void *d_workspace, size_t workspace_bytes, cudaStream_t stream, float *partials,
                         unsigned *counter)
 {
+    set_p2p_leaves_per_cta(ctx->p2p_leaves_per_cta);
     std::string msg;
     int L = 0;
     int rc = check_params(prm, n, &L, &msg);

@@ -435,6 +435,10 @@ void launch_m2l_rot(int P, int L, const int32_t *begin, const int32_t *end, cons
 // warp-specialised kernel: p2p_near_supported()).  The P2P launchers take the context's status
 // word: a bounded wait that expires raises kStatusTimeout there.
 bool p2p_near_supported();
+// P2P launch shape for the launches this thread issues next: about `leaves` target leaves per
+// CTA (0: the library's choice; at most kMaxP2PLeavesPerCta); the results do not depend on it
+constexpr int kMaxP2PLeavesPerCta = 64;
+void set_p2p_leaves_per_cta(int leaves);
 void launch_p2p_near(int L, int64_t n, const float4 *sx, const int32_t *begin, const int32_t *end,
                      const uint32_t *p2p_offs, const int32_t *p2p_ids, float eps2, float4 *near, int *status,
                      cudaStream_t s);

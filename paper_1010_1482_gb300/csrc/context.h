@@ -73,6 +73,7 @@ struct AdaptiveState {
 
 struct gbfmm_ctx {
     int device = 0;
+    int p2p_leaves_per_cta = 0;  // P2P launch shape (0: the library's choice)
     std::string err;
     int *d_status = nullptr;
     unsigned *d_counter = nullptr;

@@ -91,10 +91,16 @@ int gbfmm_graph_destroy(gbfmm_graph *g)
     return GBFMM_OK;
 }
 
-int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
-                    int32_t ncand, int32_t *best_leaf, float *best_ms)
+// times every (leaf size, P2P leaves per CTA) pair: one warm-up and one timed evaluation each
+static int tune_impl(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
+                     int32_t ncand, const int32_t *lpcs, int32_t nlpc, int32_t *best_leaf, int32_t *best_lpc,
+                     float *best_ms)
 {
-    if (!ctx || !prm || !candidates || ncand <= 0 || !best_leaf || n <= 0 || !d_xyzq) return GBFMM_EINVAL;
+    if (!ctx || !prm || !candidates || ncand <= 0 || !best_leaf || n <= 0 || !d_xyzq || nlpc <= 0 || !lpcs)
+        return GBFMM_EINVAL;
+    for (int32_t j = 0; j < nlpc; ++j)
+        if (lpcs[j] < 0 || lpcs[j] > gbfmm::kMaxP2PLeavesPerCta) return GBFMM_EINVAL;
+    const int keep = ctx->p2p_leaves_per_cta;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     // output and workspace: the context's host-path buffers, grown to the largest candidate
@@ -131,11 +137,13 @@ int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const fl
     }
     int rc = GBFMM_OK, found = 0;
     float best = FLT_MAX;
-    for (int32_t i = 0; i < ncand && rc == GBFMM_OK; ++i) {
+    for (int32_t k = 0; k < ncand * nlpc && rc == GBFMM_OK; ++k) {
+        const int32_t i = k / nlpc, j = k % nlpc;
         gbfmm_params p = *prm;
         p.leaf_size = candidates[i];
         p.flags &= ~GBFMM_FLAG_STAGE_TIMING;
         if (gbfmm_plan(&p, n, nullptr, nullptr) != GBFMM_OK) continue;  // an invalid candidate is skipped
+        ctx->p2p_leaves_per_cta = lpcs[j];
         rc = gbfmm_evaluate(ctx, &p, n, d_xyzq, ctx->h_out, ctx->h_ws, ctx->h_ws_bytes, s);  // warm-up
         if (rc != GBFMM_OK) break;
         cudaEventRecord(t0, s);
@@ -147,6 +155,7 @@ int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const fl
         if (rc == GBFMM_OK && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best) {
             best = ms;
             *best_leaf = candidates[i];
+            if (best_lpc) *best_lpc = lpcs[j];
             found = 1;
         }
     }
@@ -154,9 +163,42 @@ int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const fl
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     cudaStreamDestroy(s);
+    ctx->p2p_leaves_per_cta = keep;
     if (rc != GBFMM_OK) return rc;
     if (!found) return fail(ctx, GBFMM_EINVAL, "no valid leaf-size candidate");
     if (best_ms) *best_ms = best;
+    return GBFMM_OK;
+}
+
+int gbfmm_tune_leaf(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *candidates,
+                    int32_t ncand, int32_t *best_leaf, float *best_ms)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    const int32_t cur = ctx->p2p_leaves_per_cta;
+    return tune_impl(ctx, prm, n, d_xyzq, candidates, ncand, &cur, 1, best_leaf, nullptr, best_ms);
+}
+
+int gbfmm_tune(gbfmm_ctx *ctx, const gbfmm_params *prm, int64_t n, const float *d_xyzq, const int32_t *leaf_candidates,
+               int32_t n_leaf, const int32_t *lpc_candidates, int32_t n_lpc, int32_t *best_leaf, int32_t *best_lpc,
+               float *best_ms)
+{
+    if (!ctx) return GBFMM_EINVAL;
+    int32_t lpc = ctx->p2p_leaves_per_cta;
+    const int32_t cur = lpc;
+    const int rc = n_lpc > 0 ? tune_impl(ctx, prm, n, d_xyzq, leaf_candidates, n_leaf, lpc_candidates, n_lpc,
+                                         best_leaf, &lpc, best_ms)
+                             : tune_impl(ctx, prm, n, d_xyzq, leaf_candidates, n_leaf, &cur, 1, best_leaf, &lpc,
+                                         best_ms);
+    if (rc != GBFMM_OK) return rc;
+    ctx->p2p_leaves_per_cta = lpc;  // the context keeps the fastest launch shape
+    if (best_lpc) *best_lpc = lpc;
+    return GBFMM_OK;
+}
+
+int gbfmm_set_p2p_leaves_per_cta(gbfmm_ctx *ctx, int32_t leaves)
+{
+    if (!ctx || leaves < 0 || leaves > gbfmm::kMaxP2PLeavesPerCta) return GBFMM_EINVAL;
+    ctx->p2p_leaves_per_cta = leaves;
     return GBFMM_OK;
 }
 

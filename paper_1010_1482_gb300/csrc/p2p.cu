@@ -349,6 +349,10 @@ static int p2p_blocks_per_sm()
 // 0.525, 0.541, 0.596 ms alone and 1.158, 1.152, 1.163, 1.189, 1.248 ms for the forked step; on
 // 16M Plummer (p = 8) P2P took 8.91, 7.97, 9.29 ms with 1, 4 and one wave.
 constexpr int kP2PLeavesPerCta = 4;
+// the evaluating context's choice (gbfmm_set_p2p_leaves_per_cta, gbfmm_tune), set on entry to an
+// evaluation by the thread that issues its launches; 0: kP2PLeavesPerCta
+static thread_local int tl_leaves_per_cta = 0;
+void set_p2p_leaves_per_cta(int leaves) { tl_leaves_per_cta = leaves; }
 
 static void launch_leaf(int64_t nleaf, int L, const int32_t *leaves, const float4 *sx, const int32_t *begin,
                         const int32_t *end, const uint32_t *offs, const int32_t *ids, const float4 *far,
@@ -356,7 +360,8 @@ static void launch_leaf(int64_t nleaf, int L, const int32_t *leaves, const float
                         Span lv = Span{})
 {
     const int64_t resident = (int64_t)sm_count() * p2p_blocks_per_sm();
-    int64_t grid = (nleaf + kP2PLeavesPerCta - 1) / kP2PLeavesPerCta;
+    const int lpc = tl_leaves_per_cta > 0 ? tl_leaves_per_cta : kP2PLeavesPerCta;
+    int64_t grid = (nleaf + lpc - 1) / lpc;
     grid = std::min<int64_t>(nleaf, std::max<int64_t>(grid, resident));
     if (eps2 > 0.f)
         k_p2p_ws<true><<<(unsigned)grid, kP2PWsThreads, 0, s>>>(L, leaves, lv, nleaf, sx, begin, end, offs, ids, far,

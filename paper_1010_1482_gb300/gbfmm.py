@@ -103,6 +103,10 @@ def lib():
         "gbfmm_graph_destroy": (i, [P]),
         "gbfmm_tune_leaf": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, ctypes.c_int32,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "gbfmm_tune": (i, [P, ctypes.POINTER(gbfmm_params), i64, P, P, ctypes.c_int32, P, ctypes.c_int32,
+                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_float)]),
+        "gbfmm_set_p2p_leaves_per_cta": (i, [P, ctypes.c_int32]),
         "gbfmm_batch_create": (i, [ctypes.POINTER(P), P, ctypes.c_int32, P, P, P, P, ctypes.c_int32]),
         "gbfmm_batch_launch": (i, [P, P]),
         "gbfmm_batch_info": (i, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64)]),
@@ -417,6 +421,26 @@ def gbfmm_tune_leaf(ctx, prm: gbfmm_params, xyzq: torch.Tensor, candidates) -> t
     _check(ctx, lib().gbfmm_tune_leaf(ctx, ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _np_ptr(c), len(c),
                                       ctypes.byref(best), ctypes.byref(ms)))
     return int(best.value), float(ms.value)
+
+
+def gbfmm_tune(ctx, prm: gbfmm_params, xyzq: torch.Tensor, leaf_candidates, lpc_candidates) -> tuple:
+    """Autotuner over leaf size x P2P launch shape (target leaves per P2P CTA): (leaf, leaves per
+    CTA, ms) of the fastest pair; the context keeps that launch shape."""
+    import numpy as np
+
+    assert xyzq.is_cuda and xyzq.dtype == torch.float32 and xyzq.is_contiguous()
+    c = np.ascontiguousarray(leaf_candidates, dtype=np.int32)
+    d = np.ascontiguousarray(lpc_candidates, dtype=np.int32)
+    leaf, lpc, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(ctx, lib().gbfmm_tune(ctx, ctypes.byref(prm), xyzq.shape[0], _ptr(xyzq), _np_ptr(c), len(c),
+                                 _np_ptr(d) if len(d) else None, len(d), ctypes.byref(leaf), ctypes.byref(lpc),
+                                 ctypes.byref(ms)))
+    return int(leaf.value), int(lpc.value), float(ms.value)
+
+
+def gbfmm_set_p2p_leaves_per_cta(ctx, leaves: int) -> None:
+    """The context's P2P launch shape: about `leaves` target leaves per CTA (0: the library's)."""
+    _check(ctx, lib().gbfmm_set_p2p_leaves_per_cta(ctx, int(leaves)))
 
 
 # ---- convenience wrapper (torch-allocated workspace) -----------------------------------------

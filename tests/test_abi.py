@@ -56,6 +56,8 @@ def test_negative_n_and_null_context(lib):
         G.gbfmm_plan(prm, -1)
     assert lib.gbfmm_evaluate(None, ctypes.byref(prm), 10, None, None, None, 0, None) == G.GBFMM_EINVAL
     assert lib.gbfmm_destroy(None) == G.GBFMM_OK
+    assert lib.gbfmm_set_p2p_leaves_per_cta(None, 4) == G.GBFMM_EINVAL
+    assert lib.gbfmm_tune(None, ctypes.byref(prm), 10, None, None, 0, None, 0, None, None, None) == G.GBFMM_EINVAL
 
 
 def test_workspace_grows_linearly(lib):

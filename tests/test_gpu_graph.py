@@ -6,6 +6,9 @@
 * The adaptive tree cannot be captured (EUNSUPPORTED).
 * gbfmm_tune_leaf returns one of the candidates with a positive time, skips invalid ones, and an
   evaluation with the chosen leaf size matches the oracle FMM of that leaf size.
+* The P2P launch shape (target leaves per CTA) changes no bit of the result on either tree;
+  gbfmm_tune picks a (leaf size, launch shape) pair from the candidates, the context keeps the
+  shape, and out-of-range shapes are rejected.
 """
 import numpy as np
 import pytest
@@ -80,3 +83,31 @@ def test_tune_leaf(G, ctx, dist, tree):
     got = out.cpu().numpy().astype(np.float64)
     ref = (O.fmm_adaptive(x, 6, leaf) if tree == 1 else O.fmm(x, 6, leaf))["out"]
     assert O.rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dist,tree", [("uniform", 0), ("plummer", 1)])
+def test_p2p_launch_shape_and_tune(G, ctx, dist, tree):
+    n = 60000
+    x = inputs.make_particles(n, dist, 78)
+    xd = torch.from_numpy(x).cuda()
+    prm = G.gbfmm_default_params(p=6, leaf_size=32, tree=tree)
+    _, wsb = G.gbfmm_plan(prm, n)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
+    outs = []
+    try:
+        for lpc in (0, 1, 3, 64):
+            G.gbfmm_set_p2p_leaves_per_cta(ctx, lpc)
+            out = torch.empty_like(xd)
+            G.gbfmm_evaluate(ctx, prm, xd, out, ws)
+            G.gbfmm_sync_status(ctx)
+            outs.append(out.cpu())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        leaf, lpc, ms = G.gbfmm_tune(ctx, prm, xd, [16, 32], [1, 4])
+        assert leaf in (16, 32) and lpc in (1, 4) and ms > 0.0
+        with pytest.raises(G.GbfmmError) as ei:
+            G.gbfmm_set_p2p_leaves_per_cta(ctx, 65)
+        assert ei.value.code == G.GBFMM_EINVAL
+    finally:
+        G.gbfmm_set_p2p_leaves_per_cta(ctx, 0)
+
